@@ -1,0 +1,10 @@
+"""FP64 CPU oracle of the fused image-kernel chain.
+
+TEST INFRASTRUCTURE ONLY: only tests/, __graft_entry__.smoke() and bench.py's
+cpu_baseline / reference legs may import this package. The library's product path
+never touches it, and it shares no code with the CUDA path.
+
+`chain` wraps the C oracle (kf_oracle.c, compiled with gcc on first use);
+`partition` restates the paper's traffic model and enumerates partitions by brute
+force (Sec. VI, Fig. 5, Sec. VI-D).
+"""

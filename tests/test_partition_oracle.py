@@ -1,0 +1,96 @@
+"""Pins of the brute-force partitioner and traffic model (CPU only).
+
+Golden values come from the paper: the four partitions of three kernels (Sec. VI),
+the n(n+1)/2 candidate groups (Fig. 5), Transfer_serial = 2nBxyt (Sec. VI-D), the
+data-utilisation ratio (Eq. 3) and the closed-form box of Eq. 6.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import partition as op
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read(name):
+    with open(os.path.join(GOLD, name)) as fh:
+        return [ln.strip() for ln in fh if ln.strip() and not ln.startswith("#")]
+
+
+def test_three_kernels_have_the_four_partitions_listed_in_the_paper():
+    gold = set()
+    for ln in _read("partitions_of_three_kernels.txt"):
+        groups = tuple(tuple(int(k) - 1 for k in g.split()) for g in ln.split("|"))
+        gold.add(tuple((g[0], g[-1]) for g in groups))
+    got = {tuple(p) for p in op.all_partitions(3)}
+    assert got == gold
+
+
+def test_partition_and_candidate_group_counts():
+    for ln in _read("counts.txt"):
+        n, parts, groups = map(int, ln.split())
+        assert len(op.all_partitions(n)) == parts
+        assert len(op.candidate_groups(n)) == groups
+        # every partition covers each kernel exactly once (Fig. 5 constraint)
+        for p in op.all_partitions(n):
+            cover = np.zeros(n, dtype=int)
+            for a, b in p:
+                cover[a:b + 1] += 1
+            assert np.all(cover == 1)
+
+
+def test_serial_transfer_is_2nBxyt_for_point_stages():
+    n = 5
+    stages = [op.Stage(f"k{i}", 0, 0, 0, 1, 1) for i in range(n)]
+    N, M, T, box = 256, 256, 1000, (32, 32, 8)
+    B = N * M * T / (box[0] * box[1] * box[2])
+    unfused = [(i, i) for i in range(n)]
+    assert op.partition_cost(stages, unfused, N, M, T, box) == pytest.approx(
+        2 * n * B * box[0] * box[1] * box[2])
+    # fusing point stages leaves only the first read and the last write: 2Bxyt
+    assert op.partition_cost(stages, [(0, n - 1)], N, M, T, box) == pytest.approx(
+        2 * B * box[0] * box[1] * box[2])
+
+
+def test_fused_halo_term_grows_with_the_summed_radius():
+    stages = [op.Stage("a", 1, 1, 0, 1, 1), op.Stage("b", 2, 2, 0, 1, 1)]
+    N, M, T, box = 64, 64, 4, (16, 16, 1)
+    B = N * M * T / 256
+    got = op.group_traffic(stages, 0, 1, N, M, T, box)
+    assert got == pytest.approx(B * ((16 + 6) * (16 + 6) + 256))
+
+
+def test_data_utilisation_eq3():
+    assert op.data_utilisation((32, 32, 16), (0, 0, 0)) == 1.0
+    assert op.data_utilisation((32, 32, 16), (1, 1, 1)) == pytest.approx(
+        32 * 32 * 16 / (34 * 34 * 17))
+
+
+@pytest.mark.parametrize("beta,dx,dt", [(48 * 1024, 1, 1), (96 * 1024, 2, 1), (20000, 3, 2)])
+def test_eq6_is_the_minimiser_of_eq5(beta, dx, dt):
+    # V = (x + 2 dx)^2 (t + dt) with x^2 t = beta (two-sided spatial, one-sided temporal)
+    x_cf, t_cf = op.eq6_box(beta, dx, dt)
+    xs = np.linspace(1.0, 200.0, 400001)
+    V = (xs + 2 * dx) ** 2 * (beta / xs ** 2 + dt)
+    x_num = xs[np.argmin(V)]
+    assert x_cf == pytest.approx(x_num, rel=1e-3)
+    assert t_cf == pytest.approx(beta / x_cf ** 2, rel=1e-12)
+
+
+def test_brute_force_prefers_full_fusion_for_the_harris_chain_on_large_boxes():
+    st = op.harris_chain(4)
+    g, c = op.brute_force_best(st, 600, 800, 10, (116, 64, 1))
+    assert g == [(0, 7)]
+    unfused = op.partition_cost(st, [(i, i) for i in range(8)], 600, 800, 10, (116, 64, 1))
+    assert unfused > 40 * c
+
+
+def test_onchip_limit_forces_cuts():
+    st = op.harris_chain(4)
+    box = (116, 64, 1)
+    full = op.group_onchip(st, 0, 7, box)
+    g, _ = op.brute_force_best(st, 600, 800, 10, box, onchip_limit=full - 1)
+    assert len(g) >= 2
+    assert op.feasible(st, g, box, full - 1)
