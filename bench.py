@@ -1,0 +1,304 @@
+"""Benchmark of the fused Harris chain on synthetic high-speed video (1000 x 800 x 600 u8).
+
+One step = the whole chain (8 stages, the partition the traffic-model planner picks:
+full fusion) over the 1000-frame volume, inputs already resident in HBM. The volume
+(480 MB of frames + 480 MB of mask) is larger than L2, so no flush is needed between
+steps. Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the deliberately slow reference) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import video as sv  # noqa: E402
+
+METRIC = "fused-chain Mpixel/s & HBM roofline fraction vs unfused, 800×600×1000 u8"
+UNIT = "Mpixel/s"
+SPEC = sv.HSDV_800x600x1000
+WORKLOAD = "Harris 8-stage chain, 1000 frames x 800 rows x 600 cols u8, 64 blobs + 32 patches, seed 3"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling (every 200 ms) of one GPU while the benchmark runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id, self.rows, self.proc = gpu_id, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        rows = [r for (ts, r) in self.rows if t0 <= ts <= t1 and len(r) >= 9]
+        if not rows:
+            rows = [r for (_, r) in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(rows[0][2]),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+def make_video(rank: int):
+    P = sv.pitch_for(SPEC.W)
+    spec = SPEC if rank == 0 else sv.VideoSpec(**{**SPEC.__dict__, "seed": SPEC.seed + 1000 * rank})
+    frames, _ = sv.generate(spec, pitch=P)
+    return frames, P
+
+
+def cpu_oracle_rate(frames: np.ndarray, W: int, budget_s: float = 12.0) -> dict:
+    """The FP64 oracle as it stands, OpenMP over frames on all host cores, on a bounded
+    prefix of the volume sized to about `budget_s` seconds."""
+    from oracle import chain as oc
+    T, H, P = frames.shape
+    t0 = time.perf_counter()
+    _, _, _, used = oc.chain_volume(frames[:4], W=W)
+    probe = time.perf_counter() - t0
+    n = int(max(4, min(T, budget_s / max(probe / 4, 1e-6))))
+    t0 = time.perf_counter()
+    _, _, _, used = oc.chain_volume(frames[:n], W=W)
+    dt = time.perf_counter() - t0
+    return {"value": n * H * W / dt / 1e6, "unit": UNIT, "cores": int(used), "kind": "oracle",
+            "sample": f"first {n} of {T} frames ({n * H * W / 1e6:.1f} Mpixel), FP64, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    frames, P = make_video(0)
+    from oracle import chain as oc
+    T, H, W = SPEC.T, SPEC.H, SPEC.W
+    per_step = 24  # frames of the workload per timed step
+    for i in range(args.warmup):
+        oc.chain_volume(frames[(i * per_step) % T:(i * per_step) % T + per_step], W=W)
+    times, used = [], 1
+    for i in range(args.steps):
+        s = (i * per_step) % (T - per_step)
+        t0 = time.perf_counter()
+        _, _, _, used = oc.chain_volume(frames[s:s + per_step], W=W)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * sum(times) / len(times)
+    value = per_step * H * W / (ms / 1000) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_per_step": f"{per_step} frames", "impl": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(used), "kind": "oracle",
+                             "sample": f"{per_step} frames per step of the 1000-frame volume"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    import torch.distributed as dist
+    from paper_1509_04394_gb300 import build as kbuild
+    from paper_1509_04394_gb300 import kfuse as K
+
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0:
+        kbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    frames_h, P = make_video(rank)
+    T, H, W = SPEC.T, SPEC.H, SPEC.W
+    frames_pin = torch.from_numpy(frames_h).pin_memory()
+    frames = frames_pin.to(dev)
+    mask = torch.zeros_like(frames)
+    counts = torch.zeros(T, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ctx = K.Context(local_rank)
+    cuts, _ = K.kf_plan(ctx.h, W, H, T)  # traffic-model plan: full fusion
+    n_groups = bin(cuts).count("1") + 1
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(k):
+            fn()
+        ev1.record(stream)
+        barrier()
+        ms = ev0.elapsed_time(ev1) / k
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    def fused():
+        K.kf_run(ctx.h, cuts, frames, W, mask, counts, None, stream)
+
+    # clocks: sample across warm-up and the timed region
+    try:
+        gid = str(torch.cuda.get_device_properties(dev).uuid)
+        gid = gid if gid.startswith("GPU-") else "GPU-" + gid
+    except Exception:
+        gid = str(local_rank)
+    clk = ClockSampler(gid)
+    clk.start()
+    # soak ~1.5 s so the clock record covers the steady state
+    t_soak = time.time()
+    while time.time() - t_soak < 1.5:
+        fused()
+        torch.cuda.synchronize(dev)
+    t_a = time.time()
+    ms = timed(fused, args.steps, args.warmup)
+    t_b = time.time()
+    clk.stop()
+    clocks = clk.summary(t_soak, t_b)
+
+    px = T * H * W
+    value = world * px / (ms / 1000) / 1e6
+    hbm_peak, peak_kind = peaks()
+    alg_bytes = 2 * px + 4 * T  # frames read once, mask written once, counts
+    achieved = alg_bytes / (ms / 1000) / 1e9
+
+    # unfused sequence (one kernel per stage, volume-wide maps through HBM)
+    unf_cuts = (1 << 7) - 1
+    ws = torch.empty(K.kf_workspace_bytes(ctx.h, unf_cuts, W, H, T), dtype=torch.uint8, device=dev)
+    mask_u = torch.zeros_like(frames)
+    counts_u = torch.zeros_like(counts)
+    ms_unf = timed(lambda: K.kf_run(ctx.h, unf_cuts, frames, W, mask_u, counts_u, ws, stream), max(3, args.steps // 4), 1)
+    same = bool(torch.equal(mask_u, mask) and torch.equal(counts_u, counts))
+    unf_bytes = 98 * px  # FP32 maps: sum over stages of input + output bytes per pixel
+    # FP16 maps, unfused (half the intermediate bytes)
+    ctx16 = K.Context(local_rank, precision=K.KF_PREC_F16)
+    ws16 = torch.empty(K.kf_workspace_bytes(ctx16.h, unf_cuts, W, H, T), dtype=torch.uint8, device=dev)
+    ms_unf16 = timed(lambda: K.kf_run(ctx16.h, unf_cuts, frames, W, mask_u, counts_u, ws16, stream),
+                     max(3, args.steps // 4), 1)
+    del ws, ws16
+
+    # end to end through the public call: pinned host frames in, mask + counts out
+    mask_h = torch.empty_like(frames_pin, device="cpu").pin_memory()
+    counts_h = torch.empty(T, dtype=torch.int32).pin_memory()
+
+    def e2e_step():
+        frames.copy_(frames_pin, non_blocking=True)
+        K.kf_run(ctx.h, cuts, frames, W, mask, counts, None, stream)
+        mask_h.copy_(mask, non_blocking=True)
+        counts_h.copy_(counts, non_blocking=True)
+    ms_e2e = timed(e2e_step, max(3, args.steps // 2), 1)
+    h2d = frames_pin.numel()
+    d2h = mask_h.numel() + 4 * T
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": T, "rows": H, "cols": W, "partition_cuts": cuts,
+                   "groups": n_groups, "chunk_rows": 200, "cols_per_lane": 4,
+                   "l2": "inputs larger than L2 (480 MB frames, 480 MB mask), no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "frames_per_s": world * T / (ms / 1000),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "unfused": {"value": world * px / (ms_unf / 1000) / 1e6, "ms_per_step": ms_unf, "kernels": 8,
+                    "hbm_frac": unf_bytes / (ms_unf / 1000) / 1e9 / hbm_peak, "bit_identical_to_fused": same,
+                    "fused_speedup": ms_unf / ms},
+        "unfused_f16": {"value": world * px / (ms_unf16 / 1000) / 1e6, "ms_per_step": ms_unf16,
+                        "hbm_frac": 50 * px / (ms_unf16 / 1000) / 1e9 / hbm_peak},
+        "e2e": {"value": world * px / (ms_e2e / 1000) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e},
+        "gpu_launches": n_groups * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_rate(frames_h, W)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

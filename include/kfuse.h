@@ -1,0 +1,197 @@
+/*
+ * kfuse.h -- C ABI of the fused image-kernel chain library (libkfuse.so).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   1. declare the kernels of a chain with their data-access radii (Sec. IV, Table I;
+ *      Alg. 2 reads (2dx+1) x (2dy+1) x dt pixels per thread) -- kf_add_stage;
+ *   2. choose the partition into contiguous fused groups that minimises the predicted
+ *      global<->on-chip traffic, each kernel covered exactly once (Sec. VI, Fig. 5;
+ *      traffic of Sec. VI-D) -- kf_plan, kf_enumerate, kf_partition_traffic;
+ *   3. run the fused groups in sequence over the video volume, each group reading its
+ *      input box once and keeping its intermediates on chip (Sec. V-B, Eq. 2; Alg. 1)
+ *      -- kf_run, kf_run_group.
+ *
+ * Conventions (all calls):
+ *   - Every call returns a kf_status; nothing is thrown across the ABI.
+ *   - Pointers named "device" are CUDA device pointers owned by the caller; the library
+ *     never allocates, frees or keeps them past the call.
+ *   - Calls that take `stream` (a cudaStream_t, NULL = legacy default stream) are
+ *     asynchronous: they enqueue work and return. Launch failures are reported as
+ *     KF_ECUDA; kf_last_cuda_error() gives the CUDA error code.
+ *   - A frame is H rows x W columns; x = column (positive right), y = row (positive
+ *     down). Volumes hold T frames back to back.
+ *   - Bad arguments are rejected with KF_EINVAL before anything is enqueued.
+ *   - One context per host thread; a context is not thread-safe.
+ */
+#ifndef KFUSE_H
+#define KFUSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KF_VERSION_MAJOR 1
+#define KF_VERSION_MINOR 0
+#define KF_MAX_STAGES 24
+
+typedef enum kf_status {
+    KF_OK = 0,
+    KF_EINVAL = 1,        /* invalid argument: null pointer, shape, pitch, alignment, range */
+    KF_ENOMEM = 2,        /* host allocation failed, or workspace smaller than required    */
+    KF_ECUDA = 3,         /* a CUDA runtime call failed; see kf_last_cuda_error()          */
+    KF_ESMEM = 4,         /* a group exceeds the on-chip limit (restriction c, Sec. VII)    */
+    KF_EUNSUPPORTED = 5,  /* the declared chain can be planned but not executed            */
+    KF_ESTATE = 6,        /* call not valid for this context (e.g. run on a host-only ctx) */
+    KF_ETIMEOUT = 7       /* a bounded device-side wait expired                            */
+} kf_status;
+
+/* Stage kinds. KF_STAGE_CUSTOM stages can only be planned (radii and byte counts come
+ * from the descriptor); the eight Harris stages can also be executed, in this order: */
+typedef enum kf_stage_kind {
+    KF_STAGE_CUSTOM = 0,
+    KF_STAGE_CONVERT = 1,  /* f = u8/255                 point,         r = (0,0,0)  */
+    KF_STAGE_GAUSS_H = 2,  /* [1 4 6 4 1]/16 along x     rectangular,   r = (2,0,0)  */
+    KF_STAGE_GAUSS_V = 3,  /* [1 4 6 4 1]/16 along y     rectangular,   r = (0,2,0)  */
+    KF_STAGE_SOBEL = 4,    /* (Ix, Iy), 3x3 Sobel        gradient,      r = (1,1,0)  */
+    KF_STAGE_PRODUCTS = 5, /* Ix^2, IxIy, Iy^2           point,         r = (0,0,0)  */
+    KF_STAGE_BOX5 = 6,     /* 5x5 sum of each product    rectangular,   r = (2,2,0)  */
+    KF_STAGE_HARRIS = 7,   /* R = det - 0.04 tr^2        point,         r = (0,0,0)  */
+    KF_STAGE_NMS = 8       /* R > 1e-5 and 3x3 maximum   threshold,     r = (1,1,0)  */
+} kf_stage_kind;
+
+typedef enum kf_precision {
+    KF_PREC_F32 = 0, /* FP32 maps between groups, FP32 arithmetic                         */
+    KF_PREC_F16 = 1  /* FP16 maps between groups (true units), FP32 arithmetic on chip    */
+} kf_precision;
+
+typedef enum kf_dtype { KF_DT_U8 = 0, KF_DT_F32 = 1, KF_DT_F16 = 2 } kf_dtype;
+
+/* A kernel of the chain (Table I). Radii are one-sided: the stage reads columns
+ * x-rx..x+rx, rows y-ry..y+ry and frames t-rt..t. Byte counts are per pixel over all
+ * channels of the stage's input and output maps; 0 means "the builtin default" for the
+ * eight Harris kinds at the context precision. */
+typedef struct kf_stage_desc {
+    int kind;       /* kf_stage_kind                         */
+    int rx, ry, rt; /* one-sided radii                       */
+    double in_bytes, out_bytes;
+} kf_stage_desc;
+
+/* Volume size and the output box x*y*t of one thread block (Sec. V, Fig. 3) that the
+ * traffic model assumes. box_* = 0 selects the executor's own tile: x = the output
+ * width of a warp strip of the fully fused chain (116 columns), y = the chunk height
+ * (kf_set_chunk_rows), t = 1. */
+typedef struct kf_geometry {
+    int64_t W, H, T;
+    int64_t box_x, box_y, box_t;
+} kf_geometry;
+
+/* Input video: T frames of H rows of W uint8 pixels, row y of frame t at
+ * frames + (t*H + y)*pitch. pitch >= W and a multiple of 16 bytes; frames 16-byte
+ * aligned. Device memory, read only. */
+typedef struct kf_video {
+    const uint8_t *frames;
+    int64_t W, H, T;
+    int64_t pitch;
+} kf_video;
+
+/* Output of the chain. mask: device, same layout as the frames with mask_pitch (a
+ * multiple of 16 bytes); pixel = 1 for a corner, 0 otherwise; columns >= W untouched.
+ * counts: device, T int32, overwritten with the number of corners of each frame. */
+typedef struct kf_corners {
+    uint8_t *mask;
+    int64_t mask_pitch;
+    int32_t *counts;
+} kf_corners;
+
+/* A map between groups: `channels` planes (1..3) of T frames x H rows, row y of frame t
+ * of plane c at plane[c] + (t*frame_stride + y*pitch) elements. pitch and frame_stride
+ * in elements, multiples of 4; planes 16-byte aligned. U8 for the frames and the mask,
+ * F32/F16 for the maps of stages 1..7 (see kf_map_scale for their units). */
+typedef struct kf_map {
+    void *plane[3];
+    int channels;
+    int dtype; /* kf_dtype */
+    int64_t pitch, frame_stride;
+} kf_map;
+
+typedef struct kf_ctx kf_ctx;
+
+/* Message for a status code (static string). */
+const char *kf_status_str(kf_status s);
+/* CUDA error code of the last KF_ECUDA on this context (0 if none). */
+int kf_last_cuda_error(const kf_ctx *ctx);
+kf_status kf_version(int *major, int *minor);
+
+/* Create a context on CUDA device `device` (selects it with cudaSetDevice), or a
+ * host-only planning context when device < 0 (no CUDA call is ever made by it). */
+kf_status kf_create(int device, kf_ctx **out);
+kf_status kf_destroy(kf_ctx *ctx);
+
+/* KF_PREC_F32 (default) or KF_PREC_F16. Changes the builtin byte counts and the dtype
+ * of the maps kf_run keeps in the workspace. */
+kf_status kf_set_precision(kf_ctx *ctx, int precision);
+/* Rows per warp job of the executor (default 200, >= 1). */
+kf_status kf_set_chunk_rows(kf_ctx *ctx, int rows);
+
+/* Declare the next kernel of the chain (Sec. IV). Returns its 0-based index in *id.
+ * KF_EINVAL if the chain already holds KF_MAX_STAGES stages or radii are negative. */
+kf_status kf_add_stage(kf_ctx *ctx, const kf_stage_desc *desc, int *id);
+/* Declare the eight Harris stages in order (KF_EINVAL if stages were declared before). */
+kf_status kf_add_harris_chain(kf_ctx *ctx);
+kf_status kf_num_stages(const kf_ctx *ctx, int *n);
+
+/* ------------------------------------------------------------------ planning (host) */
+/* A partition is a cut mask: bit i set = a group boundary between stage i and i+1
+ * (0-based). 0 = everything fused into one kernel; (1<<(n-1))-1 = no fusion. */
+
+/* Traffic of one fused group [first, last] (0-based, inclusive) in bytes (Sec. VI-D):
+ * boxes * ((x+2Rx)(y+2Ry)(t+Rt) in_bytes(first) + x*y*t out_bytes(last)), with
+ * boxes = W*H*T/(x*y*t) and R* the SUM of the group's radii. */
+kf_status kf_group_traffic(const kf_ctx *ctx, int first, int last, const kf_geometry *g, double *bytes);
+/* On-chip bytes the group holds per box: (x+2Rx)(t+Rt) * sum_k (2 ry_k + 1) in_bytes_k. */
+kf_status kf_group_onchip(const kf_ctx *ctx, int first, int last, const kf_geometry *g, double *bytes);
+/* Total traffic of a partition. KF_EINVAL if the mask has bits at or above n-1. */
+kf_status kf_partition_traffic(const kf_ctx *ctx, uint32_t cuts, const kf_geometry *g, double *bytes);
+/* The partition of minimum traffic among those whose every group holds at most
+ * onchip_limit bytes (restriction c); exact, by dynamic programming over the n-1 cut
+ * points (the set-partition model of Fig. 5 restricted to contiguous groups).
+ * KF_ESMEM if no partition is feasible. */
+kf_status kf_plan(const kf_ctx *ctx, const kf_geometry *g, double onchip_limit, uint32_t *cuts, double *bytes);
+/* All 2^(n-1) cut masks in increasing order; *n_out = 2^(n-1) even when cap is smaller
+ * (only the first cap are written). */
+kf_status kf_enumerate(const kf_ctx *ctx, uint32_t *buf, int64_t cap, int64_t *n_out);
+
+/* ------------------------------------------------------------------ execution (device) */
+/* Factor that turns a stored value of the map written by 0-based stage `stage` into the
+ * chain's true units (true = stored * factor). FP32 maps hold integer-scaled values
+ * (f*255, g1*4080, g*65280, I*65280, products and sums *65280^2, R*65280^4), which keeps
+ * stages 1-4 exact; FP16 maps hold true units (factor 1). */
+kf_status kf_map_scale(const kf_ctx *ctx, int stage, double *factor);
+
+/* Bytes of device workspace kf_run needs for partition `cuts` on a T x H x W volume:
+ * the maps at the cut points, double buffered, with rows padded to 16 bytes. */
+kf_status kf_workspace_bytes(const kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_t T, size_t *bytes);
+
+/* Run the declared Harris chain with partition `cuts` on `stream`: one fused kernel per
+ * group, in chain order. Requires a device context whose chain is exactly the eight
+ * builtin stages (else KF_EUNSUPPORTED). workspace: device, >= kf_workspace_bytes, 256-byte
+ * aligned (may be NULL when cuts == 0). Writes out->mask and out->counts. With T == 0
+ * nothing is enqueued and the pointers are not inspected. */
+kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *video, const kf_corners *out,
+                 void *workspace, size_t workspace_bytes, void *stream);
+
+/* Run one fused group [first, last] (0-based stages of the builtin chain) from map `in`
+ * (the output of stage first-1; the U8 frames when first == 0) into map `out` (the
+ * output of stage last; the U8 mask when last == 7, then `counts` (T int32, device) is
+ * overwritten with per-frame corner counts). Map dtypes must match the context
+ * precision. */
+kf_status kf_run_group(kf_ctx *ctx, int first, int last, const kf_map *in, const kf_map *out,
+                       int64_t W, int64_t H, int64_t T, int32_t *counts, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KFUSE_H */

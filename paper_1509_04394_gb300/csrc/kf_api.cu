@@ -1,0 +1,478 @@
+// kf_api.cu -- host side of libkfuse.so: context, stage declarations, the partitioner
+// (traffic model + exact dynamic program + enumeration) and the group executor.
+//
+// The partitioner is the model of Sec. VI (Fig. 5): choose contiguous groups covering
+// every kernel exactly once so that the summed cost is minimal. With contiguous groups
+// the constraint matrix has consecutive ones, so the 0/1 program is solved exactly by a
+// shortest path over the n+1 cut points; the cost of a group is the traffic of Sec. VI-D
+// (global<->on-chip bytes of one fused kernel) and a group is feasible when its on-chip
+// footprint fits the limit (restriction c of Sec. VII).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/kfuse.h"
+#include "kf_params.h"
+
+struct kf_ctx {
+    int device = -1;
+    int precision = KF_PREC_F32;
+    int chunk_rows = 200;
+    int last_cuda = 0;
+    std::vector<kf_stage_desc> stages;
+};
+
+namespace {
+
+constexpr double NMS_THRESHOLD = 1e-5;  // on R in true units
+
+bool builtin_chain(const kf_ctx *c)
+{
+    if ((int)c->stages.size() != kf::NSTAGES) return false;
+    for (int i = 0; i < kf::NSTAGES; ++i)
+        if (c->stages[i].kind != i + 1) return false;
+    return true;
+}
+
+// bytes per pixel of the map written by 1-based stage k at a precision
+double builtin_map_bytes(int k, int precision)
+{
+    if (k == 0 || k == 8) return 1.0;  // u8 frames, u8 mask
+    return kf::map_channels(k) * (precision == KF_PREC_F16 ? 2.0 : 4.0);
+}
+
+kf_stage_desc builtin_desc(int kind, int precision)
+{
+    kf_stage_desc d{};
+    d.kind = kind;
+    d.rx = kf::stage_rx(kind);
+    d.ry = kf::stage_ry(kind);
+    d.rt = 0;
+    d.in_bytes = builtin_map_bytes(kind - 1, precision);
+    d.out_bytes = builtin_map_bytes(kind, precision);
+    return d;
+}
+
+// effective descriptor: builtin kinds get their default byte counts where 0
+kf_stage_desc eff(const kf_ctx *c, int i)
+{
+    kf_stage_desc d = c->stages[i];
+    if (d.kind >= KF_STAGE_CONVERT && d.kind <= KF_STAGE_NMS) {
+        const kf_stage_desc b = builtin_desc(d.kind, c->precision);
+        if (d.in_bytes == 0) d.in_bytes = b.in_bytes;
+        if (d.out_bytes == 0) d.out_bytes = b.out_bytes;
+    }
+    return d;
+}
+
+bool geom_ok(const kf_geometry *g) { return g && g->W > 0 && g->H > 0 && g->T > 0 && g->box_x >= 0 && g->box_y >= 0 && g->box_t >= 0; }
+
+void box_of(const kf_ctx *c, const kf_geometry *g, double &x, double &y, double &t)
+{
+    x = g->box_x ? (double)g->box_x : (double)kf::strip_geometry(6, 1 << 20).step;
+    y = g->box_y ? (double)g->box_y : (double)c->chunk_rows;
+    t = g->box_t ? (double)g->box_t : 1.0;
+}
+
+void group_radii(const kf_ctx *c, int a, int b, double &rx, double &ry, double &rt)
+{
+    rx = ry = rt = 0;
+    for (int k = a; k <= b; ++k) {
+        rx += c->stages[k].rx;
+        ry += c->stages[k].ry;
+        rt += c->stages[k].rt;
+    }
+}
+
+double traffic(const kf_ctx *c, int a, int b, const kf_geometry *g)
+{
+    double x, y, t, rx, ry, rt;
+    box_of(c, g, x, y, t);
+    group_radii(c, a, b, rx, ry, rt);
+    const double boxes = (double)g->W * (double)g->H * (double)g->T / (x * y * t);
+    const double per_box = (x + 2 * rx) * (y + 2 * ry) * (t + rt) * eff(c, a).in_bytes + x * y * t * eff(c, b).out_bytes;
+    return boxes * per_box;
+}
+
+double onchip(const kf_ctx *c, int a, int b, const kf_geometry *g)
+{
+    double x, y, t, rx, ry, rt;
+    box_of(c, g, x, y, t);
+    group_radii(c, a, b, rx, ry, rt);
+    double rows = 0;
+    for (int k = a; k <= b; ++k) rows += (2.0 * c->stages[k].ry + 1.0) * eff(c, k).in_bytes;
+    return (x + 2 * rx) * (t + rt) * rows;
+}
+
+kf_status cuda_fail(kf_ctx *c, cudaError_t e)
+{
+    c->last_cuda = (int)e;
+    return KF_ECUDA;
+}
+
+kf::LaunchFn launcher(int A, int B, int f16)
+{
+    switch (A) {
+    case 1: return kf::launcher_a1(B, f16);
+    case 2: return kf::launcher_a2(B, f16);
+    case 3: return kf::launcher_a3(B, f16);
+    case 4: return kf::launcher_a4(B, f16);
+    case 5: return kf::launcher_a5(B, f16);
+    case 6: return kf::launcher_a6(B, f16);
+    case 7: return kf::launcher_a7(B, f16);
+    case 8: return kf::launcher_a8(B, f16);
+    default: return nullptr;
+    }
+}
+
+bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
+
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// map validation for kf_run_group: dtype/channels as the chain requires at this point
+kf_status check_map(const kf_map *m, int stage_out, int precision, int64_t W, int64_t H)
+{
+    if (!m) return KF_EINVAL;
+    const int want_dt = (stage_out == 0 || stage_out == 8) ? KF_DT_U8 : (precision == KF_PREC_F16 ? KF_DT_F16 : KF_DT_F32);
+    const int want_ch = kf::map_channels(stage_out);
+    if (m->dtype != want_dt || m->channels != want_ch) return KF_EINVAL;
+    const int64_t align_e = want_dt == KF_DT_U8 ? 16 : 4;
+    if (m->pitch < W || m->pitch % align_e || m->frame_stride < H * m->pitch || m->frame_stride % align_e) return KF_EINVAL;
+    for (int i = 0; i < want_ch; ++i)
+        if (!m->plane[i] || !aligned(m->plane[i], 16)) return KF_EINVAL;
+    return KF_OK;
+}
+
+// Enqueue group [A..B] (1-based) with already validated maps.
+kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &out, int64_t W, int64_t H, int64_t T,
+                       int32_t *counts, cudaStream_t s)
+{
+    if (T == 0) return KF_OK;
+    kf::GroupParams p{};
+    for (int i = 0; i < 3; ++i) {
+        p.in[i] = in.plane[i];
+        p.out[i] = out.plane[i];
+    }
+    p.in_pitch = in.pitch;
+    p.in_fstride = in.frame_stride;
+    p.out_pitch = out.pitch;
+    p.out_fstride = out.frame_stride;
+    p.counts = counts;
+    p.W = (int)W;
+    p.H = (int)H;
+    const kf::StripGeom sg = kf::strip_geometry(kf::sum_rx(A, B), (int)W);
+    p.xs0 = sg.xs0;
+    p.step = sg.step;
+    p.n_strips = sg.n_strips;
+    p.chunk_rows = c->chunk_rows;
+    p.n_chunks = (int)((H + c->chunk_rows - 1) / c->chunk_rows);
+    p.n_jobs = T * p.n_chunks * p.n_strips;
+    p.thr = (float)(NMS_THRESHOLD * kf::map_scale(7));
+    const bool f16 = c->precision == KF_PREC_F16;
+    p.in_scale = (f16 && A > 1) ? (float)kf::map_scale(A - 1) : 1.0f;
+    p.out_scale = (f16 && B < 8) ? (float)(1.0 / kf::map_scale(B)) : 1.0f;
+    const int64_t blocks = (p.n_jobs + kf::WARPS_PER_BLOCK - 1) / kf::WARPS_PER_BLOCK;
+    if (blocks > 0x7fffffff) return KF_EINVAL;
+    if (B == 8) {
+        cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)T, s);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    kf::LaunchFn fn = launcher(A, B, f16 ? 1 : 0);
+    if (!fn) return KF_EINVAL;
+    const int e = fn(p, (unsigned)blocks, s);
+    if (e != 0) return cuda_fail(c, (cudaError_t)e);
+    return KF_OK;
+}
+
+struct WsPlan {
+    int64_t pitch_e = 0;      // elements per map row
+    size_t plane_bytes = 0;   // one plane of the whole volume
+    size_t buf_bytes[2] = {0, 0};
+    size_t total = 0;
+};
+
+WsPlan plan_workspace(const kf_ctx *c, uint32_t cuts, int64_t W, int64_t H, int64_t T)
+{
+    WsPlan w;
+    const size_t elem = c->precision == KF_PREC_F16 ? 2 : 4;
+    w.pitch_e = round_up(W, 8);
+    w.plane_bytes = (size_t)round_up((int64_t)(w.pitch_e * H * T * (int64_t)elem), 256);
+    int k = 0;
+    for (int i = 0; i < kf::NSTAGES - 1; ++i)
+        if (cuts >> i & 1) {
+            const size_t need = w.plane_bytes * (size_t)kf::map_channels(i + 1);
+            if (need > w.buf_bytes[k % 2]) w.buf_bytes[k % 2] = need;
+            ++k;
+        }
+    w.total = w.buf_bytes[0] + w.buf_bytes[1];
+    return w;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *kf_status_str(kf_status s)
+{
+    switch (s) {
+    case KF_OK: return "ok";
+    case KF_EINVAL: return "invalid argument";
+    case KF_ENOMEM: return "out of memory or workspace too small";
+    case KF_ECUDA: return "CUDA runtime error";
+    case KF_ESMEM: return "group exceeds the on-chip limit";
+    case KF_EUNSUPPORTED: return "chain cannot be executed";
+    case KF_ESTATE: return "call not valid for this context";
+    case KF_ETIMEOUT: return "device-side wait timed out";
+    }
+    return "unknown status";
+}
+
+int kf_last_cuda_error(const kf_ctx *ctx) { return ctx ? ctx->last_cuda : 0; }
+
+kf_status kf_version(int *major, int *minor)
+{
+    if (!major || !minor) return KF_EINVAL;
+    *major = KF_VERSION_MAJOR;
+    *minor = KF_VERSION_MINOR;
+    return KF_OK;
+}
+
+kf_status kf_create(int device, kf_ctx **out)
+{
+    if (!out) return KF_EINVAL;
+    *out = nullptr;
+    kf_ctx *c = new (std::nothrow) kf_ctx;
+    if (!c) return KF_ENOMEM;
+    c->device = device < 0 ? -1 : device;
+    if (device >= 0) {
+        cudaError_t e = cudaSetDevice(device);
+        if (e != cudaSuccess) {
+            delete c;
+            return KF_ECUDA;
+        }
+    }
+    *out = c;
+    return KF_OK;
+}
+
+kf_status kf_destroy(kf_ctx *ctx)
+{
+    delete ctx;
+    return KF_OK;
+}
+
+kf_status kf_set_precision(kf_ctx *ctx, int precision)
+{
+    if (!ctx || (precision != KF_PREC_F32 && precision != KF_PREC_F16)) return KF_EINVAL;
+    ctx->precision = precision;
+    return KF_OK;
+}
+
+kf_status kf_set_chunk_rows(kf_ctx *ctx, int rows)
+{
+    if (!ctx || rows < 1) return KF_EINVAL;
+    ctx->chunk_rows = rows;
+    return KF_OK;
+}
+
+kf_status kf_add_stage(kf_ctx *ctx, const kf_stage_desc *d, int *id)
+{
+    if (!ctx || !d) return KF_EINVAL;
+    if ((int)ctx->stages.size() >= KF_MAX_STAGES) return KF_EINVAL;
+    if (d->kind < KF_STAGE_CUSTOM || d->kind > KF_STAGE_NMS) return KF_EINVAL;
+    if (d->rx < 0 || d->ry < 0 || d->rt < 0 || d->in_bytes < 0 || d->out_bytes < 0) return KF_EINVAL;
+    if (d->kind == KF_STAGE_CUSTOM && (d->in_bytes <= 0 || d->out_bytes <= 0)) return KF_EINVAL;
+    if (d->kind != KF_STAGE_CUSTOM && (d->rx != kf::stage_rx(d->kind) || d->ry != kf::stage_ry(d->kind) || d->rt != 0))
+        return KF_EINVAL;  // builtin kinds have fixed radii
+    ctx->stages.push_back(*d);
+    if (id) *id = (int)ctx->stages.size() - 1;
+    return KF_OK;
+}
+
+kf_status kf_add_harris_chain(kf_ctx *ctx)
+{
+    if (!ctx || !ctx->stages.empty()) return KF_EINVAL;
+    for (int k = 1; k <= kf::NSTAGES; ++k) {
+        kf_stage_desc d{};
+        d.kind = k;
+        d.rx = kf::stage_rx(k);
+        d.ry = kf::stage_ry(k);
+        ctx->stages.push_back(d);
+    }
+    return KF_OK;
+}
+
+kf_status kf_num_stages(const kf_ctx *ctx, int *n)
+{
+    if (!ctx || !n) return KF_EINVAL;
+    *n = (int)ctx->stages.size();
+    return KF_OK;
+}
+
+kf_status kf_group_traffic(const kf_ctx *ctx, int first, int last, const kf_geometry *g, double *bytes)
+{
+    if (!ctx || !bytes || !geom_ok(g)) return KF_EINVAL;
+    if (first < 0 || last < first || last >= (int)ctx->stages.size()) return KF_EINVAL;
+    *bytes = traffic(ctx, first, last, g);
+    return KF_OK;
+}
+
+kf_status kf_group_onchip(const kf_ctx *ctx, int first, int last, const kf_geometry *g, double *bytes)
+{
+    if (!ctx || !bytes || !geom_ok(g)) return KF_EINVAL;
+    if (first < 0 || last < first || last >= (int)ctx->stages.size()) return KF_EINVAL;
+    *bytes = onchip(ctx, first, last, g);
+    return KF_OK;
+}
+
+kf_status kf_partition_traffic(const kf_ctx *ctx, uint32_t cuts, const kf_geometry *g, double *bytes)
+{
+    if (!ctx || !bytes || !geom_ok(g)) return KF_EINVAL;
+    const int n = (int)ctx->stages.size();
+    if (n == 0 || (n - 1 < 32 && (cuts >> (n - 1)) != 0)) return KF_EINVAL;
+    double tot = 0;
+    int a = 0;
+    for (int i = 0; i < n; ++i)
+        if (i == n - 1 || (cuts >> i & 1)) {
+            tot += traffic(ctx, a, i, g);
+            a = i + 1;
+        }
+    *bytes = tot;
+    return KF_OK;
+}
+
+kf_status kf_plan(const kf_ctx *ctx, const kf_geometry *g, double onchip_limit, uint32_t *cuts, double *bytes)
+{
+    if (!ctx || !cuts || !geom_ok(g) || !(onchip_limit > 0)) return KF_EINVAL;
+    const int n = (int)ctx->stages.size();
+    if (n == 0) return KF_EINVAL;
+    // best[j]: cheapest cover of stages [0, j); from[j]: start of its last group
+    std::vector<double> best(n + 1, INFINITY);
+    std::vector<int> from(n + 1, -1);
+    best[0] = 0;
+    for (int j = 1; j <= n; ++j)
+        for (int i = 0; i < j; ++i) {
+            if (!std::isfinite(best[i])) continue;
+            if (onchip(ctx, i, j - 1, g) > onchip_limit) continue;
+            const double v = best[i] + traffic(ctx, i, j - 1, g);
+            if (v < best[j]) {
+                best[j] = v;
+                from[j] = i;
+            }
+        }
+    if (!std::isfinite(best[n])) return KF_ESMEM;
+    uint32_t m = 0;
+    for (int j = n; j > 0; j = from[j])
+        if (from[j] > 0) m |= 1u << (from[j] - 1);
+    *cuts = m;
+    if (bytes) *bytes = best[n];
+    return KF_OK;
+}
+
+kf_status kf_enumerate(const kf_ctx *ctx, uint32_t *buf, int64_t cap, int64_t *n_out)
+{
+    if (!ctx || !n_out || cap < 0 || (cap > 0 && !buf)) return KF_EINVAL;
+    const int n = (int)ctx->stages.size();
+    if (n == 0) return KF_EINVAL;
+    const int64_t total = (int64_t)1 << (n - 1);
+    for (int64_t i = 0; i < total && i < cap; ++i) buf[i] = (uint32_t)i;
+    *n_out = total;
+    return KF_OK;
+}
+
+kf_status kf_map_scale(const kf_ctx *ctx, int stage, double *factor)
+{
+    if (!ctx || !factor || stage < 0 || stage >= kf::NSTAGES) return KF_EINVAL;
+    if (stage == kf::NSTAGES - 1 || ctx->precision == KF_PREC_F16) *factor = 1.0;
+    else *factor = 1.0 / kf::map_scale(stage + 1);
+    return KF_OK;
+}
+
+kf_status kf_workspace_bytes(const kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_t T, size_t *bytes)
+{
+    if (!ctx || !bytes || W <= 0 || H <= 0 || T < 0) return KF_EINVAL;
+    if (cuts >> (kf::NSTAGES - 1)) return KF_EINVAL;
+    *bytes = plan_workspace(ctx, cuts, W, H, T).total;
+    return KF_OK;
+}
+
+kf_status kf_run_group(kf_ctx *ctx, int first, int last, const kf_map *in, const kf_map *out, int64_t W, int64_t H,
+                       int64_t T, int32_t *counts, void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    if (ctx->device < 0) return KF_ESTATE;
+    if (!builtin_chain(ctx)) return KF_EUNSUPPORTED;
+    if (first < 0 || last < first || last >= kf::NSTAGES) return KF_EINVAL;
+    if (W <= 0 || H <= 0 || T < 0 || W > (1 << 30) || H > (1 << 30)) return KF_EINVAL;
+    const int A = first + 1, B = last + 1;
+    kf_status s = check_map(in, A - 1, ctx->precision, W, H);
+    if (s != KF_OK) return s;
+    s = check_map(out, B, ctx->precision, W, H);
+    if (s != KF_OK) return s;
+    if (B == 8 && (!counts || !aligned(counts, 4))) return KF_EINVAL;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    return launch_group(ctx, A, B, *in, *out, W, H, T, counts, static_cast<cudaStream_t>(stream));
+}
+
+kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *v, const kf_corners *o, void *ws, size_t ws_bytes,
+                 void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    if (ctx->device < 0) return KF_ESTATE;
+    if (!builtin_chain(ctx)) return KF_EUNSUPPORTED;
+    if (!v || !o) return KF_EINVAL;
+    if (cuts >> (kf::NSTAGES - 1)) return KF_EINVAL;
+    if (v->W <= 0 || v->H <= 0 || v->T < 0 || v->W > (1 << 30) || v->H > (1 << 30)) return KF_EINVAL;
+    if (v->pitch < v->W || v->pitch % 16 || o->mask_pitch < v->W || o->mask_pitch % 16) return KF_EINVAL;
+    if (v->T == 0) return KF_OK;  // nothing to read or write
+    if (!v->frames || !o->mask || !o->counts) return KF_EINVAL;
+    if (!aligned(v->frames, 16) || !aligned(o->mask, 16) || !aligned(o->counts, 4)) return KF_EINVAL;
+    const WsPlan w = plan_workspace(ctx, cuts, v->W, v->H, v->T);
+    if (w.total > 0 && (!ws || !aligned(ws, 256))) return KF_EINVAL;
+    if (ws_bytes < w.total) return KF_ENOMEM;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int dt = ctx->precision == KF_PREC_F16 ? KF_DT_F16 : KF_DT_F32;
+    const size_t elem = ctx->precision == KF_PREC_F16 ? 2 : 4;
+
+    kf_map cur{};
+    cur.plane[0] = const_cast<uint8_t *>(v->frames);
+    cur.channels = 1;
+    cur.dtype = KF_DT_U8;
+    cur.pitch = v->pitch;
+    cur.frame_stride = v->pitch * v->H;
+    int a = 1, k = 0;
+    for (int b = 1; b <= kf::NSTAGES; ++b) {
+        if (b < kf::NSTAGES && !(cuts >> (b - 1) & 1)) continue;
+        kf_map nxt{};
+        if (b == kf::NSTAGES) {
+            nxt.plane[0] = o->mask;
+            nxt.channels = 1;
+            nxt.dtype = KF_DT_U8;
+            nxt.pitch = o->mask_pitch;
+            nxt.frame_stride = o->mask_pitch * v->H;
+        } else {
+            char *base = static_cast<char *>(ws) + (k % 2 ? w.buf_bytes[0] : 0);
+            nxt.channels = kf::map_channels(b);
+            for (int c = 0; c < nxt.channels; ++c) nxt.plane[c] = base + c * w.plane_bytes;
+            nxt.dtype = dt;
+            nxt.pitch = w.pitch_e;
+            nxt.frame_stride = w.pitch_e * v->H;
+            (void)elem;
+            ++k;
+        }
+        kf_status st = launch_group(ctx, a, b, cur, nxt, v->W, v->H, v->T, o->counts, s);
+        if (st != KF_OK) return st;
+        cur = nxt;
+        a = b + 1;
+    }
+    return KF_OK;
+}
+
+}  // extern "C"

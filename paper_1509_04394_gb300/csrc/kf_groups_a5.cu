@@ -1,0 +1,27 @@
+// kf_groups_a5.cu -- fused group kernels whose first stage is stage 5 (one TU per first
+// stage so that the 72 instantiations compile in parallel).
+#include <cuda_runtime.h>
+
+#include "kf_chain.cuh"
+
+namespace kf {
+namespace {
+template <int A, int B, typename TM>
+int launch(const GroupParams &p, unsigned grid, void *stream)
+{
+    group_kernel<A, B, TM><<<grid, 32 * WARPS_PER_BLOCK, 0, static_cast<cudaStream_t>(stream)>>>(p);
+    return (int)cudaGetLastError();
+}
+}  // namespace
+
+LaunchFn launcher_a5(int B, int f16)
+{
+    switch (B) {
+    case 5: return f16 ? launch<5, 5, __half> : launch<5, 5, float>;
+    case 6: return f16 ? launch<5, 6, __half> : launch<5, 6, float>;
+    case 7: return f16 ? launch<5, 7, __half> : launch<5, 7, float>;
+    case 8: return f16 ? launch<5, 8, __half> : launch<5, 8, float>;
+    default: return nullptr;
+    }
+}
+}  // namespace kf

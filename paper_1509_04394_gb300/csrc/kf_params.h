@@ -1,0 +1,82 @@
+// kf_params.h -- launch parameters and the stage table shared by host and device code.
+#pragma once
+
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define KF_HD __host__ __device__
+#else
+#define KF_HD
+#endif
+
+#ifndef KF_C
+#define KF_C 4
+#endif
+
+namespace kf {
+
+constexpr int C = KF_C;        // columns per lane
+constexpr int STRIP = 32 * C;  // columns per warp strip
+constexpr int WARPS_PER_BLOCK = 4;
+constexpr int NSTAGES = 8;
+
+// Stage table of the Harris chain, 1-based (stage 0 = the u8 frames). One-sided radii
+// along columns (rx) and rows (ry), Table I.
+KF_HD constexpr int stage_rx(int k) { return k == 2 ? 2 : k == 4 ? 1 : k == 6 ? 2 : k == 8 ? 1 : 0; }
+KF_HD constexpr int stage_ry(int k) { return k == 3 ? 2 : k == 4 ? 1 : k == 6 ? 2 : k == 8 ? 1 : 0; }
+// channels of the map written by stage k (k = 0: the frames, k = 8: the mask)
+KF_HD constexpr int map_channels(int k) { return k == 4 ? 2 : (k == 5 || k == 6) ? 3 : 1; }
+KF_HD constexpr int sum_rx(int a, int b) { int s = 0; for (int k = a; k <= b; ++k) s += stage_rx(k); return s; }
+KF_HD constexpr int sum_ry(int a, int b) { int s = 0; for (int k = a; k <= b; ++k) s += stage_ry(k); return s; }
+// does a stage in [a, k) read horizontal neighbours? (then the input of k needs an edge fix-up)
+KF_HD constexpr bool hstencil_before(int a, int k) { for (int j = a; j < k; ++j) if (stage_rx(j) > 0) return true; return false; }
+
+// Integer scale of the FP32 map written by stage k: scaled = true * map_scale(k).
+inline constexpr double map_scale(int k)
+{
+    return k == 1 ? 255.0 : k == 2 ? 4080.0 : (k == 3 || k == 4) ? 65280.0
+         : (k == 5 || k == 6) ? 65280.0 * 65280.0 : k == 7 ? 65280.0 * 65280.0 * 65280.0 * 65280.0 : 1.0;
+}
+
+struct GroupParams {
+    const void *in[3];        // input planes (stage A-1 map; u8 frames when A == 1)
+    int64_t in_pitch;         // elements between rows
+    int64_t in_fstride;       // elements between frames
+    void *out[3];             // output planes (u8 mask when B == 8)
+    int64_t out_pitch, out_fstride;
+    int32_t *counts;          // per-frame corner counts (B == 8), pre-zeroed
+    int W, H;                 // frame size
+    int xs0, step, n_strips;  // strip s covers input columns [xs0 + s*step, +STRIP)
+    int chunk_rows, n_chunks;
+    int64_t n_jobs;           // frames * n_chunks * n_strips
+    float thr;                // NMS threshold in the scaled units of R
+    float in_scale;           // FP16 input maps: scaled value = stored * in_scale
+    float out_scale;          // FP16 output maps: stored = scaled value * out_scale
+};
+
+// Strip geometry of a group with accumulated horizontal radius rxt: input strips start
+// on a multiple of C columns (aligned vector loads), outputs tile the frame exactly.
+struct StripGeom { int xs0, step, n_strips; };
+inline StripGeom strip_geometry(int rxt, int W)
+{
+    StripGeom g;
+    g.xs0 = -((rxt + C - 1) / C) * C;
+    g.step = ((STRIP - 2 * rxt) / C) * C;
+    const int o0 = g.xs0 + rxt;  // first output column of strip 0 (<= 0)
+    g.n_strips = (W - o0 + g.step - 1) / g.step;
+    return g;
+}
+
+#ifdef __CUDACC__
+typedef int (*LaunchFn)(const GroupParams &p, unsigned grid, void *stream);
+LaunchFn launcher_a1(int B, int f16);
+LaunchFn launcher_a2(int B, int f16);
+LaunchFn launcher_a3(int B, int f16);
+LaunchFn launcher_a4(int B, int f16);
+LaunchFn launcher_a5(int B, int f16);
+LaunchFn launcher_a6(int B, int f16);
+LaunchFn launcher_a7(int B, int f16);
+LaunchFn launcher_a8(int B, int f16);
+#endif
+
+}  // namespace kf

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libkfuse.so (include/kfuse.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no arithmetic
+of the chain; all compute runs in the library's CUDA kernels. Device buffers are torch
+tensors owned by the caller; streams are torch.cuda streams (default: the current one).
+If libkfuse.so has not been built, importing works but the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkfuse.so")
+
+KF_OK, KF_EINVAL, KF_ENOMEM, KF_ECUDA, KF_ESMEM, KF_EUNSUPPORTED, KF_ESTATE, KF_ETIMEOUT = range(8)
+KF_PREC_F32, KF_PREC_F16 = 0, 1
+KF_DT_U8, KF_DT_F32, KF_DT_F16 = 0, 1, 2
+NSTAGES = 8
+STAGE_NAMES = ("convert", "gauss_h", "gauss_v", "sobel", "products", "box5", "harris", "nms")
+MAP_CHANNELS = (1, 1, 1, 1, 2, 3, 3, 1, 1)  # index = 1-based stage writing the map (0 = frames)
+
+
+class KfuseError(RuntimeError):
+    def __init__(self, call: str, status: int, cuda: int = 0):
+        self.status, self.cuda = status, cuda
+        msg = f"{call} failed: {_lib().kf_status_str(status).decode()} (status {status})"
+        if status == KF_ECUDA:
+            msg += f", CUDA error {cuda}"
+        super().__init__(msg)
+
+
+class kf_stage_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("rx", ctypes.c_int), ("ry", ctypes.c_int), ("rt", ctypes.c_int),
+                ("in_bytes", ctypes.c_double), ("out_bytes", ctypes.c_double)]
+
+
+class kf_geometry(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("W", "H", "T", "box_x", "box_y", "box_t")]
+
+
+class kf_video(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_void_p), ("W", ctypes.c_int64), ("H", ctypes.c_int64),
+                ("T", ctypes.c_int64), ("pitch", ctypes.c_int64)]
+
+
+class kf_corners(ctypes.Structure):
+    _fields_ = [("mask", ctypes.c_void_p), ("mask_pitch", ctypes.c_int64), ("counts", ctypes.c_void_p)]
+
+
+class kf_map(ctypes.Structure):
+    _fields_ = [("plane", ctypes.c_void_p * 3), ("channels", ctypes.c_int), ("dtype", ctypes.c_int),
+                ("pitch", ctypes.c_int64), ("frame_stride", ctypes.c_int64)]
+
+
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libkfuse.so is not built ({LIB_PATH}); run "
+                               "python -m paper_1509_04394_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, u32, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
+        sig = {
+            "kf_status_str": (ctypes.c_char_p, [i32]),
+            "kf_last_cuda_error": (i32, [P]),
+            "kf_version": (i32, [P, P]),
+            "kf_create": (i32, [i32, P]),
+            "kf_destroy": (i32, [P]),
+            "kf_set_precision": (i32, [P, i32]),
+            "kf_set_chunk_rows": (i32, [P, i32]),
+            "kf_add_stage": (i32, [P, P, P]),
+            "kf_add_harris_chain": (i32, [P]),
+            "kf_num_stages": (i32, [P, P]),
+            "kf_group_traffic": (i32, [P, i32, i32, P, P]),
+            "kf_group_onchip": (i32, [P, i32, i32, P, P]),
+            "kf_partition_traffic": (i32, [P, u32, P, P]),
+            "kf_plan": (i32, [P, P, dbl, P, P]),
+            "kf_enumerate": (i32, [P, P, i64, P]),
+            "kf_map_scale": (i32, [P, i32, P]),
+            "kf_workspace_bytes": (i32, [P, u32, i64, i64, i64, P]),
+            "kf_run": (i32, [P, u32, P, P, P, ctypes.c_size_t, P]),
+            "kf_run_group": (i32, [P, i32, i32, P, P, i64, i64, i64, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _L = L
+    return _L
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C entry points this binding wraps (all declared in kfuse.h)."""
+    return ["kf_status_str", "kf_last_cuda_error", "kf_version", "kf_create", "kf_destroy",
+            "kf_set_precision", "kf_set_chunk_rows", "kf_add_stage", "kf_add_harris_chain",
+            "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
+            "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group"]
+
+
+def _check(call: str, status: int, ctx=None):
+    if status != KF_OK:
+        cuda = _lib().kf_last_cuda_error(ctx) if ctx else 0
+        raise KfuseError(call, status, cuda)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else t.data_ptr()
+
+
+def _geom(W, H, T, box=(0, 0, 0)) -> kf_geometry:
+    return kf_geometry(int(W), int(H), int(T), int(box[0]), int(box[1]), int(box[2]))
+
+
+# ------------------------------------------------------------------ entry points
+def kf_version() -> tuple[int, int]:
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check("kf_version", _lib().kf_version(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def kf_create(device: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check("kf_create", _lib().kf_create(int(device), ctypes.byref(h)))
+    return h
+
+
+def kf_destroy(ctx) -> None:
+    _check("kf_destroy", _lib().kf_destroy(ctx))
+
+
+def kf_set_precision(ctx, precision: int) -> None:
+    _check("kf_set_precision", _lib().kf_set_precision(ctx, int(precision)), ctx)
+
+
+def kf_set_chunk_rows(ctx, rows: int) -> None:
+    _check("kf_set_chunk_rows", _lib().kf_set_chunk_rows(ctx, int(rows)), ctx)
+
+
+def kf_add_stage(ctx, kind: int, rx: int = 0, ry: int = 0, rt: int = 0, in_bytes: float = 0.0,
+                 out_bytes: float = 0.0) -> int:
+    d = kf_stage_desc(kind, rx, ry, rt, in_bytes, out_bytes)
+    i = ctypes.c_int()
+    _check("kf_add_stage", _lib().kf_add_stage(ctx, ctypes.byref(d), ctypes.byref(i)), ctx)
+    return i.value
+
+
+def kf_add_harris_chain(ctx) -> None:
+    _check("kf_add_harris_chain", _lib().kf_add_harris_chain(ctx), ctx)
+
+
+def kf_num_stages(ctx) -> int:
+    n = ctypes.c_int()
+    _check("kf_num_stages", _lib().kf_num_stages(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def kf_group_traffic(ctx, first: int, last: int, W, H, T, box=(0, 0, 0)) -> float:
+    g, b = _geom(W, H, T, box), ctypes.c_double()
+    _check("kf_group_traffic", _lib().kf_group_traffic(ctx, first, last, ctypes.byref(g), ctypes.byref(b)), ctx)
+    return b.value
+
+
+def kf_group_onchip(ctx, first: int, last: int, W, H, T, box=(0, 0, 0)) -> float:
+    g, b = _geom(W, H, T, box), ctypes.c_double()
+    _check("kf_group_onchip", _lib().kf_group_onchip(ctx, first, last, ctypes.byref(g), ctypes.byref(b)), ctx)
+    return b.value
+
+
+def kf_partition_traffic(ctx, cuts: int, W, H, T, box=(0, 0, 0)) -> float:
+    g, b = _geom(W, H, T, box), ctypes.c_double()
+    _check("kf_partition_traffic", _lib().kf_partition_traffic(ctx, cuts, ctypes.byref(g), ctypes.byref(b)), ctx)
+    return b.value
+
+
+def kf_plan(ctx, W, H, T, box=(0, 0, 0), onchip_limit: float = math.inf) -> tuple[int, float]:
+    g, c, b = _geom(W, H, T, box), ctypes.c_uint32(), ctypes.c_double()
+    lim = 1e300 if math.isinf(onchip_limit) else float(onchip_limit)
+    _check("kf_plan", _lib().kf_plan(ctx, ctypes.byref(g), lim, ctypes.byref(c), ctypes.byref(b)), ctx)
+    return c.value, b.value
+
+
+def kf_enumerate(ctx) -> list[int]:
+    n = ctypes.c_int64()
+    _check("kf_enumerate", _lib().kf_enumerate(ctx, None, 0, ctypes.byref(n)), ctx)
+    buf = (ctypes.c_uint32 * n.value)()
+    _check("kf_enumerate", _lib().kf_enumerate(ctx, buf, n.value, ctypes.byref(n)), ctx)
+    return list(buf)
+
+
+def kf_map_scale(ctx, stage: int) -> float:
+    f = ctypes.c_double()
+    _check("kf_map_scale", _lib().kf_map_scale(ctx, stage, ctypes.byref(f)), ctx)
+    return f.value
+
+
+def kf_workspace_bytes(ctx, cuts: int, W, H, T) -> int:
+    b = ctypes.c_size_t()
+    _check("kf_workspace_bytes", _lib().kf_workspace_bytes(ctx, cuts, W, H, T, ctypes.byref(b)), ctx)
+    return b.value
+
+
+def kf_run(ctx, cuts: int, frames, W: int, mask, counts, workspace=None, stream=None) -> None:
+    """frames, mask: uint8 CUDA tensors [T, H, pitch]; counts: int32 CUDA tensor [T]."""
+    T, H, P = frames.shape
+    v = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
+    o = kf_corners(mask.data_ptr(), int(mask.shape[2]), counts.data_ptr())
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check("kf_run", _lib().kf_run(ctx, cuts, ctypes.byref(v), ctypes.byref(o), _ptr(workspace), ws_bytes,
+                                   _stream(stream)), ctx)
+
+
+def make_map(planes, dtype: int) -> kf_map:
+    """kf_map over a list of CUDA tensors [T, H, pitch] (one per channel)."""
+    m = kf_map()
+    for i, t in enumerate(planes):
+        m.plane[i] = t.data_ptr()
+    m.channels = len(planes)
+    m.dtype = dtype
+    m.pitch = int(planes[0].shape[2])
+    m.frame_stride = int(planes[0].shape[1] * planes[0].shape[2])
+    return m
+
+
+def kf_run_group(ctx, first: int, last: int, in_planes, in_dtype: int, out_planes, out_dtype: int, W: int,
+                 counts=None, stream=None) -> None:
+    """Run fused group [first, last] (0-based) from map planes to map planes."""
+    T, H, _ = in_planes[0].shape
+    mi, mo = make_map(in_planes, in_dtype), make_map(out_planes, out_dtype)
+    _check("kf_run_group", _lib().kf_run_group(ctx, first, last, ctypes.byref(mi), ctypes.byref(mo), int(W), int(H),
+                                               int(T), _ptr(counts), _stream(stream)), ctx)
+
+
+# ------------------------------------------------------------------ convenience
+class Context:
+    """Owns one kf_ctx; the methods are the entry points above with the handle bound."""
+
+    def __init__(self, device: int = 0, precision: int = KF_PREC_F32, harris: bool = True):
+        self.h = kf_create(device)
+        self.device = device
+        if precision != KF_PREC_F32:
+            kf_set_precision(self.h, precision)
+        self.precision = precision
+        if harris:
+            kf_add_harris_chain(self.h)
+
+    def close(self):
+        if self.h:
+            kf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __getattr__(self, name):
+        f = globals().get("kf_" + name)
+        if f is None:
+            raise AttributeError(name)
+        return lambda *a, **k: f(self.h, *a, **k)
