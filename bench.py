@@ -95,11 +95,34 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
-def make_video(rank: int):
+def make_video(rank: int, T: int | None = None):
     P = sv.pitch_for(SPEC.W)
     spec = SPEC if rank == 0 else sv.VideoSpec(**{**SPEC.__dict__, "seed": SPEC.seed + 1000 * rank})
-    frames, _ = sv.generate(spec, pitch=P)
+    frames, _ = sv.generate(spec, pitch=P, frames=range(T or spec.T))
     return frames, P
+
+
+def run_profile(args):
+    """Small case for profiler captures: `--profile T` runs only the planned fused chain on
+    the first T frames (warm-up launches, then `--steps` launches), nothing else."""
+    import torch
+    from paper_1509_04394_gb300 import build as kbuild
+    from paper_1509_04394_gb300 import kfuse as K
+    kbuild.build()
+    frames_h, P = make_video(0, args.profile)
+    T, H, W = frames_h.shape[0], SPEC.H, SPEC.W
+    dev = torch.device("cuda:0")
+    frames = torch.from_numpy(frames_h).to(dev)
+    mask = torch.zeros_like(frames)
+    counts = torch.zeros(T, dtype=torch.int32, device=dev)
+    ctx = K.Context(0, precision=K.KF_PREC_F16 if args.f16 else K.KF_PREC_F32)
+    cuts = args.cuts if args.cuts >= 0 else K.kf_plan(ctx.h, W, H, T)[0]
+    ws_b = K.kf_workspace_bytes(ctx.h, cuts, W, H, T)
+    ws = torch.empty(ws_b, dtype=torch.uint8, device=dev) if ws_b else None
+    for _ in range(args.warmup + args.steps):
+        K.kf_run(ctx.h, cuts, frames, W, mask, counts, ws)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_frames": T, "cuts": cuts, "counts_sum": int(counts.sum())}))
 
 
 def cpu_oracle_rate(frames: np.ndarray, W: int, budget_s: float = 12.0) -> dict:
@@ -289,12 +312,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--profile", type=int, default=0, help="profiler case: fused chain only, on T frames")
+    ap.add_argument("--cuts", type=int, default=-1, help="partition for --profile (default: planned)")
+    ap.add_argument("--f16", action="store_true", help="FP16 maps for --profile")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)

@@ -64,10 +64,12 @@ typedef enum kf_stage_kind {
 
 typedef enum kf_precision {
     KF_PREC_F32 = 0, /* FP32 maps between groups, FP32 arithmetic                         */
-    KF_PREC_F16 = 1  /* FP16 maps between groups (true units), FP32 arithmetic on chip    */
+    KF_PREC_F16 = 1  /* 16-bit maps between groups: exact uint16 for the integer-valued
+                        maps of stages 1-3, FP16 (true units) for stages 4-7; FP32
+                        arithmetic on chip                                               */
 } kf_precision;
 
-typedef enum kf_dtype { KF_DT_U8 = 0, KF_DT_F32 = 1, KF_DT_F16 = 2 } kf_dtype;
+typedef enum kf_dtype { KF_DT_U8 = 0, KF_DT_F32 = 1, KF_DT_F16 = 2, KF_DT_U16 = 3 } kf_dtype;
 
 /* A kernel of the chain (Table I). Radii are one-sided: the stage reads columns
  * x-rx..x+rx, rows y-ry..y+ry and frames t-rt..t. Byte counts are per pixel over all
@@ -108,8 +110,9 @@ typedef struct kf_corners {
 
 /* A map between groups: `channels` planes (1..3) of T frames x H rows, row y of frame t
  * of plane c at plane[c] + (t*frame_stride + y*pitch) elements. pitch and frame_stride
- * in elements, multiples of 4; planes 16-byte aligned. U8 for the frames and the mask,
- * F32/F16 for the maps of stages 1..7 (see kf_map_scale for their units). */
+ * in elements, multiples of 4 (16 for U8); planes 16-byte aligned. U8 for the frames and
+ * the mask; for the maps of stages 1..7 F32 (KF_PREC_F32), or U16 for stages 1-3 and F16
+ * for stages 4-7 (KF_PREC_F16). kf_map_scale gives their units. */
 typedef struct kf_map {
     void *plane[3];
     int channels;
@@ -168,7 +171,8 @@ kf_status kf_enumerate(const kf_ctx *ctx, uint32_t *buf, int64_t cap, int64_t *n
 /* Factor that turns a stored value of the map written by 0-based stage `stage` into the
  * chain's true units (true = stored * factor). FP32 maps hold integer-scaled values
  * (f*255, g1*4080, g*65280, I*65280, products and sums *65280^2, R*65280^4), which keeps
- * stages 1-4 exact; FP16 maps hold true units (factor 1). */
+ * stages 1-4 exact; in the FP16 form the uint16 maps of stages 1-3 hold the same scaled
+ * integers and the FP16 maps of stages 4-7 hold true units (factor 1). */
 kf_status kf_map_scale(const kf_ctx *ctx, int stage, double *factor);
 
 /* Bytes of device workspace kf_run needs for partition `cuts` on a T x H x W volume:

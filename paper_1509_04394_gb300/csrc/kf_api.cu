@@ -133,11 +133,19 @@ bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
+// dtype of the map written by 1-based stage k (0 = frames)
+int map_dtype(int k, int precision)
+{
+    if (k == 0 || k == 8) return KF_DT_U8;
+    if (precision == KF_PREC_F32) return KF_DT_F32;
+    return k <= 3 ? KF_DT_U16 : KF_DT_F16;
+}
+
 // map validation for kf_run_group: dtype/channels as the chain requires at this point
 kf_status check_map(const kf_map *m, int stage_out, int precision, int64_t W, int64_t H)
 {
     if (!m) return KF_EINVAL;
-    const int want_dt = (stage_out == 0 || stage_out == 8) ? KF_DT_U8 : (precision == KF_PREC_F16 ? KF_DT_F16 : KF_DT_F32);
+    const int want_dt = map_dtype(stage_out, precision);
     const int want_ch = kf::map_channels(stage_out);
     if (m->dtype != want_dt || m->channels != want_ch) return KF_EINVAL;
     const int64_t align_e = want_dt == KF_DT_U8 ? 16 : 4;
@@ -173,8 +181,9 @@ kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &
     p.n_jobs = T * p.n_chunks * p.n_strips;
     p.thr = (float)(NMS_THRESHOLD * kf::map_scale(7));
     const bool f16 = c->precision == KF_PREC_F16;
-    p.in_scale = (f16 && A > 1) ? (float)kf::map_scale(A - 1) : 1.0f;
-    p.out_scale = (f16 && B < 8) ? (float)(1.0 / kf::map_scale(B)) : 1.0f;
+    // FP16 maps (stages 4-7) hold true units; uint16 and FP32 maps hold scaled units
+    p.in_scale = (f16 && A - 1 >= 4) ? (float)kf::map_scale(A - 1) : 1.0f;
+    p.out_scale = (f16 && B >= 4 && B < 8) ? (float)(1.0 / kf::map_scale(B)) : 1.0f;
     const int64_t blocks = (p.n_jobs + kf::WARPS_PER_BLOCK - 1) / kf::WARPS_PER_BLOCK;
     if (blocks > 0x7fffffff) return KF_EINVAL;
     if (B == 8) {
@@ -387,7 +396,7 @@ kf_status kf_enumerate(const kf_ctx *ctx, uint32_t *buf, int64_t cap, int64_t *n
 kf_status kf_map_scale(const kf_ctx *ctx, int stage, double *factor)
 {
     if (!ctx || !factor || stage < 0 || stage >= kf::NSTAGES) return KF_EINVAL;
-    if (stage == kf::NSTAGES - 1 || ctx->precision == KF_PREC_F16) *factor = 1.0;
+    if (stage == kf::NSTAGES - 1 || (ctx->precision == KF_PREC_F16 && stage >= 3)) *factor = 1.0;
     else *factor = 1.0 / kf::map_scale(stage + 1);
     return KF_OK;
 }
@@ -438,8 +447,6 @@ kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *v, const kf_corners
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int dt = ctx->precision == KF_PREC_F16 ? KF_DT_F16 : KF_DT_F32;
-    const size_t elem = ctx->precision == KF_PREC_F16 ? 2 : 4;
 
     kf_map cur{};
     cur.plane[0] = const_cast<uint8_t *>(v->frames);
@@ -461,10 +468,9 @@ kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *v, const kf_corners
             char *base = static_cast<char *>(ws) + (k % 2 ? w.buf_bytes[0] : 0);
             nxt.channels = kf::map_channels(b);
             for (int c = 0; c < nxt.channels; ++c) nxt.plane[c] = base + c * w.plane_bytes;
-            nxt.dtype = dt;
+            nxt.dtype = map_dtype(b, ctx->precision);
             nxt.pitch = w.pitch_e;
             nxt.frame_stride = w.pitch_e * v->H;
-            (void)elem;
             ++k;
         }
         kf_status st = launch_group(ctx, a, b, cur, nxt, v->W, v->H, v->T, o->counts, s);

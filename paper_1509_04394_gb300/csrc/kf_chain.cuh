@@ -21,8 +21,9 @@
 // g' = 65280 g, (Ix', Iy') = 65280 (Ix, Iy), products and box sums 65280^2, R 65280^4.
 // Stages 1-4 are then exact in FP32 (all values are integers below 2^24) whatever the
 // order of operations, and every later stage is one shared device function, so any
-// partition of the chain gives bit-identical results. FP16 maps are stored in true
-// units (value * scale) and rescaled on load; arithmetic stays FP32.
+// partition of the chain gives bit-identical results. In the FP16 form the maps of
+// stages 1-3 are stored as exact uint16 (scaled units) and the maps of stages 4-7 as
+// FP16 in true units (value * scale, rescaled on load); arithmetic stays FP32.
 //
 // Borders. Every stencil clamps its own input map (replicate). The group's input is
 // read with clamped coordinates. Inside the group, a map that feeds a horizontal
@@ -197,14 +198,20 @@ __device__ __forceinline__ void products(const Rows<2> &i, Rows<3> &p)
     }
 }
 
-// Stage 6: 5x5 box sum. Horizontal: ((x-2 + x-1) + (x0 + x1)) + x2. Vertical: the five
-// newest rows, oldest first, from a 5-slot ring. Output row = input row - 2.
+// Stage 6: 5x5 box sum. Horizontal: the four 5-wide windows of a lane's columns share
+// the pair sums A = x-2 + x-1, B = x0 + x1, Cp = x2 + x3, D = x4 + x5 and E = B + Cp
+// (11 adds for 4 outputs). Vertical: the five newest rows, oldest first, from a 5-slot
+// ring. Output row = input row - 2.
 __device__ __forceinline__ void box_h(const float (&x)[C], float (&o)[C])
 {
+    static_assert(C == 4, "pair-sharing box assumes 4 columns per lane");
     const Halo<2> h = halo<2>(x);
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-        o[c] = ((at<2>(x, h, c - 2) + at<2>(x, h, c - 1)) + (x[c] + at<2>(x, h, c + 1))) + at<2>(x, h, c + 2);
+    const float A = h.l[0] + h.l[1], B = x[0] + x[1], Cp = x[2] + x[3], D = h.r[0] + h.r[1];
+    const float E = B + Cp;
+    o[0] = (A + B) + x[2];
+    o[1] = h.l[1] + E;
+    o[2] = E + h.r[0];
+    o[3] = x[1] + (Cp + D);
 }
 struct BoxV {
     float ring[5][3][C];
@@ -297,19 +304,20 @@ __device__ __forceinline__ void nms_h(const float (&r)[C], float (&mh)[C])
 }
 
 // ------------------------------------------------------------------ map I/O
+// Every lane reads ONE aligned vector of C elements per map row, at column xb: its own
+// columns when they lie in the frame, else the aligned vector holding the edge column.
+// Lanes that cross a frame edge then pick, per column, the element of the clamped column.
 template <typename TM> struct MapIO;
 
 template <> struct MapIO<float> {
-    __device__ __forceinline__ static void load(const void *plane, int64_t off, bool vec, const int (&xc)[C], int64_t rowoff, float scale, float (&v)[C])
+    using Raw = float4;
+    __device__ __forceinline__ static Raw load(const void *plane, int64_t off)
     {
-        const float *p = static_cast<const float *>(plane);
-        if (vec) {
-            const float4 q = __ldg(reinterpret_cast<const float4 *>(p + off));
-            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-        } else {
-#pragma unroll
-            for (int c = 0; c < C; ++c) v[c] = __ldg(p + rowoff + xc[c]);
-        }
+        return __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(plane) + off));
+    }
+    __device__ __forceinline__ static void unpack(const Raw &q, float scale, float (&v)[C])
+    {
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
     __device__ __forceinline__ static void store(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float scale)
     {
@@ -324,18 +332,16 @@ template <> struct MapIO<float> {
 };
 
 template <> struct MapIO<__half> {
-    __device__ __forceinline__ static void load(const void *plane, int64_t off, bool vec, const int (&xc)[C], int64_t rowoff, float scale, float (&v)[C])
+    using Raw = uint2;
+    __device__ __forceinline__ static Raw load(const void *plane, int64_t off)
     {
-        const __half *p = static_cast<const __half *>(plane);
-        if (vec) {
-            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p + off));
-            const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
-            const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
-            v[0] = a.x * scale; v[1] = a.y * scale; v[2] = b.x * scale; v[3] = b.y * scale;
-        } else {
-#pragma unroll
-            for (int c = 0; c < C; ++c) v[c] = __half2float(p[rowoff + xc[c]]) * scale;
-        }
+        return __ldg(reinterpret_cast<const uint2 *>(static_cast<const __half *>(plane) + off));
+    }
+    __device__ __forceinline__ static void unpack(const Raw &q, float scale, float (&v)[C])
+    {
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+        v[0] = a.x * scale; v[1] = a.y * scale; v[2] = b.x * scale; v[3] = b.y * scale;
     }
     __device__ __forceinline__ static void store(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float scale)
     {
@@ -354,9 +360,40 @@ template <> struct MapIO<__half> {
     }
 };
 
+// Exact 16-bit integer maps (the integer-valued maps of stages 1-3 in the FP16 form).
+template <> struct MapIO<uint16_t> {
+    using Raw = uint2;
+    __device__ __forceinline__ static Raw load(const void *plane, int64_t off)
+    {
+        return __ldg(reinterpret_cast<const uint2 *>(static_cast<const uint16_t *>(plane) + off));
+    }
+    __device__ __forceinline__ static void unpack(const Raw &q, float scale, float (&v)[C])
+    {
+        v[0] = (float)(q.x & 0xffffu); v[1] = (float)(q.x >> 16); v[2] = (float)(q.y & 0xffffu); v[3] = (float)(q.y >> 16);
+    }
+    __device__ __forceinline__ static void store(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float scale)
+    {
+        uint16_t *p = static_cast<uint16_t *>(plane) + off;
+        if (in_mask == (1u << C) - 1) {
+            uint2 q;
+            q.x = __float2uint_rn(v[0]) | __float2uint_rn(v[1]) << 16;
+            q.y = __float2uint_rn(v[2]) | __float2uint_rn(v[3]) << 16;
+            *reinterpret_cast<uint2 *>(p) = q;
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) if (in_mask >> c & 1) p[c] = (uint16_t)__float2uint_rn(v[c]);
+        }
+    }
+};
+
+// Storage type of the map written by stage k: FP32 maps in the FP32 form; in the FP16
+// form exact uint16 for the integer-valued maps of stages 1-3 and FP16 from stage 4 on.
+template <int K, bool F16>
+using MapT = std::conditional_t<!F16, float, std::conditional_t<(K <= 3), uint16_t, __half>>;
+
 // ------------------------------------------------------------------ the group kernel
-template <int A, int B, typename TM>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) group_kernel(const GroupParams p)
+template <int A, int B, bool F16>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, MIN_BLOCKS) group_kernel(const GroupParams p)
 {
     static_assert(1 <= A && A <= B && B <= 8, "stage range");
     static_assert(C == 4, "map I/O assumes 4 columns per lane");
@@ -381,9 +418,15 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) group_kernel(const Group
     const int x0 = xs + C * lane;
     const int xo0 = max(xs + RXT, 0), xo1 = min(xs + RXT + p.step, W);
     const bool edgeL = xs < 0, edgeR = xs + STRIP > W;
-    int xc[C];  // clamped input columns
+    // the one aligned input vector of this lane per row, and the element each column takes
+    const int xb = x0 < 0 ? 0 : (x0 >= W ? ((W - 1) & ~(C - 1)) : x0);
+    int kc[C];
+    unsigned bsel = 0;  // byte selector of the clamped columns (u8 input)
 #pragma unroll
-    for (int c = 0; c < C; ++c) xc[c] = min(max(x0 + c, 0), W - 1);
+    for (int c = 0; c < C; ++c) {
+        kc[c] = min(max(x0 + c, 0), W - 1) - xb;
+        bsel |= (unsigned)kc[c] << (4 * c);
+    }
     const bool lane_inside = (x0 >= 0) && (x0 + C <= W);
     unsigned out_mask = 0;  // which of this lane's columns belong to the strip's output
 #pragma unroll
@@ -400,29 +443,54 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) group_kernel(const Group
     unsigned count = 0;
 
     const int64_t in_frame = frame * p.in_fstride, out_frame = frame * p.out_fstride;
+    auto in_off = [&](int row) { return in_frame + (int64_t)min(max(row, 0), H - 1) * p.in_pitch + xb; };
+
+    // Input rows are prefetched PD = 5 rows ahead into registers (slot = loop phase):
+    // u8 frames and single-channel maps. Wider maps are loaded when used.
+    using InIO = MapIO<MapT<A - 1, F16>>;
+    constexpr bool PREFETCH = (A == 1) || (NIN == 1);
+    using RawIn = std::conditional_t<A == 1, uint32_t, typename InIO::Raw>;
+    [[maybe_unused]] RawIn q[PREFETCH ? 5 : 1];
+    auto load_raw = [&](int row, int m) -> RawIn {
+        if constexpr (A == 1) return __ldg(reinterpret_cast<const uint32_t *>(static_cast<const uint8_t *>(p.in[0]) + in_off(row)));
+        else return InIO::load(p.in[m], in_off(row));
+    };
+    if constexpr (PREFETCH) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) q[k] = load_raw(t_begin + k, 0);
+    }
 
     auto step = [&](auto phase_tag, int t) {
         [[maybe_unused]] constexpr int PH = decltype(phase_tag)::value;
         const bool border = (t <= RYT) || (t >= H);
         // ---- group input row t (clamped)
-        const int64_t rowoff = in_frame + (int64_t)min(max(t, 0), H - 1) * p.in_pitch;
         [[maybe_unused]] Rows<1> f;
         [[maybe_unused]] Rows<NIN> in;
         if constexpr (A == 1) {
-            const uint8_t *fr = static_cast<const uint8_t *>(p.in[0]);
-            uint32_t w;
-            if (lane_inside) {
-                w = __ldg(reinterpret_cast<const uint32_t *>(fr + rowoff + x0));
-            } else {
-                w = 0;
-#pragma unroll
-                for (int c = 0; c < C; ++c) w |= (uint32_t)__ldg(fr + rowoff + xc[c]) << (8 * c);
-            }
+            const uint32_t w = __byte_perm(q[PH], 0u, bsel);
+            q[PH] = load_raw(t + 5, 0);
 #pragma unroll
             for (int c = 0; c < C; ++c) f.v[0][c] = u8_to_float(w, c);
         } else {
 #pragma unroll
-            for (int m = 0; m < NIN; ++m) MapIO<TM>::load(p.in[m], rowoff + x0, lane_inside, xc, rowoff, p.in_scale, in.v[m]);
+            for (int m = 0; m < NIN; ++m) {
+                RawIn raw;
+                if constexpr (PREFETCH) {
+                    raw = q[PH];
+                    q[PH] = load_raw(t + 5, 0);
+                } else {
+                    raw = load_raw(t, m);
+                }
+                float v[C];
+                InIO::unpack(raw, p.in_scale, v);
+                if (lane_inside) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) in.v[m][c] = v[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) in.v[m][c] = pick(v, kc[c]);
+                }
+            }
         }
         // ---- stage 2 (horizontal Gaussian)
         [[maybe_unused]] Rows<1> g1;
@@ -530,7 +598,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) group_kernel(const Group
                 else if constexpr (B == 6) res = &sm;
                 else res = &r;
 #pragma unroll
-                for (int m = 0; m < NOUT; ++m) MapIO<TM>::store(p.out[m], ooff, res->v[m], out_mask, p.out_scale);
+                for (int m = 0; m < NOUT; ++m) MapIO<MapT<B, F16>>::store(p.out[m], ooff, res->v[m], out_mask, p.out_scale);
             }
         }
     };

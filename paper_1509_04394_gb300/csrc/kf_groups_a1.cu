@@ -6,10 +6,10 @@
 
 namespace kf {
 namespace {
-template <int A, int B, typename TM>
+template <int A, int B, bool F16>
 int launch(const GroupParams &p, unsigned grid, void *stream)
 {
-    group_kernel<A, B, TM><<<grid, 32 * WARPS_PER_BLOCK, 0, static_cast<cudaStream_t>(stream)>>>(p);
+    group_kernel<A, B, F16><<<grid, 32 * WARPS_PER_BLOCK, 0, static_cast<cudaStream_t>(stream)>>>(p);
     return (int)cudaGetLastError();
 }
 }  // namespace
@@ -17,14 +17,14 @@ int launch(const GroupParams &p, unsigned grid, void *stream)
 LaunchFn launcher_a1(int B, int f16)
 {
     switch (B) {
-    case 1: return f16 ? launch<1, 1, __half> : launch<1, 1, float>;
-    case 2: return f16 ? launch<1, 2, __half> : launch<1, 2, float>;
-    case 3: return f16 ? launch<1, 3, __half> : launch<1, 3, float>;
-    case 4: return f16 ? launch<1, 4, __half> : launch<1, 4, float>;
-    case 5: return f16 ? launch<1, 5, __half> : launch<1, 5, float>;
-    case 6: return f16 ? launch<1, 6, __half> : launch<1, 6, float>;
-    case 7: return f16 ? launch<1, 7, __half> : launch<1, 7, float>;
-    case 8: return f16 ? launch<1, 8, __half> : launch<1, 8, float>;
+    case 1: return f16 ? launch<1, 1, true> : launch<1, 1, false>;
+    case 2: return f16 ? launch<1, 2, true> : launch<1, 2, false>;
+    case 3: return f16 ? launch<1, 3, true> : launch<1, 3, false>;
+    case 4: return f16 ? launch<1, 4, true> : launch<1, 4, false>;
+    case 5: return f16 ? launch<1, 5, true> : launch<1, 5, false>;
+    case 6: return f16 ? launch<1, 6, true> : launch<1, 6, false>;
+    case 7: return f16 ? launch<1, 7, true> : launch<1, 7, false>;
+    case 8: return f16 ? launch<1, 8, true> : launch<1, 8, false>;
     default: return nullptr;
     }
 }

@@ -6,10 +6,10 @@
 
 namespace kf {
 namespace {
-template <int A, int B, typename TM>
+template <int A, int B, bool F16>
 int launch(const GroupParams &p, unsigned grid, void *stream)
 {
-    group_kernel<A, B, TM><<<grid, 32 * WARPS_PER_BLOCK, 0, static_cast<cudaStream_t>(stream)>>>(p);
+    group_kernel<A, B, F16><<<grid, 32 * WARPS_PER_BLOCK, 0, static_cast<cudaStream_t>(stream)>>>(p);
     return (int)cudaGetLastError();
 }
 }  // namespace
@@ -17,12 +17,12 @@ int launch(const GroupParams &p, unsigned grid, void *stream)
 LaunchFn launcher_a3(int B, int f16)
 {
     switch (B) {
-    case 3: return f16 ? launch<3, 3, __half> : launch<3, 3, float>;
-    case 4: return f16 ? launch<3, 4, __half> : launch<3, 4, float>;
-    case 5: return f16 ? launch<3, 5, __half> : launch<3, 5, float>;
-    case 6: return f16 ? launch<3, 6, __half> : launch<3, 6, float>;
-    case 7: return f16 ? launch<3, 7, __half> : launch<3, 7, float>;
-    case 8: return f16 ? launch<3, 8, __half> : launch<3, 8, float>;
+    case 3: return f16 ? launch<3, 3, true> : launch<3, 3, false>;
+    case 4: return f16 ? launch<3, 4, true> : launch<3, 4, false>;
+    case 5: return f16 ? launch<3, 5, true> : launch<3, 5, false>;
+    case 6: return f16 ? launch<3, 6, true> : launch<3, 6, false>;
+    case 7: return f16 ? launch<3, 7, true> : launch<3, 7, false>;
+    case 8: return f16 ? launch<3, 8, true> : launch<3, 8, false>;
     default: return nullptr;
     }
 }

@@ -6,10 +6,10 @@
 
 namespace kf {
 namespace {
-template <int A, int B, typename TM>
+template <int A, int B, bool F16>
 int launch(const GroupParams &p, unsigned grid, void *stream)
 {
-    group_kernel<A, B, TM><<<grid, 32 * WARPS_PER_BLOCK, 0, static_cast<cudaStream_t>(stream)>>>(p);
+    group_kernel<A, B, F16><<<grid, 32 * WARPS_PER_BLOCK, 0, static_cast<cudaStream_t>(stream)>>>(p);
     return (int)cudaGetLastError();
 }
 }  // namespace
@@ -17,10 +17,10 @@ int launch(const GroupParams &p, unsigned grid, void *stream)
 LaunchFn launcher_a5(int B, int f16)
 {
     switch (B) {
-    case 5: return f16 ? launch<5, 5, __half> : launch<5, 5, float>;
-    case 6: return f16 ? launch<5, 6, __half> : launch<5, 6, float>;
-    case 7: return f16 ? launch<5, 7, __half> : launch<5, 7, float>;
-    case 8: return f16 ? launch<5, 8, __half> : launch<5, 8, float>;
+    case 5: return f16 ? launch<5, 5, true> : launch<5, 5, false>;
+    case 6: return f16 ? launch<5, 6, true> : launch<5, 6, false>;
+    case 7: return f16 ? launch<5, 7, true> : launch<5, 7, false>;
+    case 8: return f16 ? launch<5, 8, true> : launch<5, 8, false>;
     default: return nullptr;
     }
 }

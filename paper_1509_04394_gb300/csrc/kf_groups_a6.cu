@@ -6,10 +6,10 @@
 
 namespace kf {
 namespace {
-template <int A, int B, typename TM>
+template <int A, int B, bool F16>
 int launch(const GroupParams &p, unsigned grid, void *stream)
 {
-    group_kernel<A, B, TM><<<grid, 32 * WARPS_PER_BLOCK, 0, static_cast<cudaStream_t>(stream)>>>(p);
+    group_kernel<A, B, F16><<<grid, 32 * WARPS_PER_BLOCK, 0, static_cast<cudaStream_t>(stream)>>>(p);
     return (int)cudaGetLastError();
 }
 }  // namespace
@@ -17,9 +17,9 @@ int launch(const GroupParams &p, unsigned grid, void *stream)
 LaunchFn launcher_a6(int B, int f16)
 {
     switch (B) {
-    case 6: return f16 ? launch<6, 6, __half> : launch<6, 6, float>;
-    case 7: return f16 ? launch<6, 7, __half> : launch<6, 7, float>;
-    case 8: return f16 ? launch<6, 8, __half> : launch<6, 8, float>;
+    case 6: return f16 ? launch<6, 6, true> : launch<6, 6, false>;
+    case 7: return f16 ? launch<6, 7, true> : launch<6, 7, false>;
+    case 8: return f16 ? launch<6, 8, true> : launch<6, 8, false>;
     default: return nullptr;
     }
 }

@@ -17,7 +17,8 @@ namespace kf {
 
 constexpr int C = KF_C;        // columns per lane
 constexpr int STRIP = 32 * C;  // columns per warp strip
-constexpr int WARPS_PER_BLOCK = 4;
+constexpr int WARPS_PER_BLOCK = 1;  // warps never cooperate: one warp per block
+constexpr int MIN_BLOCKS = 12;      // resident blocks per SM the register budget targets
 constexpr int NSTAGES = 8;
 
 // Stage table of the Harris chain, 1-based (stage 0 = the u8 frames). One-sided radii

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libkfuse.so")
 
 KF_OK, KF_EINVAL, KF_ENOMEM, KF_ECUDA, KF_ESMEM, KF_EUNSUPPORTED, KF_ESTATE, KF_ETIMEOUT = range(8)
 KF_PREC_F32, KF_PREC_F16 = 0, 1
-KF_DT_U8, KF_DT_F32, KF_DT_F16 = 0, 1, 2
+KF_DT_U8, KF_DT_F32, KF_DT_F16, KF_DT_U16 = 0, 1, 2, 3
 NSTAGES = 8
 STAGE_NAMES = ("convert", "gauss_h", "gauss_v", "sobel", "products", "box5", "harris", "nms")
 MAP_CHANNELS = (1, 1, 1, 1, 2, 3, 3, 1, 1)  # index = 1-based stage writing the map (0 = frames)

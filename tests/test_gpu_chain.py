@@ -45,20 +45,32 @@ def random_frames(T, H, W, seed):
     return fr
 
 
+def map_dtypes(prec, s):
+    """(kf dtype, torch dtype) of the map written by 0-based stage s."""
+    if prec == K.KF_PREC_F32:
+        return K.KF_DT_F32, torch.float32
+    return (K.KF_DT_U16, torch.uint16) if s <= 2 else (K.KF_DT_F16, torch.float16)
+
+
+def as_f64(t):
+    if t.dtype == torch.uint16:  # barebones dtype: reinterpret and widen
+        return (t.view(torch.int16).to(torch.int32) & 0xFFFF).double().cpu().numpy()
+    return t.double().cpu().numpy()
+
+
 def run_unfused_maps(ctx_h, prec, fr_dev, W):
     """Each stage as its own kernel; returns the list of output map planes per stage."""
     T, H, _ = fr_dev.shape
-    dt = K.KF_DT_F16 if prec == K.KF_PREC_F16 else K.KF_DT_F32
-    tdt = torch.float16 if prec == K.KF_PREC_F16 else torch.float32
     cur, cur_dt, outs = [fr_dev], K.KF_DT_U8, []
     for s in range(7):
+        dt, tdt = map_dtypes(prec, s)
         out = [torch.empty((T, H, pitch4(W)), dtype=tdt, device=fr_dev.device) for _ in range(K.MAP_CHANNELS[s + 1])]
         K.kf_run_group(ctx_h, s, s, cur, cur_dt, out, dt, W)
         outs.append(out)
         cur, cur_dt = out, dt
     mask = torch.zeros((T, H, pitch16(W)), dtype=torch.uint8, device=fr_dev.device)
     counts = torch.full((T,), -7, dtype=torch.int32, device=fr_dev.device)
-    K.kf_run_group(ctx_h, 7, 7, cur, dt, [mask], K.KF_DT_U8, W, counts)
+    K.kf_run_group(ctx_h, 7, 7, cur, cur_dt, [mask], K.KF_DT_U8, W, counts)
     return outs, mask, counts
 
 
@@ -75,7 +87,7 @@ def test_every_stage_map_matches_the_oracle_fp32(dev, shape):
         for s in range(7):
             scale = K.kf_map_scale(ctx.h, s)
             for c, key in enumerate(MAP_KEYS[s]):
-                got = outs[s][c][t, :, :W].double().cpu().numpy() * scale
+                got = as_f64(outs[s][c][t, :, :W]) * scale
                 err = normwise(got, maps[key])
                 bound = 1e-12 if s <= 3 else TOL_F32  # stages 1-4 are exact integers in FP32
                 assert err <= bound, (s, key, t, err)
@@ -159,18 +171,25 @@ def test_chunking_does_not_change_the_result(dev, rows):
 
 
 def test_fp16_maps_stay_within_2e_3(dev):
+    """16-bit maps between every pair of stages: uint16 maps of stages 1-3 are exact,
+    FP16 maps of stages 4-7 stay within 2e-3 normwise of the FP64 oracle."""
     T, H, W = 3, 192, 432
     fr = frames_of(sv.VideoSpec(T=T, H=H, W=W, seed=14))
     ctx = K.Context(0, precision=K.KF_PREC_F16)
     fd = torch.from_numpy(fr).to(dev)
     outs, mask, counts = run_unfused_maps(ctx.h, K.KF_PREC_F16, fd, W)
+    worst = {}
     for t in range(T):
         maps, m_ref, c_ref = oc.chain_frame(fr[t][:, :W].copy())
         for s in range(7):
+            scale = K.kf_map_scale(ctx.h, s)
             for c, key in enumerate(MAP_KEYS[s]):
-                got = outs[s][c][t, :, :W].double().cpu().numpy()
-                assert normwise(got, maps[key]) <= TOL_F16, (s, key)
+                got = as_f64(outs[s][c][t, :, :W]) * scale
+                err = normwise(got, maps[key])
+                worst[key] = max(worst.get(key, 0.0), err)
+                assert err <= (1e-12 if s <= 2 else TOL_F16), (s, key, err)
         check_mask(mask[t, :, :W].cpu().numpy(), int(counts[t]), m_ref, c_ref, maps["r"], TOL_F16)
+    print("fp16 unfused normwise errors:", {k: f"{v:.2e}" for k, v in worst.items()})
     # every partition in FP16 stays within tolerance of the oracle
     for cuts in (0, 127, 0b1000000, 0b0010100):
         ws_b = K.kf_workspace_bytes(ctx.h, cuts, W, H, T)

@@ -169,4 +169,5 @@ def test_map_scales(hctx):
     assert K.kf_map_scale(hctx, 2) == pytest.approx(1 / 65280)
     assert K.kf_map_scale(hctx, 6) == pytest.approx(65280.0 ** -4)
     K.kf_set_precision(hctx, K.KF_PREC_F16)
-    assert all(K.kf_map_scale(hctx, s) == 1.0 for s in range(8))
+    assert K.kf_map_scale(hctx, 2) == pytest.approx(1 / 65280)  # exact uint16 map
+    assert all(K.kf_map_scale(hctx, s) == 1.0 for s in range(3, 8))  # FP16, true units
