@@ -83,7 +83,7 @@ typedef struct kf_stage_desc {
 
 /* Volume size and the output box x*y*t of one thread block (Sec. V, Fig. 3) that the
  * traffic model assumes. box_* = 0 selects the executor's own tile: x = the output
- * width of a warp strip of the fully fused chain (116 columns), y = the chunk height
+ * width of a warp strip of the fully fused chain (112 columns), y = the chunk height
  * (kf_set_chunk_rows), t = 1. */
 typedef struct kf_geometry {
     int64_t W, H, T;
@@ -110,7 +110,7 @@ typedef struct kf_corners {
 
 /* A map between groups: `channels` planes (1..3) of T frames x H rows, row y of frame t
  * of plane c at plane[c] + (t*frame_stride + y*pitch) elements. pitch and frame_stride
- * in elements, multiples of 4 (16 for U8); planes 16-byte aligned. U8 for the frames and
+ * in elements, each a multiple of 16 bytes; planes 16-byte aligned. U8 for the frames and
  * the mask; for the maps of stages 1..7 F32 (KF_PREC_F32), or U16 for stages 1-3 and F16
  * for stages 4-7 (KF_PREC_F16). kf_map_scale gives their units. */
 typedef struct kf_map {
@@ -128,10 +128,18 @@ const char *kf_status_str(kf_status s);
 int kf_last_cuda_error(const kf_ctx *ctx);
 kf_status kf_version(int *major, int *minor);
 
-/* Create a context on CUDA device `device` (selects it with cudaSetDevice), or a
- * host-only planning context when device < 0 (no CUDA call is ever made by it). */
+/* Create a context on CUDA device `device` (selects it with cudaSetDevice and allocates
+ * the context's 4-byte device error word), or a host-only planning context when
+ * device < 0 (no CUDA call is ever made by it). */
 kf_status kf_create(int device, kf_ctx **out);
 kf_status kf_destroy(kf_ctx *ctx);
+
+/* Synchronise the device, then return and clear the context's device error word: 0 if
+ * every bounded device-side wait of the kernels launched since the last call completed,
+ * KF_DEVERR_TIMEOUT if a wait for staged input rows expired (that job's output rows
+ * are then incomplete). */
+#define KF_DEVERR_TIMEOUT 1
+kf_status kf_device_error(kf_ctx *ctx, int *code);
 
 /* KF_PREC_F32 (default) or KF_PREC_F16. Changes the builtin byte counts and the dtype
  * of the maps kf_run keeps in the workspace. */

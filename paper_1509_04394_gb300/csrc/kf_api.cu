@@ -7,7 +7,9 @@
 // shortest path over the n+1 cut points; the cost of a group is the traffic of Sec. VI-D
 // (global<->on-chip bytes of one fused kernel) and a group is feasible when its on-chip
 // footprint fits the limit (restriction c of Sec. VII).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdint>
@@ -23,6 +25,7 @@ struct kf_ctx {
     int precision = KF_PREC_F32;
     int chunk_rows = 200;
     int last_cuda = 0;
+    int *d_err = nullptr;  // device error word of the bounded waits (4 bytes, owned)
     std::vector<kf_stage_desc> stages;
 };
 
@@ -131,7 +134,50 @@ kf::LaunchFn launcher(int A, int B, int f16)
 
 bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+CUtensorMapDataType tmap_dtype(int dt)
+{
+    switch (dt) {
+    case KF_DT_U8: return CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    case KF_DT_U16: return CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    case KF_DT_F16: return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    default: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    }
+}
+
+int dtype_bytes(int dt) { return dt == KF_DT_U8 ? 1 : (dt == KF_DT_F32 ? 4 : 2); }
+
+// 3-D descriptor {W, H, T} of one plane; box {STRIP, RB, 1}; out-of-frame reads give 0.
+bool encode_plane(CUtensorMap *m, const void *plane, int dt, int64_t pitch, int64_t fstride, int64_t W, int64_t H, int64_t T)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const int e = dtype_bytes(dt);
+    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
+    cuuint64_t strides[2] = {(cuuint64_t)(pitch * e), (cuuint64_t)(fstride * e)};
+    cuuint32_t box[3] = {(cuuint32_t)kf::STRIP, (cuuint32_t)kf::RB, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, tmap_dtype(dt), 3, const_cast<void *>(plane), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+int dtype_bytes(int dt);
 
 // dtype of the map written by 1-based stage k (0 = frames)
 int map_dtype(int k, int precision)
@@ -148,7 +194,7 @@ kf_status check_map(const kf_map *m, int stage_out, int precision, int64_t W, in
     const int want_dt = map_dtype(stage_out, precision);
     const int want_ch = kf::map_channels(stage_out);
     if (m->dtype != want_dt || m->channels != want_ch) return KF_EINVAL;
-    const int64_t align_e = want_dt == KF_DT_U8 ? 16 : 4;
+    const int64_t align_e = 16 / dtype_bytes(want_dt);  // rows and frames start on 16 bytes
     if (m->pitch < W || m->pitch % align_e || m->frame_stride < H * m->pitch || m->frame_stride % align_e) return KF_EINVAL;
     for (int i = 0; i < want_ch; ++i)
         if (!m->plane[i] || !aligned(m->plane[i], 16)) return KF_EINVAL;
@@ -165,6 +211,9 @@ kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &
         p.in[i] = in.plane[i];
         p.out[i] = out.plane[i];
     }
+    for (int i = 0; i < in.channels; ++i)
+        if (!encode_plane(&p.tmap[i], in.plane[i], in.dtype, in.pitch, in.frame_stride, W, H, T)) return KF_EINVAL;
+    p.err = c->d_err;
     p.in_pitch = in.pitch;
     p.in_fstride = in.frame_stride;
     p.out_pitch = out.pitch;
@@ -184,7 +233,7 @@ kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &
     // FP16 maps (stages 4-7) hold true units; uint16 and FP32 maps hold scaled units
     p.in_scale = (f16 && A - 1 >= 4) ? (float)kf::map_scale(A - 1) : 1.0f;
     p.out_scale = (f16 && B >= 4 && B < 8) ? (float)(1.0 / kf::map_scale(B)) : 1.0f;
-    const int64_t blocks = (p.n_jobs + kf::WARPS_PER_BLOCK - 1) / kf::WARPS_PER_BLOCK;
+    const int64_t blocks = p.n_jobs;  // one warp (one job) per block
     if (blocks > 0x7fffffff) return KF_EINVAL;
     if (B == 8) {
         cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)T, s);
@@ -259,7 +308,10 @@ kf_status kf_create(int device, kf_ctx **out)
     c->device = device < 0 ? -1 : device;
     if (device >= 0) {
         cudaError_t e = cudaSetDevice(device);
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
         if (e != cudaSuccess) {
+            if (c->d_err) cudaFree(c->d_err);
             delete c;
             return KF_ECUDA;
         }
@@ -270,7 +322,23 @@ kf_status kf_create(int device, kf_ctx **out)
 
 kf_status kf_destroy(kf_ctx *ctx)
 {
+    if (ctx && ctx->d_err) {
+        cudaSetDevice(ctx->device);
+        cudaFree(ctx->d_err);
+    }
     delete ctx;
+    return KF_OK;
+}
+
+kf_status kf_device_error(kf_ctx *ctx, int *code)
+{
+    if (!ctx || !code) return KF_EINVAL;
+    if (ctx->device < 0) return KF_ESTATE;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(code, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
     return KF_OK;
 }
 

@@ -201,7 +201,9 @@ __device__ __forceinline__ void products(const Rows<2> &i, Rows<3> &p)
 // Stage 6: 5x5 box sum. Horizontal: the four 5-wide windows of a lane's columns share
 // the pair sums A = x-2 + x-1, B = x0 + x1, Cp = x2 + x3, D = x4 + x5 and E = B + Cp
 // (11 adds for 4 outputs). Vertical: the five newest rows, oldest first, from a 5-slot
-// ring. Output row = input row - 2.
+// register ring addressed by the compile-time loop phase (the row loop is unrolled by 5,
+// so no register is ever moved); the order is by age, the same in every partition.
+// Output row = input row - 2.
 __device__ __forceinline__ void box_h(const float (&x)[C], float (&o)[C])
 {
     static_assert(C == 4, "pair-sharing box assumes 4 columns per lane");
@@ -303,23 +305,117 @@ __device__ __forceinline__ void nms_h(const float (&r)[C], float (&mh)[C])
     for (int c = 0; c < C; ++c) mh[c] = fmaxf(fmaxf(at<1>(r, h, c - 1), r[c]), at<1>(r, h, c + 1));
 }
 
-// ------------------------------------------------------------------ map I/O
-// Every lane reads ONE aligned vector of C elements per map row, at column xb: its own
-// columns when they lie in the frame, else the aligned vector holding the edge column.
-// Lanes that cross a frame edge then pick, per column, the element of the clamped column.
-template <typename TM> struct MapIO;
+// ------------------------------------------------------------------ TMA staging
+// The group's input rows reach shared memory by TMA tensor copies: one copy per channel
+// brings RB rows x STRIP columns of one frame; NST such stages form a ring, each with an
+// mbarrier. Columns outside the frame and rows past its end arrive as zeros (handled by
+// the clamped reads below and by the vertical stages' replay). Every wait is bounded:
+// on expiry the kernel records KF_DEVERR_TIMEOUT in the device error word, waits once
+// more (bounded) for its copies in flight, and leaves.
 
-template <> struct MapIO<float> {
-    using Raw = float4;
-    __device__ __forceinline__ static Raw load(const void *plane, int64_t off)
+constexpr unsigned WAIT_LIMIT = 1u << 22;  // try_wait rounds before giving up
+constexpr int DEVERR_TIMEOUT = 1;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; returns false if the limit expired
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    for (unsigned i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Reading one staged row: each lane reads its C elements (or, when its columns cross a
+// frame edge, the elements of the clamped columns) and converts them to float.
+template <typename TM> struct Staged;
+template <> struct Staged<uint8_t> {
+    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float, float (&v)[C])
     {
-        return __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(plane) + off));
+        uint32_t w;
+        if (inside) {
+            w = *reinterpret_cast<const uint32_t *>(row + C * lane);
+        } else {
+            w = 0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) w |= (uint32_t)row[off[c]] << (8 * c);
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[c] = u8_to_float(w, c);
     }
-    __device__ __forceinline__ static void unpack(const Raw &q, float scale, float (&v)[C])
+};
+template <> struct Staged<float> {
+    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float, float (&v)[C])
     {
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        const float *r = reinterpret_cast<const float *>(row);
+        if (inside) {
+            const float4 q = reinterpret_cast<const float4 *>(r)[lane];
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) v[c] = r[off[c]];
+        }
     }
-    __device__ __forceinline__ static void store(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float scale)
+};
+template <> struct Staged<__half> {
+    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float scale, float (&v)[C])
+    {
+        const __half *r = reinterpret_cast<const __half *>(row);
+        if (inside) {
+            const uint2 q = reinterpret_cast<const uint2 *>(r)[lane];
+            const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+            v[0] = a.x * scale; v[1] = a.y * scale; v[2] = b.x * scale; v[3] = b.y * scale;
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) v[c] = __half2float(r[off[c]]) * scale;
+        }
+    }
+};
+template <> struct Staged<uint16_t> {
+    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float, float (&v)[C])
+    {
+        const uint16_t *r = reinterpret_cast<const uint16_t *>(row);
+        if (inside) {
+            const uint2 q = reinterpret_cast<const uint2 *>(r)[lane];
+            v[0] = (float)(q.x & 0xffffu); v[1] = (float)(q.x >> 16); v[2] = (float)(q.y & 0xffffu); v[3] = (float)(q.y >> 16);
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) v[c] = (float)r[off[c]];
+        }
+    }
+};
+
+// ------------------------------------------------------------------ map stores
+template <typename TM> struct Store;
+template <> struct Store<float> {
+    __device__ __forceinline__ static void row(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float)
     {
         float *p = static_cast<float *>(plane) + off;
         if (in_mask == (1u << C) - 1) {
@@ -330,20 +426,8 @@ template <> struct MapIO<float> {
         }
     }
 };
-
-template <> struct MapIO<__half> {
-    using Raw = uint2;
-    __device__ __forceinline__ static Raw load(const void *plane, int64_t off)
-    {
-        return __ldg(reinterpret_cast<const uint2 *>(static_cast<const __half *>(plane) + off));
-    }
-    __device__ __forceinline__ static void unpack(const Raw &q, float scale, float (&v)[C])
-    {
-        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
-        v[0] = a.x * scale; v[1] = a.y * scale; v[2] = b.x * scale; v[3] = b.y * scale;
-    }
-    __device__ __forceinline__ static void store(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float scale)
+template <> struct Store<__half> {
+    __device__ __forceinline__ static void row(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float scale)
     {
         __half *p = static_cast<__half *>(plane) + off;
         if (in_mask == (1u << C) - 1) {
@@ -359,19 +443,8 @@ template <> struct MapIO<__half> {
         }
     }
 };
-
-// Exact 16-bit integer maps (the integer-valued maps of stages 1-3 in the FP16 form).
-template <> struct MapIO<uint16_t> {
-    using Raw = uint2;
-    __device__ __forceinline__ static Raw load(const void *plane, int64_t off)
-    {
-        return __ldg(reinterpret_cast<const uint2 *>(static_cast<const uint16_t *>(plane) + off));
-    }
-    __device__ __forceinline__ static void unpack(const Raw &q, float scale, float (&v)[C])
-    {
-        v[0] = (float)(q.x & 0xffffu); v[1] = (float)(q.x >> 16); v[2] = (float)(q.y & 0xffffu); v[3] = (float)(q.y >> 16);
-    }
-    __device__ __forceinline__ static void store(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float scale)
+template <> struct Store<uint16_t> {
+    __device__ __forceinline__ static void row(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float)
     {
         uint16_t *p = static_cast<uint16_t *>(plane) + off;
         if (in_mask == (1u << C) - 1) {
@@ -386,54 +459,92 @@ template <> struct MapIO<uint16_t> {
     }
 };
 
-// Storage type of the map written by stage k: FP32 maps in the FP32 form; in the FP16
-// form exact uint16 for the integer-valued maps of stages 1-3 and FP16 from stage 4 on.
+// Storage type of the map written by stage k (k = 0: the u8 frames): FP32 maps in the
+// FP32 form; in the FP16 form exact uint16 for the integer-valued maps of stages 1-3 and
+// FP16 from stage 4 on.
 template <int K, bool F16>
-using MapT = std::conditional_t<!F16, float, std::conditional_t<(K <= 3), uint16_t, __half>>;
+using MapT = std::conditional_t<K == 0, uint8_t, std::conditional_t<!F16, float, std::conditional_t<(K <= 3), uint16_t, __half>>>;
+
+// Shared-memory plan of a group: mbarriers and NST input stages of RB rows.
+template <int A, int B, bool F16> struct SmemPlan {
+    static constexpr int NIN = map_channels(A - 1);
+    static constexpr int ELEM = (int)sizeof(MapT<A - 1, F16>);
+    static constexpr int ROW_BYTES = STRIP * ELEM;               // one staged row of one channel
+    static constexpr int CH_BYTES = RB * ROW_BYTES;              // one stage of one channel
+    static constexpr int STAGE_BYTES = NIN * CH_BYTES;
+    static constexpr int NST = STAGE_BYTES <= 2048 ? 4 : (STAGE_BYTES <= 4096 ? 3 : 2);
+    static_assert(RB == 5, "one stage per 5-row block (the box ring period)");
+    static constexpr bool HAS6 = A <= 6 && 6 <= B;
+    static constexpr int BAR_OFF = 0;
+    static constexpr int IN_OFF = 128;
+    static constexpr int BOX_OFF = IN_OFF + NST * STAGE_BYTES;  // end of the plan
+    static constexpr int BYTES = BOX_OFF;
+};
 
 // ------------------------------------------------------------------ the group kernel
 template <int A, int B, bool F16>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, MIN_BLOCKS) group_kernel(const GroupParams p)
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN_BLOCKS_BOX : MIN_BLOCKS) group_kernel(const __grid_constant__ GroupParams p)
 {
     static_assert(1 <= A && A <= B && B <= 8, "stage range");
-    static_assert(C == 4, "map I/O assumes 4 columns per lane");
+    static_assert(C == 4, "lanes own 4 columns");
+    static_assert(WARPS_PER_BLOCK == 1, "one warp per block: the staging ring is per warp");
+    using SP = SmemPlan<A, B, F16>;
+    using TIN = MapT<A - 1, F16>;
     constexpr int RXT = sum_rx(A, B);
     constexpr int RYT = sum_ry(A, B);
-    constexpr int NIN = map_channels(A - 1);
+    constexpr int NIN = SP::NIN;
     constexpr int NOUT = map_channels(B);
-    // cumulative vertical delay before stage k
-    constexpr int D2 = sum_ry(A, 1), D3 = sum_ry(A, 2), D4 = sum_ry(A, 3), D6 = sum_ry(A, 5), D8 = sum_ry(A, 7);
-    constexpr bool HAS3 = A <= 3 && 3 <= B, HAS4 = A <= 4 && 4 <= B, HAS6 = A <= 6 && 6 <= B, HAS8 = A <= 8 && 8 <= B;
+    constexpr int D3 = sum_ry(A, 2), D4 = sum_ry(A, 3), D6 = sum_ry(A, 5), D8 = sum_ry(A, 7);
+    constexpr bool HAS3 = A <= 3 && 3 <= B, HAS4 = A <= 4 && 4 <= B, HAS6 = SP::HAS6, HAS8 = A <= 8 && 8 <= B;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SP::BAR_OFF);
+    unsigned char *stage_buf = smem + SP::IN_OFF;
 
     const int lane = threadIdx.x & 31;
-    const int64_t job = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
-    if (job >= p.n_jobs) return;  // whole warp leaves together
+    const int64_t job = blockIdx.x;
+    if (job >= p.n_jobs) return;
     const int strip = (int)(job % p.n_strips);
     const int64_t rest = job / p.n_strips;
     const int chunk = (int)(rest % p.n_chunks);
-    const int64_t frame = rest / p.n_chunks;
+    const int frame = (int)(rest / p.n_chunks);
     const int W = p.W, H = p.H;
 
-    const int xs = p.xs0 + strip * p.step;
+    const int xs = p.xs0 + strip * p.step;  // multiple of 16 columns: TMA-aligned
     const int x0 = xs + C * lane;
     const int xo0 = max(xs + RXT, 0), xo1 = min(xs + RXT + p.step, W);
     const bool edgeL = xs < 0, edgeR = xs + STRIP > W;
-    // the one aligned input vector of this lane per row, and the element each column takes
-    const int xb = x0 < 0 ? 0 : (x0 >= W ? ((W - 1) & ~(C - 1)) : x0);
-    int kc[C];
-    unsigned bsel = 0;  // byte selector of the clamped columns (u8 input)
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        kc[c] = min(max(x0 + c, 0), W - 1) - xb;
-        bsel |= (unsigned)kc[c] << (4 * c);
-    }
     const bool lane_inside = (x0 >= 0) && (x0 + C <= W);
-    unsigned out_mask = 0;  // which of this lane's columns belong to the strip's output
+    int off[C];  // staged-tile offset of each column's clamped source
+#pragma unroll
+    for (int c = 0; c < C; ++c) off[c] = min(max(x0 + c, 0), W - 1) - xs;
+    unsigned out_mask = 0;
 #pragma unroll
     for (int c = 0; c < C; ++c) out_mask |= (x0 + c >= xo0 && x0 + c < xo1) ? (1u << c) : 0u;
 
     const int y0 = chunk * p.chunk_rows, y1 = min(y0 + p.chunk_rows, H);
     const int t_begin = max(y0 - RYT, 0), t_end = y1 + RYT;
+    // stages whose first row lies in the frame; rows of later stages (all past H-1) are
+    // replaced by the vertical replay or never stored, so they are neither copied nor awaited
+    const int n_stages = min((t_end - t_begin + RB - 1) / RB, (H - t_begin + RB - 1) / RB);
+
+    // ---- staging ring: init barriers, issue the first NST stages
+    int issued = 0;  // stages issued so far (the same count on every lane)
+    auto issue = [&](int k) {  // lane 0 only
+        uint64_t *bar = bars + (k % SP::NST);
+        unsigned char *dst = stage_buf + (k % SP::NST) * SP::STAGE_BYTES;
+        mbar_expect_tx(bar, SP::STAGE_BYTES);
+#pragma unroll
+        for (int m = 0; m < NIN; ++m) tma_load_3d(dst + m * SP::CH_BYTES, &p.tmap[m], xs, t_begin + k * RB, frame, bar);
+    };
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < SP::NST; ++s) mbar_init(bars + s, 1);
+        mbar_fence_init();
+        for (int k = 0; k < SP::NST && k < n_stages; ++k) issue(k);
+    }
+    issued = min(SP::NST, n_stages);
+    __syncwarp();
 
     // on-chip state of the vertical stages
     std::conditional_t<HAS3, GaussV, Empty> s3{};
@@ -441,57 +552,21 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, MIN_BLOCKS) group_kernel
     std::conditional_t<HAS6, BoxV, Empty> s6{};
     std::conditional_t<HAS8, NmsV, Empty> s8{};
     unsigned count = 0;
+    bool failed = false;
+    int k_fail = 0;
+    const int64_t out_frame = (int64_t)frame * p.out_fstride;
 
-    const int64_t in_frame = frame * p.in_fstride, out_frame = frame * p.out_fstride;
-    auto in_off = [&](int row) { return in_frame + (int64_t)min(max(row, 0), H - 1) * p.in_pitch + xb; };
-
-    // Input rows are prefetched PD = 5 rows ahead into registers (slot = loop phase):
-    // u8 frames and single-channel maps. Wider maps are loaded when used.
-    using InIO = MapIO<MapT<A - 1, F16>>;
-    constexpr bool PREFETCH = (A == 1) || (NIN == 1);
-    using RawIn = std::conditional_t<A == 1, uint32_t, typename InIO::Raw>;
-    [[maybe_unused]] RawIn q[PREFETCH ? 5 : 1];
-    auto load_raw = [&](int row, int m) -> RawIn {
-        if constexpr (A == 1) return __ldg(reinterpret_cast<const uint32_t *>(static_cast<const uint8_t *>(p.in[0]) + in_off(row)));
-        else return InIO::load(p.in[m], in_off(row));
-    };
-    if constexpr (PREFETCH) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) q[k] = load_raw(t_begin + k, 0);
-    }
-
-    auto step = [&](auto phase_tag, int t) {
-        [[maybe_unused]] constexpr int PH = decltype(phase_tag)::value;
+    // One row step at loop phase PH (= row within the staged block, = box ring slot).
+    auto step = [&](auto phase_tag, int t, const unsigned char *sbuf) {
+        constexpr int PH = decltype(phase_tag)::value;
         const bool border = (t <= RYT) || (t >= H);
-        // ---- group input row t (clamped)
-        [[maybe_unused]] Rows<1> f;
+        // ---- group input row t (staged; rows past the last copied stage are stale and unused)
+        const unsigned char *srow = sbuf + PH * SP::ROW_BYTES;
         [[maybe_unused]] Rows<NIN> in;
-        if constexpr (A == 1) {
-            const uint32_t w = __byte_perm(q[PH], 0u, bsel);
-            q[PH] = load_raw(t + 5, 0);
 #pragma unroll
-            for (int c = 0; c < C; ++c) f.v[0][c] = u8_to_float(w, c);
-        } else {
-#pragma unroll
-            for (int m = 0; m < NIN; ++m) {
-                RawIn raw;
-                if constexpr (PREFETCH) {
-                    raw = q[PH];
-                    q[PH] = load_raw(t + 5, 0);
-                } else {
-                    raw = load_raw(t, m);
-                }
-                float v[C];
-                InIO::unpack(raw, p.in_scale, v);
-                if (lane_inside) {
-#pragma unroll
-                    for (int c = 0; c < C; ++c) in.v[m][c] = v[c];
-                } else {
-#pragma unroll
-                    for (int c = 0; c < C; ++c) in.v[m][c] = pick(v, kc[c]);
-                }
-            }
-        }
+        for (int m = 0; m < NIN; ++m) Staged<TIN>::read(srow + m * SP::CH_BYTES, lane, lane_inside, off, p.in_scale, in.v[m]);
+        [[maybe_unused]] Rows<1> f;
+        if constexpr (A == 1) f = in;
         // ---- stage 2 (horizontal Gaussian)
         [[maybe_unused]] Rows<1> g1;
         if constexpr (A <= 2 && 2 <= B) {
@@ -554,29 +629,29 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, MIN_BLOCKS) group_kernel
             sm = in;
         }
         // ---- stage 7 (Harris)
-        [[maybe_unused]] Rows<1> r;
+        [[maybe_unused]] Rows<1> r7;
         if constexpr (A <= 7 && 7 <= B) {
-            harris(sm, r.v[0]);
+            harris(sm, r7.v[0]);
         } else if constexpr (A == 8) {
-            r = in;
+            r7 = in;
         }
         // ---- stage 8 (threshold + NMS), input row t - D8
         [[maybe_unused]] unsigned bits = 0;
         if constexpr (HAS8) {
             if constexpr (hstencil_before(A, 8))
-                if (edgeL | edgeR) fix_edges<1>(r, xs, x0, W, edgeL, edgeR);
+                if (edgeL | edgeR) fix_edges<1>(r7, xs, x0, W, edgeL, edgeR);
             float mh[C];
-            nms_h(r.v[0], mh);
+            nms_h(r7.v[0], mh);
             if (border) {
                 const int i = t - D8;
-                if (i == 0) s8.fill(mh, r.v[0]);
-                if (i >= H) s8.replay(mh, r.v[0]);
+                if (i == 0) s8.fill(mh, r7.v[0]);
+                if (i >= H) s8.replay(mh, r7.v[0]);
             }
-            bits = s8.push(mh, r.v[0], p.thr);
+            bits = s8.push(mh, r7.v[0], p.thr);
         }
         // ---- group output row t - RYT
         const int o = t - RYT;
-        if (o >= y0 && o < y1 && out_mask) {
+        if (o >= y0 && out_mask) {  // o < y1 holds: t < y1 + RYT
             const int64_t ooff = out_frame + (int64_t)o * p.out_pitch + x0;
             if constexpr (B == 8) {
                 const unsigned kept = bits & out_mask;
@@ -596,25 +671,56 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, MIN_BLOCKS) group_kernel
                 else if constexpr (B == 4) res = &ixy;
                 else if constexpr (B == 5) res = &pr;
                 else if constexpr (B == 6) res = &sm;
-                else res = &r;
+                else res = &r7;
 #pragma unroll
-                for (int m = 0; m < NOUT; ++m) MapIO<MapT<B, F16>>::store(p.out[m], ooff, res->v[m], out_mask, p.out_scale);
+                for (int m = 0; m < NOUT; ++m) Store<MapT<B, F16>>::row(p.out[m], ooff, res->v[m], out_mask, p.out_scale);
             }
         }
     };
 
-    for (int t = t_begin; t < t_end; t += 5) {
-        step(std::integral_constant<int, 0>{}, t);
+    // Blocks of RB = 5 rows: wait for the block's stage, run the 5 unrolled row steps,
+    // then hand the stage buffer back to TMA for block k + NST.
+    using P0 = std::integral_constant<int, 0>;
+    using P1 = std::integral_constant<int, 1>;
+    using P2 = std::integral_constant<int, 2>;
+    using P3 = std::integral_constant<int, 3>;
+    using P4 = std::integral_constant<int, 4>;
+#pragma unroll 1
+    for (int k = 0, t = t_begin; t < t_end; ++k, t += RB) {
+        if (k < n_stages) {
+            const bool ok = __all_sync(FULL, mbar_wait(bars + (k % SP::NST), (unsigned)(k / SP::NST) & 1u));
+            if (!ok) {  // warp-uniform
+                failed = true;
+                k_fail = k;
+                break;
+            }
+        }
+        const unsigned char *sbuf = stage_buf + (k % SP::NST) * SP::STAGE_BYTES;
+        step(P0{}, t, sbuf);
         if (t + 1 >= t_end) break;
-        step(std::integral_constant<int, 1>{}, t + 1);
+        step(P1{}, t + 1, sbuf);
         if (t + 2 >= t_end) break;
-        step(std::integral_constant<int, 2>{}, t + 2);
+        step(P2{}, t + 2, sbuf);
         if (t + 3 >= t_end) break;
-        step(std::integral_constant<int, 3>{}, t + 3);
+        step(P3{}, t + 3, sbuf);
         if (t + 4 >= t_end) break;
-        step(std::integral_constant<int, 4>{}, t + 4);
+        step(P4{}, t + 4, sbuf);
+        if (k + SP::NST < n_stages) {
+            __syncwarp();  // every lane has read the stage
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(k + SP::NST);
+            }
+            issued = k + SP::NST + 1;
+        }
     }
 
+    if (failed) {
+        // record, then give the copies still in flight a bounded chance to land
+        if (lane == 0) atomicOr(p.err, DEVERR_TIMEOUT);
+        for (int k = k_fail; k < issued; ++k) mbar_wait(bars + (k % SP::NST), (unsigned)(k / SP::NST) & 1u);
+        return;
+    }
     if constexpr (B == 8) {
         const unsigned tot = __reduce_add_sync(FULL, count);
         if (lane == 0 && tot) atomicAdd(p.counts + frame, (int)tot);

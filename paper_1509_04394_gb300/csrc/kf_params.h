@@ -1,6 +1,7 @@
 // kf_params.h -- launch parameters and the stage table shared by host and device code.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only; the library does not link libcuda)
 #include <stdint.h>
 
 #ifdef __CUDACC__
@@ -18,8 +19,11 @@ namespace kf {
 constexpr int C = KF_C;        // columns per lane
 constexpr int STRIP = 32 * C;  // columns per warp strip
 constexpr int WARPS_PER_BLOCK = 1;  // warps never cooperate: one warp per block
-constexpr int MIN_BLOCKS = 12;      // resident blocks per SM the register budget targets
+constexpr int MIN_BLOCKS = 16;      // resident blocks per SM the register budget targets
+constexpr int MIN_BLOCKS_BOX = 12;  // ... for groups holding the 5-row box ring in registers
 constexpr int NSTAGES = 8;
+constexpr int RB = 5;           // rows per TMA stage = rows per unrolled loop block
+constexpr int STRIP_ALIGN = 16; // strips start on multiples of 16 columns (16-byte TMA x for u8)
 
 // Stage table of the Harris chain, 1-based (stage 0 = the u8 frames). One-sided radii
 // along columns (rx) and rows (ry), Table I.
@@ -40,6 +44,8 @@ inline constexpr double map_scale(int k)
 }
 
 struct GroupParams {
+    CUtensorMap tmap[3];      // TMA descriptors of the input planes: {W, H, T}, box {STRIP, RB, 1}
+    int *err;                 // device error word (bounded waits that expired)
     const void *in[3];        // input planes (stage A-1 map; u8 frames when A == 1)
     int64_t in_pitch;         // elements between rows
     int64_t in_fstride;       // elements between frames
@@ -56,13 +62,14 @@ struct GroupParams {
 };
 
 // Strip geometry of a group with accumulated horizontal radius rxt: input strips start
-// on a multiple of C columns (aligned vector loads), outputs tile the frame exactly.
+// on a multiple of STRIP_ALIGN columns (a legal TMA x for every map type), outputs tile
+// the frame exactly.
 struct StripGeom { int xs0, step, n_strips; };
 inline StripGeom strip_geometry(int rxt, int W)
 {
     StripGeom g;
-    g.xs0 = -((rxt + C - 1) / C) * C;
-    g.step = ((STRIP - 2 * rxt) / C) * C;
+    g.xs0 = -((rxt + STRIP_ALIGN - 1) / STRIP_ALIGN) * STRIP_ALIGN;
+    g.step = ((STRIP - 2 * rxt) / STRIP_ALIGN) * STRIP_ALIGN;
     const int o0 = g.xs0 + rxt;  // first output column of strip 0 (<= 0)
     g.n_strips = (W - o0 + g.step - 1) / g.step;
     return g;
@@ -70,6 +77,8 @@ inline StripGeom strip_geometry(int rxt, int W)
 
 #ifdef __CUDACC__
 typedef int (*LaunchFn)(const GroupParams &p, unsigned grid, void *stream);
+// bytes per element of the map written by 1-based stage k (0 = frames) at a precision
+inline int map_elem_bytes(int k, bool f16) { return (k == 0 || k == 8) ? 1 : (f16 ? 2 : 4); }
 LaunchFn launcher_a1(int B, int f16);
 LaunchFn launcher_a2(int B, int f16);
 LaunchFn launcher_a3(int B, int f16);

@@ -71,6 +71,7 @@ def _lib():
             "kf_version": (i32, [P, P]),
             "kf_create": (i32, [i32, P]),
             "kf_destroy": (i32, [P]),
+            "kf_device_error": (i32, [P, P]),
             "kf_set_precision": (i32, [P, i32]),
             "kf_set_chunk_rows": (i32, [P, i32]),
             "kf_add_stage": (i32, [P, P, P]),
@@ -95,7 +96,7 @@ def _lib():
 
 def exported_symbols() -> list[str]:
     """Names of the C entry points this binding wraps (all declared in kfuse.h)."""
-    return ["kf_status_str", "kf_last_cuda_error", "kf_version", "kf_create", "kf_destroy",
+    return ["kf_status_str", "kf_last_cuda_error", "kf_version", "kf_create", "kf_destroy", "kf_device_error",
             "kf_set_precision", "kf_set_chunk_rows", "kf_add_stage", "kf_add_harris_chain",
             "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
             "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group"]
@@ -139,6 +140,13 @@ def kf_create(device: int) -> ctypes.c_void_p:
 
 def kf_destroy(ctx) -> None:
     _check("kf_destroy", _lib().kf_destroy(ctx))
+
+
+def kf_device_error(ctx) -> int:
+    """Synchronise and return (then clear) the context's device error word."""
+    c = ctypes.c_int()
+    _check("kf_device_error", _lib().kf_device_error(ctx, ctypes.byref(c)), ctx)
+    return c.value
 
 
 def kf_set_precision(ctx, precision: int) -> None:

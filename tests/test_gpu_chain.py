@@ -17,7 +17,7 @@ from oracle import chain as oc  # noqa: E402
 from paper_1509_04394_gb300 import build as kbuild  # noqa: E402
 from paper_1509_04394_gb300 import kfuse as K  # noqa: E402
 from synth import video as sv  # noqa: E402
-from tests._parity import (TOL_F16, TOL_F32, check_mask, normwise, pitch4, pitch16)  # noqa: E402
+from tests._parity import (TOL_F16, TOL_F32, check_mask, normwise, pitch16)  # noqa: E402
 
 MAP_KEYS = (("f",), ("g1",), ("g",), ("ix", "iy"), ("pxx", "pxy", "pyy"), ("sxx", "sxy", "syy"), ("r",))
 
@@ -64,7 +64,7 @@ def run_unfused_maps(ctx_h, prec, fr_dev, W):
     cur, cur_dt, outs = [fr_dev], K.KF_DT_U8, []
     for s in range(7):
         dt, tdt = map_dtypes(prec, s)
-        out = [torch.empty((T, H, pitch4(W)), dtype=tdt, device=fr_dev.device) for _ in range(K.MAP_CHANNELS[s + 1])]
+        out = [torch.empty((T, H, pitch16(W)), dtype=tdt, device=fr_dev.device) for _ in range(K.MAP_CHANNELS[s + 1])]
         K.kf_run_group(ctx_h, s, s, cur, cur_dt, out, dt, W)
         outs.append(out)
         cur, cur_dt = out, dt
@@ -107,6 +107,7 @@ def test_all_128_partitions_are_bit_identical_to_the_unfused_chain(dev):
         counts = torch.zeros(T, dtype=torch.int32, device=dev)
         K.kf_run(ctx.h, cuts, fd, W, mask, counts, ws if ws_b else None)
         results[cuts] = (mask.cpu().numpy(), counts.cpu().numpy())
+    assert K.kf_device_error(ctx.h) == 0
     ref_m, ref_c = results[127]
     for cuts, (m, c) in results.items():
         assert np.array_equal(m, ref_m), cuts
@@ -117,7 +118,7 @@ def test_all_128_partitions_are_bit_identical_to_the_unfused_chain(dev):
         check_mask(ref_m[t, :, :W], int(ref_c[t]), m_ref, c_ref, maps["r"], TOL_F32)
     # R through a fused group [0..6] equals R through the unfused stages, bit for bit
     outs, _, _ = run_unfused_maps(ctx.h, K.KF_PREC_F32, fd, W)
-    r = torch.empty((T, H, pitch4(W)), dtype=torch.float32, device=dev)
+    r = torch.empty((T, H, pitch16(W)), dtype=torch.float32, device=dev)
     K.kf_run_group(ctx.h, 0, 6, [fd], K.KF_DT_U8, [r], K.KF_DT_F32, W)
     assert torch.equal(r[:, :, :W], outs[6][0][:, :, :W])
 
@@ -135,6 +136,7 @@ def test_ragged_and_degenerate_frames(dev, H, W):
         mask = torch.full((T, H, pitch16(W)), 9, dtype=torch.uint8, device=dev)
         counts = torch.zeros(T, dtype=torch.int32, device=dev)
         K.kf_run(ctx.h, cuts, fd, W, mask, counts, ws if ws_b else None)
+        assert K.kf_device_error(ctx.h) == 0
         m = mask.cpu().numpy()
         assert np.all(m[:, :, W:] == 9), "columns past W must be untouched"
         for t in range(T):
@@ -160,7 +162,7 @@ def test_chunking_does_not_change_the_result(dev, rows):
     for r in (200, rows):
         ctx = K.Context(0)
         K.kf_set_chunk_rows(ctx.h, r)
-        r_map = torch.empty((T, H, pitch4(W)), dtype=torch.float32, device=dev)
+        r_map = torch.empty((T, H, pitch16(W)), dtype=torch.float32, device=dev)
         K.kf_run_group(ctx.h, 0, 6, [fd], K.KF_DT_U8, [r_map], K.KF_DT_F32, W)
         mask = torch.zeros((T, H, pitch16(W)), dtype=torch.uint8, device=dev)
         counts = torch.zeros(T, dtype=torch.int32, device=dev)
@@ -220,7 +222,7 @@ def test_full_size_workload_on_sampled_frames(dev):
     mask = torch.zeros_like(full)
     counts = torch.zeros(spec.T, dtype=torch.int32, device=dev)
     K.kf_run(ctx.h, cuts, full, spec.W, mask, counts, None)
-    torch.cuda.synchronize()
+    assert K.kf_device_error(ctx.h) == 0
     for i, t in enumerate(sample):
         maps, m_ref, c_ref = oc.chain_frame(fr_s[i][:, :spec.W].copy())
         check_mask(mask[t, :, :spec.W].cpu().numpy(), int(counts[t]), m_ref, c_ref, maps["r"], TOL_F32)
