@@ -203,6 +203,26 @@ kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *video, const kf_cor
 kf_status kf_run_group(kf_ctx *ctx, int first, int last, const kf_map *in, const kf_map *out,
                        int64_t W, int64_t H, int64_t T, int32_t *counts, void *stream);
 
+/* ------------------------------------------------------------------ no-allocation run */
+/* kf_run with the workspace in a fixed array that the library itself holds on every GPU
+ * that loads it (KF_STATIC_WORKSPACE_BYTES per GPU, kept until the process exits). The
+ * paper has no counterpart; this call exists for callers that cannot call cudaMalloc or
+ * hand over device memory: a plug-in running inside a host framework that owns all
+ * device allocations, or a real-time pipeline whose memory footprint is fixed at start-up.
+ * The caller still passes the video and the output buffers, as for kf_run.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *   - The first call on a device looks up the device address of that device's array
+ *     (cudaGetSymbolAddress, with the context's device current); make that first call
+ *     before any stream capture.
+ *   - KF_ENOMEM when kf_workspace_bytes(cuts, W, H, T) exceeds KF_STATIC_WORKSPACE_BYTES:
+ *     split the volume into fewer frames per call (cuts == 0 needs no workspace).
+ *   - All calls on a device share the one array and it keeps the last call's contents
+ *     (the chain overwrites every map it reads, so nothing needs clearing). Calls whose
+ *     kernels overlap on the GPU (other streams, other host threads) race on it:
+ *     serialise them. */
+#define KF_STATIC_WORKSPACE_BYTES (64u << 20)
+kf_status kf_run_static(kf_ctx *ctx, uint32_t cuts, const kf_video *video, const kf_corners *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -272,6 +272,10 @@ WsPlan plan_workspace(const kf_ctx *c, uint32_t cuts, int64_t W, int64_t H, int6
 
 }  // namespace
 
+namespace kf {
+int ctx_device(const kf_ctx *ctx) { return ctx ? ctx->device : -1; }
+}  // namespace kf
+
 extern "C" {
 
 const char *kf_status_str(kf_status s)

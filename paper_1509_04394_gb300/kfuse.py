@@ -86,6 +86,7 @@ def _lib():
             "kf_workspace_bytes": (i32, [P, u32, i64, i64, i64, P]),
             "kf_run": (i32, [P, u32, P, P, P, ctypes.c_size_t, P]),
             "kf_run_group": (i32, [P, i32, i32, P, P, i64, i64, i64, P, P]),
+            "kf_run_static": (i32, [P, u32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -99,7 +100,7 @@ def exported_symbols() -> list[str]:
     return ["kf_status_str", "kf_last_cuda_error", "kf_version", "kf_create", "kf_destroy", "kf_device_error",
             "kf_set_precision", "kf_set_chunk_rows", "kf_add_stage", "kf_add_harris_chain",
             "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
-            "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group"]
+            "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -228,6 +229,18 @@ def kf_run(ctx, cuts: int, frames, W: int, mask, counts, workspace=None, stream=
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check("kf_run", _lib().kf_run(ctx, cuts, ctypes.byref(v), ctypes.byref(o), _ptr(workspace), ws_bytes,
                                    _stream(stream)), ctx)
+
+
+KF_STATIC_WORKSPACE_BYTES = 64 << 20
+
+
+def kf_run_static(ctx, cuts: int, frames, W: int, mask, counts, stream=None) -> None:
+    """kf_run with the library's fixed per-GPU workspace: for callers that cannot allocate
+    device memory. Same tensors as kf_run, no workspace argument."""
+    T, H, P = frames.shape
+    v = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
+    o = kf_corners(mask.data_ptr(), int(mask.shape[2]), counts.data_ptr())
+    _check("kf_run_static", _lib().kf_run_static(ctx, cuts, ctypes.byref(v), ctypes.byref(o), _stream(stream)), ctx)
 
 
 def make_map(planes, dtype: int) -> kf_map:
