@@ -34,6 +34,22 @@ SPEC = sv.HSDV_800x600x1000
 WORKLOAD = "Harris 8-stage chain, 1000 frames x 800 rows x 600 cols u8, 64 blobs + 32 patches, seed 3"
 
 
+def kernel_counters():
+    """ncu counters of the fused kernel from profiles/fused_chain_traffic.json, only while
+    the kernel source still hashes to the captured version (else None)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "fused_chain_traffic.json")) as fh:
+            rec = json.load(fh)
+        h = hashlib.sha256()
+        for f in ("paper_1509_04394_gb300/csrc/kf_chain.cuh", "paper_1509_04394_gb300/csrc/kf_params.h"):
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        return rec if rec.get("source_sha256") == h.hexdigest() else None
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -246,6 +262,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     hbm_peak, peak_kind = peaks()
     alg_bytes = 2 * px + 4 * T  # frames read once, mask written once, counts
     achieved = alg_bytes / (ms / 1000) / 1e9
+    rec = kernel_counters() if T == 1000 else None
+    traffic = rec["dram_bytes_per_launch_1000_frames"] if rec else None
+    # instruction-issue roofline: 152 SMs x 4 schedulers x 1 warp instruction per cycle
+    sm_mhz = (clocks.get("sm_mhz") or 2070.0)
+    issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e9  # G warp-instructions / s
+    alu = None
+    if rec:
+        ach = rec["warp_instructions_per_launch_1000_frames"] / (ms / 1000) / 1e9
+        alu = {"bound": "alu", "achieved": ach, "peak": issue_peak, "unit": "Gwarp-inst/s",
+               "frac": ach / issue_peak, "peak_kind": "152 SMs x 4 schedulers x SM clock",
+               "instructions_per_launch": rec["warp_instructions_per_launch_1000_frames"]}
 
     # unfused sequence (one kernel per stage, volume-wide maps through HBM)
     unf_cuts = (1 << 7) - 1
@@ -285,8 +312,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "frames_per_s": world * T / (ms / 1000),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes},
+        "alu_roofline": alu,
         "unfused": {"value": world * px / (ms_unf / 1000) / 1e6, "ms_per_step": ms_unf, "kernels": 8,
                     "hbm_frac": unf_bytes / (ms_unf / 1000) / 1e9 / hbm_peak, "bit_identical_to_fused": same,
                     "fused_speedup": ms_unf / ms},
