@@ -203,6 +203,36 @@ kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *video, const kf_cor
 kf_status kf_run_group(kf_ctx *ctx, int first, int last, const kf_map *in, const kf_map *out,
                        int64_t W, int64_t H, int64_t T, int32_t *counts, void *stream);
 
+/* ------------------------------------------------------------------ tracking */
+/* The temporal stages after the chain. Selecting a frame's strongest corners needs the
+ * whole frame, a kernel-to-kernel dependency (Sec. V-A c) that closes the chain's
+ * fusable set, as the Kalman step does in Table IV; tracking forms the next set.
+ * Per frame t >= 1: the K corners of frame t with the largest R (ties: lower raster
+ * index first), and one Lucas-Kanade step per corner against frame t-1 over a 7x7
+ * window (every index clamped): A = sum [gx^2, gx gy; gx gy, gy^2], b = sum [gx gt, gy gt],
+ * (u, v) = -A^-1 b, gx, gy = Sobel of the smoothed frame t divided by 8, gt = smoothed
+ * frame t minus smoothed frame t-1. Window sums in FP32; determinant and solve in FP64;
+ * a window with |det| <= 1e-12 (A00 + A11)^2 is reported singular (u = v = 0). */
+typedef struct kf_tracks {
+    int32_t K;          /* points per frame, 1..1024                                      */
+    int32_t *n_points;  /* device, T: points of frame t (min(K, corners); 0 for t = 0)   */
+    int32_t *idx;       /* device, T*K: raster index y*W + x, strongest first             */
+    float *u, *v;       /* device, T*K: motion from frame t-1 to t in px/frame, x / y     */
+    int32_t *status;    /* device, T*K: 0 solved, 1 singular window                       */
+} kf_tracks;
+
+/* Workspace of kf_track: per frame a corner-candidate list of max(1024, ceil(W*H/4))
+ * 8-byte entries and a counter. A frame with more corners than that sets
+ * KF_DEVERR_OVERFLOW in the device error word (its selection then covers only the
+ * listed corners). */
+#define KF_DEVERR_OVERFLOW 2
+kf_status kf_track_workspace_bytes(const kf_ctx *ctx, int64_t W, int64_t H, int64_t T, size_t *bytes);
+/* The whole hot path on `stream`: the fully fused chain (mask, counts as kf_run with
+ * cuts == 0), then corner selection and tracking into `tracks`. workspace: device,
+ * >= kf_track_workspace_bytes, 256-byte aligned. W*H must be below 2^31. */
+kf_status kf_track(kf_ctx *ctx, const kf_video *video, const kf_corners *out, const kf_tracks *tracks,
+                   void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------------ no-allocation run */
 /* kf_run with the workspace in a fixed array that the library itself holds on every GPU
  * that loads it (KF_STATIC_WORKSPACE_BYTES per GPU, kept until the process exits). The

@@ -203,7 +203,8 @@ kf_status check_map(const kf_map *m, int stage_out, int precision, int64_t W, in
 
 // Enqueue group [A..B] (1-based) with already validated maps.
 kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &out, int64_t W, int64_t H, int64_t T,
-                       int32_t *counts, cudaStream_t s)
+                       int32_t *counts, cudaStream_t s, unsigned long long *cand = nullptr, int *cand_count = nullptr,
+                       int64_t cand_cap = 0)
 {
     if (T == 0) return KF_OK;
     kf::GroupParams p{};
@@ -214,6 +215,9 @@ kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &
     for (int i = 0; i < in.channels; ++i)
         if (!encode_plane(&p.tmap[i], in.plane[i], in.dtype, in.pitch, in.frame_stride, W, H, T)) return KF_EINVAL;
     p.err = c->d_err;
+    p.cand = cand;
+    p.cand_count = cand_count;
+    p.cand_cap = (int)cand_cap;
     p.in_pitch = in.pitch;
     p.in_fstride = in.frame_stride;
     p.out_pitch = out.pitch;
@@ -550,6 +554,66 @@ kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *v, const kf_corners
         cur = nxt;
         a = b + 1;
     }
+    return KF_OK;
+}
+
+kf_status kf_track_workspace_bytes(const kf_ctx *ctx, int64_t W, int64_t H, int64_t T, size_t *bytes)
+{
+    if (!ctx || !bytes || W <= 0 || H <= 0 || T < 0 || W > (1 << 30) || H > (1 << 30) || W * H > 0x7fffffffLL)
+        return KF_EINVAL;
+    *bytes = (size_t)round_up(4 * T, 256) + (size_t)(8 * kf::cand_capacity(W, H) * T);
+    return KF_OK;
+}
+
+kf_status kf_track(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf_tracks *tr, void *ws, size_t ws_bytes,
+                   void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    if (ctx->device < 0) return KF_ESTATE;
+    if (!builtin_chain(ctx)) return KF_EUNSUPPORTED;
+    if (!v || !o || !tr) return KF_EINVAL;
+    if (v->W <= 0 || v->H <= 0 || v->T < 0 || v->W > (1 << 30) || v->H > (1 << 30) || v->W * v->H > 0x7fffffffLL)
+        return KF_EINVAL;
+    if (v->pitch < v->W || v->pitch % 16 || o->mask_pitch < v->W || o->mask_pitch % 16) return KF_EINVAL;
+    if (tr->K < 1 || tr->K > 1024) return KF_EINVAL;
+    if (v->T == 0) return KF_OK;
+    if (!v->frames || !o->mask || !o->counts || !tr->n_points || !tr->idx || !tr->u || !tr->v || !tr->status)
+        return KF_EINVAL;
+    if (!aligned(v->frames, 16) || !aligned(o->mask, 16) || !aligned(o->counts, 4) || !aligned(tr->n_points, 4) ||
+        !aligned(tr->idx, 4) || !aligned(tr->u, 4) || !aligned(tr->v, 4) || !aligned(tr->status, 4))
+        return KF_EINVAL;
+    size_t need = 0;
+    kf_track_workspace_bytes(ctx, v->W, v->H, v->T, &need);
+    if (!ws || !aligned(ws, 256)) return KF_EINVAL;
+    if (ws_bytes < need) return KF_ENOMEM;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int *cand_count = static_cast<int *>(ws);
+    auto *cand = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + round_up(4 * v->T, 256));
+    const int64_t cap = kf::cand_capacity(v->W, v->H);
+    e = cudaMemsetAsync(cand_count, 0, sizeof(int) * (size_t)v->T, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    // the fusable set of the chain: one fused kernel, which also lists each frame's corners
+    kf_map fin{}, fout{};
+    fin.plane[0] = const_cast<uint8_t *>(v->frames);
+    fin.channels = 1;
+    fin.dtype = KF_DT_U8;
+    fin.pitch = v->pitch;
+    fin.frame_stride = v->pitch * v->H;
+    fout.plane[0] = o->mask;
+    fout.channels = 1;
+    fout.dtype = KF_DT_U8;
+    fout.pitch = o->mask_pitch;
+    fout.frame_stride = o->mask_pitch * v->H;
+    kf_status st = launch_group(ctx, 1, kf::NSTAGES, fin, fout, v->W, v->H, v->T, o->counts, s, cand, cand_count, cap);
+    if (st != KF_OK) return st;
+    // the tracking set, after the kernel-to-kernel dependency
+    int r = kf::launch_select(cand, cand_count, (int)cap, tr->K, (int)v->T, tr->n_points, tr->idx, stream);
+    if (r) return cuda_fail(ctx, (cudaError_t)r);
+    r = kf::launch_lk(v->frames, v->pitch, (int)v->W, (int)v->H, (int)v->T, tr->K, tr->n_points, tr->idx, tr->u, tr->v,
+                      tr->status, stream);
+    if (r) return cuda_fail(ctx, (cudaError_t)r);
     return KF_OK;
 }
 

@@ -283,16 +283,17 @@ struct NmsV {
 #pragma unroll
         for (int c = 0; c < C; ++c) { mh[c] = p[0][c]; r[c] = rc[c]; }
     }
-    // returns the 4 mask bits of the output row (input row - 1) in bits 0..C-1
-    __device__ __forceinline__ unsigned push(const float (&mh)[C], const float (&r)[C], float thr)
+    // returns the 4 mask bits of the output row (input row - 1) in bits 0..C-1, and the
+    // response of that row in `centre`
+    __device__ __forceinline__ unsigned push(const float (&mh)[C], const float (&r)[C], float thr, float (&centre)[C])
     {
         unsigned bits = 0;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const float m1 = fmaxf(mh[c], p[0][c]);
             const float m9 = fmaxf(m1, p[1][c]);
-            const float centre = rc[c];
-            bits |= ((centre > thr) & (centre >= m9)) ? (1u << c) : 0u;
+            centre[c] = rc[c];
+            bits |= ((centre[c] > thr) & (centre[c] >= m9)) ? (1u << c) : 0u;
             p[0][c] = mh[c]; p[1][c] = m1; rc[c] = r[c];
         }
         return bits;
@@ -315,6 +316,7 @@ __device__ __forceinline__ void nms_h(const float (&r)[C], float (&mh)[C])
 
 constexpr unsigned WAIT_LIMIT = 1u << 22;  // try_wait rounds before giving up
 constexpr int DEVERR_TIMEOUT = 1;
+constexpr int DEVERR_OVERFLOW = 2;  // a frame had more corner candidates than cand_cap
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -637,6 +639,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
         }
         // ---- stage 8 (threshold + NMS), input row t - D8
         [[maybe_unused]] unsigned bits = 0;
+        [[maybe_unused]] float centre[C];
         if constexpr (HAS8) {
             if constexpr (hstencil_before(A, 8))
                 if (edgeL | edgeR) fix_edges<1>(r7, xs, x0, W, edgeL, edgeR);
@@ -647,10 +650,40 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
                 if (i == 0) s8.fill(mh, r7.v[0]);
                 if (i >= H) s8.replay(mh, r7.v[0]);
             }
-            bits = s8.push(mh, r7.v[0], p.thr);
+            bits = s8.push(mh, r7.v[0], p.thr, centre);
         }
         // ---- group output row t - RYT
         const int o = t - RYT;
+        if constexpr (B == 8) {
+            // corner candidates of the tracking stage: one warp-aggregated append per row
+            if (p.cand && o >= y0) {  // warp-uniform
+                const unsigned kept = bits & out_mask;
+                const unsigned n = __popc(kept);
+                unsigned incl = n;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const unsigned y = __shfl_up_sync(FULL, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                const unsigned total = __shfl_sync(FULL, incl, 31);
+                if (total) {
+                    unsigned base = 0;
+                    if (lane == 31) base = atomicAdd(reinterpret_cast<unsigned *>(p.cand_count) + frame, total);
+                    base = __shfl_sync(FULL, base, 31);
+                    unsigned pos = base + incl - n;
+                    unsigned long long *dst = p.cand + (int64_t)frame * p.cand_cap;
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        if (kept >> c & 1) {
+                            const unsigned raster = (unsigned)(o * W + x0 + c);
+                            if (pos < (unsigned)p.cand_cap)
+                                dst[pos] = (unsigned long long)__float_as_uint(centre[c]) << 32 | (0xffffffffu - raster);
+                            ++pos;
+                        }
+                    if (lane == 31 && base + total > (unsigned)p.cand_cap) atomicOr(p.err, DEVERR_OVERFLOW);
+                }
+            }
+        }
         if (o >= y0 && out_mask) {  // o < y1 holds: t < y1 + RYT
             const int64_t ooff = out_frame + (int64_t)o * p.out_pitch + x0;
             if constexpr (B == 8) {

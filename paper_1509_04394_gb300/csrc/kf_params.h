@@ -36,6 +36,10 @@ KF_HD constexpr int sum_ry(int a, int b) { int s = 0; for (int k = a; k <= b; ++
 // does a stage in [a, k) read horizontal neighbours? (then the input of k needs an edge fix-up)
 KF_HD constexpr bool hstencil_before(int a, int k) { for (int j = a; j < k; ++j) if (stage_rx(j) > 0) return true; return false; }
 
+// Capacity of a frame's corner-candidate list for the tracking stage: a quarter of the
+// frame (3x3 maxima cannot be denser, except on plateaus), at least 1024.
+inline int64_t cand_capacity(int64_t W, int64_t H) { const int64_t q = (W * H + 3) / 4; return q < 1024 ? 1024 : q; }
+
 // Integer scale of the FP32 map written by stage k: scaled = true * map_scale(k).
 inline constexpr double map_scale(int k)
 {
@@ -59,6 +63,11 @@ struct GroupParams {
     float thr;                // NMS threshold in the scaled units of R
     float in_scale;           // FP16 input maps: scaled value = stored * in_scale
     float out_scale;          // FP16 output maps: stored = scaled value * out_scale
+    // corner candidates for the tracking stage (B == 8, optional): per frame a list of
+    // keys (R bits << 32 | ~raster index), cand_cap per frame, cand_count[frame] entries
+    unsigned long long *cand;
+    int *cand_count;
+    int cand_cap;
 };
 
 // Strip geometry of a group with accumulated horizontal radius rxt: input strips start
@@ -87,6 +96,10 @@ LaunchFn launcher_a5(int B, int f16);
 LaunchFn launcher_a6(int B, int f16);
 LaunchFn launcher_a7(int B, int f16);
 LaunchFn launcher_a8(int B, int f16);
+int launch_select(const unsigned long long *cand, const int *cand_count, int cap, int K, int T, int32_t *n_points,
+                  int32_t *idx, void *stream);
+int launch_lk(const uint8_t *frames, int64_t pitch, int W, int H, int T, int K, const int32_t *n_points,
+              const int32_t *idx, float *u, float *v, int32_t *status, void *stream);
 #endif
 
 }  // namespace kf

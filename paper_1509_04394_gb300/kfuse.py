@@ -49,6 +49,11 @@ class kf_corners(ctypes.Structure):
     _fields_ = [("mask", ctypes.c_void_p), ("mask_pitch", ctypes.c_int64), ("counts", ctypes.c_void_p)]
 
 
+class kf_tracks(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("n_points", ctypes.c_void_p), ("idx", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
 class kf_map(ctypes.Structure):
     _fields_ = [("plane", ctypes.c_void_p * 3), ("channels", ctypes.c_int), ("dtype", ctypes.c_int),
                 ("pitch", ctypes.c_int64), ("frame_stride", ctypes.c_int64)]
@@ -87,6 +92,8 @@ def _lib():
             "kf_run": (i32, [P, u32, P, P, P, ctypes.c_size_t, P]),
             "kf_run_group": (i32, [P, i32, i32, P, P, i64, i64, i64, P, P]),
             "kf_run_static": (i32, [P, u32, P, P, P]),
+            "kf_track_workspace_bytes": (i32, [P, i64, i64, i64, P]),
+            "kf_track": (i32, [P, P, P, P, P, ctypes.c_size_t, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -100,7 +107,8 @@ def exported_symbols() -> list[str]:
     return ["kf_status_str", "kf_last_cuda_error", "kf_version", "kf_create", "kf_destroy", "kf_device_error",
             "kf_set_precision", "kf_set_chunk_rows", "kf_add_stage", "kf_add_harris_chain",
             "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
-            "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static"]
+            "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static",
+            "kf_track_workspace_bytes", "kf_track"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -229,6 +237,24 @@ def kf_run(ctx, cuts: int, frames, W: int, mask, counts, workspace=None, stream=
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check("kf_run", _lib().kf_run(ctx, cuts, ctypes.byref(v), ctypes.byref(o), _ptr(workspace), ws_bytes,
                                    _stream(stream)), ctx)
+
+
+def kf_track_workspace_bytes(ctx, W, H, T) -> int:
+    b = ctypes.c_size_t()
+    _check("kf_track_workspace_bytes", _lib().kf_track_workspace_bytes(ctx, W, H, T, ctypes.byref(b)), ctx)
+    return b.value
+
+
+def kf_track(ctx, frames, W: int, mask, counts, K: int, n_points, idx, u, v, status, workspace, stream=None) -> None:
+    """Fused chain + corner selection + LK tracking. idx, u, v, status: [T, K] CUDA tensors
+    (int32, float32, float32, int32); n_points: int32 [T]."""
+    T, H, P = frames.shape
+    vid = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
+    o = kf_corners(mask.data_ptr(), int(mask.shape[2]), counts.data_ptr())
+    tr = kf_tracks(int(K), n_points.data_ptr(), idx.data_ptr(), u.data_ptr(), v.data_ptr(), status.data_ptr())
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("kf_track", _lib().kf_track(ctx, ctypes.byref(vid), ctypes.byref(o), ctypes.byref(tr), workspace.data_ptr(),
+                                       ws_bytes, _stream(stream)), ctx)
 
 
 KF_STATIC_WORKSPACE_BYTES = 64 << 20

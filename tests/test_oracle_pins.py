@@ -246,3 +246,27 @@ def test_lk_recovers_a_known_translation(u, v):
     assert inner.sum() >= 8
     err = np.hypot(uu[inner] - u, vv[inner] - v)
     assert np.median(err) <= 0.1
+
+
+def test_lk_tracks_slow_checker_patches_of_the_synthetic_video():
+    # Ground truth from the generator: every point inside a checker patch (3 px in from
+    # its edge, 8 px in from the frame edge) moves with the patch. One linearised LK step
+    # is accurate for sub-pixel motion: patches slower than 1 px/frame must come out
+    # within 0.25 px/frame (median).
+    from synth import video as sv
+    spec = sv.VideoSpec(T=6, H=400, W=300, seed=7, n_blobs=16, n_patches=16)
+    fr, sc = sv.generate(spec)
+    errs = []
+    for t in range(1, spec.T):
+        idx, u, v, st = oc.track_pair(fr[t - 1], fr[t], K=256)
+        py, px = idx // spec.W, idx % spec.W
+        X, Y = sc.position(t)
+        for i in range(len(idx)):
+            if st[i] or not (8 <= px[i] < spec.W - 8 and 8 <= py[i] < spec.H - 8):
+                continue
+            for o in np.nonzero(sc.kind == 1)[0]:
+                dx, dy = (px[i] - X[o]) % spec.W, (py[i] - Y[o]) % spec.H
+                if 3 <= dx <= 13 and 3 <= dy <= 13 and np.hypot(sc.vx[o], sc.vy[o]) < 1.0:
+                    errs.append(np.hypot(u[i] - sc.vx[o], v[i] - sc.vy[o]))
+    assert len(errs) >= 30
+    assert np.median(errs) <= 0.25
