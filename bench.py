@@ -1,7 +1,9 @@
 """Benchmark of the fused Harris chain on synthetic high-speed video (1000 x 800 x 600 u8).
 
-One step = the whole chain (8 stages, the partition the traffic-model planner picks:
-full fusion) over the 1000-frame volume, inputs already resident in HBM. The volume
+One step = the whole hot path over the 1000-frame volume, inputs already resident in
+HBM: the 8-stage chain in the partition the traffic-model planner picks (full fusion),
+then per frame the 256 strongest corners and one Lucas-Kanade step against the previous
+frame. The volume
 (480 MB of frames + 480 MB of mask) is larger than L2, so no flush is needed between
 steps. Prints ONE JSON line (rank 0).
 
@@ -133,28 +135,40 @@ def run_profile(args):
     counts = torch.zeros(T, dtype=torch.int32, device=dev)
     ctx = K.Context(0, precision=K.KF_PREC_F16 if args.f16 else K.KF_PREC_F32)
     cuts = args.cuts if args.cuts >= 0 else K.kf_plan(ctx.h, W, H, T)[0]
-    ws_b = K.kf_workspace_bytes(ctx.h, cuts, W, H, T)
-    ws = torch.empty(ws_b, dtype=torch.uint8, device=dev) if ws_b else None
-    for _ in range(args.warmup + args.steps):
-        K.kf_run(ctx.h, cuts, frames, W, mask, counts, ws)
+    if args.track:  # the whole hot path: fused chain with corner lists, selection, LK
+        KP = 256
+        n_pts = torch.zeros(T, dtype=torch.int32, device=dev)
+        idx = torch.zeros((T, KP), dtype=torch.int32, device=dev)
+        uu, vv = torch.zeros((T, KP), device=dev), torch.zeros((T, KP), device=dev)
+        st = torch.zeros((T, KP), dtype=torch.int32, device=dev)
+        ws = torch.empty(K.kf_track_workspace_bytes(ctx.h, W, H, T), dtype=torch.uint8, device=dev)
+        for _ in range(args.warmup + args.steps):
+            K.kf_track(ctx.h, frames, W, mask, counts, KP, n_pts, idx, uu, vv, st, ws)
+    else:
+        ws_b = K.kf_workspace_bytes(ctx.h, cuts, W, H, T)
+        ws = torch.empty(ws_b, dtype=torch.uint8, device=dev) if ws_b else None
+        for _ in range(args.warmup + args.steps):
+            K.kf_run(ctx.h, cuts, frames, W, mask, counts, ws)
     torch.cuda.synchronize()
     print(json.dumps({"profile_frames": T, "cuts": cuts, "counts_sum": int(counts.sum())}))
 
 
 def cpu_oracle_rate(frames: np.ndarray, W: int, budget_s: float = 12.0) -> dict:
-    """The FP64 oracle as it stands, OpenMP over frames on all host cores, on a bounded
-    prefix of the volume sized to about `budget_s` seconds."""
+    """The FP64 oracle as it stands, on the whole hot path (chain + corner selection +
+    LK per frame pair), OpenMP over frame pairs on all host cores, on a bounded prefix of
+    the volume sized to about `budget_s` seconds."""
     from oracle import chain as oc
     T, H, P = frames.shape
     t0 = time.perf_counter()
-    _, _, _, used = oc.chain_volume(frames[:4], W=W)
+    oc.track_volume(frames[:5], W=W)
     probe = time.perf_counter() - t0
-    n = int(max(4, min(T, budget_s / max(probe / 4, 1e-6))))
+    n = int(max(5, min(T, 1 + budget_s / max(probe / 4, 1e-6))))
     t0 = time.perf_counter()
-    _, _, _, used = oc.chain_volume(frames[:n], W=W)
+    _, _, _, _, _, used = oc.track_volume(frames[:n], W=W)
     dt = time.perf_counter() - t0
-    return {"value": n * H * W / dt / 1e6, "unit": UNIT, "cores": int(used), "kind": "oracle",
-            "sample": f"first {n} of {T} frames ({n * H * W / 1e6:.1f} Mpixel), FP64, {dt:.1f} s"}
+    return {"value": (n - 1) * H * W / dt / 1e6, "unit": UNIT, "cores": int(used), "kind": "oracle",
+            "sample": f"frame pairs of the first {n} of {T} frames ({(n - 1) * H * W / 1e6:.1f} Mpixel), "
+                      f"FP64 chain + tracking, {dt:.1f} s"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -164,21 +178,22 @@ def run_reference(args, rank: int, world: int):
     frames, P = make_video(0)
     from oracle import chain as oc
     T, H, W = SPEC.T, SPEC.H, SPEC.W
-    per_step = 24  # frames of the workload per timed step
+    per_step = 25  # frames of the workload per timed step (24 tracked frame pairs)
     for i in range(args.warmup):
-        oc.chain_volume(frames[(i * per_step) % T:(i * per_step) % T + per_step], W=W)
+        oc.track_volume(frames[(i * per_step) % T:(i * per_step) % T + per_step], W=W)
     times, used = [], 1
     for i in range(args.steps):
         s = (i * per_step) % (T - per_step)
         t0 = time.perf_counter()
-        _, _, _, used = oc.chain_volume(frames[s:s + per_step], W=W)
+        _, _, _, _, _, used = oc.track_volume(frames[s:s + per_step], W=W)
         times.append(time.perf_counter() - t0)
     ms = 1000 * sum(times) / len(times)
-    value = per_step * H * W / (ms / 1000) / 1e6
+    value = (per_step - 1) * H * W / (ms / 1000) / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_per_step": f"{per_step} frames", "impl": "FP64 CPU oracle"},
+            "config": {"workload": WORKLOAD, "sample_per_step": f"{per_step} frames ({per_step - 1} tracked pairs)",
+                       "impl": "FP64 CPU oracle: chain + corner selection + LK"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(used), "kind": "oracle",
                              "sample": f"{per_step} frames per step of the 1000-frame volume"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -203,15 +218,22 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     frames_h, P = make_video(rank)
     T, H, W = SPEC.T, SPEC.H, SPEC.W
+    KP = 256  # tracked points per frame
     frames_pin = torch.from_numpy(frames_h).pin_memory()
     frames = frames_pin.to(dev)
     mask = torch.zeros_like(frames)
     counts = torch.zeros(T, dtype=torch.int32, device=dev)
+    n_pts = torch.zeros(T, dtype=torch.int32, device=dev)
+    idx = torch.zeros((T, KP), dtype=torch.int32, device=dev)
+    uu = torch.zeros((T, KP), dtype=torch.float32, device=dev)
+    vv = torch.zeros((T, KP), dtype=torch.float32, device=dev)
+    st = torch.zeros((T, KP), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     ctx = K.Context(local_rank)
     cuts, _ = K.kf_plan(ctx.h, W, H, T)  # traffic-model plan: full fusion
     n_groups = bin(cuts).count("1") + 1
+    ws_track = torch.empty(K.kf_track_workspace_bytes(ctx.h, W, H, T), dtype=torch.uint8, device=dev)
 
     def barrier():
         if world > 1:
@@ -235,10 +257,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             ms = float(t.item())
         return ms
 
-    def fused():
+    def step():  # the whole hot path: fused chain, corner selection, LK tracking
+        K.kf_track(ctx.h, frames, W, mask, counts, KP, n_pts, idx, uu, vv, st, ws_track, stream)
+
+    def chain():  # the dominant kernel alone: the fused chain as the planner partitions it
         K.kf_run(ctx.h, cuts, frames, W, mask, counts, None, stream)
 
-    # clocks: sample across warm-up and the timed region
+    # clocks: sample across a ~1.5 s soak and the timed region
     try:
         gid = str(torch.cuda.get_device_properties(dev).uuid)
         gid = gid if gid.startswith("GPU-") else "GPU-" + gid
@@ -246,22 +271,22 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         gid = str(local_rank)
     clk = ClockSampler(gid)
     clk.start()
-    # soak ~1.5 s so the clock record covers the steady state
     t_soak = time.time()
     while time.time() - t_soak < 1.5:
-        fused()
+        step()
         torch.cuda.synchronize(dev)
-    t_a = time.time()
-    ms = timed(fused, args.steps, args.warmup)
+    ms = timed(step, args.steps, args.warmup)
+    ms_chain = timed(chain, args.steps, args.warmup)
     t_b = time.time()
     clk.stop()
     clocks = clk.summary(t_soak, t_b)
+    dev_err = K.kf_device_error(ctx.h)
 
     px = T * H * W
     value = world * px / (ms / 1000) / 1e6
     hbm_peak, peak_kind = peaks()
     alg_bytes = 2 * px + 4 * T  # frames read once, mask written once, counts
-    achieved = alg_bytes / (ms / 1000) / 1e9
+    achieved = alg_bytes / (ms_chain / 1000) / 1e9
     rec = kernel_counters() if T == 1000 else None
     traffic = rec["dram_bytes_per_launch_1000_frames"] if rec else None
     # instruction-issue roofline: 152 SMs x 4 schedulers x 1 warp instruction per cycle
@@ -269,7 +294,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e9  # G warp-instructions / s
     alu = None
     if rec:
-        ach = rec["warp_instructions_per_launch_1000_frames"] / (ms / 1000) / 1e9
+        ach = rec["warp_instructions_per_launch_1000_frames"] / (ms_chain / 1000) / 1e9
         alu = {"bound": "alu", "achieved": ach, "peak": issue_peak, "unit": "Gwarp-inst/s",
                "frac": ach / issue_peak, "peak_kind": "152 SMs x 4 schedulers x SM clock",
                "instructions_per_launch": rec["warp_instructions_per_launch_1000_frames"]}
@@ -282,47 +307,55 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ms_unf = timed(lambda: K.kf_run(ctx.h, unf_cuts, frames, W, mask_u, counts_u, ws, stream), max(3, args.steps // 4), 1)
     same = bool(torch.equal(mask_u, mask) and torch.equal(counts_u, counts))
     unf_bytes = 98 * px  # FP32 maps: sum over stages of input + output bytes per pixel
-    # FP16 maps, unfused (half the intermediate bytes)
+    # 16-bit maps, unfused (half the intermediate bytes)
     ctx16 = K.Context(local_rank, precision=K.KF_PREC_F16)
     ws16 = torch.empty(K.kf_workspace_bytes(ctx16.h, unf_cuts, W, H, T), dtype=torch.uint8, device=dev)
     ms_unf16 = timed(lambda: K.kf_run(ctx16.h, unf_cuts, frames, W, mask_u, counts_u, ws16, stream),
                      max(3, args.steps // 4), 1)
     del ws, ws16
 
-    # end to end through the public call: pinned host frames in, mask + counts out
+    # end to end through the public call: pinned host frames in; mask, counts and tracks out
     mask_h = torch.empty_like(frames_pin, device="cpu").pin_memory()
-    counts_h = torch.empty(T, dtype=torch.int32).pin_memory()
+    outs_d = (counts, n_pts, idx, uu, vv, st)
+    outs_h = [torch.empty_like(t, device="cpu").pin_memory() for t in outs_d]
 
     def e2e_step():
         frames.copy_(frames_pin, non_blocking=True)
-        K.kf_run(ctx.h, cuts, frames, W, mask, counts, None, stream)
+        step()
         mask_h.copy_(mask, non_blocking=True)
-        counts_h.copy_(counts, non_blocking=True)
+        for hst, d in zip(outs_h, outs_d):
+            hst.copy_(d, non_blocking=True)
     ms_e2e = timed(e2e_step, max(3, args.steps // 2), 1)
     h2d = frames_pin.numel()
-    d2h = mask_h.numel() + 4 * T
+    d2h = mask_h.numel() + sum(t.numel() * t.element_size() for t in outs_h)
+    tracked = int(n_pts.sum())
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames": T, "rows": H, "cols": W, "partition_cuts": cuts,
+        "config": {"workload": WORKLOAD, "frames": T, "rows": H, "cols": W, "step": "fused 8-stage chain + "
+                   f"top-{KP} corner selection + LK tracking per frame pair", "partition_cuts": cuts,
                    "groups": n_groups, "chunk_rows": 200, "cols_per_lane": 4,
                    "l2": "inputs larger than L2 (480 MB frames, 480 MB mask), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "frames_per_s": world * T / (ms / 1000),
+        "tracked_points_per_s": world * tracked / (ms / 1000),
+        "chain_only": {"value": world * px / (ms_chain / 1000) / 1e6, "ms_per_step": ms_chain,
+                       "kernel": "group_kernel<1,8> (full fusion)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": alg_bytes},
+                     "kernel": "fused chain, timed alone", "algorithmic_bytes_per_launch": alg_bytes},
         "alu_roofline": alu,
         "unfused": {"value": world * px / (ms_unf / 1000) / 1e6, "ms_per_step": ms_unf, "kernels": 8,
                     "hbm_frac": unf_bytes / (ms_unf / 1000) / 1e9 / hbm_peak, "bit_identical_to_fused": same,
-                    "fused_speedup": ms_unf / ms},
+                    "fused_chain_speedup": ms_unf / ms_chain},
         "unfused_f16": {"value": world * px / (ms_unf16 / 1000) / 1e6, "ms_per_step": ms_unf16,
                         "hbm_frac": 50 * px / (ms_unf16 / 1000) / 1e9 / hbm_peak},
         "e2e": {"value": world * px / (ms_e2e / 1000) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e},
-        "gpu_launches": n_groups * args.steps,
+        "gpu_launches": 3 * args.steps,  # fused chain, selection, LK per step
+        "device_error": dev_err,
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -343,6 +376,7 @@ def main():
     ap.add_argument("--profile", type=int, default=0, help="profiler case: fused chain only, on T frames")
     ap.add_argument("--cuts", type=int, default=-1, help="partition for --profile (default: planned)")
     ap.add_argument("--f16", action="store_true", help="FP16 maps for --profile")
+    ap.add_argument("--track", action="store_true", help="--profile the whole path with tracking")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))

@@ -55,6 +55,8 @@ def lib():
         L.kfo_lk.argtypes = [i32, i32, vp, vp, vp, vp, i32, vp, i32, vp, vp, vp]
         L.kfo_track_pair.restype = i32
         L.kfo_track_pair.argtypes = [i32, i32, vp, vp, i64, dbl, dbl, i32, i32, vp, vp, vp, vp]
+        L.kfo_track_volume.restype = i32
+        L.kfo_track_volume.argtypes = [i32, i32, i32, vp, i64, dbl, dbl, i32, i32, vp, vp, vp, vp, vp, i32]
         _lib = L
     return _lib
 
@@ -188,3 +190,22 @@ def track_pair(prev: np.ndarray, cur: np.ndarray, W: int | None = None, K: int =
     if n < 0:
         raise MemoryError("oracle allocation failed")
     return idx[:n].copy(), u[:n].copy(), v[:n].copy(), st[:n].copy()
+
+
+def track_volume(frames: np.ndarray, W: int | None = None, K: int = 256, win: int = 3, k: float = HARRIS_K,
+                 thr: float = THRESHOLD, nthreads: int = 0):
+    """Tracking of every frame pair of frames [T, H, pitch] on all host cores.
+
+    Returns (n [T], idx [T, K], u [T, K], v [T, K], status [T, K], threads used)."""
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    T, H, P = frames.shape
+    W = P if W is None else W
+    n = np.zeros(T, dtype=np.int32)
+    idx = np.full((T, K), -1, dtype=np.int32)
+    u, v = np.zeros((T, K)), np.zeros((T, K))
+    st = np.zeros((T, K), dtype=np.int32)
+    used = lib().kfo_track_volume(T, H, W, _p(frames), P, k, thr, K, win, _p(n), _p(idx), _p(u), _p(v), _p(st),
+                                  nthreads)
+    if T > 1 and int(n[1:].min()) < 0:
+        raise MemoryError("oracle allocation failed")
+    return n, idx, u, v, st, int(used)

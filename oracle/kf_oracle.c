@@ -294,3 +294,26 @@ int kfo_track_pair(int H, int W, const uint8_t *prev, const uint8_t *cur, int64_
     free(mask);
     return np;
 }
+
+/* Tracking over a volume: frame pairs (t-1, t) for t = 1..T-1, one pair per OpenMP
+ * task; frame 0 has no points. Outputs are T*K arrays (row t = frame t) and n[T].
+ * Returns the number of threads used. */
+int kfo_track_volume(int T, int H, int W, const uint8_t *in, int64_t pitch, double k, double thr, int K, int win,
+                     int32_t *n, int32_t *idx, double *u, double *v, int32_t *status, int nthreads)
+{
+    int used = 1;
+    if (T > 0) n[0] = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int t = 1; t < T; ++t) {
+        const int64_t o = (int64_t)t * K;
+        n[t] = kfo_track_pair(H, W, in + (int64_t)(t - 1) * H * pitch, in + (int64_t)t * H * pitch, pitch, k, thr, K, win,
+                              idx + o, u + o, v + o, status + o);
+#ifdef _OPENMP
+        if (t == 1) used = omp_get_num_threads();
+#endif
+    }
+    return used;
+}

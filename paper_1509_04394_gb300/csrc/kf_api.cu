@@ -243,7 +243,8 @@ kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &
         cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)T, s);
         if (e != cudaSuccess) return cuda_fail(c, e);
     }
-    kf::LaunchFn fn = launcher(A, B, f16 ? 1 : 0);
+    kf::LaunchFn fn = cand ? ((A == 1 && B == kf::NSTAGES) ? kf::launch_chain_with_candidates : nullptr)
+                           : launcher(A, B, f16 ? 1 : 0);
     if (!fn) return KF_EINVAL;
     const int e = fn(p, (unsigned)blocks, s);
     if (e != 0) return cuda_fail(c, (cudaError_t)e);

@@ -468,7 +468,7 @@ template <int K, bool F16>
 using MapT = std::conditional_t<K == 0, uint8_t, std::conditional_t<!F16, float, std::conditional_t<(K <= 3), uint16_t, __half>>>;
 
 // Shared-memory plan of a group: mbarriers and NST input stages of RB rows.
-template <int A, int B, bool F16> struct SmemPlan {
+template <int A, int B, bool F16, bool CAND = false> struct SmemPlan {
     static constexpr int NIN = map_channels(A - 1);
     static constexpr int ELEM = (int)sizeof(MapT<A - 1, F16>);
     static constexpr int ROW_BYTES = STRIP * ELEM;               // one staged row of one channel
@@ -479,18 +479,21 @@ template <int A, int B, bool F16> struct SmemPlan {
     static constexpr bool HAS6 = A <= 6 && 6 <= B;
     static constexpr int BAR_OFF = 0;
     static constexpr int IN_OFF = 128;
-    static constexpr int BOX_OFF = IN_OFF + NST * STAGE_BYTES;  // end of the plan
-    static constexpr int BYTES = BOX_OFF;
+    static constexpr int CAND_OFF = IN_OFF + NST * STAGE_BYTES;
+    static constexpr int CAND_BLOCK = RB * STRIP;  // corners of one 5-row block, at most
+    static constexpr int CAND_MAX = 1536;          // per-warp buffer, flushed when it may not hold another block
+    static constexpr int BYTES = CAND_OFF + (CAND ? CAND_MAX * 8 : 0);
 };
 
 // ------------------------------------------------------------------ the group kernel
-template <int A, int B, bool F16>
+template <int A, int B, bool F16, bool CAND = false>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN_BLOCKS_BOX : MIN_BLOCKS) group_kernel(const __grid_constant__ GroupParams p)
 {
+    static_assert(!CAND || B == 8, "corner candidates come from the NMS stage");
     static_assert(1 <= A && A <= B && B <= 8, "stage range");
     static_assert(C == 4, "lanes own 4 columns");
     static_assert(WARPS_PER_BLOCK == 1, "one warp per block: the staging ring is per warp");
-    using SP = SmemPlan<A, B, F16>;
+    using SP = SmemPlan<A, B, F16, CAND>;
     using TIN = MapT<A - 1, F16>;
     constexpr int RXT = sum_rx(A, B);
     constexpr int RYT = sum_ry(A, B);
@@ -554,6 +557,24 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
     std::conditional_t<HAS6, BoxV, Empty> s6{};
     std::conditional_t<HAS8, NmsV, Empty> s8{};
     unsigned count = 0;
+    [[maybe_unused]] unsigned long long *cand_buf = reinterpret_cast<unsigned long long *>(smem + SP::CAND_OFF);
+    [[maybe_unused]] unsigned cand_fill = 0;  // entries in cand_buf (warp-uniform)
+    auto flush_candidates = [&](bool force) {
+        if constexpr (CAND) {
+            if (cand_fill && (force || cand_fill > (unsigned)(SP::CAND_MAX - SP::CAND_BLOCK))) {
+                __syncwarp();
+                unsigned pos = 0;
+                if (lane == 0) pos = atomicAdd(reinterpret_cast<unsigned *>(p.cand_count) + frame, cand_fill);
+                pos = __shfl_sync(FULL, pos, 0);
+                unsigned long long *dst = p.cand + (int64_t)frame * p.cand_cap;
+                for (unsigned i = lane; i < cand_fill; i += 32)
+                    if (pos + i < (unsigned)p.cand_cap) dst[pos + i] = cand_buf[i];
+                if (lane == 0 && pos + cand_fill > (unsigned)p.cand_cap) atomicOr(p.err, DEVERR_OVERFLOW);
+                __syncwarp();
+                cand_fill = 0;
+            }
+        }
+    };
     bool failed = false;
     int k_fail = 0;
     const int64_t out_frame = (int64_t)frame * p.out_fstride;
@@ -654,34 +675,25 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
         }
         // ---- group output row t - RYT
         const int o = t - RYT;
-        if constexpr (B == 8) {
-            // corner candidates of the tracking stage: one warp-aggregated append per row
-            if (p.cand && o >= y0) {  // warp-uniform
+        if constexpr (CAND) {
+            // corner candidates of the tracking stage: appended to the warp's buffer in
+            // shared memory (positions from four ballots); one global atomic per flush, and
+            // a flush only when the buffer might not hold another 5-row block, or at the end
+            if (o >= y0) {  // warp-uniform
                 const unsigned kept = bits & out_mask;
-                const unsigned n = __popc(kept);
-                unsigned incl = n;
+                const unsigned lt = (1u << lane) - 1u;
+                unsigned base = cand_fill;
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const unsigned y = __shfl_up_sync(FULL, incl, d);
-                    if (lane >= d) incl += y;
+                for (int c = 0; c < C; ++c) {
+                    const unsigned b = __ballot_sync(FULL, kept >> c & 1);
+                    if (kept >> c & 1) {
+                        const unsigned raster = (unsigned)(o * W + x0 + c);
+                        cand_buf[base + __popc(b & lt)] =
+                            (unsigned long long)__float_as_uint(centre[c]) << 32 | (0xffffffffu - raster);
+                    }
+                    base += __popc(b);
                 }
-                const unsigned total = __shfl_sync(FULL, incl, 31);
-                if (total) {
-                    unsigned base = 0;
-                    if (lane == 31) base = atomicAdd(reinterpret_cast<unsigned *>(p.cand_count) + frame, total);
-                    base = __shfl_sync(FULL, base, 31);
-                    unsigned pos = base + incl - n;
-                    unsigned long long *dst = p.cand + (int64_t)frame * p.cand_cap;
-#pragma unroll
-                    for (int c = 0; c < C; ++c)
-                        if (kept >> c & 1) {
-                            const unsigned raster = (unsigned)(o * W + x0 + c);
-                            if (pos < (unsigned)p.cand_cap)
-                                dst[pos] = (unsigned long long)__float_as_uint(centre[c]) << 32 | (0xffffffffu - raster);
-                            ++pos;
-                        }
-                    if (lane == 31 && base + total > (unsigned)p.cand_cap) atomicOr(p.err, DEVERR_OVERFLOW);
-                }
+                cand_fill = base;
             }
         }
         if (o >= y0 && out_mask) {  // o < y1 holds: t < y1 + RYT
@@ -738,6 +750,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
         step(P3{}, t + 3, sbuf);
         if (t + 4 >= t_end) break;
         step(P4{}, t + 4, sbuf);
+        flush_candidates(false);
         if (k + SP::NST < n_stages) {
             __syncwarp();  // every lane has read the stage
             if (lane == 0) {
@@ -754,6 +767,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
         for (int k = k_fail; k < issued; ++k) mbar_wait(bars + (k % SP::NST), (unsigned)(k / SP::NST) & 1u);
         return;
     }
+    flush_candidates(true);  // what is left at the end of the job
     if constexpr (B == 8) {
         const unsigned tot = __reduce_add_sync(FULL, count);
         if (lane == 0 && tot) atomicAdd(p.counts + frame, (int)tot);

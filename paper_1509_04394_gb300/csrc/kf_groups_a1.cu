@@ -14,6 +14,14 @@ int launch(const GroupParams &p, unsigned grid, void *stream)
 }
 }  // namespace
 
+// the fully fused chain that also lists every frame's corners for the tracking stage
+int launch_chain_with_candidates(const GroupParams &p, unsigned grid, void *stream)
+{
+    group_kernel<1, 8, false, true><<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<1, 8, false, true>::BYTES,
+                                      static_cast<cudaStream_t>(stream)>>>(p);
+    return (int)cudaGetLastError();
+}
+
 LaunchFn launcher_a1(int B, int f16)
 {
     switch (B) {

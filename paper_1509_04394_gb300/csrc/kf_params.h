@@ -96,6 +96,7 @@ LaunchFn launcher_a5(int B, int f16);
 LaunchFn launcher_a6(int B, int f16);
 LaunchFn launcher_a7(int B, int f16);
 LaunchFn launcher_a8(int B, int f16);
+int launch_chain_with_candidates(const GroupParams &p, unsigned grid, void *stream);
 int launch_select(const unsigned long long *cand, const int *cand_count, int cap, int K, int T, int32_t *n_points,
                   int32_t *idx, void *stream);
 int launch_lk(const uint8_t *frames, int64_t pitch, int W, int H, int T, int K, const int32_t *n_points,

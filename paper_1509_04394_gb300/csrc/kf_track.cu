@@ -9,7 +9,7 @@
 //      stronger corners and, at equal R, lower raster indices); an exact MSB-first radix
 //      select (8 passes of 8 bits) finds the K-th largest key, a bitonic sort orders the
 //      winners;
-//   2. lk_kernel: per selected point of frame t >= 1, one Lucas-Kanade step against
+//   2. lk_kernel: per selected point of frame t >= 1 (one half-warp each), one Lucas-Kanade step against
 //      frame t-1 over a 7x7 window: A = sum [gx^2, gx gy; gx gy, gy^2],
 //      b = sum [gx gt, gy gt], (u, v) = -A^-1 b, gx, gy = Sobel of the smoothed frame t
 //      over 8, gt = difference of the smoothed frames. The smoothed patches are recomputed
@@ -109,68 +109,146 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const unsigned long
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// smoothed frame g (scaled by 65280, exact) on the grid rows [r0, r0+nr) x cols [c0, c0+nc)
-__device__ void smooth_grid(const uint8_t *f, int64_t pitch, int W, int H, int r0, int nr, int c0, int nc, float (&g)[9][9])
-{
-    // horizontal pass on the rows the vertical pass reads (clamped), the chain's order
-    const int q0 = max(r0 - 2, 0), q1 = min(r0 + nr - 1 + 2, H - 1);
-    float g1[13][9];
-    for (int y = q0; y <= q1; ++y) {
-        const uint8_t *row = f + (int64_t)y * pitch;
-        for (int j = 0; j < nc; ++j) {
-            const int x = c0 + j;
-            const float a = row[clampi(x - 2, 0, W - 1)], b = row[clampi(x - 1, 0, W - 1)], c = row[x],
-                        d = row[clampi(x + 1, 0, W - 1)], e = row[clampi(x + 2, 0, W - 1)];
-            float t = a + e;
-            t = fmaf(4.0f, b + d, t);
-            g1[y - q0][j] = fmaf(6.0f, c, t);
-        }
-    }
-    for (int i = 0; i < nr; ++i) {
-        const int y = r0 + i;
-        for (int j = 0; j < nc; ++j) {
-            const float a = g1[clampi(y - 2, 0, H - 1) - q0][j], b = g1[clampi(y - 1, 0, H - 1) - q0][j], c = g1[y - q0][j],
-                        d = g1[clampi(y + 1, 0, H - 1) - q0][j], e = g1[clampi(y + 2, 0, H - 1) - q0][j];
-            g[i][j] = (a + e) + 4.0f * (b + d) + 6.0f * c;  // integers < 2^24: exact in any order
-        }
-    }
-}
+constexpr unsigned FULLM = 0xffffffffu;
+constexpr int LK_WARPS = 4;  // warps per block; each half-warp (16 lanes) takes one point
 
-__global__ void __launch_bounds__(128) lk_kernel(const uint8_t *frames, int64_t pitch, int W, int H, int T, int K,
-                                                 const int32_t *n_points, const int32_t *idx, float *u_out, float *v_out,
-                                                 int32_t *status)
+// One half-warp per point. The clamped rows and columns within 4 of the point form a grid
+// of nr x nc (<= 9 x 9) positions that holds every smoothed value the 7x7 window and its
+// Sobel neighbours read. Lane j < nq of the half computes the horizontal Gaussian of frame
+// row q0 + j on the grid columns; lane i < nr gathers its five vertical taps by shuffles
+// and holds smoothed grid row r0 + i; lane d < 7 accumulates window row d - 3. All values
+// up to the Sobel output are integers below 2^24, exact in FP32 and equal to the chain's.
+__global__ void __launch_bounds__(32 * LK_WARPS) lk_kernel(const uint8_t *frames, int64_t pitch, int W, int H, int T,
+                                                           int K, const int32_t *n_points, const int32_t *idx,
+                                                           float *u_out, float *v_out, int32_t *status)
 {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)T * K) return;
-    const int frame = (int)(gid / K), i = (int)(gid % K);
-    if (frame == 0 || i >= n_points[frame]) return;
-    const int p = idx[gid];
+    const int lane = threadIdx.x & 15;  // lane within the half-warp
+    const int64_t gid = ((int64_t)blockIdx.x * LK_WARPS + (threadIdx.x >> 5)) * 2 + ((threadIdx.x >> 4) & 1);
+    const int frame_g = (int)(gid / K), i = (int)(gid % K);
+    const bool valid = gid < (int64_t)T * K && frame_g > 0 && i < n_points[frame_g];
+    if (!__any_sync(FULLM, valid)) return;  // warp-uniform
+    // an idle half works on a stand-in point (row 0, column 0 of frames 0 and 1) and stores nothing
+    const int frame = valid ? frame_g : 1;
+    const int p = valid ? idx[gid] : 0;
     const int py = p / W, px = p % W;
-    // grid of the clamped rows/columns within 4 of the point: holds every g the 7x7
-    // window and its Sobel neighbours read
     const int r0 = max(py - 4, 0), nr = min(py + 4, H - 1) - r0 + 1;
     const int c0 = max(px - 4, 0), nc = min(px + 4, W - 1) - c0 + 1;
-    float gt[9][9], gp[9][9];
+    const int q0 = max(r0 - 2, 0), nq = min(r0 + nr - 1 + 2, H - 1) - q0 + 1;
     const int64_t fstride = (int64_t)H * pitch;
-    smooth_grid(frames + (int64_t)frame * fstride, pitch, W, H, r0, nr, c0, nc, gt);
-    smooth_grid(frames + (int64_t)(frame - 1) * fstride, pitch, W, H, r0, nr, c0, nc, gp);
-    float a00 = 0, a01 = 0, a11 = 0, b0 = 0, b1 = 0;
-    for (int dy = -3; dy <= 3; ++dy) {
-        const int qy = clampi(py + dy, 0, H - 1);
-        const int ym = clampi(qy - 1, 0, H - 1) - r0, y0 = qy - r0, yp = clampi(qy + 1, 0, H - 1) - r0;
-        for (int dx = -3; dx <= 3; ++dx) {
-            const int qx = clampi(px + dx, 0, W - 1);
-            const int xm = clampi(qx - 1, 0, W - 1) - c0, x0 = qx - c0, xq = clampi(qx + 1, 0, W - 1) - c0;
-            const float ix = (gt[ym][xq] - gt[ym][xm]) + 2.0f * (gt[y0][xq] - gt[y0][xm]) + (gt[yp][xq] - gt[yp][xm]);
-            const float iy = (gt[yp][xm] - gt[ym][xm]) + 2.0f * (gt[yp][x0] - gt[ym][x0]) + (gt[yp][xq] - gt[ym][xq]);
-            const float it = gt[y0][x0] - gp[y0][x0];
-            a00 = fmaf(ix, ix, a00);
-            a01 = fmaf(ix, iy, a01);
-            a11 = fmaf(iy, iy, a11);
-            b0 = fmaf(ix, it, b0);
-            b1 = fmaf(iy, it, b1);
+    const uint8_t *fc = frames + (int64_t)frame * fstride, *fp = fc - fstride;
+
+    // horizontal pass: lane j holds g1 of row q0 + j (both frames) on the grid columns;
+    // the lane loads the 13 clamped bytes of its row once per frame
+    float h_c[9], h_p[9];
+    {
+        const int y = q0 + min(lane, nq - 1);
+        const uint8_t *rc = fc + (int64_t)y * pitch, *rp = fp + (int64_t)y * pitch;
+        float bc[13], bp[13];
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {  // byte j: column c0 - 2 + j, clamped
+            const int x = clampi(c0 - 2 + j, 0, W - 1);
+            bc[j] = (float)rc[x];
+            bp[j] = (float)rp[x];
+        }
+        const bool inner = (c0 >= 2) && (c0 + 10 <= W - 1);  // no clamping inside the 13 bytes
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            if (inner) {
+                float t = bc[j] + bc[j + 4];
+                t = fmaf(4.0f, bc[j + 1] + bc[j + 3], t);
+                h_c[j] = fmaf(6.0f, bc[j + 2], t);
+                float u = bp[j] + bp[j + 4];
+                u = fmaf(4.0f, bp[j + 1] + bp[j + 3], u);
+                h_p[j] = fmaf(6.0f, bp[j + 2], u);
+            } else {  // grid column x = c0 + j (clamped to the grid) and its clamped taps
+                const int x = c0 + min(j, nc - 1);
+                float t = (float)rc[clampi(x - 2, 0, W - 1)] + (float)rc[clampi(x + 2, 0, W - 1)];
+                t = fmaf(4.0f, (float)rc[clampi(x - 1, 0, W - 1)] + (float)rc[clampi(x + 1, 0, W - 1)], t);
+                h_c[j] = fmaf(6.0f, (float)rc[x], t);
+                float u = (float)rp[clampi(x - 2, 0, W - 1)] + (float)rp[clampi(x + 2, 0, W - 1)];
+                u = fmaf(4.0f, (float)rp[clampi(x - 1, 0, W - 1)] + (float)rp[clampi(x + 1, 0, W - 1)], u);
+                h_p[j] = fmaf(6.0f, (float)rp[x], u);
+            }
         }
     }
+    // vertical pass: lane i holds smoothed row r0 + i
+    float g_c[9], g_p[9];
+    {
+        const int y = r0 + min(lane, nr - 1);
+        int src[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) src[k] = clampi(y + k - 2, 0, H - 1) - q0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            float a[5], b[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                a[k] = __shfl_sync(FULLM, h_c[j], src[k], 16);
+                b[k] = __shfl_sync(FULLM, h_p[j], src[k], 16);
+            }
+            g_c[j] = (a[0] + a[4]) + 4.0f * (a[1] + a[3]) + 6.0f * a[2];
+            g_p[j] = (b[0] + b[4]) + 4.0f * (b[1] + b[3]) + 6.0f * b[2];
+        }
+    }
+    // window row d = lane - 3 (lanes 0..6): Sobel rows ym, y0, yp of the clamped window row
+    const int dy = min(lane, 6) - 3;
+    const int qy = clampi(py + dy, 0, H - 1);
+    const int lm = clampi(qy - 1, 0, H - 1) - r0, l0 = qy - r0, lp = clampi(qy + 1, 0, H - 1) - r0;
+    float gm[9], gz[9], gq[9], gpz[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        gm[j] = __shfl_sync(FULLM, g_c[j], lm, 16);
+        gz[j] = __shfl_sync(FULLM, g_c[j], l0, 16);
+        gq[j] = __shfl_sync(FULLM, g_c[j], lp, 16);
+        gpz[j] = __shfl_sync(FULLM, g_p[j], l0, 16);
+    }
+    float a00 = 0, a01 = 0, a11 = 0, b0 = 0, b1 = 0;
+    auto accumulate = [&](float vm_m, float vm_0, float vm_q, float vz_m, float vz_0, float vz_q, float vq_m, float vq_0,
+                          float vq_q, float vp_0) {
+        const float ix = (vm_q - vm_m) + 2.0f * (vz_q - vz_m) + (vq_q - vq_m);
+        const float iy = (vq_m - vm_m) + 2.0f * (vq_0 - vm_0) + (vq_q - vm_q);
+        const float it = vz_0 - vp_0;
+        a00 = fmaf(ix, ix, a00);
+        a01 = fmaf(ix, iy, a01);
+        a11 = fmaf(iy, iy, a11);
+        b0 = fmaf(ix, it, b0);
+        b1 = fmaf(iy, it, b1);
+    };
+    if (lane < 7) {
+        if (px >= 4 && px <= W - 5) {  // no column clamping: grid column of dx is dx + 4
+#pragma unroll
+            for (int dx = -3; dx <= 3; ++dx) {
+                const int m = dx + 3, z = dx + 4, q = dx + 5;
+                accumulate(gm[m], gm[z], gm[q], gz[m], gz[z], gz[q], gq[m], gq[z], gq[q], gpz[z]);
+            }
+        } else {
+#pragma unroll
+            for (int dx = -3; dx <= 3; ++dx) {
+                const int qx = clampi(px + dx, 0, W - 1);
+                const int xm = clampi(qx - 1, 0, W - 1) - c0, x0 = qx - c0, xq = clampi(qx + 1, 0, W - 1) - c0;
+                // columns are runtime indices into 9-element rows: select without local memory
+                float vm_m = 0, vm_q = 0, vz_m = 0, vz_0 = 0, vz_q = 0, vq_m = 0, vq_0 = 0, vq_q = 0, vm_0 = 0, vp_0 = 0;
+#pragma unroll
+                for (int j = 0; j < 9; ++j) {
+                    vm_m = j == xm ? gm[j] : vm_m; vm_0 = j == x0 ? gm[j] : vm_0; vm_q = j == xq ? gm[j] : vm_q;
+                    vz_m = j == xm ? gz[j] : vz_m; vz_0 = j == x0 ? gz[j] : vz_0; vz_q = j == xq ? gz[j] : vz_q;
+                    vq_m = j == xm ? gq[j] : vq_m; vq_0 = j == x0 ? gq[j] : vq_0; vq_q = j == xq ? gq[j] : vq_q;
+                    vp_0 = j == x0 ? gpz[j] : vp_0;
+                }
+                accumulate(vm_m, vm_0, vm_q, vz_m, vz_0, vz_q, vq_m, vq_0, vq_q, vp_0);
+            }
+        }
+    }
+    // sum the 7 window rows (fixed order: lanes 0..6 by a tree within the warp)
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+        a00 += __shfl_down_sync(FULLM, a00, off, 16);
+        a01 += __shfl_down_sync(FULLM, a01, off, 16);
+        a11 += __shfl_down_sync(FULLM, a11, off, 16);
+        b0 += __shfl_down_sync(FULLM, b0, off, 16);
+        b1 += __shfl_down_sync(FULLM, b1, off, 16);
+    }
+    if (lane != 0 || !valid) return;
     // scaled units: gx = ix / (8 s), gt = it / s with s = 65280, so -A^-1 b = -8 A'^-1 b'
     const double A00 = a00, A01 = a01, A11 = a11, B0 = b0, B1 = b1;
     const double det = A00 * A11 - A01 * A01;
@@ -200,8 +278,9 @@ int launch_lk(const uint8_t *frames, int64_t pitch, int W, int H, int T, int K, 
               const int32_t *idx, float *u, float *v, int32_t *status, void *stream)
 {
     const int64_t n = (int64_t)T * K;
-    const unsigned blocks = (unsigned)((n + 127) / 128);
-    lk_kernel<<<blocks, 128, 0, static_cast<cudaStream_t>(stream)>>>(frames, pitch, W, H, T, K, n_points, idx, u, v, status);
+    const unsigned blocks = (unsigned)((n + 2 * LK_WARPS - 1) / (2 * LK_WARPS));
+    lk_kernel<<<blocks, 32 * LK_WARPS, 0, static_cast<cudaStream_t>(stream)>>>(frames, pitch, W, H, T, K, n_points, idx, u,
+                                                                                v, status);
     return (int)cudaGetLastError();
 }
 

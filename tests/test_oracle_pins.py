@@ -270,3 +270,17 @@ def test_lk_tracks_slow_checker_patches_of_the_synthetic_video():
                     errs.append(np.hypot(u[i] - sc.vx[o], v[i] - sc.vy[o]))
     assert len(errs) >= 30
     assert np.median(errs) <= 0.25
+
+
+def test_track_volume_is_track_pair_on_every_frame_pair():
+    from synth import video as sv
+    fr, _ = sv.generate(sv.VideoSpec(T=4, H=60, W=70, seed=9, n_blobs=6, n_patches=4))
+    n, idx, u, v, st, used = oc.track_volume(fr, K=32)
+    assert n[0] == 0 and used >= 1
+    for t in range(1, 4):
+        i2, u2, v2, s2 = oc.track_pair(fr[t - 1], fr[t], K=32)
+        assert n[t] == len(i2)
+        np.testing.assert_array_equal(idx[t, :n[t]], i2)
+        np.testing.assert_array_equal(u[t, :n[t]], u2)
+        np.testing.assert_array_equal(v[t, :n[t]], v2)
+        np.testing.assert_array_equal(st[t, :n[t]], s2)
