@@ -233,6 +233,38 @@ kf_status kf_track_workspace_bytes(const kf_ctx *ctx, int64_t W, int64_t H, int6
 kf_status kf_track(kf_ctx *ctx, const kf_video *video, const kf_corners *out, const kf_tracks *tracks,
                    void *workspace, size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------------ batches */
+/* Many independent videos of different sizes and lengths through the fully fused chain
+ * (and optionally the tracking stages) as ONE persistent kernel launch: every resident
+ * warp pops jobs (video, frame, row chunk, column strip) from one global queue until it
+ * is empty, so long and short videos share the GPU without a per-video launch. The
+ * launch, the counter resets and the batched selection and LK kernels are captured once
+ * into a CUDA graph by kf_batch_create and replayed by kf_batch_run. FP32 contexts only
+ * (full fusion has no maps between groups). The chunk height is the context's
+ * (kf_set_chunk_rows / kf_tune_chunk_rows) at creation. */
+typedef struct kf_batch kf_batch;
+/* Workspace of a batch of n videos; track_K = 0 without tracking, else the points per
+ * frame (1..1024). */
+kf_status kf_batch_workspace_bytes(const kf_ctx *ctx, const kf_video *videos, int n, int track_K, size_t *bytes);
+/* videos, outs: n entries; tracks: NULL, or n entries with the same K. The workspace
+ * (>= kf_batch_workspace_bytes, 256-byte aligned) and every buffer named here must stay
+ * allocated and in place while the batch exists: the graph refers to them. Synchronous
+ * (copies the per-video descriptors into the workspace, captures and instantiates the
+ * graph). */
+kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners *outs, const kf_tracks *tracks, int n,
+                          void *workspace, size_t workspace_bytes, kf_batch **out);
+/* Enqueue one run of the batch on `stream` (asynchronous): every video's mask, counts and,
+ * if requested, tracks are rewritten. */
+kf_status kf_batch_run(kf_batch *batch, void *stream);
+kf_status kf_batch_destroy(kf_batch *batch);
+
+/* Autotuner of the executor's tile height: runs the fully fused chain on `video` once
+ * per candidate chunk height (after one warm-up), `reps` times each, times them with CUDA
+ * events on `stream`, keeps the fastest in the context and returns it (and its time in
+ * ms when best_ms is not NULL). Synchronous. */
+kf_status kf_tune_chunk_rows(kf_ctx *ctx, const kf_video *video, const kf_corners *out, const int *candidates, int n,
+                             int reps, void *stream, int *best_rows, float *best_ms);
+
 /* ------------------------------------------------------------------ no-allocation run */
 /* kf_run with the workspace in a fixed array that the library itself holds on every GPU
  * that loads it (KF_STATIC_WORKSPACE_BYTES per GPU, kept until the process exits). The

@@ -201,13 +201,11 @@ kf_status check_map(const kf_map *m, int stage_out, int precision, int64_t W, in
     return KF_OK;
 }
 
-// Enqueue group [A..B] (1-based) with already validated maps.
-kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &out, int64_t W, int64_t H, int64_t T,
-                       int32_t *counts, cudaStream_t s, unsigned long long *cand = nullptr, int *cand_count = nullptr,
-                       int64_t cand_cap = 0)
+// Parameter block of group [A..B] (1-based) over already validated maps.
+kf_status fill_params(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &out, int64_t W, int64_t H, int64_t T,
+                      int32_t *counts, unsigned long long *cand, int *cand_count, int64_t cand_cap, kf::GroupParams &p)
 {
-    if (T == 0) return KF_OK;
-    kf::GroupParams p{};
+    p = kf::GroupParams{};
     for (int i = 0; i < 3; ++i) {
         p.in[i] = in.plane[i];
         p.out[i] = out.plane[i];
@@ -237,8 +235,21 @@ kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &
     // FP16 maps (stages 4-7) hold true units; uint16 and FP32 maps hold scaled units
     p.in_scale = (f16 && A - 1 >= 4) ? (float)kf::map_scale(A - 1) : 1.0f;
     p.out_scale = (f16 && B >= 4 && B < 8) ? (float)(1.0 / kf::map_scale(B)) : 1.0f;
+    if (p.n_jobs > 0x7fffffff) return KF_EINVAL;
+    return KF_OK;
+}
+
+// Enqueue group [A..B] (1-based) with already validated maps.
+kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &out, int64_t W, int64_t H, int64_t T,
+                       int32_t *counts, cudaStream_t s, unsigned long long *cand = nullptr, int *cand_count = nullptr,
+                       int64_t cand_cap = 0)
+{
+    if (T == 0) return KF_OK;
+    kf::GroupParams p;
+    kf_status st = fill_params(c, A, B, in, out, W, H, T, counts, cand, cand_count, cand_cap, p);
+    if (st != KF_OK) return st;
+    const bool f16 = c->precision == KF_PREC_F16;
     const int64_t blocks = p.n_jobs;  // one warp (one job) per block
-    if (blocks > 0x7fffffff) return KF_EINVAL;
     if (B == 8) {
         cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)T, s);
         if (e != cudaSuccess) return cuda_fail(c, e);
@@ -610,11 +621,265 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf
     kf_status st = launch_group(ctx, 1, kf::NSTAGES, fin, fout, v->W, v->H, v->T, o->counts, s, cand, cand_count, cap);
     if (st != KF_OK) return st;
     // the tracking set, after the kernel-to-kernel dependency
-    int r = kf::launch_select(cand, cand_count, (int)cap, tr->K, (int)v->T, tr->n_points, tr->idx, stream);
+    kf::TrackVideo tv{};
+    tv.frames = v->frames;
+    tv.pitch = v->pitch;
+    tv.W = (int)v->W;
+    tv.H = (int)v->H;
+    tv.T = (int)v->T;
+    tv.cand = cand;
+    tv.cand_count = cand_count;
+    tv.cand_cap = (int)cap;
+    tv.n_points = tr->n_points;
+    tv.idx = tr->idx;
+    tv.status = tr->status;
+    tv.u = tr->u;
+    tv.v = tr->v;
+    tv.frame_begin = 0;
+    int r = kf::launch_select(tv, nullptr, 1, v->T, tr->K, stream);
     if (r) return cuda_fail(ctx, (cudaError_t)r);
-    r = kf::launch_lk(v->frames, v->pitch, (int)v->W, (int)v->H, (int)v->T, tr->K, tr->n_points, tr->idx, tr->u, tr->v,
-                      tr->status, stream);
+    r = kf::launch_lk(tv, nullptr, 1, v->T, tr->K, stream);
     if (r) return cuda_fail(ctx, (cudaError_t)r);
+    return KF_OK;
+}
+
+}  // extern "C"
+
+struct kf_batch {
+    int device = -1;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+struct BatchLayout {
+    size_t params = 0, items = 0, queue = 0, tracks = 0, cand_count = 0, cand = 0, total = 0;
+};
+
+BatchLayout batch_layout(const kf_video *videos, int n, bool track)
+{
+    BatchLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o = (size_t)round_up((int64_t)(o + bytes), 256); return at; };
+    L.params = take(sizeof(kf::GroupParams) * (size_t)n);
+    L.items = take(sizeof(int64_t) * (size_t)(n + 1));
+    L.queue = take(sizeof(unsigned long long));
+    if (track) {
+        int64_t frames = 0, cand = 0;
+        for (int i = 0; i < n; ++i) {
+            frames += videos[i].T;
+            cand += videos[i].T * kf::cand_capacity(videos[i].W, videos[i].H);
+        }
+        L.tracks = take(sizeof(kf::TrackVideo) * (size_t)n);
+        L.cand_count = take(sizeof(int) * (size_t)frames);
+        L.cand = take(sizeof(unsigned long long) * (size_t)cand);
+    }
+    L.total = o;
+    return L;
+}
+
+bool video_ok(const kf_video *v)
+{
+    return v && v->W > 0 && v->H > 0 && v->T > 0 && v->W <= (1 << 30) && v->H <= (1 << 30) && v->W * v->H <= 0x7fffffffLL &&
+           v->pitch >= v->W && v->pitch % 16 == 0 && v->frames && aligned(v->frames, 16);
+}
+
+}  // namespace
+
+extern "C" {
+
+kf_status kf_batch_workspace_bytes(const kf_ctx *ctx, const kf_video *videos, int n, int track_K, size_t *bytes)
+{
+    if (!ctx || !videos || n < 1 || !bytes || track_K < 0 || track_K > 1024) return KF_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (videos[i].W <= 0 || videos[i].H <= 0 || videos[i].T <= 0) return KF_EINVAL;
+    *bytes = batch_layout(videos, n, track_K > 0).total;
+    return KF_OK;
+}
+
+kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners *outs, const kf_tracks *tracks, int n,
+                          void *ws, size_t ws_bytes, kf_batch **out)
+{
+    if (!ctx || !videos || !outs || n < 1 || !out) return KF_EINVAL;
+    *out = nullptr;
+    if (ctx->device < 0) return KF_ESTATE;
+    if (!builtin_chain(ctx) || ctx->precision != KF_PREC_F32) return KF_EUNSUPPORTED;
+    const bool track = tracks != nullptr;
+    const int K = track ? tracks[0].K : 0;
+    for (int i = 0; i < n; ++i) {
+        const kf_video &v = videos[i];
+        const kf_corners &o = outs[i];
+        if (!video_ok(&v)) return KF_EINVAL;
+        if (!o.mask || !o.counts || o.mask_pitch < v.W || o.mask_pitch % 16 || !aligned(o.mask, 16) || !aligned(o.counts, 4))
+            return KF_EINVAL;
+        if (track) {
+            const kf_tracks &t = tracks[i];
+            if (t.K != K || K < 1 || K > 1024 || !t.n_points || !t.idx || !t.u || !t.v || !t.status) return KF_EINVAL;
+        }
+    }
+    const BatchLayout L = batch_layout(videos, n, track);
+    if (!ws || !aligned(ws, 256)) return KF_EINVAL;
+    if (ws_bytes < L.total) return KF_ENOMEM;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    char *base = static_cast<char *>(ws);
+    auto *d_params = reinterpret_cast<kf::GroupParams *>(base + L.params);
+    auto *d_items = reinterpret_cast<int64_t *>(base + L.items);
+    auto *d_queue = reinterpret_cast<unsigned long long *>(base + L.queue);
+    auto *d_tracks = reinterpret_cast<kf::TrackVideo *>(base + L.tracks);
+    int *d_cand_count = reinterpret_cast<int *>(base + L.cand_count);
+    auto *d_cand = reinterpret_cast<unsigned long long *>(base + L.cand);
+
+    std::vector<kf::GroupParams> hp((size_t)n);
+    std::vector<int64_t> items((size_t)n + 1, 0);
+    std::vector<kf::TrackVideo> ht(track ? (size_t)n : 0);
+    int64_t frame_begin = 0, cand_off = 0;
+    for (int i = 0; i < n; ++i) {
+        const kf_video &v = videos[i];
+        kf_map fin{}, fout{};
+        fin.plane[0] = const_cast<uint8_t *>(v.frames);
+        fin.channels = 1;
+        fin.dtype = KF_DT_U8;
+        fin.pitch = v.pitch;
+        fin.frame_stride = v.pitch * v.H;
+        fout.plane[0] = outs[i].mask;
+        fout.channels = 1;
+        fout.dtype = KF_DT_U8;
+        fout.pitch = outs[i].mask_pitch;
+        fout.frame_stride = outs[i].mask_pitch * v.H;
+        const int64_t cap = track ? kf::cand_capacity(v.W, v.H) : 0;
+        kf_status st = fill_params(ctx, 1, kf::NSTAGES, fin, fout, v.W, v.H, v.T, outs[i].counts,
+                                   track ? d_cand + cand_off : nullptr, track ? d_cand_count + frame_begin : nullptr, cap,
+                                   hp[(size_t)i]);
+        if (st != KF_OK) return st;
+        items[(size_t)i + 1] = items[(size_t)i] + hp[(size_t)i].n_jobs;
+        if (track) {
+            kf::TrackVideo &tv = ht[(size_t)i];
+            tv.frames = v.frames;
+            tv.pitch = v.pitch;
+            tv.W = (int)v.W;
+            tv.H = (int)v.H;
+            tv.T = (int)v.T;
+            tv.cand = d_cand + cand_off;
+            tv.cand_count = d_cand_count + frame_begin;
+            tv.cand_cap = (int)cap;
+            tv.n_points = tracks[i].n_points;
+            tv.idx = tracks[i].idx;
+            tv.status = tracks[i].status;
+            tv.u = tracks[i].u;
+            tv.v = tracks[i].v;
+            tv.frame_begin = frame_begin;
+        }
+        frame_begin += v.T;
+        cand_off += v.T * cap;
+    }
+    e = cudaMemcpy(d_params, hp.data(), sizeof(kf::GroupParams) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_items, items.data(), sizeof(int64_t) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && track)
+        e = cudaMemcpy(d_tracks, ht.data(), sizeof(kf::TrackVideo) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+
+    // one CUDA graph: reset the queue and counters, the persistent chain, selection, LK
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    const int per_sm = kf::batch_chain_blocks_per_sm(track);
+    if (per_sm < 1) return cuda_fail(ctx, cudaErrorInvalidConfiguration);
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), cs);
+    if (e == cudaSuccess && track) e = cudaMemsetAsync(d_cand_count, 0, sizeof(int) * (size_t)frame_begin, cs);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaMemsetAsync(outs[i].counts, 0, sizeof(int32_t) * (size_t)videos[i].T, cs);
+    if (e == cudaSuccess) {
+        const int r = kf::launch_batch_chain(d_params, d_items, n, d_queue, track, (unsigned)(sms * per_sm), cs);
+        if (r) e = (cudaError_t)r;
+    }
+    if (e == cudaSuccess && track) {
+        const kf::TrackVideo none{};
+        int r = kf::launch_select(none, d_tracks, n, frame_begin, K, cs);
+        if (!r) r = kf::launch_lk(none, d_tracks, n, frame_begin, K, cs);
+        if (r) e = (cudaError_t)r;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    kf_batch *b = new (std::nothrow) kf_batch;
+    if (!b) {
+        cudaGraphExecDestroy(exec);
+        return KF_ENOMEM;
+    }
+    b->device = ctx->device;
+    b->exec = exec;
+    *out = b;
+    return KF_OK;
+}
+
+kf_status kf_batch_run(kf_batch *b, void *stream)
+{
+    if (!b || !b->exec) return KF_EINVAL;
+    if (cudaSetDevice(b->device) != cudaSuccess) return KF_ECUDA;
+    return cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? KF_OK : KF_ECUDA;
+}
+
+kf_status kf_batch_destroy(kf_batch *b)
+{
+    if (b) {
+        if (b->exec) {
+            cudaSetDevice(b->device);
+            cudaGraphExecDestroy(b->exec);
+        }
+        delete b;
+    }
+    return KF_OK;
+}
+
+kf_status kf_tune_chunk_rows(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const int *candidates, int n, int reps,
+                             void *stream, int *best_rows, float *best_ms)
+{
+    if (!ctx || !v || !o || !candidates || n < 1 || reps < 1 || !best_rows) return KF_EINVAL;
+    if (ctx->device < 0) return KF_ESTATE;
+    for (int i = 0; i < n; ++i)
+        if (candidates[i] < 1) return KF_EINVAL;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return KF_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return KF_ECUDA;
+    }
+    const int keep = ctx->chunk_rows;
+    int best = keep;
+    float best_t = INFINITY;
+    kf_status st = KF_OK;
+    for (int i = 0; i < n && st == KF_OK; ++i) {
+        ctx->chunk_rows = candidates[i];
+        st = kf_run(ctx, 0, v, o, nullptr, 0, stream);  // warm-up
+        if (st != KF_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == KF_OK; ++r) st = kf_run(ctx, 0, v, o, nullptr, 0, stream);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = KF_ECUDA;
+        float ms = 0;
+        if (st == KF_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / reps < best_t) {
+            best_t = ms / reps;
+            best = candidates[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->chunk_rows = st == KF_OK ? best : keep;
+    if (st != KF_OK) return st;
+    *best_rows = best;
+    if (best_ms) *best_ms = best_t;
     return KF_OK;
 }
 

@@ -486,8 +486,14 @@ template <int A, int B, bool F16, bool CAND = false> struct SmemPlan {
 };
 
 // ------------------------------------------------------------------ the group kernel
-template <int A, int B, bool F16, bool CAND = false>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN_BLOCKS_BOX : MIN_BLOCKS) group_kernel(const __grid_constant__ GroupParams p)
+// One job: a STRIP-column strip of one frame over one chunk of rows of the group [A..B].
+// `p` is the launch's parameter block (param space) or one video's descriptor (global
+// memory, batched launches); `kbase` counts the staging-ring stages used by earlier jobs
+// of this warp, so the ring's mbarrier phases carry over from job to job. Returns false
+// when a bounded wait expired (the warp must stop).
+template <int A, int B, bool F16, bool CAND>
+__device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsigned char *smem, unsigned &kbase,
+                                        bool global_desc)
 {
     static_assert(!CAND || B == 8, "corner candidates come from the NMS stage");
     static_assert(1 <= A && A <= B && B <= 8, "stage range");
@@ -502,13 +508,10 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
     constexpr int D3 = sum_ry(A, 2), D4 = sum_ry(A, 3), D6 = sum_ry(A, 5), D8 = sum_ry(A, 7);
     constexpr bool HAS3 = A <= 3 && 3 <= B, HAS4 = A <= 4 && 4 <= B, HAS6 = SP::HAS6, HAS8 = A <= 8 && 8 <= B;
 
-    extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SP::BAR_OFF);
     unsigned char *stage_buf = smem + SP::IN_OFF;
 
     const int lane = threadIdx.x & 31;
-    const int64_t job = blockIdx.x;
-    if (job >= p.n_jobs) return;
     const int strip = (int)(job % p.n_strips);
     const int64_t rest = job / p.n_strips;
     const int chunk = (int)(rest % p.n_chunks);
@@ -534,18 +537,23 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
     const int n_stages = min((t_end - t_begin + RB - 1) / RB, (H - t_begin + RB - 1) / RB);
 
     // ---- staging ring: init barriers, issue the first NST stages
+    // stage k of this job is ring stage g = kbase + k: buffer g % NST, mbarrier phase g / NST
     int issued = 0;  // stages issued so far (the same count on every lane)
+    auto slot = [&](int k) { return (int)((kbase + (unsigned)k) % SP::NST); };
+    auto parity = [&](int k) { return ((kbase + (unsigned)k) / SP::NST) & 1u; };
     auto issue = [&](int k) {  // lane 0 only
-        uint64_t *bar = bars + (k % SP::NST);
-        unsigned char *dst = stage_buf + (k % SP::NST) * SP::STAGE_BYTES;
+        uint64_t *bar = bars + slot(k);
+        unsigned char *dst = stage_buf + slot(k) * SP::STAGE_BYTES;
         mbar_expect_tx(bar, SP::STAGE_BYTES);
 #pragma unroll
         for (int m = 0; m < NIN; ++m) tma_load_3d(dst + m * SP::CH_BYTES, &p.tmap[m], xs, t_begin + k * RB, frame, bar);
     };
+    __syncwarp();  // the previous job's lanes have read every stage buffer
     if (lane == 0) {
-#pragma unroll
-        for (int s = 0; s < SP::NST; ++s) mbar_init(bars + s, 1);
-        mbar_fence_init();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (global_desc)  // descriptor written to global memory by the host before the launch
+            for (int m = 0; m < NIN; ++m)
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(&p.tmap[m])) : "memory");
         for (int k = 0; k < SP::NST && k < n_stages; ++k) issue(k);
     }
     issued = min(SP::NST, n_stages);
@@ -733,14 +741,14 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
 #pragma unroll 1
     for (int k = 0, t = t_begin; t < t_end; ++k, t += RB) {
         if (k < n_stages) {
-            const bool ok = __all_sync(FULL, mbar_wait(bars + (k % SP::NST), (unsigned)(k / SP::NST) & 1u));
+            const bool ok = __all_sync(FULL, mbar_wait(bars + slot(k), parity(k)));
             if (!ok) {  // warp-uniform
                 failed = true;
                 k_fail = k;
                 break;
             }
         }
-        const unsigned char *sbuf = stage_buf + (k % SP::NST) * SP::STAGE_BYTES;
+        const unsigned char *sbuf = stage_buf + slot(k) * SP::STAGE_BYTES;
         step(P0{}, t, sbuf);
         if (t + 1 >= t_end) break;
         step(P1{}, t + 1, sbuf);
@@ -764,13 +772,64 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
     if (failed) {
         // record, then give the copies still in flight a bounded chance to land
         if (lane == 0) atomicOr(p.err, DEVERR_TIMEOUT);
-        for (int k = k_fail; k < issued; ++k) mbar_wait(bars + (k % SP::NST), (unsigned)(k / SP::NST) & 1u);
-        return;
+        for (int k = k_fail; k < issued; ++k) mbar_wait(bars + slot(k), parity(k));
+        return false;
     }
     flush_candidates(true);  // what is left at the end of the job
     if constexpr (B == 8) {
         const unsigned tot = __reduce_add_sync(FULL, count);
         if (lane == 0 && tot) atomicAdd(p.counts + frame, (int)tot);
+    }
+    kbase += (unsigned)n_stages;
+    return true;
+}
+
+template <int NST>
+__device__ __forceinline__ void init_ring(unsigned char *smem)
+{
+    if ((threadIdx.x & 31) == 0) {
+        uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+#pragma unroll
+        for (int s = 0; s < NST; ++s) mbar_init(bars + s, 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+}
+
+// One job per block (one warp): the launch's blocks enumerate the jobs.
+template <int A, int B, bool F16, bool CAND = false>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN_BLOCKS_BOX : MIN_BLOCKS) group_kernel(const __grid_constant__ GroupParams p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    if ((int64_t)blockIdx.x >= p.n_jobs) return;
+    init_ring<SmemPlan<A, B, F16, CAND>::NST>(smem);
+    unsigned kbase = 0;
+    run_job<A, B, F16, CAND>(p, blockIdx.x, smem, kbase, false);
+}
+
+// Persistent batch over many videos (the fully fused chain): each resident warp pops
+// jobs from one global counter until the queue is empty. Job j of the batch belongs to
+// the video v with item_begin[v] <= j < item_begin[v + 1] (binary search) and is that
+// video's job j - item_begin[v], run with its own descriptor.
+template <bool CAND>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, MIN_BLOCKS_BOX) batch_kernel(const GroupParams *videos, const int64_t *item_begin,
+                                                                                      int n_videos, unsigned long long *queue)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    init_ring<SmemPlan<1, 8, false, CAND>::NST>(smem);
+    const int64_t n_items = item_begin[n_videos];
+    unsigned kbase = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if ((threadIdx.x & 31) == 0) item = atomicAdd(queue, 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if ((int64_t)item >= n_items) break;
+        int lo = 0, hi = n_videos - 1;  // last v with item_begin[v] <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (item_begin[mid] <= (int64_t)item) lo = mid; else hi = mid - 1;
+        }
+        if (!run_job<1, 8, false, CAND>(videos[lo], (int64_t)item - item_begin[lo], smem, kbase, true)) break;
     }
 }
 

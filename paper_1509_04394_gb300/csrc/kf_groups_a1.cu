@@ -14,6 +14,29 @@ int launch(const GroupParams &p, unsigned grid, void *stream)
 }
 }  // namespace
 
+// the persistent batch of fully fused chains over many videos
+int launch_batch_chain(const GroupParams *videos, const int64_t *item_begin, int n_videos, unsigned long long *queue,
+                       bool cand, unsigned grid, void *stream)
+{
+    if (cand)
+        batch_kernel<true><<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<1, 8, false, true>::BYTES, static_cast<cudaStream_t>(stream)>>>(
+            videos, item_begin, n_videos, queue);
+    else
+        batch_kernel<false><<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<1, 8, false, false>::BYTES, static_cast<cudaStream_t>(stream)>>>(
+            videos, item_begin, n_videos, queue);
+    return (int)cudaGetLastError();
+}
+
+int batch_chain_blocks_per_sm(bool cand)
+{
+    int n = 0;
+    cudaError_t e = cand ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<true>, 32 * WARPS_PER_BLOCK,
+                                                                         SmemPlan<1, 8, false, true>::BYTES)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<false>, 32 * WARPS_PER_BLOCK,
+                                                                         SmemPlan<1, 8, false, false>::BYTES);
+    return e == cudaSuccess ? n : 0;
+}
+
 // the fully fused chain that also lists every frame's corners for the tracking stage
 int launch_chain_with_candidates(const GroupParams &p, unsigned grid, void *stream)
 {

@@ -70,6 +70,20 @@ struct GroupParams {
     int cand_cap;
 };
 
+// One video of the tracking stage (by value for a single video, or an array in device
+// memory for a batch: frame_begin = the global index of its frame 0 in the batch).
+struct TrackVideo {
+    const uint8_t *frames;
+    int64_t pitch;
+    int W, H, T;
+    const unsigned long long *cand;  // corner-candidate lists, cand_cap per frame
+    const int *cand_count;
+    int cand_cap;
+    int32_t *n_points, *idx, *status;
+    float *u, *v;
+    int64_t frame_begin;
+};
+
 // Strip geometry of a group with accumulated horizontal radius rxt: input strips start
 // on a multiple of STRIP_ALIGN columns (a legal TMA x for every map type), outputs tile
 // the frame exactly.
@@ -97,10 +111,13 @@ LaunchFn launcher_a6(int B, int f16);
 LaunchFn launcher_a7(int B, int f16);
 LaunchFn launcher_a8(int B, int f16);
 int launch_chain_with_candidates(const GroupParams &p, unsigned grid, void *stream);
-int launch_select(const unsigned long long *cand, const int *cand_count, int cap, int K, int T, int32_t *n_points,
-                  int32_t *idx, void *stream);
-int launch_lk(const uint8_t *frames, int64_t pitch, int W, int H, int T, int K, const int32_t *n_points,
-              const int32_t *idx, float *u, float *v, int32_t *status, void *stream);
+// tracking kernels over one video (vids == nullptr: `one`) or a table of n videos with
+// total_frames frames in all
+int launch_select(const TrackVideo &one, const TrackVideo *vids, int n, int64_t total_frames, int K, void *stream);
+int launch_lk(const TrackVideo &one, const TrackVideo *vids, int n, int64_t total_frames, int K, void *stream);
+int launch_batch_chain(const GroupParams *videos, const int64_t *item_begin, int n_videos, unsigned long long *queue,
+                       bool cand, unsigned grid, void *stream);
+int batch_chain_blocks_per_sm(bool cand);
 #endif
 
 }  // namespace kf

@@ -27,11 +27,26 @@ namespace {
 constexpr int SEL_THREADS = 256;
 constexpr int MAX_K = 1024;
 
-__global__ void __launch_bounds__(SEL_THREADS) select_kernel(const unsigned long long *cand, const int *cand_count,
-                                                             int cap, int K, int32_t *n_points, int32_t *idx_out)
+// the video of global frame g: the last v with frame_begin <= g
+__device__ __forceinline__ const TrackVideo &video_of(const TrackVideo &one, const TrackVideo *vids, int n, int64_t g)
 {
-    const int frame = blockIdx.x;
+    if (!vids) return one;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (vids[mid].frame_begin <= g) lo = mid; else hi = mid - 1;
+    }
+    return vids[lo];
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) select_kernel(const TrackVideo one, const TrackVideo *vids, int n_videos,
+                                                             int K)
+{
+    const TrackVideo &vd = video_of(one, vids, n_videos, blockIdx.x);
+    const int frame = (int)(blockIdx.x - vd.frame_begin);
     const int tid = threadIdx.x;
+    const int cap = vd.cand_cap;
+    int32_t *n_points = vd.n_points, *idx_out = vd.idx;
     __shared__ unsigned hist[256];
     __shared__ unsigned long long sel[MAX_K];
     __shared__ unsigned nsel;
@@ -40,8 +55,8 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const unsigned long
         if (tid == 0) n_points[0] = 0;
         return;
     }
-    const unsigned long long *keys = cand + (int64_t)frame * cap;
-    const int n = min(cand_count[frame], cap);
+    const unsigned long long *keys = vd.cand + (int64_t)frame * cap;
+    const int n = min(vd.cand_count[frame], cap);
     const int kk = min(n, K);
     unsigned long long kth = 0;  // every key >= kth is selected
     if (n > K) {
@@ -118,24 +133,29 @@ constexpr int LK_WARPS = 4;  // warps per block; each half-warp (16 lanes) takes
 // row q0 + j on the grid columns; lane i < nr gathers its five vertical taps by shuffles
 // and holds smoothed grid row r0 + i; lane d < 7 accumulates window row d - 3. All values
 // up to the Sobel output are integers below 2^24, exact in FP32 and equal to the chain's.
-__global__ void __launch_bounds__(32 * LK_WARPS) lk_kernel(const uint8_t *frames, int64_t pitch, int W, int H, int T,
-                                                           int K, const int32_t *n_points, const int32_t *idx,
-                                                           float *u_out, float *v_out, int32_t *status)
+__global__ void __launch_bounds__(32 * LK_WARPS) lk_kernel(const TrackVideo one, const TrackVideo *vids, int n_videos,
+                                                           int64_t total_frames, int K)
 {
     const int lane = threadIdx.x & 15;  // lane within the half-warp
     const int64_t gid = ((int64_t)blockIdx.x * LK_WARPS + (threadIdx.x >> 5)) * 2 + ((threadIdx.x >> 4) & 1);
-    const int frame_g = (int)(gid / K), i = (int)(gid % K);
-    const bool valid = gid < (int64_t)T * K && frame_g > 0 && i < n_points[frame_g];
+    const int64_t gframe = gid / K;
+    const int i = (int)(gid % K);
+    const TrackVideo &vd = video_of(one, vids, n_videos, min(gframe, total_frames - 1));
+    const int frame_g = (int)(gframe - vd.frame_begin);
+    const int W = vd.W, H = vd.H;
+    const int64_t pitch = vd.pitch;
+    const bool valid = gframe < total_frames && frame_g > 0 && i < vd.n_points[frame_g];
     if (!__any_sync(FULLM, valid)) return;  // warp-uniform
-    // an idle half works on a stand-in point (row 0, column 0 of frames 0 and 1) and stores nothing
-    const int frame = valid ? frame_g : 1;
-    const int p = valid ? idx[gid] : 0;
+    // an idle half works on a stand-in point (row 0, column 0 of its video's frame 0,
+    // against itself) and stores nothing
+    const int frame = valid ? frame_g : 0;
+    const int p = valid ? vd.idx[(int64_t)frame_g * K + i] : 0;
     const int py = p / W, px = p % W;
     const int r0 = max(py - 4, 0), nr = min(py + 4, H - 1) - r0 + 1;
     const int c0 = max(px - 4, 0), nc = min(px + 4, W - 1) - c0 + 1;
     const int q0 = max(r0 - 2, 0), nq = min(r0 + nr - 1 + 2, H - 1) - q0 + 1;
     const int64_t fstride = (int64_t)H * pitch;
-    const uint8_t *fc = frames + (int64_t)frame * fstride, *fp = fc - fstride;
+    const uint8_t *fc = vd.frames + (int64_t)frame * fstride, *fp = frame > 0 ? fc - fstride : fc;
 
     // horizontal pass: lane j holds g1 of row q0 + j (both frames) on the grid columns;
     // the lane loads the 13 clamped bytes of its row once per frame
@@ -250,37 +270,37 @@ __global__ void __launch_bounds__(32 * LK_WARPS) lk_kernel(const uint8_t *frames
     }
     if (lane != 0 || !valid) return;
     // scaled units: gx = ix / (8 s), gt = it / s with s = 65280, so -A^-1 b = -8 A'^-1 b'
+    const int64_t o = (int64_t)frame_g * K + i;
     const double A00 = a00, A01 = a01, A11 = a11, B0 = b0, B1 = b1;
     const double det = A00 * A11 - A01 * A01;
     const double tr = A00 + A11;
     if (fabs(det) <= 1e-12 * tr * tr) {
-        u_out[gid] = 0.0f;
-        v_out[gid] = 0.0f;
-        status[gid] = 1;
+        vd.u[o] = 0.0f;
+        vd.v[o] = 0.0f;
+        vd.status[o] = 1;
     } else {
-        u_out[gid] = (float)(-8.0 * (A11 * B0 - A01 * B1) / det);
-        v_out[gid] = (float)(-8.0 * (A00 * B1 - A01 * B0) / det);
-        status[gid] = 0;
+        vd.u[o] = (float)(-8.0 * (A11 * B0 - A01 * B1) / det);
+        vd.v[o] = (float)(-8.0 * (A00 * B1 - A01 * B0) / det);
+        vd.status[o] = 0;
     }
 }
 
 }  // namespace
 
-int launch_select(const unsigned long long *cand, const int *cand_count, int cap, int K, int T, int32_t *n_points,
-                  int32_t *idx, void *stream)
+int launch_select(const TrackVideo &one, const TrackVideo *vids, int n, int64_t total_frames, int K, void *stream)
 {
-    if (K < 1 || K > MAX_K) return (int)cudaErrorInvalidValue;
-    select_kernel<<<T, SEL_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(cand, cand_count, cap, K, n_points, idx);
+    if (K < 1 || K > MAX_K || total_frames > 0x7fffffff) return (int)cudaErrorInvalidValue;
+    if (total_frames == 0) return 0;
+    select_kernel<<<(unsigned)total_frames, SEL_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(one, vids, n, K);
     return (int)cudaGetLastError();
 }
 
-int launch_lk(const uint8_t *frames, int64_t pitch, int W, int H, int T, int K, const int32_t *n_points,
-              const int32_t *idx, float *u, float *v, int32_t *status, void *stream)
+int launch_lk(const TrackVideo &one, const TrackVideo *vids, int n, int64_t total_frames, int K, void *stream)
 {
-    const int64_t n = (int64_t)T * K;
-    const unsigned blocks = (unsigned)((n + 2 * LK_WARPS - 1) / (2 * LK_WARPS));
-    lk_kernel<<<blocks, 32 * LK_WARPS, 0, static_cast<cudaStream_t>(stream)>>>(frames, pitch, W, H, T, K, n_points, idx, u,
-                                                                                v, status);
+    const int64_t slots = total_frames * K;
+    if (slots == 0) return 0;
+    const unsigned blocks = (unsigned)((slots + 2 * LK_WARPS - 1) / (2 * LK_WARPS));
+    lk_kernel<<<blocks, 32 * LK_WARPS, 0, static_cast<cudaStream_t>(stream)>>>(one, vids, n, total_frames, K);
     return (int)cudaGetLastError();
 }
 

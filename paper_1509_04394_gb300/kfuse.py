@@ -94,6 +94,11 @@ def _lib():
             "kf_run_static": (i32, [P, u32, P, P, P]),
             "kf_track_workspace_bytes": (i32, [P, i64, i64, i64, P]),
             "kf_track": (i32, [P, P, P, P, P, ctypes.c_size_t, P]),
+            "kf_batch_workspace_bytes": (i32, [P, P, i32, i32, P]),
+            "kf_batch_create": (i32, [P, P, P, P, i32, P, ctypes.c_size_t, P]),
+            "kf_batch_run": (i32, [P, P]),
+            "kf_batch_destroy": (i32, [P]),
+            "kf_tune_chunk_rows": (i32, [P, P, P, P, i32, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -108,7 +113,8 @@ def exported_symbols() -> list[str]:
             "kf_set_precision", "kf_set_chunk_rows", "kf_add_stage", "kf_add_harris_chain",
             "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
             "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static",
-            "kf_track_workspace_bytes", "kf_track"]
+            "kf_track_workspace_bytes", "kf_track", "kf_batch_workspace_bytes", "kf_batch_create",
+            "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -255,6 +261,58 @@ def kf_track(ctx, frames, W: int, mask, counts, K: int, n_points, idx, u, v, sta
     ws_bytes = workspace.numel() * workspace.element_size()
     _check("kf_track", _lib().kf_track(ctx, ctypes.byref(vid), ctypes.byref(o), ctypes.byref(tr), workspace.data_ptr(),
                                        ws_bytes, _stream(stream)), ctx)
+
+
+def _videos(frames_list, W_list):
+    arr = (kf_video * len(frames_list))()
+    for i, (f, W) in enumerate(zip(frames_list, W_list)):
+        T, H, P = f.shape
+        arr[i] = kf_video(f.data_ptr(), int(W), int(H), int(T), int(P))
+    return arr
+
+
+def kf_batch_workspace_bytes(ctx, frames_list, W_list, K: int = 0) -> int:
+    v = _videos(frames_list, W_list)
+    b = ctypes.c_size_t()
+    _check("kf_batch_workspace_bytes", _lib().kf_batch_workspace_bytes(ctx, v, len(frames_list), int(K), ctypes.byref(b)),
+           ctx)
+    return b.value
+
+
+def kf_batch_create(ctx, frames_list, W_list, masks, counts_list, workspace, tracks=None):
+    """tracks: None or a list of (K, n_points, idx, u, v, status) tensors per video."""
+    n = len(frames_list)
+    v = _videos(frames_list, W_list)
+    o = (kf_corners * n)(*[kf_corners(m.data_ptr(), int(m.shape[2]), c.data_ptr()) for m, c in zip(masks, counts_list)])
+    tr = None
+    if tracks is not None:
+        tr = (kf_tracks * n)(*[kf_tracks(int(K), a.data_ptr(), b.data_ptr(), c.data_ptr(), d.data_ptr(), e.data_ptr())
+                               for (K, a, b, c, d, e) in tracks])
+    h = ctypes.c_void_p()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("kf_batch_create", _lib().kf_batch_create(ctx, v, o, tr, n, workspace.data_ptr(), ws_bytes, ctypes.byref(h)),
+           ctx)
+    return h
+
+
+def kf_batch_run(batch, stream=None) -> None:
+    _check("kf_batch_run", _lib().kf_batch_run(batch, _stream(stream)))
+
+
+def kf_batch_destroy(batch) -> None:
+    _check("kf_batch_destroy", _lib().kf_batch_destroy(batch))
+
+
+def kf_tune_chunk_rows(ctx, frames, W: int, mask, counts, candidates, reps: int = 3, stream=None):
+    T, H, P = frames.shape
+    vid = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
+    o = kf_corners(mask.data_ptr(), int(mask.shape[2]), counts.data_ptr())
+    cand = (ctypes.c_int * len(candidates))(*candidates)
+    best, ms = ctypes.c_int(), ctypes.c_float()
+    _check("kf_tune_chunk_rows", _lib().kf_tune_chunk_rows(ctx, ctypes.byref(vid), ctypes.byref(o), cand, len(candidates),
+                                                           int(reps), _stream(stream), ctypes.byref(best),
+                                                           ctypes.byref(ms)), ctx)
+    return best.value, ms.value
 
 
 KF_STATIC_WORKSPACE_BYTES = 64 << 20

@@ -1,0 +1,102 @@
+"""Batched form: uneven videos through one persistent launch replayed from a CUDA graph.
+
+Every video's mask, counts and tracks must equal, bit for bit, what kf_run (full
+fusion) and kf_track give for that video alone, on two replays of the graph; the
+autotuner must return one of its candidates and keep it in the context.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1509_04394_gb300 import build as kbuild  # noqa: E402
+from paper_1509_04394_gb300 import kfuse as K  # noqa: E402
+from synth import video as sv  # noqa: E402
+
+SHAPES = [(3, 64, 100), (5, 40, 300), (2, 130, 77), (4, 96, 150), (1, 20, 20), (2, 7, 3)]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kbuild.build()
+    return torch.device("cuda:0")
+
+
+def _videos(dev):
+    out = []
+    for i, (T, H, W) in enumerate(SHAPES):
+        fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=60 + i, n_blobs=6, n_patches=4), pitch=sv.pitch_for(W))
+        out.append((torch.from_numpy(fr).to(dev), W))
+    return out
+
+
+@pytest.mark.parametrize("track", [False, True])
+def test_batch_equals_per_video_runs(dev, track):
+    ctx = K.Context(0)
+    vids = _videos(dev)
+    KP = 16
+    masks = [torch.full_like(f, 5) for f, _ in vids]
+    counts = [torch.full((f.shape[0],), -1, dtype=torch.int32, device=dev) for f, _ in vids]
+    tracks = None
+    if track:
+        tracks = []
+        for f, _ in vids:
+            T = f.shape[0]
+            tracks.append((KP, torch.full((T,), -1, dtype=torch.int32, device=dev),
+                           torch.full((T, KP), -1, dtype=torch.int32, device=dev),
+                           torch.zeros((T, KP), device=dev), torch.zeros((T, KP), device=dev),
+                           torch.full((T, KP), -1, dtype=torch.int32, device=dev)))
+    ws = torch.empty(K.kf_batch_workspace_bytes(ctx.h, [f for f, _ in vids], [w for _, w in vids], KP if track else 0),
+                     dtype=torch.uint8, device=dev)
+    b = K.kf_batch_create(ctx.h, [f for f, _ in vids], [w for _, w in vids], masks, counts, ws, tracks)
+    try:
+        for rep in range(2):
+            if rep:
+                for m in masks:
+                    m.fill_(5)
+            K.kf_batch_run(b)
+            torch.cuda.synchronize()
+            assert K.kf_device_error(ctx.h) == 0
+            for i, (f, W) in enumerate(vids):
+                T = f.shape[0]
+                m_ref = torch.zeros_like(f)
+                c_ref = torch.zeros(T, dtype=torch.int32, device=dev)
+                if track:
+                    n_r = torch.zeros(T, dtype=torch.int32, device=dev)
+                    i_r = torch.zeros((T, KP), dtype=torch.int32, device=dev)
+                    u_r, v_r = torch.zeros((T, KP), device=dev), torch.zeros((T, KP), device=dev)
+                    s_r = torch.zeros((T, KP), dtype=torch.int32, device=dev)
+                    wst = torch.empty(K.kf_track_workspace_bytes(ctx.h, W, f.shape[1], T), dtype=torch.uint8, device=dev)
+                    K.kf_track(ctx.h, f, W, m_ref, c_ref, KP, n_r, i_r, u_r, v_r, s_r, wst)
+                    _, n_b, i_b, u_b, v_b, s_b = tracks[i]
+                    assert torch.equal(n_b, n_r), i
+                    for t in range(1, T):
+                        n = int(n_r[t])
+                        assert torch.equal(i_b[t, :n], i_r[t, :n]), (i, t)
+                        assert torch.equal(u_b[t, :n], u_r[t, :n]) and torch.equal(v_b[t, :n], v_r[t, :n]), (i, t)
+                        assert torch.equal(s_b[t, :n], s_r[t, :n]), (i, t)
+                else:
+                    K.kf_run(ctx.h, 0, f, W, m_ref, c_ref, None)
+                assert torch.equal(masks[i][:, :, :W], m_ref[:, :, :W]), i
+                assert torch.all(masks[i][:, :, W:] == 5), i
+                assert torch.equal(counts[i], c_ref), i
+    finally:
+        K.kf_batch_destroy(b)
+
+
+def test_autotuner_picks_a_candidate(dev):
+    ctx = K.Context(0)
+    fr, _ = sv.generate(sv.VideoSpec(T=8, H=200, W=300, seed=70), pitch=sv.pitch_for(300))
+    f = torch.from_numpy(fr).to(dev)
+    m = torch.zeros_like(f)
+    c = torch.zeros(8, dtype=torch.int32, device=dev)
+    best, ms = K.kf_tune_chunk_rows(ctx.h, f, 300, m, c, [32, 100, 200], reps=2)
+    assert best in (32, 100, 200) and ms > 0
+    m2 = torch.zeros_like(f)
+    c2 = torch.zeros_like(c)
+    K.kf_set_chunk_rows(ctx.h, 200)
+    K.kf_run(ctx.h, 0, f, 300, m2, c2, None)
+    assert torch.equal(m, m2) and torch.equal(c, c2)
