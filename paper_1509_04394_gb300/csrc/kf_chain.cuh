@@ -517,6 +517,11 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
     const int chunk = (int)(rest % p.n_chunks);
     const int frame = (int)(rest / p.n_chunks);
     const int W = p.W, H = p.H;
+    // per-job copies of the fields the row loop uses: with `p` in global memory the
+    // compiler could not keep them in registers across the loop's stores
+    const int64_t out_pitch = p.out_pitch;
+    const float thr = p.thr, in_scale = p.in_scale, out_scale = p.out_scale;
+    void *const out_plane[3] = {p.out[0], p.out[1], p.out[2]};
 
     const int xs = p.xs0 + strip * p.step;  // multiple of 16 columns: TMA-aligned
     const int x0 = xs + C * lane;
@@ -595,7 +600,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
         const unsigned char *srow = sbuf + PH * SP::ROW_BYTES;
         [[maybe_unused]] Rows<NIN> in;
 #pragma unroll
-        for (int m = 0; m < NIN; ++m) Staged<TIN>::read(srow + m * SP::CH_BYTES, lane, lane_inside, off, p.in_scale, in.v[m]);
+        for (int m = 0; m < NIN; ++m) Staged<TIN>::read(srow + m * SP::CH_BYTES, lane, lane_inside, off, in_scale, in.v[m]);
         [[maybe_unused]] Rows<1> f;
         if constexpr (A == 1) f = in;
         // ---- stage 2 (horizontal Gaussian)
@@ -679,7 +684,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
                 if (i == 0) s8.fill(mh, r7.v[0]);
                 if (i >= H) s8.replay(mh, r7.v[0]);
             }
-            bits = s8.push(mh, r7.v[0], p.thr, centre);
+            bits = s8.push(mh, r7.v[0], thr, centre);
         }
         // ---- group output row t - RYT
         const int o = t - RYT;
@@ -705,10 +710,10 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
             }
         }
         if (o >= y0 && out_mask) {  // o < y1 holds: t < y1 + RYT
-            const int64_t ooff = out_frame + (int64_t)o * p.out_pitch + x0;
+            const int64_t ooff = out_frame + (int64_t)o * out_pitch + x0;
             if constexpr (B == 8) {
                 const unsigned kept = bits & out_mask;
-                uint8_t *mp = static_cast<uint8_t *>(p.out[0]) + ooff;
+                uint8_t *mp = static_cast<uint8_t *>(out_plane[0]) + ooff;
                 if (out_mask == (1u << C) - 1) {
                     *reinterpret_cast<uint32_t *>(mp) = (kept & 1u) | (kept & 2u) << 7 | (kept & 4u) << 14 | (kept & 8u) << 21;
                 } else {
@@ -726,7 +731,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
                 else if constexpr (B == 6) res = &sm;
                 else res = &r7;
 #pragma unroll
-                for (int m = 0; m < NOUT; ++m) Store<MapT<B, F16>>::row(p.out[m], ooff, res->v[m], out_mask, p.out_scale);
+                for (int m = 0; m < NOUT; ++m) Store<MapT<B, F16>>::row(out_plane[m], ooff, res->v[m], out_mask, out_scale);
             }
         }
     };
