@@ -265,6 +265,51 @@ kf_status kf_batch_destroy(kf_batch *batch);
 kf_status kf_tune_chunk_rows(kf_ctx *ctx, const kf_video *video, const kf_corners *out, const int *candidates, int n,
                              int reps, void *stream, int *best_rows, float *best_ms);
 
+/* ------------------------------------------------------------------ kernel DAGs */
+/* Arbitrary DAGs of generic image kernels (Sec. III's chain generalised to one or two
+ * inputs per kernel), for planning with learned costs. Node 0 is the frame (u8 / 255);
+ * stage i (1-based) writes node i and reads in1 (and in2) < i. Every stencil clamps its
+ * own input. Kinds:                                                                     */
+#define KF_G_AFFINE 1  /* y = a x + b                                                    */
+#define KF_G_ABS 2     /* y = |x|                                                        */
+#define KF_G_PRODUCT 3 /* y = min(max(x1 x2, -16), 16)                                   */
+#define KF_G_STENCIL 4 /* separable binomial smoothing, radius 0..3: C(2r, r+k) / 4^r    */
+#define KF_G_MAX3 5    /* 3x3 maximum                                                    */
+#define KF_DAG_MAX_STAGES 24
+#define KF_NFEAT 12
+typedef struct kf_gstage {
+    int kind, in1, in2, radius;
+    float a, b;
+} kf_gstage;
+typedef struct kf_dag kf_dag;
+/* The DAG's output is its last node. Groups are contiguous ranges of the stage order; a
+ * group runs as one fused kernel (Alg. 1: its input boxes copied to shared memory once,
+ * stages on shared-memory tiles, only the maps later groups read are stored). */
+kf_status kf_dag_create(kf_ctx *ctx, const kf_gstage *stages, int n, kf_dag **out);
+kf_status kf_dag_destroy(kf_dag *dag);
+/* For group [first, last] (0-based stages): KF_NFEAT cost-model features (stages,
+ * stencils, largest input halo, summed radii, bytes in and out per pixel, shared memory
+ * per block in KiB, peak live tiles, arithmetic per pixel with halo recompute, external
+ * inputs, stored outputs, log of the volume), its on-chip bytes per block and its
+ * traffic (Sec. VI-D over the executor's 32 x 16 tile). Any pointer may be NULL. */
+kf_status kf_dag_group_info(const kf_dag *dag, int first, int last, int64_t W, int64_t H, int64_t T, float *features,
+                            double *onchip_bytes, double *traffic_bytes);
+/* Exact minimum-cost partition for per-group costs group_cost[g] (n(n+1)/2 entries, group
+ * [a, b] at a*n - a(a-1)/2 + (b-a), 0-based; negative or infinite = infeasible), by the
+ * same dynamic program as kf_plan. */
+kf_status kf_dag_plan(const kf_dag *dag, const double *group_cost, uint32_t *cuts, double *cost);
+/* Workspace of kf_dag_run / kf_dag_time_groups: one float map per node. */
+kf_status kf_dag_workspace_bytes(const kf_dag *dag, int64_t W, int64_t H, int64_t T, size_t *bytes);
+/* Run partition `cuts` on `stream`; the output node's map goes to `out` (T x H rows of
+ * out_pitch floats). KF_ESMEM if a group exceeds the on-chip limit. T <= 65535. */
+kf_status kf_dag_run(kf_dag *dag, uint32_t cuts, const kf_video *video, float *out, int64_t out_pitch, void *workspace,
+                     size_t workspace_bytes, void *stream);
+/* Measure every candidate group: runs the DAG unfused once, then each of the n(n+1)/2
+ * groups (one warm-up, `reps` timed launches, CUDA events on `stream`); ms[g] = mean
+ * time, -1 for infeasible groups. Synchronous. */
+kf_status kf_dag_time_groups(kf_dag *dag, const kf_video *video, float *out, int64_t out_pitch, void *workspace,
+                             size_t workspace_bytes, int reps, void *stream, float *ms);
+
 /* ------------------------------------------------------------------ no-allocation run */
 /* kf_run with the workspace in a fixed array that the library itself holds on every GPU
  * that loads it (KF_STATIC_WORKSPACE_BYTES per GPU, kept until the process exits). The

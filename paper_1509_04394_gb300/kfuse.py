@@ -99,6 +99,13 @@ def _lib():
             "kf_batch_run": (i32, [P, P]),
             "kf_batch_destroy": (i32, [P]),
             "kf_tune_chunk_rows": (i32, [P, P, P, P, i32, i32, P, P, P]),
+            "kf_dag_create": (i32, [P, P, i32, P]),
+            "kf_dag_destroy": (i32, [P]),
+            "kf_dag_group_info": (i32, [P, i32, i32, i64, i64, i64, P, P, P]),
+            "kf_dag_plan": (i32, [P, P, P, P]),
+            "kf_dag_workspace_bytes": (i32, [P, i64, i64, i64, P]),
+            "kf_dag_run": (i32, [P, u32, P, P, i64, P, ctypes.c_size_t, P]),
+            "kf_dag_time_groups": (i32, [P, P, P, i64, P, ctypes.c_size_t, i32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -114,7 +121,8 @@ def exported_symbols() -> list[str]:
             "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
             "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static",
             "kf_track_workspace_bytes", "kf_track", "kf_batch_workspace_bytes", "kf_batch_create",
-            "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows"]
+            "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows", "kf_dag_create", "kf_dag_destroy",
+            "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -313,6 +321,73 @@ def kf_tune_chunk_rows(ctx, frames, W: int, mask, counts, candidates, reps: int 
                                                            int(reps), _stream(stream), ctypes.byref(best),
                                                            ctypes.byref(ms)), ctx)
     return best.value, ms.value
+
+
+KF_NFEAT = 12
+
+
+class kf_gstage(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("in1", ctypes.c_int), ("in2", ctypes.c_int), ("radius", ctypes.c_int),
+                ("a", ctypes.c_float), ("b", ctypes.c_float)]
+
+
+def kf_dag_create(ctx, rows):
+    """rows: (kind, in1, in2, radius, a, b) per stage (synth.dags.to_array)."""
+    arr = (kf_gstage * len(rows))(*[kf_gstage(int(k), int(i1), int(i2), int(r), float(a), float(b))
+                                    for (k, i1, i2, r, a, b) in rows])
+    h = ctypes.c_void_p()
+    _check("kf_dag_create", _lib().kf_dag_create(ctx, arr, len(rows), ctypes.byref(h)), ctx)
+    return h
+
+
+def kf_dag_destroy(dag) -> None:
+    _check("kf_dag_destroy", _lib().kf_dag_destroy(dag))
+
+
+def kf_dag_group_info(dag, first: int, last: int, W, H, T):
+    """(features [KF_NFEAT], on-chip bytes, traffic bytes) of group [first, last]."""
+    f = (ctypes.c_float * KF_NFEAT)()
+    oc_, tr = ctypes.c_double(), ctypes.c_double()
+    _check("kf_dag_group_info", _lib().kf_dag_group_info(dag, first, last, W, H, T, f, ctypes.byref(oc_),
+                                                         ctypes.byref(tr)))
+    return list(f), oc_.value, tr.value
+
+
+def kf_dag_plan(dag, group_cost) -> tuple[int, float]:
+    arr = (ctypes.c_double * len(group_cost))(*[float(c) for c in group_cost])
+    c, cost = ctypes.c_uint32(), ctypes.c_double()
+    _check("kf_dag_plan", _lib().kf_dag_plan(dag, arr, ctypes.byref(c), ctypes.byref(cost)))
+    return c.value, cost.value
+
+
+def kf_dag_workspace_bytes(dag, W, H, T) -> int:
+    b = ctypes.c_size_t()
+    _check("kf_dag_workspace_bytes", _lib().kf_dag_workspace_bytes(dag, W, H, T, ctypes.byref(b)))
+    return b.value
+
+
+def kf_dag_run(dag, cuts: int, frames, W: int, out, workspace, stream=None) -> None:
+    """frames: uint8 [T, H, pitch]; out: float32 [T, H, opitch] (CUDA tensors)."""
+    T, H, P = frames.shape
+    v = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
+    _check("kf_dag_run", _lib().kf_dag_run(dag, cuts, ctypes.byref(v), out.data_ptr(), int(out.shape[2]),
+                                           workspace.data_ptr(), workspace.numel(), _stream(stream)))
+
+
+def group_index(n: int, a: int, b: int) -> int:
+    """Index of 0-based group [a, b] among the n(n+1)/2 candidate groups."""
+    return a * n - a * (a - 1) // 2 + (b - a)
+
+
+def kf_dag_time_groups(dag, n: int, frames, W: int, out, workspace, reps: int = 3, stream=None) -> list[float]:
+    """Measured mean time (ms) of every candidate group of an n-stage DAG, -1 if infeasible."""
+    T, H, P = frames.shape
+    v = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
+    ms = (ctypes.c_float * (n * (n + 1) // 2))()
+    _check("kf_dag_time_groups", _lib().kf_dag_time_groups(dag, ctypes.byref(v), out.data_ptr(), int(out.shape[2]),
+                                                           workspace.data_ptr(), workspace.numel(), int(reps),
+                                                           _stream(stream), ms))
+    return list(ms)
 
 
 KF_STATIC_WORKSPACE_BYTES = 64 << 20

@@ -1,0 +1,76 @@
+"""GPU parity of the fused DAG executor against the FP64 oracle.
+
+Every node is computed by the same formula whatever the grouping, so every partition
+must give the same bits; the unfused and fused results stay within 1e-4 (normwise) of
+the FP64 oracle across chains of up to 24 FP32 stages."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import dag as od  # noqa: E402
+from paper_1509_04394_gb300 import build as kbuild  # noqa: E402
+from paper_1509_04394_gb300 import kfuse as K  # noqa: E402
+from synth import dags as sd  # noqa: E402
+from synth import video as sv  # noqa: E402
+from tests._parity import normwise  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kbuild.build()
+    return torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("seed,shape", [(1, (2, 37, 53)), (2, (2, 64, 96)), (3, (3, 16, 32)), (4, (1, 5, 7)),
+                                        (5, (2, 70, 130))])
+def test_dag_partitions_match_the_oracle(dev, seed, shape):
+    T, H, W = shape
+    rows = sd.to_array(sd.random_dag(seed))
+    n = len(rows)
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=seed, n_blobs=4, n_patches=2), pitch=sv.pitch_for(W))
+    ctx = K.Context(0, harris=False)
+    dag = K.kf_dag_create(ctx.h, rows)
+    f = torch.from_numpy(fr).to(dev)
+    ws = torch.empty(K.kf_dag_workspace_bytes(dag, W, H, T), dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(seed)
+    parts = [(1 << (n - 1)) - 1, 0] + [int(rng.integers(0, 1 << (n - 1))) for _ in range(4)]
+    outs = {}
+    for cuts in parts:
+        out = torch.full((T, H, sv.pitch_for(W)), float("nan"), dtype=torch.float32, device=dev)
+        try:
+            K.kf_dag_run(dag, cuts, f, W, out, ws)
+        except K.KfuseError as e:
+            assert e.status == K.KF_ESMEM  # a group too large for shared memory
+            continue
+        outs[cuts] = out[:, :, :W].cpu()
+    ref = outs[(1 << (n - 1)) - 1]
+    for cuts, o in outs.items():
+        assert torch.equal(o, ref), cuts
+    for t in range(T):
+        nodes = od.run_frame(rows, fr[t][:, :W])
+        assert normwise(ref[t].double().numpy(), nodes[-1]) <= 1e-4
+    K.kf_dag_destroy(dag)
+
+
+def test_group_timing_covers_every_group(dev):
+    rows = sd.to_array(sd.random_dag(9, 12, 14))
+    n = len(rows)
+    T, H, W = 2, 128, 256
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=9), pitch=sv.pitch_for(W))
+    ctx = K.Context(0, harris=False)
+    dag = K.kf_dag_create(ctx.h, rows)
+    f = torch.from_numpy(fr).to(dev)
+    ws = torch.empty(K.kf_dag_workspace_bytes(dag, W, H, T), dtype=torch.uint8, device=dev)
+    out = torch.zeros((T, H, W), dtype=torch.float32, device=dev)
+    ms = K.kf_dag_time_groups(dag, n, f, W, out, ws, reps=2)
+    assert len(ms) == n * (n + 1) // 2
+    for a in range(n):
+        for b in range(a, n):
+            _, onchip, _ = K.kf_dag_group_info(dag, a, b, W, H, T)
+            t = ms[K.group_index(n, a, b)]
+            assert (t > 0) == (onchip <= 200 * 1024), (a, b, t, onchip)
+    K.kf_dag_destroy(dag)
