@@ -310,6 +310,30 @@ kf_status kf_dag_run(kf_dag *dag, uint32_t cuts, const kf_video *video, float *o
 kf_status kf_dag_time_groups(kf_dag *dag, const kf_video *video, float *out, int64_t out_pitch, void *workspace,
                              size_t workspace_bytes, int reps, void *stream, float *ms);
 
+/* ------------------------------------------------------------------ learned cost model */
+/* A 3-layer MLP (width 64, ReLU, FP32) predicting a fused group's runtime from its
+ * KF_NFEAT features, in place of the execution-time estimate C_i of the partition model
+ * (Sec. VI, Fig. 5). Inputs: log1p(features) standardised by the training set; output:
+ * standardised log(ms). Parameters: W1 (64 x KF_NFEAT, row = unit), b1, W2 (64 x 64),
+ * b2, w3 (64), b3. The model lives in the context. */
+#define KF_MLP_NPARAMS (64 * KF_NFEAT + 64 + 64 * 64 + 64 + 64 + 1)
+/* Train on n measured groups (features n x KF_NFEAT, runtimes ms > 0) with `steps`
+ * full-batch Adam steps on the GPU (He initialisation from `seed`; deterministic). Device
+ * memory for the data and the optimiser is allocated for the call and freed before it
+ * returns. Returns the final mean squared error on the standardised log-runtimes. */
+kf_status kf_costmodel_train(kf_ctx *ctx, const float *features, const float *ms, int n, int steps, float lr,
+                             unsigned seed, float *final_loss);
+/* Host-side prediction (ms) for n feature rows; KF_ESTATE before training or set. */
+kf_status kf_costmodel_predict(kf_ctx *ctx, const float *features, int n, float *ms);
+/* Loss and gradient of the raw network (no standardisation) at `params` for inputs x
+ * (n x KF_NFEAT) and targets y, computed by the training kernels on the GPU. */
+kf_status kf_costmodel_grad(kf_ctx *ctx, const float *params, const float *x, const float *y, int n, float *grad,
+                            float *loss);
+/* Save / load: params (KF_MLP_NPARAMS), norm = feature means (KF_NFEAT), feature
+ * deviations (KF_NFEAT), log-runtime mean, log-runtime deviation. */
+kf_status kf_costmodel_get(kf_ctx *ctx, float *params, float *norm);
+kf_status kf_costmodel_set(kf_ctx *ctx, const float *params, const float *norm);
+
 /* ------------------------------------------------------------------ no-allocation run */
 /* kf_run with the workspace in a fixed array that the library itself holds on every GPU
  * that loads it (KF_STATIC_WORKSPACE_BYTES per GPU, kept until the process exits). The

@@ -20,14 +20,7 @@
 #include "../../include/kfuse.h"
 #include "kf_params.h"
 
-struct kf_ctx {
-    int device = -1;
-    int precision = KF_PREC_F32;
-    int chunk_rows = 200;
-    int last_cuda = 0;
-    int *d_err = nullptr;  // device error word of the bounded waits (4 bytes, owned)
-    std::vector<kf_stage_desc> stages;
-};
+#include "kf_ctx.h"
 
 namespace {
 
@@ -342,6 +335,7 @@ kf_status kf_create(int device, kf_ctx **out)
 
 kf_status kf_destroy(kf_ctx *ctx)
 {
+    if (ctx) kf::costmodel_free(ctx);
     if (ctx && ctx->d_err) {
         cudaSetDevice(ctx->device);
         cudaFree(ctx->d_err);

@@ -1,0 +1,21 @@
+// kf_ctx.h -- the context object behind the opaque kf_ctx handle (library-internal).
+#pragma once
+
+#include <vector>
+
+#include "../../include/kfuse.h"
+
+namespace kf {
+struct CostModel;                   // kf_mlp.cu
+void costmodel_free(kf_ctx *ctx);   // kf_mlp.cu
+}  // namespace kf
+
+struct kf_ctx {
+    int device = -1;
+    int precision = KF_PREC_F32;
+    int chunk_rows = 200;
+    int last_cuda = 0;
+    int *d_err = nullptr;  // device error word of the bounded waits (4 bytes, owned)
+    std::vector<kf_stage_desc> stages;
+    kf::CostModel *cm = nullptr;  // learned cost model (host parameters), owned
+};

@@ -106,6 +106,11 @@ def _lib():
             "kf_dag_workspace_bytes": (i32, [P, i64, i64, i64, P]),
             "kf_dag_run": (i32, [P, u32, P, P, i64, P, ctypes.c_size_t, P]),
             "kf_dag_time_groups": (i32, [P, P, P, i64, P, ctypes.c_size_t, i32, P, P]),
+            "kf_costmodel_train": (i32, [P, P, P, i32, i32, ctypes.c_float, ctypes.c_uint, P]),
+            "kf_costmodel_predict": (i32, [P, P, i32, P]),
+            "kf_costmodel_grad": (i32, [P, P, P, P, i32, P, P]),
+            "kf_costmodel_get": (i32, [P, P, P]),
+            "kf_costmodel_set": (i32, [P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -122,7 +127,9 @@ def exported_symbols() -> list[str]:
             "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static",
             "kf_track_workspace_bytes", "kf_track", "kf_batch_workspace_bytes", "kf_batch_create",
             "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows", "kf_dag_create", "kf_dag_destroy",
-            "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups"]
+            "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups",
+            "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_grad", "kf_costmodel_get",
+            "kf_costmodel_set"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -388,6 +395,59 @@ def kf_dag_time_groups(dag, n: int, frames, W: int, out, workspace, reps: int = 
                                                            workspace.data_ptr(), workspace.numel(), int(reps),
                                                            _stream(stream), ms))
     return list(ms)
+
+
+KF_MLP_NPARAMS = 64 * KF_NFEAT + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def _fptr(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data
+
+
+def kf_costmodel_train(ctx, features, ms, steps: int = 2000, lr: float = 3e-3, seed: int = 0) -> float:
+    """features: [n, KF_NFEAT], ms: [n] (numpy). Returns the final standardised MSE."""
+    f, fp = _fptr(features)
+    m, mp = _fptr(ms)
+    loss = ctypes.c_float()
+    _check("kf_costmodel_train", _lib().kf_costmodel_train(ctx, fp, mp, int(m.shape[0]), int(steps), float(lr),
+                                                           int(seed), ctypes.byref(loss)), ctx)
+    return loss.value
+
+
+def kf_costmodel_predict(ctx, features):
+    import numpy as np
+    f, fp = _fptr(features)
+    out = np.empty(f.shape[0], dtype=np.float32)
+    _check("kf_costmodel_predict", _lib().kf_costmodel_predict(ctx, fp, int(f.shape[0]), out.ctypes.data), ctx)
+    return out
+
+
+def kf_costmodel_grad(ctx, params, x, y):
+    import numpy as np
+    p, pp = _fptr(params)
+    xx, xp = _fptr(x)
+    yy, yp = _fptr(y)
+    g = np.empty(KF_MLP_NPARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check("kf_costmodel_grad", _lib().kf_costmodel_grad(ctx, pp, xp, yp, int(yy.shape[0]), g.ctypes.data,
+                                                         ctypes.byref(loss)), ctx)
+    return loss.value, g
+
+
+def kf_costmodel_get(ctx):
+    import numpy as np
+    p = np.empty(KF_MLP_NPARAMS, dtype=np.float32)
+    nrm = np.empty(2 * KF_NFEAT + 2, dtype=np.float32)
+    _check("kf_costmodel_get", _lib().kf_costmodel_get(ctx, p.ctypes.data, nrm.ctypes.data), ctx)
+    return p, nrm
+
+
+def kf_costmodel_set(ctx, params, norm) -> None:
+    p, pp = _fptr(params)
+    n, np_ = _fptr(norm)
+    _check("kf_costmodel_set", _lib().kf_costmodel_set(ctx, pp, np_), ctx)
 
 
 KF_STATIC_WORKSPACE_BYTES = 64 << 20
