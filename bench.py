@@ -462,6 +462,60 @@ def run_batch48(args):
                       "chunk_rows": best_rows, "device_error": K.kf_device_error(ctx.h)}), flush=True)
 
 
+def run_costmodel(args):
+    """The learned-cost-model workload: 400 random kernel DAGs (12-24 stages) on synthetic
+    1080x1920 video; every candidate group of every DAG is timed by the executor on a
+    prefix of the video (per-frame cost does not depend on the frame count); the MLP is
+    trained on 300 DAGs and ranks partitions of the 100 held out, judged by the measured
+    cost of its choice against the measured optimum and against the traffic model."""
+    import torch
+    from paper_1509_04394_gb300 import build as kbuild
+    from paper_1509_04394_gb300 import costmodel as cm
+    from paper_1509_04394_gb300 import kfuse as K
+    from synth import dags as sd
+    kbuild.build()
+    dev = torch.device("cuda:0")
+    W, H, T = 1920, 1080, args.cm_frames
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=5), pitch=W)
+    f = torch.from_numpy(fr).to(dev)
+    ctx = K.kf_create(0)
+    t0 = time.time()
+    meas = [cm.measure(ctx, sd.to_array(sd.random_dag(4000 + s)), f, W, 4000 + s) for s in range(400)]
+    t1 = time.time()
+    X, y = cm.dataset(meas[:300])
+    loss = K.kf_costmodel_train(ctx, X, y, steps=4000, lr=3e-3, seed=1)
+    t2 = time.time()
+    ev = cm.evaluate(ctx, meas[300:])
+    # end-to-end check of the additive model: run the chosen partitions of 10 held-out DAGs
+    e2e = []
+    for m in meas[300:310]:
+        dag = K.kf_dag_create(ctx, m.rows)
+        ws = torch.empty(K.kf_dag_workspace_bytes(dag, W, H, T), dtype=torch.uint8, device=dev)
+        out = torch.empty((T, H, W), dtype=torch.float32, device=dev)
+        row = next(r for r in ev["per_dag"] if r["seed"] == m.seed)
+        for name, cuts in row["plans"].items():
+            K.kf_dag_run(dag, cuts, f, W, out, ws)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                K.kf_dag_run(dag, cuts, f, W, out, ws)
+            e1.record()
+            torch.cuda.synchronize()
+            e2e.append({"seed": m.seed, "plan": name, "run_ms": e0.elapsed_time(e1) / 3,
+                        "sum_of_groups_ms": cm.partition_cost(m, cuts)})
+        K.kf_dag_destroy(dag)
+        del ws, out
+    ev.pop("per_dag")
+    ratio = [r["run_ms"] / r["sum_of_groups_ms"] for r in e2e]
+    print(json.dumps({"workload": f"400 random DAGs (12-24 stages), 1080x1920 u8, groups timed on {T} frames",
+                      "train_dags": 300, "held_out_dags": 100, "train_samples": int(len(y)),
+                      "final_std_mse": loss, "measure_s": t1 - t0, "train_s": t2 - t1, **ev,
+                      "end_to_end_over_sum_of_groups": {"median": float(np.median(ratio)), "min": float(min(ratio)),
+                                                        "max": float(max(ratio)), "runs": len(ratio)}}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -474,12 +528,16 @@ def main():
     ap.add_argument("--f16", action="store_true", help="FP16 maps for --profile")
     ap.add_argument("--track", action="store_true", help="--profile the whole path with tracking")
     ap.add_argument("--batch48", action="store_true", help="the 48-video batching workload")
+    ap.add_argument("--costmodel", action="store_true", help="the learned-cost-model workload")
+    ap.add_argument("--cm-frames", type=int, default=4, help="frames the groups are timed on (--costmodel)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.batch48:
+    if args.costmodel:
+        run_costmodel(args)
+    elif args.batch48:
         run_batch48(args)
     elif args.profile:
         run_profile(args)
