@@ -112,6 +112,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time (replicas: every rank processes its own volume)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(pixels_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job Mpixel/s: the pixels of all ranks over the slowest rank's time."""
+    return world * pixels_per_rank / (ms / 1000) / 1e6
+
+
 # ------------------------------------------------------------------ workload
 def make_video(rank: int, T: int | None = None):
     P = sv.pitch_for(SPEC.W)
@@ -250,12 +267,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             fn()
         ev1.record(stream)
         barrier()
-        ms = ev0.elapsed_time(ev1) / k
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ev0.elapsed_time(ev1) / k, world, dev)
 
     def step():  # the whole hot path: fused chain, corner selection, LK tracking
         K.kf_track(ctx.h, frames, W, mask, counts, KP, n_pts, idx, uu, vv, st, ws_track, stream)
@@ -283,7 +295,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     dev_err = K.kf_device_error(ctx.h)
 
     px = T * H * W
-    value = world * px / (ms / 1000) / 1e6
+    value = job_rate(px, world, ms)
     hbm_peak, peak_kind = peaks()
     alg_bytes = 2 * px + 4 * T  # frames read once, mask written once, counts
     achieved = alg_bytes / (ms_chain / 1000) / 1e9
