@@ -779,6 +779,10 @@ kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners 
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     const int per_sm = kf::batch_chain_blocks_per_sm(track);
     if (per_sm < 1) return cuda_fail(ctx, cudaErrorInvalidConfiguration);
+    if (track) {
+        const int r = kf::prepare_select();
+        if (r) return cuda_fail(ctx, (cudaError_t)r);
+    }
     cudaStream_t cs;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(ctx, e);

@@ -480,9 +480,9 @@ template <int A, int B, bool F16, bool CAND = false> struct SmemPlan {
     static constexpr int BAR_OFF = 0;
     static constexpr int IN_OFF = 128;
     static constexpr int CAND_OFF = IN_OFF + NST * STAGE_BYTES;
-    static constexpr int CAND_BLOCK = RB * STRIP;  // corners of one 5-row block, at most
-    static constexpr int CAND_MAX = 1536;          // per-warp buffer, flushed when it may not hold another block
-    static constexpr int BYTES = CAND_OFF + (CAND ? CAND_MAX * 8 : 0);
+    static constexpr int CAND_LANE = 48;            // buffered corners per lane (entry j of lane l at j * 32 + l)
+    static constexpr int CAND_BLOCK = RB * C;       // corners a lane may add in one 5-row block, at most
+    static constexpr int BYTES = CAND_OFF + (CAND ? CAND_LANE * 32 * 8 : 0);
 };
 
 // ------------------------------------------------------------------ the group kernel
@@ -571,20 +571,29 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
     std::conditional_t<HAS8, NmsV, Empty> s8{};
     unsigned count = 0;
     [[maybe_unused]] unsigned long long *cand_buf = reinterpret_cast<unsigned long long *>(smem + SP::CAND_OFF);
-    [[maybe_unused]] unsigned cand_fill = 0;  // entries in cand_buf (warp-uniform)
+    [[maybe_unused]] unsigned cand_n = 0;  // this lane's buffered corners
+    // Hand the buffered corners to the frame's list: one global atomic per warp for the
+    // space, lane offsets from a warp scan of the lane counts. Done when some lane might
+    // not hold another 5-row block, and at the end of the job.
     auto flush_candidates = [&](bool force) {
         if constexpr (CAND) {
-            if (cand_fill && (force || cand_fill > (unsigned)(SP::CAND_MAX - SP::CAND_BLOCK))) {
-                __syncwarp();
+            if (__any_sync(FULL, force ? cand_n != 0 : cand_n > (unsigned)(SP::CAND_LANE - SP::CAND_BLOCK))) {
+                unsigned incl = cand_n;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const unsigned y = __shfl_up_sync(FULL, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                const unsigned total = __shfl_sync(FULL, incl, 31);
                 unsigned pos = 0;
-                if (lane == 0) pos = atomicAdd(reinterpret_cast<unsigned *>(p.cand_count) + frame, cand_fill);
+                if (lane == 0) pos = atomicAdd(reinterpret_cast<unsigned *>(p.cand_count) + frame, total);
                 pos = __shfl_sync(FULL, pos, 0);
                 unsigned long long *dst = p.cand + (int64_t)frame * p.cand_cap;
-                for (unsigned i = lane; i < cand_fill; i += 32)
-                    if (pos + i < (unsigned)p.cand_cap) dst[pos + i] = cand_buf[i];
-                if (lane == 0 && pos + cand_fill > (unsigned)p.cand_cap) atomicOr(p.err, DEVERR_OVERFLOW);
-                __syncwarp();
-                cand_fill = 0;
+                const unsigned mine = pos + incl - cand_n;
+                for (unsigned j = 0; j < cand_n; ++j)
+                    if (mine + j < (unsigned)p.cand_cap) dst[mine + j] = cand_buf[j * 32 + lane];
+                if (lane == 0 && pos + total > (unsigned)p.cand_cap) atomicOr(p.err, DEVERR_OVERFLOW);
+                cand_n = 0;
             }
         }
     };
@@ -689,24 +698,20 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
         // ---- group output row t - RYT
         const int o = t - RYT;
         if constexpr (CAND) {
-            // corner candidates of the tracking stage: appended to the warp's buffer in
-            // shared memory (positions from four ballots); one global atomic per flush, and
-            // a flush only when the buffer might not hold another 5-row block, or at the end
+            // corner candidates of the tracking stage: each lane appends its own to its
+            // column of the buffer in shared memory (no per-row warp coordination)
             if (o >= y0) {  // warp-uniform
-                const unsigned kept = bits & out_mask;
-                const unsigned lt = (1u << lane) - 1u;
-                unsigned base = cand_fill;
+                unsigned kept = bits & out_mask;
+                const unsigned lo0 = 0xffffffffu - (unsigned)(o * W + x0);  // ~raster of column x0
+                while (kept) {
+                    const int c = __ffs(kept) - 1;
+                    kept &= kept - 1;
+                    float rc = centre[0];
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const unsigned b = __ballot_sync(FULL, kept >> c & 1);
-                    if (kept >> c & 1) {
-                        const unsigned raster = (unsigned)(o * W + x0 + c);
-                        cand_buf[base + __popc(b & lt)] =
-                            (unsigned long long)__float_as_uint(centre[c]) << 32 | (0xffffffffu - raster);
-                    }
-                    base += __popc(b);
+                    for (int cc = 1; cc < C; ++cc) rc = c == cc ? centre[cc] : rc;
+                    cand_buf[cand_n * 32 + lane] = (unsigned long long)__float_as_uint(rc) << 32 | (lo0 - (unsigned)c);
+                    ++cand_n;
                 }
-                cand_fill = base;
             }
         }
         if (o >= y0 && out_mask) {  // o < y1 holds: t < y1 + RYT

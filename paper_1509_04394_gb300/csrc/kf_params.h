@@ -38,7 +38,13 @@ KF_HD constexpr bool hstencil_before(int a, int k) { for (int j = a; j < k; ++j)
 
 // Capacity of a frame's corner-candidate list for the tracking stage: a quarter of the
 // frame (3x3 maxima cannot be denser, except on plateaus), at least 1024.
-inline int64_t cand_capacity(int64_t W, int64_t H) { const int64_t q = (W * H + 3) / 4; return q < 1024 ? 1024 : q; }
+// keys per frame: a quarter of the pixels (3x3 maxima are at most that dense), at least
+// 1024, even (each frame's list starts on 16 bytes)
+inline int64_t cand_capacity(int64_t W, int64_t H)
+{
+    const int64_t q = (W * H + 3) / 4;
+    return q < 1024 ? 1024 : q + (q & 1);
+}
 
 // Integer scale of the FP32 map written by stage k: scaled = true * map_scale(k).
 inline constexpr double map_scale(int k)
@@ -113,6 +119,7 @@ LaunchFn launcher_a8(int B, int f16);
 int launch_chain_with_candidates(const GroupParams &p, unsigned grid, void *stream);
 // tracking kernels over one video (vids == nullptr: `one`) or a table of n videos with
 // total_frames frames in all
+int prepare_select();  // per-device launch attributes of the selection kernel (before graph capture)
 int launch_select(const TrackVideo &one, const TrackVideo *vids, int n, int64_t total_frames, int K, void *stream);
 int launch_lk(const TrackVideo &one, const TrackVideo *vids, int n, int64_t total_frames, int K, void *stream);
 int launch_batch_chain(const GroupParams *videos, const int64_t *item_begin, int n_videos, unsigned long long *queue,

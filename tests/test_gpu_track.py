@@ -138,3 +138,16 @@ def test_slow_checker_patches_are_tracked_to_their_true_motion(dev):
                     errs.append(np.hypot(out["u"][t, i] - sc.vx[o], out["v"][t, i] - sc.vy[o]))
     assert len(errs) >= 30
     assert np.median(errs) <= 0.25
+
+
+@pytest.mark.parametrize("H,W,Kp", [(480, 640, 256), (720, 960, 1024), (720, 960, 7)])
+def test_selection_with_many_candidates(dev, H, W, Kp):
+    """Noise frames: about 3% of pixels are corner candidates, so the 480 x 640 frames'
+    lists (~9k keys) are selected from shared memory and the 720 x 960 frames' (~21k
+    keys) from global memory."""
+    rng = np.random.default_rng(H + Kp)
+    fr = rng.integers(0, 256, (3, H, W), dtype=np.uint8)
+    out = run_track(dev, fr, W, Kp)
+    assert out["counts"][1] > (12288 if H == 720 else 5000)
+    checked = sum(check_frame(fr, t, W, out, Kp) for t in range(1, 3))
+    assert checked >= min(Kp, 5)
