@@ -37,14 +37,16 @@ WORKLOAD = "Harris 8-stage chain, 1000 frames x 800 rows x 600 cols u8, 64 blobs
 
 
 def kernel_counters():
-    """ncu counters of the fused kernel from profiles/fused_chain_traffic.json, only while
-    the kernel source still hashes to the captured version (else None)."""
+    """ncu counters of the step's dominant kernel (the fused chain with corner lists) from
+    profiles/fused_chain_traffic.json, only while its source still hashes to the captured
+    version (else None)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "fused_chain_traffic.json")) as fh:
             rec = json.load(fh)
         h = hashlib.sha256()
-        for f in ("paper_1509_04394_gb300/csrc/kf_chain.cuh", "paper_1509_04394_gb300/csrc/kf_params.h"):
+        for f in ("paper_1509_04394_gb300/csrc/kf_chain.cuh", "paper_1509_04394_gb300/csrc/kf_params.h",
+                  "paper_1509_04394_gb300/csrc/kf_groups_a1.cu"):
             with open(os.path.join(ROOT, f), "rb") as fh:
                 h.update(fh.read())
         return rec if rec.get("source_sha256") == h.hexdigest() else None
@@ -257,10 +259,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(fn, k, w):
+    def timed(fn, k, w, between=None):
         for _ in range(w):
             fn()
         barrier()
+        if between:
+            between()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(k):
@@ -287,7 +291,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     while time.time() - t_soak < 1.5:
         step()
         torch.cuda.synchronize(dev)
-    ms = timed(step, args.steps, args.warmup)
+    # the step, with each of its kernels bracketed by CUDA events on the launching stream
+    K.kf_set_kernel_timing(ctx.h, True)
+    ms = timed(step, args.steps, args.warmup, between=lambda: K.kf_kernel_times(ctx.h))
+    kt = K.kf_kernel_times(ctx.h)
+    K.kf_set_kernel_timing(ctx.h, False)
     ms_chain = timed(chain, args.steps, args.warmup)
     t_b = time.time()
     clk.stop()
@@ -297,8 +305,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     px = T * H * W
     value = job_rate(px, world, ms)
     hbm_peak, peak_kind = peaks()
-    alg_bytes = 2 * px + 4 * T  # frames read once, mask written once, counts
-    achieved = alg_bytes / (ms_chain / 1000) / 1e9
+    n_corners = int(counts.sum())
+    # per-kernel device time inside the timed step (max over ranks)
+    kernels = {}
+    for name, (n, tot) in kt.items():
+        if n:
+            kernels[name] = {"launches": n, "ms_per_launch": max_over_ranks(tot / n, world, dev)}
+    step_kernel_ms = sum(k["ms_per_launch"] * k["launches"] for k in kernels.values())
+    for k in kernels.values():
+        k["share"] = k["ms_per_launch"] * k["launches"] / step_kernel_ms
+    dom = kernels["chain_corners"]["ms_per_launch"]
+    # algorithmic bytes of the dominant kernel: frames read once, mask written once, one
+    # 8-byte key per corner, the per-frame corner and candidate counts
+    alg_bytes = 2 * px + 8 * n_corners + 8 * T
+    achieved = alg_bytes / (dom / 1000) / 1e9
     rec = kernel_counters() if T == 1000 else None
     traffic = rec["dram_bytes_per_launch_1000_frames"] if rec else None
     # instruction-issue roofline: 152 SMs x 4 schedulers x 1 warp instruction per cycle
@@ -306,10 +326,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e9  # G warp-instructions / s
     alu = None
     if rec:
-        ach = rec["warp_instructions_per_launch_1000_frames"] / (ms_chain / 1000) / 1e9
+        ach = rec["warp_instructions_per_launch_1000_frames"] / (dom / 1000) / 1e9
         alu = {"bound": "alu", "achieved": ach, "peak": issue_peak, "unit": "Gwarp-inst/s",
                "frac": ach / issue_peak, "peak_kind": "152 SMs x 4 schedulers x SM clock",
-               "instructions_per_launch": rec["warp_instructions_per_launch_1000_frames"]}
+               "instructions_per_launch": rec["warp_instructions_per_launch_1000_frames"],
+               "kernel": rec["kernel"]}
 
     # batched form: the same workload as one video of a persistent-kernel batch (graph replay)
     bws = torch.empty(K.kf_batch_workspace_bytes(ctx.h, [frames], [W], KP), dtype=torch.uint8, device=dev)
@@ -370,10 +391,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "frames_per_s": world * T / (ms / 1000),
         "tracked_points_per_s": world * tracked / (ms / 1000),
         "chain_only": {"value": world * px / (ms_chain / 1000) / 1e6, "ms_per_step": ms_chain,
-                       "kernel": "group_kernel<1,8> (full fusion)"},
+                       "kernel": "group_kernel<1,8> (full fusion, no corner lists), timed alone by kf_run",
+                       "hbm_frac": (2 * px + 4 * T) / (ms_chain / 1000) / 1e9 / hbm_peak},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "fused chain, timed alone", "algorithmic_bytes_per_launch": alg_bytes},
+                     "kernel": "group_kernel<1,8> with corner lists (the step's dominant kernel, timed inside the step)",
+                     "ms_per_launch": dom, "algorithmic_bytes_per_launch": alg_bytes},
+        "kernels_in_step": kernels,
         "alu_roofline": alu,
         "batched_form": {"value": world * px / (ms_batch / 1000) / 1e6, "ms_per_step": ms_batch,
                          "what": "the same step as one video of a persistent-kernel batch replayed from a CUDA graph",
@@ -386,7 +410,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                         "hbm_frac": 50 * px / (ms_unf16 / 1000) / 1e9 / hbm_peak},
         "e2e": {"value": world * px / (ms_e2e / 1000) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e},
-        "gpu_launches": 3 * args.steps,  # fused chain, selection, LK per step
+        "gpu_launches": sum(k["launches"] for k in kernels.values()),  # counted by the library's event pairs
         "device_error": dev_err,
         "clocks": clocks,
     }

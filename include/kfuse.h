@@ -354,6 +354,22 @@ kf_status kf_costmodel_set(kf_ctx *ctx, const float *params, const float *norm);
 #define KF_STATIC_WORKSPACE_BYTES (64u << 20)
 kf_status kf_run_static(kf_ctx *ctx, uint32_t cuts, const kf_video *video, const kf_corners *out, void *stream);
 
+/* ------------------------------------------------------------------ kernel timing */
+/* Per-kernel device time of the library's own launches (instrumentation; the paper
+ * times whole kernels the same way, Sec. VI). While timing is on, kf_run, kf_run_group
+ * and kf_track record a CUDA event pair on the launching stream around every kernel they
+ * launch (the work itself is unchanged); kf_kernel_times waits for the recorded events
+ * and returns, per kernel kind, the launches and their summed milliseconds since the
+ * previous kf_kernel_times (or since timing was switched on), then clears the record.
+ * Kinds: KF_KT_GROUP a fused group of the chain (kf_run, kf_run_group), KF_KT_CHAIN_CORNERS
+ * the fully fused chain that also lists each frame's corners (kf_track), KF_KT_SELECT the
+ * corner selection, KF_KT_LK the Lucas-Kanade step. Events are created on first use and
+ * reused; KF_ECUDA if an event call fails. Not for use inside stream capture. */
+typedef enum { KF_KT_GROUP = 0, KF_KT_CHAIN_CORNERS = 1, KF_KT_SELECT = 2, KF_KT_LK = 3, KF_KT_COUNT = 4 } kf_kernel_kind;
+kf_status kf_set_kernel_timing(kf_ctx *ctx, int on);
+/* launches[KF_KT_COUNT], ms[KF_KT_COUNT]: host arrays */
+kf_status kf_kernel_times(kf_ctx *ctx, int64_t *launches, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -233,6 +233,50 @@ kf_status fill_params(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &o
 }
 
 // Enqueue group [A..B] (1-based) with already validated maps.
+// kernel timing: an event pair around one launch when the context's timing is on
+cudaEvent_t timing_event(kf_ctx *c)
+{
+    if (!c->spare_events.empty()) {
+        cudaEvent_t e = c->spare_events.back();
+        c->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+}
+struct TimedLaunch {
+    kf_ctx *c;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    TimedLaunch(kf_ctx *ctx, int k, cudaStream_t st) : c(ctx), kind(k), s(st)
+    {
+        if (!c->timing) return;
+        a = timing_event(c);
+        b = timing_event(c);
+        if (a && b && cudaEventRecord(a, s) == cudaSuccess) return;
+        if (a) c->spare_events.push_back(a);
+        if (b) c->spare_events.push_back(b);
+        a = b = nullptr;  // this launch goes untimed
+    }
+    void done()  // after a successful launch
+    {
+        if (!a) return;
+        if (cudaEventRecord(b, s) == cudaSuccess) {
+            c->timed.push_back({kind, a, b});
+        } else {
+            c->spare_events.push_back(a);
+            c->spare_events.push_back(b);
+        }
+        a = b = nullptr;
+    }
+    ~TimedLaunch()
+    {
+        if (a) c->spare_events.push_back(a);
+        if (b) c->spare_events.push_back(b);
+    }
+};
+
 kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &out, int64_t W, int64_t H, int64_t T,
                        int32_t *counts, cudaStream_t s, unsigned long long *cand = nullptr, int *cand_count = nullptr,
                        int64_t cand_cap = 0)
@@ -250,8 +294,10 @@ kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &
     kf::LaunchFn fn = cand ? ((A == 1 && B == kf::NSTAGES) ? kf::launch_chain_with_candidates : nullptr)
                            : launcher(A, B, f16 ? 1 : 0);
     if (!fn) return KF_EINVAL;
+    TimedLaunch tl(c, cand ? KF_KT_CHAIN_CORNERS : KF_KT_GROUP, s);
     const int e = fn(p, (unsigned)blocks, s);
     if (e != 0) return cuda_fail(c, (cudaError_t)e);
+    tl.done();
     return KF_OK;
 }
 
@@ -336,6 +382,14 @@ kf_status kf_create(int device, kf_ctx **out)
 kf_status kf_destroy(kf_ctx *ctx)
 {
     if (ctx) kf::costmodel_free(ctx);
+    if (ctx && (!ctx->timed.empty() || !ctx->spare_events.empty())) {
+        cudaSetDevice(ctx->device);
+        for (const kf_ctx::Timed &t : ctx->timed) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+        for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
+    }
     if (ctx && ctx->d_err) {
         cudaSetDevice(ctx->device);
         cudaFree(ctx->d_err);
@@ -630,11 +684,51 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf
     tv.u = tr->u;
     tv.v = tr->v;
     tv.frame_begin = 0;
-    int r = kf::launch_select(tv, nullptr, 1, v->T, tr->K, stream);
-    if (r) return cuda_fail(ctx, (cudaError_t)r);
-    r = kf::launch_lk(tv, nullptr, 1, v->T, tr->K, stream);
-    if (r) return cuda_fail(ctx, (cudaError_t)r);
+    {
+        TimedLaunch tl(ctx, KF_KT_SELECT, s);
+        const int r = kf::launch_select(tv, nullptr, 1, v->T, tr->K, stream);
+        if (r) return cuda_fail(ctx, (cudaError_t)r);
+        tl.done();
+    }
+    {
+        TimedLaunch tl(ctx, KF_KT_LK, s);
+        const int r = kf::launch_lk(tv, nullptr, 1, v->T, tr->K, stream);
+        if (r) return cuda_fail(ctx, (cudaError_t)r);
+        tl.done();
+    }
     return KF_OK;
+}
+
+kf_status kf_set_kernel_timing(kf_ctx *ctx, int on)
+{
+    if (!ctx) return KF_EINVAL;
+    ctx->timing = on != 0;
+    return KF_OK;
+}
+
+kf_status kf_kernel_times(kf_ctx *ctx, int64_t *launches, double *ms)
+{
+    if (!ctx || !launches || !ms) return KF_EINVAL;
+    for (int k = 0; k < KF_KT_COUNT; ++k) {
+        launches[k] = 0;
+        ms[k] = 0.0;
+    }
+    cudaError_t err = cudaSuccess;
+    for (const kf_ctx::Timed &t : ctx->timed) {
+        float dt = 0.f;
+        cudaError_t e = cudaEventSynchronize(t.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&dt, t.a, t.b);
+        if (e == cudaSuccess) {
+            launches[t.kind] += 1;
+            ms[t.kind] += dt;
+        } else if (err == cudaSuccess) {
+            err = e;
+        }
+        ctx->spare_events.push_back(t.a);
+        ctx->spare_events.push_back(t.b);
+    }
+    ctx->timed.clear();
+    return err == cudaSuccess ? KF_OK : cuda_fail(ctx, err);
 }
 
 }  // extern "C"

@@ -147,6 +147,55 @@ struct GaussV {
     }
 };
 
+// Stages 2-3 on the frame's bytes, two columns per 32-bit word (16-bit lanes: lo = column
+// c, hi = column c + 1). Used by groups that start at the frames and contain both
+// Gaussian passes. All Gaussian values are integers (g1' <= 16 * 255, g' <= 65280 < 2^16)
+// and every partial sum is at most its total, so no lane carries into the next and the
+// results equal the FP32 passes exactly.
+__device__ __forceinline__ uint32_t binom5_packed(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e)
+{
+    return (a + e) + ((b + d) << 2) + c * 6u;
+}
+// g1' of the lane's 4 columns from its bytes w and its neighbours' (L left, R right):
+// h01 = (g1'(x0), g1'(x0+1)), h23 = (g1'(x0+2), g1'(x0+3))
+__device__ __forceinline__ void gauss_h_packed(uint32_t L, uint32_t w, uint32_t R, uint32_t &h01, uint32_t &h23)
+{
+    static_assert(C == 4, "packed Gaussian assumes 4 columns per lane");
+    const uint32_t pm2 = __byte_perm(L, 0, 0x4342);  // (b-2, b-1)
+    const uint32_t p0 = __byte_perm(w, 0, 0x4140);   // (b0, b1)
+    const uint32_t p2 = __byte_perm(w, 0, 0x4342);   // (b2, b3)
+    const uint32_t p4 = __byte_perm(R, 0, 0x4140);   // (b4, b5)
+    const uint32_t pm1 = __funnelshift_r(pm2, p0, 16), p1 = __funnelshift_r(p0, p2, 16), p3 = __funnelshift_r(p2, p4, 16);
+    h01 = binom5_packed(pm2, pm1, p0, p1, p2);
+    h23 = binom5_packed(p0, p1, p2, p3, p4);
+}
+// Stage 3 as four (1,1) passes on the packed words (as GaussV, two columns per word).
+struct GaussVPacked {
+    uint32_t z[4][2];
+    __device__ __forceinline__ void fill(const uint32_t (&x)[2])
+    {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) { z[0][c] = x[c]; z[1][c] = x[c] << 1; z[2][c] = x[c] << 2; z[3][c] = x[c] << 3; }
+    }
+    __device__ __forceinline__ void replay(uint32_t (&x)[2])
+    {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) x[c] = z[0][c];
+    }
+    __device__ __forceinline__ void push(const uint32_t (&x)[2], uint32_t (&o)[2])
+    {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t a = x[c] + z[0][c], b = a + z[1][c], d = b + z[2][c];
+            o[c] = d + z[3][c];
+            z[0][c] = x[c]; z[1][c] = a; z[2][c] = b; z[3][c] = d;
+        }
+    }
+};
+// the two 16-bit lanes of a word as FP32 (exact)
+__device__ __forceinline__ float lo16_to_float(uint32_t x) { return __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7610)) - 8388608.0f; }
+__device__ __forceinline__ float hi16_to_float(uint32_t x) { return __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7632)) - 8388608.0f; }
+
 // Stage 4: Sobel. Per row: Dx = g(x+1) - g(x-1), Sx = g(x-1) + 2 g(x) + g(x+1);
 // then Ix = Dx(r-1) + 2 Dx(r) + Dx(r+1) = (1,1)^2 pass of Dx, Iy = Sx(r+1) - Sx(r-1) =
 // (1,-1) then (1,1) pass of Sx. Output row = input row - 1.
@@ -358,16 +407,18 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 // frame edge, the elements of the clamped columns) and converts them to float.
 template <typename TM> struct Staged;
 template <> struct Staged<uint8_t> {
+    // the lane's 4 bytes (clamped columns for a lane at a frame edge) in one word
+    __device__ __forceinline__ static uint32_t word(const unsigned char *row, int lane, bool inside, const int (&off)[C])
+    {
+        if (inside) return *reinterpret_cast<const uint32_t *>(row + C * lane);
+        uint32_t w = 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) w |= (uint32_t)row[off[c]] << (8 * c);
+        return w;
+    }
     __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float, float (&v)[C])
     {
-        uint32_t w;
-        if (inside) {
-            w = *reinterpret_cast<const uint32_t *>(row + C * lane);
-        } else {
-            w = 0;
-#pragma unroll
-            for (int c = 0; c < C; ++c) w |= (uint32_t)row[off[c]] << (8 * c);
-        }
+        const uint32_t w = word(row, lane, inside, off);
 #pragma unroll
         for (int c = 0; c < C; ++c) v[c] = u8_to_float(w, c);
     }
@@ -565,7 +616,10 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
     __syncwarp();
 
     // on-chip state of the vertical stages
-    std::conditional_t<HAS3, GaussV, Empty> s3{};
+    // groups that start at the frames and contain both Gaussian passes run them packed
+    constexpr bool PACKED = A == 1 && B >= 3 && std::is_same<TIN, uint8_t>::value;
+    std::conditional_t<HAS3 && !PACKED, GaussV, Empty> s3{};
+    std::conditional_t<PACKED, GaussVPacked, Empty> s3p{};
     std::conditional_t<HAS4, SobelV, Empty> s4{};
     std::conditional_t<HAS6, BoxV, Empty> s6{};
     std::conditional_t<HAS8, NmsV, Empty> s8{};
@@ -608,12 +662,30 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
         // ---- group input row t (staged; rows past the last copied stage are stale and unused)
         const unsigned char *srow = sbuf + PH * SP::ROW_BYTES;
         [[maybe_unused]] Rows<NIN> in;
+        [[maybe_unused]] Rows<1> f;
+        [[maybe_unused]] Rows<1> g1;
+        [[maybe_unused]] Rows<1> g;
+        if constexpr (PACKED) {
+            // ---- stages 2-3 on packed bytes, input row t (stage 3: input row t - D3)
+            const uint32_t w = Staged<uint8_t>::word(srow, lane, lane_inside, off);
+            const uint32_t L = __shfl_up_sync(FULL, w, 1), R = __shfl_down_sync(FULL, w, 1);
+            uint32_t h[2], o[2];
+            gauss_h_packed(L, w, R, h[0], h[1]);
+            if (border) {
+                const int i = t - D3;
+                if (i == 0) s3p.fill(h);
+                if (i >= H) s3p.replay(h);
+            }
+            s3p.push(h, o);
+            g.v[0][0] = lo16_to_float(o[0]);
+            g.v[0][1] = hi16_to_float(o[0]);
+            g.v[0][2] = lo16_to_float(o[1]);
+            g.v[0][3] = hi16_to_float(o[1]);
+        } else {
 #pragma unroll
         for (int m = 0; m < NIN; ++m) Staged<TIN>::read(srow + m * SP::CH_BYTES, lane, lane_inside, off, in_scale, in.v[m]);
-        [[maybe_unused]] Rows<1> f;
         if constexpr (A == 1) f = in;
         // ---- stage 2 (horizontal Gaussian)
-        [[maybe_unused]] Rows<1> g1;
         if constexpr (A <= 2 && 2 <= B) {
             if constexpr (A == 1) gauss_h(f.v[0], g1.v[0]);
             else gauss_h(in.v[0], g1.v[0]);
@@ -621,7 +693,6 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
             g1 = in;
         }
         // ---- stage 3 (vertical Gaussian), input row t - D3
-        [[maybe_unused]] Rows<1> g;
         if constexpr (HAS3) {
             if (border) {
                 const int i = t - D3;
@@ -631,6 +702,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
             s3.push(g1.v[0], g.v[0]);
         } else if constexpr (A == 4) {
             g = in;
+        }
         }
         // ---- stage 4 (Sobel), input row t - D4
         [[maybe_unused]] Rows<2> ixy;

@@ -1,6 +1,8 @@
 // kf_ctx.h -- the context object behind the opaque kf_ctx handle (library-internal).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <vector>
 
 #include "../../include/kfuse.h"
@@ -18,4 +20,9 @@ struct kf_ctx {
     int *d_err = nullptr;  // device error word of the bounded waits (4 bytes, owned)
     std::vector<kf_stage_desc> stages;
     kf::CostModel *cm = nullptr;  // learned cost model (host parameters), owned
+    // kernel timing: recorded (kind, start, end) event triples, and spare events (owned)
+    struct Timed { int kind; cudaEvent_t a, b; };
+    bool timing = false;
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> spare_events;
 };

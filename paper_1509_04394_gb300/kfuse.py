@@ -111,6 +111,8 @@ def _lib():
             "kf_costmodel_grad": (i32, [P, P, P, P, i32, P, P]),
             "kf_costmodel_get": (i32, [P, P, P]),
             "kf_costmodel_set": (i32, [P, P, P]),
+            "kf_set_kernel_timing": (i32, [P, i32]),
+            "kf_kernel_times": (i32, [P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -129,7 +131,7 @@ def exported_symbols() -> list[str]:
             "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows", "kf_dag_create", "kf_dag_destroy",
             "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups",
             "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_grad", "kf_costmodel_get",
-            "kf_costmodel_set"]
+            "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -460,6 +462,23 @@ def kf_run_static(ctx, cuts: int, frames, W: int, mask, counts, stream=None) -> 
     v = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
     o = kf_corners(mask.data_ptr(), int(mask.shape[2]), counts.data_ptr())
     _check("kf_run_static", _lib().kf_run_static(ctx, cuts, ctypes.byref(v), ctypes.byref(o), _stream(stream)), ctx)
+
+
+KF_KT_GROUP, KF_KT_CHAIN_CORNERS, KF_KT_SELECT, KF_KT_LK, KF_KT_COUNT = 0, 1, 2, 3, 4
+KERNEL_KINDS = ("group", "chain_corners", "select", "lk")
+
+
+def kf_set_kernel_timing(ctx, on: bool) -> None:
+    """Bracket every kernel the context launches with CUDA events on its stream."""
+    _check("kf_set_kernel_timing", _lib().kf_set_kernel_timing(ctx, 1 if on else 0), ctx)
+
+
+def kf_kernel_times(ctx) -> dict[str, tuple[int, float]]:
+    """Per kernel kind: (launches, summed ms) since the previous call; clears the record."""
+    n = (ctypes.c_int64 * KF_KT_COUNT)()
+    ms = (ctypes.c_double * KF_KT_COUNT)()
+    _check("kf_kernel_times", _lib().kf_kernel_times(ctx, n, ms), ctx)
+    return {KERNEL_KINDS[k]: (int(n[k]), float(ms[k])) for k in range(KF_KT_COUNT)}
 
 
 def make_map(planes, dtype: int) -> kf_map:

@@ -151,3 +151,33 @@ def test_selection_with_many_candidates(dev, H, W, Kp):
     assert out["counts"][1] > (12288 if H == 720 else 5000)
     checked = sum(check_frame(fr, t, W, out, Kp) for t in range(1, 3))
     assert checked >= min(Kp, 5)
+
+
+def test_kernel_timing_counts_every_launch(dev):
+    """With timing on, kf_track records one event pair per kernel it launches (the chain
+    with corner lists, selection, LK) and kf_run one per fused group; the record clears."""
+    fr, _ = sv.generate(sv.VideoSpec(T=3, H=96, W=160, seed=5, n_blobs=6, n_patches=4), pitch=sv.pitch_for(160))
+    T, H, P = fr.shape
+    ctx = K.Context(0)
+    frames = torch.from_numpy(fr).to(dev)
+    mask = torch.zeros_like(frames)
+    counts = torch.zeros(T, dtype=torch.int32, device=dev)
+    n = torch.zeros(T, dtype=torch.int32, device=dev)
+    idx = torch.zeros((T, 16), dtype=torch.int32, device=dev)
+    u, v = torch.zeros((T, 16), device=dev), torch.zeros((T, 16), device=dev)
+    st = torch.zeros((T, 16), dtype=torch.int32, device=dev)
+    ws = torch.empty(K.kf_track_workspace_bytes(ctx.h, 160, H, T), dtype=torch.uint8, device=dev)
+    K.kf_track(ctx.h, frames, 160, mask, counts, 16, n, idx, u, v, st, ws)  # untimed
+    K.kf_set_kernel_timing(ctx.h, True)
+    for _ in range(2):
+        K.kf_track(ctx.h, frames, 160, mask, counts, 16, n, idx, u, v, st, ws)
+    cuts = 0b1000100  # three groups
+    wsr = torch.empty(K.kf_workspace_bytes(ctx.h, cuts, 160, H, T), dtype=torch.uint8, device=dev)
+    K.kf_run(ctx.h, cuts, frames, 160, mask, counts, wsr)
+    kt = K.kf_kernel_times(ctx.h)
+    assert {k: c for k, (c, _) in kt.items()} == {"group": 3, "chain_corners": 2, "select": 2, "lk": 2}
+    assert all(ms > 0 for c, ms in kt.values())
+    assert all(c == 0 for c, _ in K.kf_kernel_times(ctx.h).values())
+    K.kf_set_kernel_timing(ctx.h, False)
+    K.kf_track(ctx.h, frames, 160, mask, counts, 16, n, idx, u, v, st, ws)
+    assert all(c == 0 for c, _ in K.kf_kernel_times(ctx.h).values())
