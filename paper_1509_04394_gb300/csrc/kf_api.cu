@@ -153,15 +153,16 @@ CUtensorMapDataType tmap_dtype(int dt)
 
 int dtype_bytes(int dt) { return dt == KF_DT_U8 ? 1 : (dt == KF_DT_F32 ? 4 : 2); }
 
-// 3-D descriptor {W, H, T} of one plane; box {STRIP, RB, 1}; out-of-frame reads give 0.
-bool encode_plane(CUtensorMap *m, const void *plane, int dt, int64_t pitch, int64_t fstride, int64_t W, int64_t H, int64_t T)
+// 3-D descriptor {W, H, T} of one plane; box {box_x, RB, 1}; out-of-frame reads give 0.
+bool encode_plane(CUtensorMap *m, const void *plane, int dt, int64_t pitch, int64_t fstride, int64_t W, int64_t H, int64_t T,
+                  int box_x = kf::STRIP)
 {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return false;
     const int e = dtype_bytes(dt);
     cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
     cuuint64_t strides[2] = {(cuuint64_t)(pitch * e), (cuuint64_t)(fstride * e)};
-    cuuint32_t box[3] = {(cuuint32_t)kf::STRIP, (cuuint32_t)kf::RB, 1};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)kf::RB, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(m, tmap_dtype(dt), 3, const_cast<void *>(plane), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -220,9 +221,15 @@ kf_status fill_params(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &o
     p.xs0 = sg.xs0;
     p.step = sg.step;
     p.n_strips = sg.n_strips;
+    p.half_last = sg.half_last;
+    if (p.half_last)
+        for (int i = 0; i < in.channels; ++i)
+            if (!encode_plane(&p.tmap_half[i], in.plane[i], in.dtype, in.pitch, in.frame_stride, W, H, T, kf::STRIP / 2))
+                return KF_EINVAL;
+    p.T = (int)T;
     p.chunk_rows = c->chunk_rows;
     p.n_chunks = (int)((H + c->chunk_rows - 1) / c->chunk_rows);
-    p.n_jobs = T * p.n_chunks * p.n_strips;
+    p.n_jobs = T * p.n_chunks * (p.n_strips - p.half_last) + (T + 1) / 2 * p.n_chunks * p.half_last;
     p.thr = (float)(NMS_THRESHOLD * kf::map_scale(7));
     const bool f16 = c->precision == KF_PREC_F16;
     // FP16 maps (stages 4-7) hold true units; uint16 and FP32 maps hold scaled units

@@ -64,11 +64,12 @@ __device__ __forceinline__ float pick(const float (&v)[C], int c)
 
 // Columns of this lane outside [0, W) take the value of the edge column (per-stage
 // clamp of an on-chip map). Warp-uniform: called only by warps that cross an edge.
+// lbase: first lane of the lane's strip (16 for the second half strip of a pair).
 template <int N>
-__device__ __forceinline__ void fix_edges(Rows<N> &r, int xs, int x0, int W, bool L, bool R)
+__device__ __forceinline__ void fix_edges(Rows<N> &r, int xs, int x0, int W, bool L, bool R, int lbase)
 {
     if (L) {
-        const int src = (-xs) / C;  // column 0 sits at register 0 of lane src (xs % C == 0)
+        const int src = lbase + (-xs) / C;  // column 0 sits at register 0 of lane src (xs % C == 0)
 #pragma unroll
         for (int m = 0; m < N; ++m) {
             const float e = __shfl_sync(FULL, r.v[m][0], src);
@@ -77,7 +78,7 @@ __device__ __forceinline__ void fix_edges(Rows<N> &r, int xs, int x0, int W, boo
         }
     }
     if (R) {
-        const int src = (W - 1 - xs) / C, reg = (W - 1 - xs) % C;
+        const int src = lbase + (W - 1 - xs) / C, reg = (W - 1 - xs) % C;
 #pragma unroll
         for (int m = 0; m < N; ++m) {
             const float e = __shfl_sync(FULL, pick(r.v[m], reg), src);
@@ -524,7 +525,13 @@ template <int A, int B, bool F16, bool CAND = false> struct SmemPlan {
     static constexpr int ELEM = (int)sizeof(MapT<A - 1, F16>);
     static constexpr int ROW_BYTES = STRIP * ELEM;               // one staged row of one channel
     static constexpr int CH_BYTES = RB * ROW_BYTES;              // one stage of one channel
-    static constexpr int STAGE_BYTES = NIN * CH_BYTES;
+    // a half-strip job stages two frames' half rows as two blocks of RB x ROW_BYTES/2,
+    // the second at HALF_OFF (TMA destinations stay on 128 bytes)
+    static constexpr int HALF_ROW = ROW_BYTES / 2;
+    static constexpr int HALF_OFF = (RB * HALF_ROW + 127) / 128 * 128;
+    static constexpr int CH_STRIDE = ((CH_BYTES > HALF_OFF + RB * HALF_ROW ? CH_BYTES : HALF_OFF + RB * HALF_ROW) + 127) / 128 * 128;
+    static constexpr int STAGE_BYTES = NIN * CH_STRIDE;
+    static constexpr int TX_BYTES = NIN * CH_BYTES;              // bytes one stage's copies bring
     static constexpr int NST = STAGE_BYTES <= 2048 ? 4 : (STAGE_BYTES <= 4096 ? 3 : 2);
     static_assert(RB == 5, "one stage per 5-row block (the box ring period)");
     static constexpr bool HAS6 = A <= 6 && 6 <= B;
@@ -542,7 +549,7 @@ template <int A, int B, bool F16, bool CAND = false> struct SmemPlan {
 // memory, batched launches); `kbase` counts the staging-ring stages used by earlier jobs
 // of this warp, so the ring's mbarrier phases carry over from job to job. Returns false
 // when a bounded wait expired (the warp must stop).
-template <int A, int B, bool F16, bool CAND>
+template <int A, int B, bool F16, bool CAND, bool PAIRED>
 __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsigned char *smem, unsigned &kbase,
                                         bool global_desc)
 {
@@ -563,10 +570,29 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
     unsigned char *stage_buf = smem + SP::IN_OFF;
 
     const int lane = threadIdx.x & 31;
-    const int strip = (int)(job % p.n_strips);
-    const int64_t rest = job / p.n_strips;
-    const int chunk = (int)(rest % p.n_chunks);
-    const int frame = (int)(rest / p.n_chunks);
+    // jobs: full strips (frame, chunk, strip) first, then the half strips of frame pairs
+    const int full_strips = p.n_strips - p.half_last;
+    const int64_t full_jobs = (int64_t)p.T * p.n_chunks * full_strips;
+    constexpr bool paired = PAIRED;  // job >= full_jobs
+    int strip, chunk, frame0;
+    if constexpr (!paired) {
+        strip = (int)(job % full_strips);
+        const int64_t rest = job / full_strips;
+        chunk = (int)(rest % p.n_chunks);
+        frame0 = (int)(rest / p.n_chunks);
+    } else {
+        const int64_t q = job - full_jobs;
+        strip = p.n_strips - 1;
+        chunk = (int)(q % p.n_chunks);
+        frame0 = 2 * (int)(q / p.n_chunks);
+    }
+    // a pair's lanes 16-31 run frame0 + 1 (none when T is odd and this is the last pair:
+    // those lanes then recompute frame0's half strip and store nothing)
+    const int half = paired ? lane >> 4 : 0;
+    const int sl = paired ? lane & 15 : lane;  // lane within its strip
+    const int lbase = lane - sl;
+    const bool active = frame0 + half < p.T;
+    const int frame = active ? frame0 + half : frame0;
     const int W = p.W, H = p.H;
     // per-job copies of the fields the row loop uses: with `p` in global memory the
     // compiler could not keep them in registers across the loop's stores
@@ -575,16 +601,19 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
     void *const out_plane[3] = {p.out[0], p.out[1], p.out[2]};
 
     const int xs = p.xs0 + strip * p.step;  // multiple of 16 columns: TMA-aligned
-    const int x0 = xs + C * lane;
+    const int x0 = xs + C * sl;
     const int xo0 = max(xs + RXT, 0), xo1 = min(xs + RXT + p.step, W);
-    const bool edgeL = xs < 0, edgeR = xs + STRIP > W;
+    const bool edgeL = xs < 0, edgeR = xs + (paired ? STRIP / 2 : STRIP) > W;
     const bool lane_inside = (x0 >= 0) && (x0 + C <= W);
     int off[C];  // staged-tile offset of each column's clamped source
 #pragma unroll
     for (int c = 0; c < C; ++c) off[c] = min(max(x0 + c, 0), W - 1) - xs;
     unsigned out_mask = 0;
 #pragma unroll
-    for (int c = 0; c < C; ++c) out_mask |= (x0 + c >= xo0 && x0 + c < xo1) ? (1u << c) : 0u;
+    for (int c = 0; c < C; ++c) out_mask |= (active && x0 + c >= xo0 && x0 + c < xo1) ? (1u << c) : 0u;
+    // staged rows of this lane's strip: base, row pitch, and the lane's position in them
+    const int lane_sbase = paired ? half * SP::HALF_OFF : 0;
+    const int row_pitch = paired ? SP::HALF_ROW : SP::ROW_BYTES;
 
     const int y0 = chunk * p.chunk_rows, y1 = min(y0 + p.chunk_rows, H);
     const int t_begin = max(y0 - RYT, 0), t_end = y1 + RYT;
@@ -597,19 +626,30 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
     int issued = 0;  // stages issued so far (the same count on every lane)
     auto slot = [&](int k) { return (int)((kbase + (unsigned)k) % SP::NST); };
     auto parity = [&](int k) { return ((kbase + (unsigned)k) / SP::NST) & 1u; };
+    const int frame1 = min(frame0 + 1, p.T - 1);
     auto issue = [&](int k) {  // lane 0 only
         uint64_t *bar = bars + slot(k);
         unsigned char *dst = stage_buf + slot(k) * SP::STAGE_BYTES;
-        mbar_expect_tx(bar, SP::STAGE_BYTES);
+        mbar_expect_tx(bar, SP::TX_BYTES);
+        if constexpr (!paired) {
 #pragma unroll
-        for (int m = 0; m < NIN; ++m) tma_load_3d(dst + m * SP::CH_BYTES, &p.tmap[m], xs, t_begin + k * RB, frame, bar);
+            for (int m = 0; m < NIN; ++m) tma_load_3d(dst + m * SP::CH_STRIDE, &p.tmap[m], xs, t_begin + k * RB, frame0, bar);
+        } else {
+#pragma unroll
+            for (int m = 0; m < NIN; ++m) {
+                tma_load_3d(dst + m * SP::CH_STRIDE, &p.tmap_half[m], xs, t_begin + k * RB, frame0, bar);
+                tma_load_3d(dst + m * SP::CH_STRIDE + SP::HALF_OFF, &p.tmap_half[m], xs, t_begin + k * RB, frame1, bar);
+            }
+        }
     };
     __syncwarp();  // the previous job's lanes have read every stage buffer
     if (lane == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (global_desc)  // descriptor written to global memory by the host before the launch
-            for (int m = 0; m < NIN; ++m)
-                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(&p.tmap[m])) : "memory");
+            for (int m = 0; m < NIN; ++m) {
+                const CUtensorMap *d = paired ? &p.tmap_half[m] : &p.tmap[m];
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(d)) : "memory");
+            }
         for (int k = 0; k < SP::NST && k < n_stages; ++k) issue(k);
     }
     issued = min(SP::NST, n_stages);
@@ -632,21 +672,23 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
     auto flush_candidates = [&](bool force) {
         if constexpr (CAND) {
             if (__any_sync(FULL, force ? cand_n != 0 : cand_n > (unsigned)(SP::CAND_LANE - SP::CAND_BLOCK))) {
+                // scan within each strip's lanes (two 16-lane segments in a half-strip pair)
+                const int seg = paired ? 16 : 32;
                 unsigned incl = cand_n;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
-                    const unsigned y = __shfl_up_sync(FULL, incl, d);
-                    if (lane >= d) incl += y;
+                    const unsigned y = __shfl_up_sync(FULL, incl, d, seg);
+                    if (d < seg && sl >= d) incl += y;
                 }
-                const unsigned total = __shfl_sync(FULL, incl, 31);
+                const unsigned total = __shfl_sync(FULL, incl, seg - 1, seg);
                 unsigned pos = 0;
-                if (lane == 0) pos = atomicAdd(reinterpret_cast<unsigned *>(p.cand_count) + frame, total);
-                pos = __shfl_sync(FULL, pos, 0);
+                if (sl == 0 && total) pos = atomicAdd(reinterpret_cast<unsigned *>(p.cand_count) + frame, total);
+                pos = __shfl_sync(FULL, pos, 0, seg);
                 unsigned long long *dst = p.cand + (int64_t)frame * p.cand_cap;
                 const unsigned mine = pos + incl - cand_n;
                 for (unsigned j = 0; j < cand_n; ++j)
                     if (mine + j < (unsigned)p.cand_cap) dst[mine + j] = cand_buf[j * 32 + lane];
-                if (lane == 0 && pos + total > (unsigned)p.cand_cap) atomicOr(p.err, DEVERR_OVERFLOW);
+                if (sl == 0 && pos + total > (unsigned)p.cand_cap) atomicOr(p.err, DEVERR_OVERFLOW);
                 cand_n = 0;
             }
         }
@@ -660,14 +702,14 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
         constexpr int PH = decltype(phase_tag)::value;
         const bool border = (t <= RYT) || (t >= H);
         // ---- group input row t (staged; rows past the last copied stage are stale and unused)
-        const unsigned char *srow = sbuf + PH * SP::ROW_BYTES;
+        const unsigned char *srow = sbuf + lane_sbase + PH * row_pitch;
         [[maybe_unused]] Rows<NIN> in;
         [[maybe_unused]] Rows<1> f;
         [[maybe_unused]] Rows<1> g1;
         [[maybe_unused]] Rows<1> g;
         if constexpr (PACKED) {
             // ---- stages 2-3 on packed bytes, input row t (stage 3: input row t - D3)
-            const uint32_t w = Staged<uint8_t>::word(srow, lane, lane_inside, off);
+            const uint32_t w = Staged<uint8_t>::word(srow, sl, lane_inside, off);
             const uint32_t L = __shfl_up_sync(FULL, w, 1), R = __shfl_down_sync(FULL, w, 1);
             uint32_t h[2], o[2];
             gauss_h_packed(L, w, R, h[0], h[1]);
@@ -683,7 +725,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
             g.v[0][3] = hi16_to_float(o[1]);
         } else {
 #pragma unroll
-        for (int m = 0; m < NIN; ++m) Staged<TIN>::read(srow + m * SP::CH_BYTES, lane, lane_inside, off, in_scale, in.v[m]);
+        for (int m = 0; m < NIN; ++m) Staged<TIN>::read(srow + m * SP::CH_STRIDE, sl, lane_inside, off, in_scale, in.v[m]);
         if constexpr (A == 1) f = in;
         // ---- stage 2 (horizontal Gaussian)
         if constexpr (A <= 2 && 2 <= B) {
@@ -708,7 +750,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
         [[maybe_unused]] Rows<2> ixy;
         if constexpr (HAS4) {
             if constexpr (hstencil_before(A, 4))
-                if (edgeL | edgeR) fix_edges<1>(g, xs, x0, W, edgeL, edgeR);
+                if (edgeL | edgeR) fix_edges<1>(g, xs, x0, W, edgeL, edgeR, lbase);
             float dx[C], sx[C];
             sobel_h(g.v[0], dx, sx);
             if (border) {
@@ -724,7 +766,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
         [[maybe_unused]] Rows<3> pr;
         if constexpr (A <= 5 && 5 <= B) {
             if constexpr (hstencil_before(A, 6) && HAS6)
-                if (edgeL | edgeR) fix_edges<2>(ixy, xs, x0, W, edgeL, edgeR);
+                if (edgeL | edgeR) fix_edges<2>(ixy, xs, x0, W, edgeL, edgeR, lbase);
             products(ixy, pr);
         } else if constexpr (A == 6) {
             pr = in;
@@ -757,7 +799,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
         [[maybe_unused]] float centre[C];
         if constexpr (HAS8) {
             if constexpr (hstencil_before(A, 8))
-                if (edgeL | edgeR) fix_edges<1>(r7, xs, x0, W, edgeL, edgeR);
+                if (edgeL | edgeR) fix_edges<1>(r7, xs, x0, W, edgeL, edgeR, lbase);
             float mh[C];
             nms_h(r7.v[0], mh);
             if (border) {
@@ -773,17 +815,16 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
             // corner candidates of the tracking stage: each lane appends its own to its
             // column of the buffer in shared memory (no per-row warp coordination)
             if (o >= y0) {  // warp-uniform
-                unsigned kept = bits & out_mask;
+                const unsigned kept = bits & out_mask;
                 const unsigned lo0 = 0xffffffffu - (unsigned)(o * W + x0);  // ~raster of column x0
-                while (kept) {
-                    const int c = __ffs(kept) - 1;
-                    kept &= kept - 1;
-                    float rc = centre[0];
+                unsigned long long *slot = cand_buf + cand_n * 32 + lane;
 #pragma unroll
-                    for (int cc = 1; cc < C; ++cc) rc = c == cc ? centre[cc] : rc;
-                    cand_buf[cand_n * 32 + lane] = (unsigned long long)__float_as_uint(rc) << 32 | (lo0 - (unsigned)c);
-                    ++cand_n;
+                for (int c = 0; c < C; ++c) {  // straight-line, predicated: no divergent loop
+                    const bool k = kept >> c & 1;
+                    if (k) *slot = (unsigned long long)__float_as_uint(centre[c]) << 32 | (lo0 - (unsigned)c);
+                    slot += k ? 32 : 0;
                 }
+                cand_n = (unsigned)(slot - cand_buf - lane) >> 5;
             }
         }
         if (o >= y0 && out_mask) {  // o < y1 holds: t < y1 + RYT
@@ -859,8 +900,12 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
     }
     flush_candidates(true);  // what is left at the end of the job
     if constexpr (B == 8) {
-        const unsigned tot = __reduce_add_sync(FULL, count);
-        if (lane == 0 && tot) atomicAdd(p.counts + frame, (int)tot);
+        // per strip: one 32-lane strip, or the two 16-lane halves of a pair
+        unsigned tot = count;
+#pragma unroll
+        for (int d = 8; d > 0; d >>= 1) tot += __shfl_xor_sync(FULL, tot, d);
+        tot += paired ? 0u : __shfl_xor_sync(FULL, tot, 16);
+        if (sl == 0 && tot) atomicAdd(p.counts + frame, (int)tot);
     }
     kbase += (unsigned)n_stages;
     return true;
@@ -878,6 +923,16 @@ __device__ __forceinline__ void init_ring(unsigned char *smem)
     __syncwarp();
 }
 
+// a job of either kind: full strip, or a pair of half strips (warp-uniform choice)
+template <int A, int B, bool F16, bool CAND>
+__device__ __forceinline__ bool run_any_job(const GroupParams &p, int64_t job, unsigned char *smem, unsigned &kbase,
+                                            bool global_desc)
+{
+    if (job < (int64_t)p.T * p.n_chunks * (p.n_strips - p.half_last))
+        return run_job<A, B, F16, CAND, false>(p, job, smem, kbase, global_desc);
+    return run_job<A, B, F16, CAND, true>(p, job, smem, kbase, global_desc);
+}
+
 // One job per block (one warp): the launch's blocks enumerate the jobs.
 template <int A, int B, bool F16, bool CAND = false>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN_BLOCKS_BOX : MIN_BLOCKS) group_kernel(const __grid_constant__ GroupParams p)
@@ -886,7 +941,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN
     if ((int64_t)blockIdx.x >= p.n_jobs) return;
     init_ring<SmemPlan<A, B, F16, CAND>::NST>(smem);
     unsigned kbase = 0;
-    run_job<A, B, F16, CAND>(p, blockIdx.x, smem, kbase, false);
+    run_any_job<A, B, F16, CAND>(p, blockIdx.x, smem, kbase, false);
 }
 
 // Persistent batch over many videos (the fully fused chain): each resident warp pops
@@ -911,7 +966,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, MIN_BLOCKS_BOX) batch_ke
             const int mid = (lo + hi + 1) >> 1;
             if (item_begin[mid] <= (int64_t)item) lo = mid; else hi = mid - 1;
         }
-        if (!run_job<1, 8, false, CAND>(videos[lo], (int64_t)item - item_begin[lo], smem, kbase, true)) break;
+        if (!run_any_job<1, 8, false, CAND>(videos[lo], (int64_t)item - item_begin[lo], smem, kbase, true)) break;
     }
 }
 

@@ -55,6 +55,7 @@ inline constexpr double map_scale(int k)
 
 struct GroupParams {
     CUtensorMap tmap[3];      // TMA descriptors of the input planes: {W, H, T}, box {STRIP, RB, 1}
+    CUtensorMap tmap_half[3]; // the same planes with box {STRIP/2, RB, 1} (half strips; unused otherwise)
     int *err;                 // device error word (bounded waits that expired)
     const void *in[3];        // input planes (stage A-1 map; u8 frames when A == 1)
     int64_t in_pitch;         // elements between rows
@@ -64,8 +65,10 @@ struct GroupParams {
     int32_t *counts;          // per-frame corner counts (B == 8), pre-zeroed
     int W, H;                 // frame size
     int xs0, step, n_strips;  // strip s covers input columns [xs0 + s*step, +STRIP)
+    int half_last;            // 1: the last strip is half wide, and one warp runs it for two frames
+    int T;                    // frames
     int chunk_rows, n_chunks;
-    int64_t n_jobs;           // frames * n_chunks * n_strips
+    int64_t n_jobs;           // T * n_chunks * (n_strips - half_last) + ceil(T/2) * n_chunks * half_last
     float thr;                // NMS threshold in the scaled units of R
     float in_scale;           // FP16 input maps: scaled value = stored * in_scale
     float out_scale;          // FP16 output maps: stored = scaled value * out_scale
@@ -93,7 +96,10 @@ struct TrackVideo {
 // Strip geometry of a group with accumulated horizontal radius rxt: input strips start
 // on a multiple of STRIP_ALIGN columns (a legal TMA x for every map type), outputs tile
 // the frame exactly.
-struct StripGeom { int xs0, step, n_strips; };
+// The last strip is a half strip (STRIP/2 columns) when that width still reaches the
+// frame's last column; a warp then runs the half strips of two frames side by side
+// (lanes 0-15 and 16-31), so the mostly idle last strip costs half a warp per frame.
+struct StripGeom { int xs0, step, n_strips, half_last; };
 inline StripGeom strip_geometry(int rxt, int W)
 {
     StripGeom g;
@@ -101,6 +107,8 @@ inline StripGeom strip_geometry(int rxt, int W)
     g.step = ((STRIP - 2 * rxt) / STRIP_ALIGN) * STRIP_ALIGN;
     const int o0 = g.xs0 + rxt;  // first output column of strip 0 (<= 0)
     g.n_strips = (W - o0 + g.step - 1) / g.step;
+    const int xs_last = g.xs0 + (g.n_strips - 1) * g.step;
+    g.half_last = (g.n_strips > 1 && xs_last + STRIP / 2 - rxt >= W) ? 1 : 0;
     return g;
 }
 

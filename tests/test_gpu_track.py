@@ -100,7 +100,8 @@ def check_frame(fr, t, W, out, Kp):
     return checked
 
 
-@pytest.mark.parametrize("shape,Kp", [((4, 192, 432), 256), ((3, 77, 130), 64), ((3, 40, 50), 1024), ((3, 96, 150), 1)])
+@pytest.mark.parametrize("shape,Kp", [((4, 192, 432), 256), ((3, 77, 130), 64), ((3, 40, 50), 1024), ((3, 96, 150), 1),
+                                      ((5, 120, 600), 256)])
 def test_tracking_matches_the_oracle(dev, shape, Kp):
     T, H, W = shape
     fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=41, n_blobs=12, n_patches=8), pitch=sv.pitch_for(W))
