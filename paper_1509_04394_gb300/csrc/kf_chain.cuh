@@ -544,13 +544,34 @@ template <int A, int B, bool F16, bool CAND = false> struct SmemPlan {
 };
 
 // ------------------------------------------------------------------ the group kernel
-// One job: a STRIP-column strip of one frame over one chunk of rows of the group [A..B].
-// `p` is the launch's parameter block (param space) or one video's descriptor (global
-// memory, batched launches); `kbase` counts the staging-ring stages used by earlier jobs
-// of this warp, so the ring's mbarrier phases carry over from job to job. Returns false
-// when a bounded wait expired (the warp must stop).
+// Job order: the full strips (strip fastest, then chunk, then frame), then the half-strip
+// jobs of the frame pairs (chunk fastest). The half-strip jobs run a second instance of
+// the row loop; kept together at the end, each SM runs one instance at a time, which
+// keeps the instruction cache to one loop body (interleaving them with the full strips,
+// to find their columns still in L2, measured 40% slower).
+struct JobPos { int strip, chunk, frame0; bool paired; };
+__device__ __forceinline__ JobPos decode_job(const GroupParams &p, int64_t job)
+{
+    JobPos j;
+    const int F = p.n_strips - p.half_last;  // full strips per frame
+    const int64_t full_jobs = (int64_t)p.T * p.n_chunks * F;
+    j.paired = job >= full_jobs;
+    if (!j.paired) {
+        j.strip = (int)(job % F);
+        const int64_t rest = job / F;
+        j.chunk = (int)(rest % p.n_chunks);
+        j.frame0 = (int)(rest / p.n_chunks);
+    } else {
+        const int64_t q = job - full_jobs;
+        j.strip = F;
+        j.chunk = (int)(q % p.n_chunks);
+        j.frame0 = 2 * (int)(q / p.n_chunks);
+    }
+    return j;
+}
+
 template <int A, int B, bool F16, bool CAND, bool PAIRED>
-__device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsigned char *smem, unsigned &kbase,
+__device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, unsigned char *smem, unsigned &kbase,
                                         bool global_desc)
 {
     static_assert(!CAND || B == 8, "corner candidates come from the NMS stage");
@@ -570,22 +591,8 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, int64_t job, unsig
     unsigned char *stage_buf = smem + SP::IN_OFF;
 
     const int lane = threadIdx.x & 31;
-    // jobs: full strips (frame, chunk, strip) first, then the half strips of frame pairs
-    const int full_strips = p.n_strips - p.half_last;
-    const int64_t full_jobs = (int64_t)p.T * p.n_chunks * full_strips;
-    constexpr bool paired = PAIRED;  // job >= full_jobs
-    int strip, chunk, frame0;
-    if constexpr (!paired) {
-        strip = (int)(job % full_strips);
-        const int64_t rest = job / full_strips;
-        chunk = (int)(rest % p.n_chunks);
-        frame0 = (int)(rest / p.n_chunks);
-    } else {
-        const int64_t q = job - full_jobs;
-        strip = p.n_strips - 1;
-        chunk = (int)(q % p.n_chunks);
-        frame0 = 2 * (int)(q / p.n_chunks);
-    }
+    constexpr bool paired = PAIRED;  // == jp.paired
+    const int strip = jp.strip, chunk = jp.chunk, frame0 = jp.frame0;
     // a pair's lanes 16-31 run frame0 + 1 (none when T is odd and this is the last pair:
     // those lanes then recompute frame0's half strip and store nothing)
     const int half = paired ? lane >> 4 : 0;
@@ -928,9 +935,9 @@ template <int A, int B, bool F16, bool CAND>
 __device__ __forceinline__ bool run_any_job(const GroupParams &p, int64_t job, unsigned char *smem, unsigned &kbase,
                                             bool global_desc)
 {
-    if (job < (int64_t)p.T * p.n_chunks * (p.n_strips - p.half_last))
-        return run_job<A, B, F16, CAND, false>(p, job, smem, kbase, global_desc);
-    return run_job<A, B, F16, CAND, true>(p, job, smem, kbase, global_desc);
+    const JobPos jp = decode_job(p, job);
+    if (!jp.paired) return run_job<A, B, F16, CAND, false>(p, jp, smem, kbase, global_desc);
+    return run_job<A, B, F16, CAND, true>(p, jp, smem, kbase, global_desc);
 }
 
 // One job per block (one warp): the launch's blocks enumerate the jobs.
