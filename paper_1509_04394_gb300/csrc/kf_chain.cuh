@@ -538,9 +538,11 @@ template <int A, int B, bool F16, bool CAND = false> struct SmemPlan {
     static constexpr int BAR_OFF = 0;
     static constexpr int IN_OFF = 128;
     static constexpr int CAND_OFF = IN_OFF + NST * STAGE_BYTES;
-    static constexpr int CAND_LANE = 48;            // buffered corners per lane (entry j of lane l at j * 32 + l)
+    static constexpr int CAND_LANE = 32;            // buffered corners per lane (entry j of lane l at j * 32 + l)
     static constexpr int CAND_BLOCK = RB * C;       // corners a lane may add in one 5-row block, at most
-    static constexpr int BYTES = CAND_OFF + (CAND ? CAND_LANE * 32 * 8 : 0);
+    static constexpr int RING_OFF = CAND_OFF + (CAND ? CAND_LANE * 32 * 8 : 0);
+    static constexpr int RING_BYTES = RB * 32 * C * 4;  // R of the block's output rows, per lane
+    static constexpr int BYTES = RING_OFF + (CAND ? RING_BYTES : 0);
 };
 
 // ------------------------------------------------------------------ the group kernel
@@ -673,6 +675,26 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
     unsigned count = 0;
     [[maybe_unused]] unsigned long long *cand_buf = reinterpret_cast<unsigned long long *>(smem + SP::CAND_OFF);
     [[maybe_unused]] unsigned cand_n = 0;  // this lane's buffered corners
+    // Corners of the current 5-row block: bit 4*PH + c of cand_bits marks column c of the
+    // output row of phase PH, whose R values wait in r_ring[PH][lane]; at the end of the
+    // block each lane turns its marked corners into keys in its buffer column.
+    [[maybe_unused]] float4 *r_ring = reinterpret_cast<float4 *>(smem + SP::RING_OFF);
+    [[maybe_unused]] unsigned cand_bits = 0;
+    [[maybe_unused]] int cand_o0 = 0;  // output row of phase 0 of the block
+    auto emit_candidates = [&]() {
+        if constexpr (CAND) {
+            while (cand_bits) {  // divergent: lanes with corners only
+                const int j = __ffs(cand_bits) - 1;
+                cand_bits &= cand_bits - 1;
+                const int ph = j >> 2, c = j & 3;
+                const float4 rv = r_ring[ph * 32 + lane];
+                const float r = c == 0 ? rv.x : c == 1 ? rv.y : c == 2 ? rv.z : rv.w;
+                const unsigned raster = (unsigned)((cand_o0 + ph) * W + x0 + c);
+                cand_buf[cand_n * 32 + lane] = (unsigned long long)__float_as_uint(r) << 32 | (0xffffffffu - raster);
+                ++cand_n;
+            }
+        }
+    };
     // Hand the buffered corners to the frame's list: one global atomic per warp for the
     // space, lane offsets from a warp scan of the lane counts. Done when some lane might
     // not hold another 5-row block, and at the end of the job.
@@ -819,20 +841,10 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         // ---- group output row t - RYT
         const int o = t - RYT;
         if constexpr (CAND) {
-            // corner candidates of the tracking stage: each lane appends its own to its
-            // column of the buffer in shared memory (no per-row warp coordination)
-            if (o >= y0) {  // warp-uniform
-                const unsigned kept = bits & out_mask;
-                const unsigned lo0 = 0xffffffffu - (unsigned)(o * W + x0);  // ~raster of column x0
-                unsigned long long *slot = cand_buf + cand_n * 32 + lane;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {  // straight-line, predicated: no divergent loop
-                    const bool k = kept >> c & 1;
-                    if (k) *slot = (unsigned long long)__float_as_uint(centre[c]) << 32 | (lo0 - (unsigned)c);
-                    slot += k ? 32 : 0;
-                }
-                cand_n = (unsigned)(slot - cand_buf - lane) >> 5;
-            }
+            // corner candidates of the tracking stage: mark them, keep the row's R
+            if constexpr (PH == 0) cand_o0 = o;
+            r_ring[PH * 32 + lane] = make_float4(centre[0], centre[1], centre[2], centre[3]);
+            if (o >= y0) cand_bits |= (bits & out_mask) << (4 * PH);  // warp-uniform test
         }
         if (o >= y0 && out_mask) {  // o < y1 holds: t < y1 + RYT
             const int64_t ooff = out_frame + (int64_t)o * out_pitch + x0;
@@ -888,6 +900,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         step(P3{}, t + 3, sbuf);
         if (t + 4 >= t_end) break;
         step(P4{}, t + 4, sbuf);
+        emit_candidates();
         flush_candidates(false);
         if (k + SP::NST < n_stages) {
             __syncwarp();  // every lane has read the stage
@@ -905,6 +918,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         for (int k = k_fail; k < issued; ++k) mbar_wait(bars + slot(k), parity(k));
         return false;
     }
+    emit_candidates();       // a block cut short by the end of the job
     flush_candidates(true);  // what is left at the end of the job
     if constexpr (B == 8) {
         // per strip: one 32-lane strip, or the two 16-lane halves of a pair
