@@ -5,6 +5,8 @@ cpu_baseline / reference legs may import this package. The library's product pat
 never touches it, and it shares no code with the CUDA path.
 
 `chain` wraps the C oracle (kf_oracle.c, compiled with gcc on first use);
+`pchain` is the paper's own chain (Table II / Table IV: gray, IIR, Gaussian, gradient,
+threshold, then Kalman) in numpy;
 `partition` restates the paper's traffic model and enumerates partitions by brute
 force (Sec. VI, Fig. 5, Sec. VI-D).
 """
