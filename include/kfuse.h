@@ -354,6 +354,65 @@ kf_status kf_costmodel_set(kf_ctx *ctx, const float *params, const float *norm);
 #define KF_STATIC_WORKSPACE_BYTES (64u << 20)
 kf_status kf_run_static(kf_ctx *ctx, uint32_t cuts, const kf_video *video, const kf_corners *out, void *stream);
 
+/* ------------------------------------------------------------------ the paper's own chain */
+/* The chain of Sec. VII (Table II / Table IV), as one more fusable set: K1 convert RGBA to
+ * gray, K2 IIR filter (a point operation over frames), K3 Gaussian smoothing, K4 gradient
+ * filter, K5 threshold computation; then K6, a Kalman filter over feature positions,
+ * after the kernel-to-kernel dependency. The paper names the steps, not their formulas;
+ * the readings (all in the library's scaled units, true value = scaled / scale):
+ *   K1  Y' = 77 R + 150 G + 29 B                        (scale 65280; alpha ignored)
+ *   K2  y'_0 = Y'_0, y'_t = y'_{t-1} + (Y'_t - y'_{t-1}) / 4   (FP32; scale 65280)
+ *   K3  G' = sum w(dy) w(dx) y'(clamp(p + d)), w = [1 2 1]     (scale 16 * 65280)
+ *   K4  M' = |sum s(dy) (G'(y+dy,x+1) - G'(y+dy,x-1))| + |same transposed|, s = [1 2 1],
+ *       indices clamped on G'                                  (scale 16 * 65280)
+ *   K5  mask = M' > 0.25 * 16 * 65280 (u8 0/1); per frame the mask count; per region of a
+ *       4 x 4 grid (region of pixel (y, x) = (4y / H) * 4 + 4x / W, integer division) the
+ *       mask pixels' count, sum of x and sum of y (int32 triples; frames whose sums
+ *       could pass 2^31, max(W, H) (W H / 16 + W + H) >= 2^31, are rejected)
+ *   K6  per region, a constant-velocity Kalman filter (state px, py, vx, vy; white
+ *       acceleration q = 0.5 per frame; measurement = the region's mask centroid, noise
+ *       r = 4 px^2; starts at the first frame with a measurement, P0 = diag(r, r, 100, 100))
+ * Partitions of K1..K5: bit i of `cuts` (i = 0..3) cuts between K(i+1) and K(i+2); 0 is
+ * "Full Fusion", 0b0010 (K1 K2 | K3 K4 K5) the paper's "Two Fusion", 0b1111 "No Fusion".
+ * Maps between groups are FP32 planes of the workspace. Execution: each warp owns a
+ * 32 x 32 tile of the group's input (lanes = columns, rows streamed); a group holding K2
+ * keeps its 32 IIR states per lane in registers and walks all T frames, so no IIR state
+ * ever goes through memory. */
+#define KF_PC_STAGES 5
+#define KF_PC_REGIONS 16
+typedef struct {
+    const uint8_t *rgba;  /* device, T x H rows of `pitch` pixels of 4 bytes (R, G, B, A) */
+    int64_t W, H, T;
+    int64_t pitch;        /* pixels per row, >= W; rgba 16-byte aligned */
+} kf_pc_video;
+typedef struct {
+    uint8_t *mask;        /* device, T x H x mask_pitch bytes */
+    int64_t mask_pitch;   /* >= W */
+    int32_t *counts;      /* device, [T], written (no pre-zeroing needed) */
+    int32_t *regions;     /* device, [T][KF_PC_REGIONS][3] (count, sum x, sum y), written */
+} kf_pc_out;
+/* Predicted bytes moved by a partition (Sec. VI-D with the executor's 32 x 32 tiles:
+ * a group reads its input tile with halo and writes its output tile; a group holding K2
+ * carries the filter state on chip, so it has no temporal halo). */
+kf_status kf_pc_traffic(kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_t T, double *bytes);
+/* The partition of minimum predicted traffic (exact DP over the 16). */
+kf_status kf_pc_plan(kf_ctx *ctx, int64_t W, int64_t H, int64_t T, uint32_t *cuts, double *bytes);
+/* Workspace of a partition: two FP32 planes of T x H x round_up(W, 8) (0 for cuts == 0). */
+kf_status kf_pc_workspace_bytes(kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_t T, size_t *bytes);
+kf_status kf_pc_run(kf_ctx *ctx, uint32_t cuts, const kf_pc_video *video, const kf_pc_out *out, void *workspace,
+                    size_t workspace_bytes, void *stream);
+/* One group [a..b] (0-based stages, a <= b <= 4) over explicit maps. in: a == 0 the RGBA
+ * frames (video), else an FP32 map [T][H][in_pitch] of stage a-1. out: b == 4 the mask
+ * outputs (out_mask), else an FP32 map [T][H][out_pitch] of stage b. */
+kf_status kf_pc_run_group(kf_ctx *ctx, int a, int b, const kf_pc_video *video, const float *in, int64_t in_pitch,
+                          float *out, int64_t out_pitch, const kf_pc_out *out_mask, void *stream);
+/* K6 over [T][n_tracks][3] region sums (device): states [T][n_tracks][4] (FP64, device) and
+ * status [T][n_tracks] (0 not started, 1 updated, 2 predicted only). One thread per track
+ * walks the frames; the x and y axes share one 2 x 2 covariance (the model is the same
+ * per axis), which is the 4 x 4 filter's exact block structure. */
+kf_status kf_pc_kalman(kf_ctx *ctx, const int32_t *regions, int64_t T, int n_tracks, double *states, int32_t *status,
+                       void *stream);
+
 /* ------------------------------------------------------------------ kernel timing */
 /* Per-kernel device time of the library's own launches (instrumentation; the paper
  * times whole kernels the same way, Sec. VI). While timing is on, kf_run, kf_run_group

@@ -112,6 +112,12 @@ def _lib():
             "kf_costmodel_get": (i32, [P, P, P]),
             "kf_costmodel_set": (i32, [P, P, P]),
             "kf_set_kernel_timing": (i32, [P, i32]),
+            "kf_pc_traffic": (i32, [P, u32, i64, i64, i64, P]),
+            "kf_pc_plan": (i32, [P, i64, i64, i64, P, P]),
+            "kf_pc_workspace_bytes": (i32, [P, u32, i64, i64, i64, P]),
+            "kf_pc_run": (i32, [P, u32, P, P, P, ctypes.c_size_t, P]),
+            "kf_pc_run_group": (i32, [P, i32, i32, P, P, i64, P, i64, P, P]),
+            "kf_pc_kalman": (i32, [P, P, i64, i32, P, P, P]),
             "kf_kernel_times": (i32, [P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -131,7 +137,8 @@ def exported_symbols() -> list[str]:
             "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows", "kf_dag_create", "kf_dag_destroy",
             "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups",
             "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_grad", "kf_costmodel_get",
-            "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times"]
+            "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times", "kf_pc_traffic", "kf_pc_plan",
+            "kf_pc_workspace_bytes", "kf_pc_run", "kf_pc_run_group", "kf_pc_kalman"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -531,3 +538,86 @@ class Context:
         if f is None:
             raise AttributeError(name)
         return lambda *a, **k: f(self.h, *a, **k)
+
+
+# ------------------------------------------------------------------ the paper's own chain
+KF_PC_STAGES, KF_PC_REGIONS = 5, 16
+PC_SCALE = (65280.0, 65280.0, 16 * 65280.0, 16 * 65280.0)  # stage maps 0..3: scaled = true * scale
+
+
+class kf_pc_video(ctypes.Structure):
+    _fields_ = [("rgba", ctypes.c_void_p), ("W", ctypes.c_int64), ("H", ctypes.c_int64), ("T", ctypes.c_int64),
+                ("pitch", ctypes.c_int64)]
+
+
+class kf_pc_out(ctypes.Structure):
+    _fields_ = [("mask", ctypes.c_void_p), ("mask_pitch", ctypes.c_int64), ("counts", ctypes.c_void_p),
+                ("regions", ctypes.c_void_p)]
+
+
+def _pc_video(frames, W: int, T: int | None = None, H: int | None = None):
+    """frames: uint8 tensor [T, H, pitch, 4] (RGBA), or None with explicit T and H."""
+    if frames is None:
+        return kf_pc_video(0, int(W), int(H), int(T), int(W))
+    t, h, pitch, c = frames.shape
+    assert c == 4
+    return kf_pc_video(frames.data_ptr(), int(W), int(h), int(t), int(pitch))
+
+
+def _pc_out(mask, counts, regions):
+    return kf_pc_out(mask.data_ptr(), int(mask.shape[2]), counts.data_ptr(), regions.data_ptr())
+
+
+def kf_pc_traffic(ctx, cuts: int, W: int, H: int, T: int) -> float:
+    b = ctypes.c_double()
+    _check("kf_pc_traffic", _lib().kf_pc_traffic(ctx, int(cuts), int(W), int(H), int(T), ctypes.byref(b)), ctx)
+    return b.value
+
+
+def kf_pc_plan(ctx, W: int, H: int, T: int) -> tuple[int, float]:
+    c, b = ctypes.c_uint32(), ctypes.c_double()
+    _check("kf_pc_plan", _lib().kf_pc_plan(ctx, int(W), int(H), int(T), ctypes.byref(c), ctypes.byref(b)), ctx)
+    return c.value, b.value
+
+
+def kf_pc_workspace_bytes(ctx, cuts: int, W: int, H: int, T: int) -> int:
+    n = ctypes.c_size_t()
+    _check("kf_pc_workspace_bytes", _lib().kf_pc_workspace_bytes(ctx, int(cuts), int(W), int(H), int(T),
+                                                                   ctypes.byref(n)), ctx)
+    return n.value
+
+
+def kf_pc_run(ctx, cuts: int, frames, W: int, mask, counts, regions, workspace=None, stream=None) -> None:
+    """frames [T, H, pitch, 4] u8 RGBA; mask [T, H, mask_pitch] u8; counts [T] int32;
+    regions [T, 16, 3] int32 (all CUDA tensors)."""
+    v = _pc_video(frames, W)
+    o = _pc_out(mask, counts, regions)
+    ws = 0 if workspace is None else workspace.data_ptr()
+    nb = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check("kf_pc_run", _lib().kf_pc_run(ctx, int(cuts), ctypes.byref(v), ctypes.byref(o), ws, nb, _stream(stream)),
+           ctx)
+
+
+def kf_pc_run_group(ctx, a: int, b: int, W: int, frames=None, inp=None, out=None, mask_out=None, T=None, H=None,
+                    stream=None) -> None:
+    """One group [a..b]: input RGBA frames (a == 0) or an FP32 map [T, H, pitch]; output an
+    FP32 map [T, H, pitch] (b < 4) or (mask, counts, regions) (b == 4)."""
+    if frames is not None:
+        v = _pc_video(frames, W)
+    else:
+        v = kf_pc_video(0, int(W), int(inp.shape[1]), int(inp.shape[0]), int(W))
+    ip = 0 if inp is None else inp.data_ptr()
+    ipitch = 0 if inp is None else int(inp.shape[2])
+    op_ = 0 if out is None else out.data_ptr()
+    opitch = 0 if out is None else int(out.shape[2])
+    mo = None if mask_out is None else _pc_out(*mask_out)
+    _check("kf_pc_run_group", _lib().kf_pc_run_group(ctx, int(a), int(b), ctypes.byref(v), ip, ipitch, op_, opitch,
+                                                       ctypes.byref(mo) if mo is not None else None,
+                                                       _stream(stream)), ctx)
+
+
+def kf_pc_kalman(ctx, regions, states, status, stream=None) -> None:
+    """regions [T, N, 3] int32 -> states [T, N, 4] float64, status [T, N] int32 (CUDA tensors)."""
+    T, N, _ = regions.shape
+    _check("kf_pc_kalman", _lib().kf_pc_kalman(ctx, regions.data_ptr(), int(T), int(N), states.data_ptr(),
+                                               status.data_ptr(), _stream(stream)), ctx)

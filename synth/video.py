@@ -221,3 +221,16 @@ def generate(spec: VideoSpec, pitch: int | None = None, frames: range | None = N
 def pitch_for(W: int, align: int = 16) -> int:
     """Row pitch in bytes: W rounded up to a multiple of `align`."""
     return (W + align - 1) // align * align
+
+
+def rgba_of(gray: np.ndarray) -> np.ndarray:
+    """Colour frames [..., 4] u8 from gray frames [...] u8, for the RGBA workloads: the
+    channels are the gray value, a brightened copy and its negative (so no single channel
+    carries the luma), alpha 255: R = v, G = min(255, (4 v) // 5 + 30), B = 255 - v."""
+    v = gray.astype(np.int32)
+    out = np.empty(gray.shape + (4,), dtype=np.uint8)
+    out[..., 0] = v
+    out[..., 1] = np.minimum(255, (4 * v) // 5 + 30)
+    out[..., 2] = 255 - v
+    out[..., 3] = 255
+    return out

@@ -1,0 +1,76 @@
+"""Host-side checks of the paper's own chain (CPU only): the traffic model restated
+plainly for every partition (tile 32 x 32, halo = number of spatial stages in the
+group), the planner's choice, workspace sizes, and argument rejection on a host-only
+context."""
+import itertools
+
+import pytest
+
+from paper_1509_04394_gb300 import kfuse as K
+
+
+@pytest.fixture
+def hctx():
+    h = K.kf_create(-1)
+    yield h
+    K.kf_destroy(h)
+
+
+def groups_of(cuts):
+    a, out = 0, []
+    for i in range(5):
+        if i == 4 or (cuts >> i) & 1:
+            out.append((a, i))
+            a = i + 1
+    return out
+
+
+def expected_bytes(cuts, W, H, T):
+    in_b = [4, 4, 4, 4, 4]   # input of stage k: RGBA (k = 0) or an FP32 map
+    out_b = [4, 4, 4, 4, 1]  # output of stage k: FP32 map, or the u8 mask
+    tot = 0.0
+    for a, b in groups_of(cuts):
+        halo = sum(1 for s in (2, 3) if a <= s <= b)
+        out = 32 - 2 * halo
+        tot += W * H * T * (in_b[a] * 32 * 32 / out ** 2 + out_b[b])
+    return tot + T * 4 * (1 + 3 * 16)
+
+
+@pytest.mark.parametrize("cuts", range(16))
+def test_traffic_model_of_every_partition(hctx, cuts):
+    W, H, T = 1024, 1024, 1000
+    assert K.kf_pc_traffic(hctx, cuts, W, H, T) == pytest.approx(expected_bytes(cuts, W, H, T), rel=1e-12)
+
+
+def test_plan_is_full_fusion_and_orders_the_papers_partitions(hctx):
+    for W, H in ((256, 256), (512, 512), (1024, 1024), (600, 800)):
+        cuts, b = K.kf_pc_plan(hctx, W, H, 1000)
+        assert cuts == 0 and b == pytest.approx(expected_bytes(0, W, H, 1000))
+        full, two, none = (K.kf_pc_traffic(hctx, c, W, H, 1000) for c in (0, 0b0010, 0b1111))
+        assert full < two < none
+        assert min(K.kf_pc_traffic(hctx, c, W, H, 1000) for c in range(16)) == b
+
+
+def test_workspace_sizes(hctx):
+    plane = -(-(1024 * 512 * 3 * 4) // 256) * 256  # pitch round_up(1020, 8) = 1024
+    assert K.kf_pc_workspace_bytes(hctx, 0, 1020, 512, 3) == 0
+    assert K.kf_pc_workspace_bytes(hctx, 0b0010, 1020, 512, 3) == plane
+    for c in (0b0011, 0b1111):
+        assert K.kf_pc_workspace_bytes(hctx, c, 1020, 512, 3) == 2 * plane
+
+
+def test_argument_rejection(hctx):
+    L = K._lib()
+    with pytest.raises(K.KfuseError):
+        K.kf_pc_traffic(hctx, 16, 8, 8, 1)
+    with pytest.raises(K.KfuseError):
+        K.kf_pc_traffic(hctx, 0, 0, 8, 1)
+    v = K.kf_pc_video(0, 8, 8, 1, 8)
+    assert L.kf_pc_run(hctx, 0, K.ctypes.byref(v), None, None, 0, None) == K.KF_EINVAL
+    # region sums would pass 2^31: rejected before any launch
+    big = K.kf_pc_video(16, 40000, 40000, 1, 40000)
+    assert L.kf_pc_run_group(hctx, 1, 2, K.ctypes.byref(big), 16, 40000, 16, 40000, None, None) == K.KF_EINVAL
+    ok = K.kf_pc_video(16, 64, 32, 2, 64)
+    assert L.kf_pc_run_group(hctx, 1, 2, K.ctypes.byref(ok), 16, 64, 16, 64, None, None) == K.KF_ESTATE
+    assert L.kf_pc_kalman(hctx, 16, 5, 16, 16, 16, None) == K.KF_ESTATE
+    assert L.kf_pc_kalman(hctx, 16, -1, 16, 16, 16, None) == K.KF_EINVAL
