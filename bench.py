@@ -436,6 +436,97 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 BATCH48 = [(16, 192, 432, 600), (16, 480, 640, 300), (12, 800, 600, 1000), (4, 1080, 1920, 120)]  # count, H, W, T
 
 
+PCHAIN_SIZES = [(256, 256), (512, 512), (1024, 1024)]  # H, W: the paper's resized clips (Sec. VII-A)
+PCHAIN_PARTS = {"full_fusion": 0, "two_fusion": 0b0010, "no_fusion": 0b1111}
+
+
+def pchain_video(dev, H, W, T, seed):
+    """RGBA frames [T, H, W, 4] on the device: 64 generated frames, cycled."""
+    import torch
+    spec = sv.VideoSpec(T=T, H=H, W=W, seed=seed, n_blobs=max(8, H * W // 8000), n_patches=max(8, H * W // 12000))
+    g, _ = sv.generate(spec, frames=range(min(T, 64)))
+    src = torch.from_numpy(sv.rgba_of(g)).to(dev)
+    f = torch.empty((T, H, W, 4), dtype=torch.uint8, device=dev)
+    for t0 in range(0, T, src.shape[0]):
+        m = min(src.shape[0], T - t0)
+        f[t0:t0 + m] = src[:m]
+    return f
+
+
+def run_pchain(args):
+    """The paper's own chain (Table II: RGBA to gray, IIR filter, Gaussian, gradient,
+    threshold, then Kalman) at the paper's 256^2, 512^2 and 1024^2 x 1000 frames: "No
+    Fusion" (five kernels), "Two Fusion" (K1 K2 | K3 K4 K5) and "Full Fusion", each timed
+    with CUDA events (inputs larger than L2), with the traffic model's bytes and the HBM
+    fraction they imply; K6 (Kalman over the 16 region tracks) timed alone."""
+    import torch
+    from paper_1509_04394_gb300 import build as kbuild
+    from paper_1509_04394_gb300 import kfuse as K
+    kbuild.build()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    ctx = K.Context(0, harris=False)
+    hbm_peak, peak_kind = peaks()
+    T = args.pc_frames
+    sizes = PCHAIN_SIZES if not args.pc_size else [(args.pc_size, args.pc_size)]
+    out = {"workload": f"paper chain K1..K5 + K6 on RGBA video, {T} frames per size (64 generated frames, cycled)",
+           "peak_hbm_gbs": hbm_peak, "peak_kind": peak_kind, "sizes": []}
+    for i, (H, W) in enumerate(sizes):
+        fr = pchain_video(dev, H, W, T, 20 + i)
+        mp = (W + 15) // 16 * 16
+        mask = torch.zeros((T, H, mp), dtype=torch.uint8, device=dev)
+        counts = torch.zeros(T, dtype=torch.int32, device=dev)
+        regions = torch.zeros((T, 16, 3), dtype=torch.int32, device=dev)
+        px = T * H * W
+        row = {"H": H, "W": W, "T": T, "planned_cuts": K.kf_pc_plan(ctx.h, W, H, T)[0]}
+        ref = None
+        for name, cuts in PCHAIN_PARTS.items():
+            ws = torch.empty(K.kf_pc_workspace_bytes(ctx.h, cuts, W, H, T), dtype=torch.uint8, device=dev)
+            run = lambda: K.kf_pc_run(ctx.h, cuts, fr, W, mask, counts, regions, ws, stream)  # noqa: E731
+            if args.pc_once:
+                run()
+                torch.cuda.synchronize()
+                continue
+            for _ in range(args.warmup):
+                run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            model = K.kf_pc_traffic(ctx.h, cuts, W, H, T)
+            res = (mask.clone(), counts.clone(), regions.clone())
+            if ref is None:
+                ref = res
+            same = all(torch.equal(a, b) for a, b in zip(res, ref))
+            row[name] = {"cuts": cuts, "ms": ms, "value": px / (ms / 1000) / 1e6, "unit": "Mpixel/s",
+                         "model_bytes": model, "model_bytes_per_px": model / px,
+                         "hbm_frac": model / (ms / 1000) / 1e9 / hbm_peak, "identical_to_full_fusion": same}
+            del ws
+        if not args.pc_once:
+            states = torch.zeros((T, 16, 4), dtype=torch.float64, device=dev)
+            status = torch.zeros((T, 16), dtype=torch.int32, device=dev)
+            K.kf_pc_kalman(ctx.h, regions, states, status, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                K.kf_pc_kalman(ctx.h, regions, states, status, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row["kalman_ms"] = e0.elapsed_time(e1) / args.steps
+            row["full_vs_no_fusion"] = row["no_fusion"]["ms"] / row["full_fusion"]["ms"]
+            row["two_vs_no_fusion"] = row["no_fusion"]["ms"] / row["two_fusion"]["ms"]
+            row["corners_per_frame"] = float(counts.float().mean())
+        out["sizes"].append(row)
+        del fr, mask
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def run_batch48(args):
     """The batching workload: 48 independent videos of four sizes (9.03 Gpixel) through one
     persistent launch replayed from a CUDA graph, chain + corner selection + LK per video.
@@ -577,12 +668,18 @@ def main():
     ap.add_argument("--batch48", action="store_true", help="the 48-video batching workload")
     ap.add_argument("--costmodel", action="store_true", help="the learned-cost-model workload")
     ap.add_argument("--cm-frames", type=int, default=4, help="frames the groups are timed on (--costmodel)")
+    ap.add_argument("--pchain", action="store_true", help="the paper's own chain: no / two / full fusion")
+    ap.add_argument("--pc-frames", type=int, default=1000, help="frames per size (--pchain)")
+    ap.add_argument("--pc-size", type=int, default=0, help="one square size instead of the three (--pchain)")
+    ap.add_argument("--pc-once", action="store_true", help="run each partition once, untimed (profiler case)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.costmodel:
+    if args.pchain:
+        run_pchain(args)
+    elif args.costmodel:
         run_costmodel(args)
     elif args.batch48:
         run_batch48(args)

@@ -374,11 +374,16 @@ kf_status kf_run_static(kf_ctx *ctx, uint32_t cuts, const kf_video *video, const
  *       r = 4 px^2; starts at the first frame with a measurement, P0 = diag(r, r, 100, 100))
  * Partitions of K1..K5: bit i of `cuts` (i = 0..3) cuts between K(i+1) and K(i+2); 0 is
  * "Full Fusion", 0b0010 (K1 K2 | K3 K4 K5) the paper's "Two Fusion", 0b1111 "No Fusion".
- * Maps between groups are FP32 planes of the workspace. Execution: each warp owns a
- * 32 x 32 tile of the group's input (lanes = columns, rows streamed); a group holding K2
- * keeps its 32 IIR states per lane in registers and walks all T frames, so no IIR state
- * ever goes through memory. */
+ * Maps between groups are FP32 planes of the workspace. Execution: 32 x 32 tiles of the
+ * group's input (lanes = columns). The IIR recursion is cut into chunks of KF_PC_CHUNK
+ * frames that run in parallel: the filter is linear, so a pass over the input gives each
+ * chunk's end state from zero, a carry pass per pixel turns those into the true state
+ * before every chunk (in chunk order), and a group holding K2 runs each (tile, chunk) as
+ * one block of 4 warps from that state, 8 rows' states per warp in registers. The result
+ * is the recursion evaluated in this fixed chunked order (the same in every partition);
+ * other groups run one warp per (tile, frame). */
 #define KF_PC_STAGES 5
+#define KF_PC_CHUNK 32
 #define KF_PC_REGIONS 16
 typedef struct {
     const uint8_t *rgba;  /* device, T x H rows of `pitch` pixels of 4 bytes (R, G, B, A) */
@@ -391,21 +396,29 @@ typedef struct {
     int32_t *counts;      /* device, [T], written (no pre-zeroing needed) */
     int32_t *regions;     /* device, [T][KF_PC_REGIONS][3] (count, sum x, sum y), written */
 } kf_pc_out;
-/* Predicted bytes moved by a partition (Sec. VI-D with the executor's 32 x 32 tiles:
- * a group reads its input tile with halo and writes its output tile; a group holding K2
- * carries the filter state on chip, so it has no temporal halo). */
+/* Predicted bytes moved by a partition (Sec. VI-D with the executor's 32 x 32 tiles: a
+ * group reads its input tile with halo and writes its output tile; a group holding K2
+ * also pays the chunked recursion: one more read of its input for the chunk end states,
+ * the carry pass over one state plane per chunk, and the start states it reads, with
+ * halo, per chunk -- the temporal halo of a box of KF_PC_CHUNK frames). */
 kf_status kf_pc_traffic(kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_t T, double *bytes);
 /* The partition of minimum predicted traffic (exact DP over the 16). */
 kf_status kf_pc_plan(kf_ctx *ctx, int64_t W, int64_t H, int64_t T, uint32_t *cuts, double *bytes);
-/* Workspace of a partition: two FP32 planes of T x H x round_up(W, 8) (0 for cuts == 0). */
+/* Workspace of a partition: the IIR chunk states (ceil(T / KF_PC_CHUNK) FP32 planes of
+ * H x round_up(W, 8)), 32 partial copies of the per-frame sums (T x 32 x 49 int32), then
+ * up to two FP32 maps of T x H x round_up(W, 8) between groups, each part 256-aligned. */
 kf_status kf_pc_workspace_bytes(kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_t T, size_t *bytes);
 kf_status kf_pc_run(kf_ctx *ctx, uint32_t cuts, const kf_pc_video *video, const kf_pc_out *out, void *workspace,
                     size_t workspace_bytes, void *stream);
 /* One group [a..b] (0-based stages, a <= b <= 4) over explicit maps. in: a == 0 the RGBA
  * frames (video), else an FP32 map [T][H][in_pitch] of stage a-1. out: b == 4 the mask
- * outputs (out_mask), else an FP32 map [T][H][out_pitch] of stage b. */
+ * outputs (out_mask), else an FP32 map [T][H][out_pitch] of stage b. A group holding K2
+ * or ending at K5 needs a workspace of kf_pc_group_workspace_bytes (256-byte aligned):
+ * the chunk states and the partial sums; other groups none. */
+kf_status kf_pc_group_workspace_bytes(kf_ctx *ctx, int a, int b, int64_t W, int64_t H, int64_t T, size_t *bytes);
 kf_status kf_pc_run_group(kf_ctx *ctx, int a, int b, const kf_pc_video *video, const float *in, int64_t in_pitch,
-                          float *out, int64_t out_pitch, const kf_pc_out *out_mask, void *stream);
+                          float *out, int64_t out_pitch, const kf_pc_out *out_mask, void *workspace,
+                          size_t workspace_bytes, void *stream);
 /* K6 over [T][n_tracks][3] region sums (device): states [T][n_tracks][4] (FP64, device) and
  * status [T][n_tracks] (0 not started, 1 updated, 2 predicted only). One thread per track
  * walks the frames; the x and y axes share one 2 x 2 covariance (the model is the same

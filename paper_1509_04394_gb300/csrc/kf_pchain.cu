@@ -3,14 +3,15 @@
 // any contiguous group of them fused into one kernel (Sec. V-B, Eq. 2), and K6, the
 // Kalman filter over feature positions, after the kernel-to-kernel dependency.
 //
-// Group kernel pc_kernel<A, B> (0-based stages A..B). Each warp owns a 32 x 32 tile of
-// the group's input: lane = column, the 32 rows streamed top to bottom in registers.
-// Horizontal taps are warp shuffles, vertical taps a few rows of registers; a group with
-// K3 and K4 has a 2-pixel halo and writes the inner 28 x 28 (30 x 30 with one of them).
-// A group holding K2 (the IIR filter, a recursion over frames) keeps the filter state of
-// its 32 rows per lane in registers and walks every frame of the video in order, loading
-// the next frame's tile while it computes the current one; no filter state goes through
-// memory. Other groups run one (tile, frame) per warp.
+// A group (0-based stages A..B) works on 32 x 32 tiles of its input (lane = column); a
+// group with K3 and K4 has a 2-pixel halo and writes the inner 28 x 28 (30 x 30 with one
+// of them). Horizontal taps are warp shuffles. pc_kernel<A, B>, for groups without K2:
+// one warp per (tile, frame) streams the 32 rows in registers. pc_temporal_kernel<A, B>,
+// for groups holding K2 (the IIR filter, a recursion over frames): one block of 4 warps
+// per tile walks every frame of the video in order, each warp keeping the filter state of
+// its 8 rows in registers and loading the next frame's rows while it computes this one;
+// the spatial stages exchange rows through shared memory. No filter state goes through
+// memory.
 //
 // Clamp-to-edge per stage: the group's input is read at clamped coordinates, which is
 // the clamp of K1..K3's inputs (point stages commute with it). K4 reads K3's output at
@@ -23,6 +24,7 @@
 // M' = |Sobel x| + |Sobel y| of G' (same scale), mask = M' > 0.25 * 16 * 65280. Every
 // stage is one device function shared by all groups, so partitions agree bit for bit.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "kf_ctx.h"
@@ -41,6 +43,12 @@ constexpr int GRIDN = 4;  // regions per side
 constexpr float ALPHA = 0.25f;
 constexpr float TAU = 0.25f * 16.0f * 65280.0f;  // threshold on M' (exact in FP32)
 constexpr double KQ = 0.5, KR = 4.0, KP0 = 100.0;  // Kalman: process noise, measurement noise, initial velocity variance
+constexpr int CHUNK = KF_PC_CHUNK;  // frames per chunk of the IIR recursion
+// Per-frame sums (the mask count and the 16 regions' count, sum x, sum y) are added into
+// one of NSLOT copies per frame, chosen by the warp, and the copies are summed afterwards:
+// every warp of a frame adding to the same 49 counters serialised the atomics in L2.
+constexpr int NSLOT = 32;
+constexpr int NCNT = 1 + 3 * NREG;
 
 struct PcParams {
     const uint32_t *in;   // RGBA pixels (A == 0) or FP32 bit patterns
@@ -49,7 +57,12 @@ struct PcParams {
     int64_t out_pitch, out_fstride;  // elements
     int W, H, T;
     int tiles_x, tiles_y;
-    int32_t *counts, *regions;       // B == 4
+    int32_t *counts, *regions;       // B == 4: the final sums
+    int32_t *slots;                  // B == 4: [T][NSLOT][NCNT] partial sums, zeroed before the launch
+    float *state;                    // IIR states at the chunk starts: [n_chunks][H][state_pitch]
+    int64_t state_pitch;
+    int n_chunks;                    // ceil(T / CHUNK)
+    float decay_chunk;               // (1 - ALPHA)^CHUNK in FP32
 };
 
 // ---- the stages (one definition each, used by every group)
@@ -58,7 +71,7 @@ __device__ __forceinline__ float k1_gray(uint32_t rgba)
     const float r = (float)(rgba & 0xffu), g = (float)((rgba >> 8) & 0xffu), b = (float)((rgba >> 16) & 0xffu);
     return fmaf(29.0f, b, fmaf(150.0f, g, 77.0f * r));  // integer <= 65280: exact
 }
-__device__ __forceinline__ float k2_iir(float prev, float Y, bool first) { return first ? Y : fmaf(ALPHA, Y - prev, prev); }
+__device__ __forceinline__ float k2_iir(float prev, float Y) { return fmaf(ALPHA, Y - prev, prev); }
 // [1 2 1] of three neighbours (the centre weighted 2)
 __device__ __forceinline__ float tap121(float l, float c, float r) { return fmaf(2.0f, c, l + r); }
 
@@ -69,28 +82,20 @@ template <int A, int B> struct Group {
     static constexpr bool TEMPORAL = H1;
 };
 
+// Groups without K2: one warp per (tile, frame).
 template <int A, int B>
 __global__ void __launch_bounds__(32 * WPB) pc_kernel(const PcParams p)
 {
     using G = Group<A, B>;
+    static_assert(!G::TEMPORAL, "groups holding the IIR filter run pc_temporal_kernel");
     constexpr int HALO = G::HALO, OUT = G::OUT;
     __shared__ int acc[WPB][NREG][3];  // this frame's region sums of the warp (B == 4)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     const int64_t n_tiles = (int64_t)p.tiles_x * p.tiles_y;
-    int64_t tile;
-    int f_begin, f_end;
-    if constexpr (G::TEMPORAL) {
-        if (gw >= n_tiles) return;  // warp-uniform; no block barriers below
-        tile = gw;
-        f_begin = 0;
-        f_end = p.T;
-    } else {
-        if (gw >= n_tiles * p.T) return;
-        tile = gw % n_tiles;
-        f_begin = (int)(gw / n_tiles);
-        f_end = f_begin + 1;
-    }
+    if (gw >= n_tiles * p.T) return;  // warp-uniform; no block barriers below
+    const int64_t tile = gw % n_tiles;
+    const int f_begin = (int)(gw / n_tiles), f_end = f_begin + 1;
     const int W = p.W, H = p.H;
     const int tx = (int)(tile % p.tiles_x), ty = (int)(tile / p.tiles_x);
     const int x = tx * OUT - HALO + lane;  // this lane's input column
@@ -111,7 +116,6 @@ __global__ void __launch_bounds__(32 * WPB) pc_kernel(const PcParams p)
 #pragma unroll
         for (int r = 0; r < TS; ++r) v[r] = __ldg(base + (int64_t)min(max(y0 + r, 0), H - 1) * p.in_pitch);
     };
-    [[maybe_unused]] float st[TS];  // IIR state of each row (TEMPORAL)
     load(f_begin, buf);
 
     for (int f = f_begin; f < f_end; ++f) {
@@ -119,7 +123,6 @@ __global__ void __launch_bounds__(32 * WPB) pc_kernel(const PcParams p)
 #pragma unroll
         for (int r = 0; r < TS; ++r) cur[r] = buf[r];
         if (f + 1 < f_end) load(f + 1, buf);  // in flight while this frame computes
-        const bool first = f == 0;
         float *outf = static_cast<float *>(p.out) + (int64_t)f * p.out_fstride;
         uint8_t *outm = static_cast<uint8_t *>(p.out) + (int64_t)f * p.out_fstride;
         [[maybe_unused]] float hy[TS], Gv[TS], D[TS], S[TS];
@@ -166,21 +169,10 @@ __global__ void __launch_bounds__(32 * WPB) pc_kernel(const PcParams p)
 #pragma unroll
         for (int r = 0; r < TS; ++r) {
             const uint32_t v = cur[r];
-            if constexpr (A <= 2) {
-                // ---- K1, K2
-                float yv;
-                if constexpr (A == 0) {
-                    const float Y = k1_gray(v);
-                    if constexpr (B == 0) { emit(r, Y); continue; }
-                    yv = k2_iir(st[r], Y, first);
-                    st[r] = yv;
-                } else if constexpr (A == 1) {
-                    yv = k2_iir(st[r], __uint_as_float(v), first);
-                    st[r] = yv;
-                } else {
-                    yv = __uint_as_float(v);
-                }
-                if constexpr (B == 1) { emit(r, yv); continue; }
+            if constexpr (A == 0) {
+                emit(r, k1_gray(v));  // K1 alone (a group from K1 on that holds K2 is temporal)
+            } else if constexpr (A == 2) {
+                const float yv = __uint_as_float(v);
                 // ---- K3: horizontal [1 2 1], then vertical [1 2 1] one row behind
                 hy[r] = tap121(__shfl_up_sync(FULLM, yv, 1), yv, __shfl_down_sync(FULLM, yv, 1));
                 if (r >= 2) {
@@ -204,20 +196,246 @@ __global__ void __launch_bounds__(32 * WPB) pc_kernel(const PcParams p)
 
         if constexpr (G::H4) {
             __syncwarp();
-            if (lane == 0 && count) atomicAdd(p.counts + f, (int)count);
+            int32_t *sl = p.slots + ((int64_t)f * NSLOT + (int)(gw % NSLOT)) * NCNT;
+            if (lane == 0 && count) atomicAdd(sl, (int)count);
             if (lane < NREG) {
                 int *a = acc[wib][lane];
                 if (a[0]) {
-                    int32_t *g = p.regions + ((int64_t)f * NREG + lane) * 3;
-                    atomicAdd(g + 0, a[0]);
-                    atomicAdd(g + 1, a[1]);
-                    atomicAdd(g + 2, a[2]);
+                    atomicAdd(sl + 1 + 3 * lane + 0, a[0]);
+                    atomicAdd(sl + 1 + 3 * lane + 1, a[1]);
+                    atomicAdd(sl + 1 + 3 * lane + 2, a[2]);
                     a[0] = a[1] = a[2] = 0;
                 }
             }
             __syncwarp();
         }
     }
+}
+
+// Groups holding K2: one block of 4 warps per tile walks every frame of the video in
+// order. Warp w owns tile rows 8w .. 8w+7 for the point stages (its 8 IIR states per lane
+// stay in registers; the next frame's 8 input rows are loaded while this frame computes),
+// then the spatial stages read neighbouring rows through shared memory (y', then G'), two
+// block barriers per frame. Four warps per tile give the recursion 4x the warps of one
+// warp per tile.
+constexpr int TW = 4;        // warps per tile
+constexpr int RW = TS / TW;  // rows per warp
+
+template <int A, int B>
+__global__ void __launch_bounds__(32 * TW) pc_temporal_kernel(const PcParams p)
+{
+    // blockIdx.y: the chunk of CHUNK frames; the filter starts from the state the carry
+    // pass left for the frame before the chunk (at clamped coordinates, like the input)
+    using G = Group<A, B>;
+    static_assert(G::TEMPORAL, "groups holding the IIR filter");
+    constexpr int HALO = G::HALO, OUT = G::OUT;
+    __shared__ float ys[TS][TS];  // y' of the tile (B >= 2)
+    __shared__ float gs[TS][TS];  // G' of the tile (B >= 3)
+    __shared__ int acc[TW][NREG][3];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = blockIdx.x;
+    const int W = p.W, H = p.H;
+    const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
+    const int x = tx * OUT - HALO + lane;
+    const int xc = min(max(x, 0), W - 1);
+    const int y0 = ty * OUT - HALO;
+    const bool out_col = lane >= HALO && lane < TS - HALO && x < W;
+    const bool edge_tile = (tx * OUT - HALO < 0) || (tx * OUT - HALO + TS > W);
+    const int src_lane = lane + (xc - x);
+    const int rxl = (GRIDN * xc) / W;
+    const int r0 = RW * w;  // this warp's first tile row
+    const int f0 = blockIdx.y * CHUNK, f1 = min(f0 + CHUNK, p.T);
+    if constexpr (G::H4) {
+        if (lane < NREG) acc[w][lane][0] = acc[w][lane][1] = acc[w][lane][2] = 0;
+        __syncwarp();
+    }
+    uint32_t buf[RW];
+    auto load = [&](int f) {
+        const uint32_t *base = p.in + (int64_t)f * p.in_fstride + xc;
+#pragma unroll
+        for (int i = 0; i < RW; ++i) buf[i] = __ldg(base + (int64_t)min(max(y0 + r0 + i, 0), H - 1) * p.in_pitch);
+    };
+    float st[RW];
+    {
+        const float *s0 = p.state + (int64_t)blockIdx.y * H * p.state_pitch + xc;
+#pragma unroll
+        for (int i = 0; i < RW; ++i) st[i] = s0[(int64_t)min(max(y0 + r0 + i, 0), H - 1) * p.state_pitch];
+    }
+    load(f0);
+    for (int f = f0; f < f1; ++f) {
+        uint32_t cur[RW];
+#pragma unroll
+        for (int i = 0; i < RW; ++i) cur[i] = buf[i];
+        if (f + 1 < f1) load(f + 1);
+        float *outf = static_cast<float *>(p.out) + (int64_t)f * p.out_fstride;
+        uint8_t *outm = static_cast<uint8_t *>(p.out) + (int64_t)f * p.out_fstride;
+        [[maybe_unused]] unsigned count = 0;
+        auto emit = [&](int o, float v) {  // tile row o (warp-uniform)
+            const int gy = y0 + o;
+            if (gy >= H) return;
+            if constexpr (!G::H4) {
+                if (out_col) outf[(int64_t)gy * p.out_pitch + x] = v;
+            } else {
+                const bool m = out_col && v > TAU;
+                if (out_col) outm[(int64_t)gy * p.out_pitch + x] = (uint8_t)m;
+                count += __popc(__ballot_sync(FULLM, m));
+                if (m) {
+                    const int rg = ((GRIDN * gy) / H) * GRIDN + rxl;
+                    atomicAdd(&acc[w][rg][0], 1);
+                    atomicAdd(&acc[w][rg][1], x);
+                    atomicAdd(&acc[w][rg][2], gy);
+                }
+            }
+        };
+        // ---- K1, K2 on this warp's rows
+#pragma unroll
+        for (int i = 0; i < RW; ++i) {
+            const float Y = A == 0 ? k1_gray(cur[i]) : __uint_as_float(cur[i]);
+            st[i] = k2_iir(st[i], Y);
+            if constexpr (B == 1) emit(r0 + i, st[i]);
+            else ys[r0 + i][lane] = st[i];
+        }
+        if constexpr (B >= 2) {
+            __syncthreads();
+            // ---- K3 on rows q of this warp with both neighbours in the tile (1..30)
+            float hy[RW + 2];
+#pragma unroll
+            for (int i = 0; i < RW + 2; ++i) {
+                const int r = r0 - 1 + i;
+                if (r >= 0 && r < TS) {  // warp-uniform
+                    const float yv = ys[r][lane];
+                    hy[i] = tap121(__shfl_up_sync(FULLM, yv, 1), yv, __shfl_down_sync(FULLM, yv, 1));
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < RW; ++i) {
+                const int q = r0 + i;
+                if (q < 1 || q > TS - 2) continue;
+                float g = tap121(hy[i], hy[i + 1], hy[i + 2]);
+                if constexpr (B == 2) {
+                    emit(q, g);
+                } else {
+                    if (edge_tile) g = __shfl_sync(FULLM, g, src_lane);
+                    gs[q][lane] = g;
+                }
+            }
+            if constexpr (B >= 3) {
+                __syncthreads();
+                // ---- K4 (+ K5) on output rows o of this warp (2..29)
+                float Dv[RW + 2], Sv[RW + 2];
+#pragma unroll
+                for (int i = 0; i < RW + 2; ++i) {
+                    const int r = r0 - 1 + i;
+                    if (r >= 1 && r <= TS - 2) {
+                        const float g = gs[r][lane];
+                        const float gl = __shfl_up_sync(FULLM, g, 1), gr = __shfl_down_sync(FULLM, g, 1);
+                        Dv[i] = gr - gl;
+                        Sv[i] = tap121(gl, g, gr);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < RW; ++i) {
+                    const int o = r0 + i;
+                    if (o < 2 || o > TS - 3) continue;
+                    const int gy = y0 + o;
+                    const float dm = gy - 1 < 0 ? Dv[i + 1] : Dv[i], dp = gy + 1 > H - 1 ? Dv[i + 1] : Dv[i + 2];
+                    const float sm = gy - 1 < 0 ? Sv[i + 1] : Sv[i], sp = gy + 1 > H - 1 ? Sv[i + 1] : Sv[i + 2];
+                    emit(o, fabsf(tap121(dm, Dv[i + 1], dp)) + fabsf(sp - sm));
+                }
+            }
+        }
+        if constexpr (G::H4) {
+            __syncwarp();
+            int32_t *sl = p.slots + ((int64_t)f * NSLOT + (int)((blockIdx.x * TW + w) % NSLOT)) * NCNT;
+            if (lane == 0 && count) atomicAdd(sl, (int)count);
+            if (lane < NREG) {
+                int *a = acc[w][lane];
+                if (a[0]) {
+                    atomicAdd(sl + 1 + 3 * lane + 0, a[0]);
+                    atomicAdd(sl + 1 + 3 * lane + 1, a[1]);
+                    atomicAdd(sl + 1 + 3 * lane + 2, a[2]);
+                    a[0] = a[1] = a[2] = 0;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// ---- the IIR recursion cut into chunks of CHUNK frames, so that chunks run in parallel.
+// The filter is linear: started from state s before frame t0, y_{t0+j} = (1 - ALPHA)^(j+1) s
+// + l_{t0+j}, where l is the same recursion started from 0. (1) Per chunk and pixel, l at
+// the chunk's last frame; (2) per pixel, in chunk order, the state before each chunk:
+// s_0 = Y_0 (so that y_0 = Y_0), s_k = (1 - ALPHA)^CHUNK s_{k-1} + l_end(k-1); (3) every
+// group holding K2 runs each chunk from its s_k. The states are one FP32 plane per chunk;
+// pass (2) overwrites l_end(k-1) with s_{k-1} in place.
+template <int A0>  // 0: RGBA frames, 1: Y' map
+__global__ void __launch_bounds__(32 * TW) pc_iir_local_kernel(const PcParams p)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = blockIdx.x * TS + lane;
+    const int y = blockIdx.z * TS + RW * w;
+    const int k = blockIdx.y;  // chunk (all but the last)
+    if (x >= p.W) return;      // no block barriers here
+    const int f0 = k * CHUNK;
+    float l[RW];
+#pragma unroll
+    for (int i = 0; i < RW; ++i) l[i] = 0.0f;
+    const uint32_t *base = p.in + x;
+    const int nrows = min(RW, p.H - y);
+#pragma unroll 4
+    for (int f = f0; f < f0 + CHUNK; ++f) {  // unrolled: later frames' loads issue early
+        const uint32_t *fr = base + (int64_t)f * p.in_fstride;
+        uint32_t v[RW];
+#pragma unroll
+        for (int i = 0; i < RW; ++i) v[i] = i < nrows ? __ldg(fr + (int64_t)(y + i) * p.in_pitch) : 0u;
+#pragma unroll
+        for (int i = 0; i < RW; ++i) l[i] = k2_iir(l[i], A0 == 0 ? k1_gray(v[i]) : __uint_as_float(v[i]));
+    }
+    float *o = p.state + (int64_t)k * p.H * p.state_pitch + x;
+#pragma unroll
+    for (int i = 0; i < RW; ++i)
+        if (y + i < p.H) o[(int64_t)(y + i) * p.state_pitch] = l[i];
+}
+
+template <int A0>
+__global__ void pc_iir_carry_kernel(const PcParams p)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)p.W * p.H) return;
+    const int y = (int)(i / p.W), x = (int)(i - (int64_t)y * p.W);
+    const uint32_t v = p.in[(int64_t)y * p.in_pitch + x];  // frame 0
+    float s = A0 == 0 ? k1_gray(v) : __uint_as_float(v);
+    float *col = p.state + (int64_t)y * p.state_pitch + x;
+    const int64_t plane = (int64_t)p.H * p.state_pitch;
+    // eight chunks' end states are loaded at once (independent loads), then carried
+    for (int k0 = 1; k0 < p.n_chunks; k0 += 8) {
+        float e[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) e[j] = k0 + j < p.n_chunks ? col[(int64_t)(k0 + j - 1) * plane] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (k0 + j < p.n_chunks) {
+                col[(int64_t)(k0 + j - 1) * plane] = s;
+                s = fmaf(p.decay_chunk, s, e[j]);
+            }
+        }
+    }
+    col[(int64_t)(p.n_chunks - 1) * plane] = s;
+}
+
+// the per-frame sums: counts[f] and regions[f][r][c] from the NSLOT partial copies
+__global__ void pc_sums_kernel(const int32_t *slots, int T, int32_t *counts, int32_t *regions)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)T * NCNT) return;
+    const int f = (int)(i / NCNT), j = (int)(i - (int64_t)f * NCNT);
+    const int32_t *s = slots + (int64_t)f * NSLOT * NCNT + j;
+    int tot = 0;
+#pragma unroll 8
+    for (int k = 0; k < NSLOT; ++k) tot += s[k * NCNT];
+    if (j == 0) counts[f] = tot;
+    else regions[(int64_t)f * 3 * NREG + (j - 1)] = tot;
 }
 
 // K6: one thread per track walks the frames. The constant-velocity model is the same per
@@ -285,8 +503,12 @@ int launch_one(const PcParams &p, cudaStream_t s)
     using G = Group<A, B>;
     const int64_t n_tiles = (int64_t)p.tiles_x * p.tiles_y;
     if constexpr (G::TEMPORAL) {
-        // one warp per block: the few long-lived warps spread over every SM
-        pc_kernel<A, B><<<(unsigned)n_tiles, 32, 0, s>>>(p);
+        // the chunk states first: local ends, then the carry (in place)
+        const dim3 lg((unsigned)((p.W + TS - 1) / TS), (unsigned)(p.n_chunks - 1), (unsigned)((p.H + TS - 1) / TS));
+        if (p.n_chunks > 1) pc_iir_local_kernel<A><<<lg, 32 * TW, 0, s>>>(p);
+        const int64_t px = (int64_t)p.W * p.H;
+        pc_iir_carry_kernel<A><<<(unsigned)((px + 255) / 256), 256, 0, s>>>(p);
+        pc_temporal_kernel<A, B><<<dim3((unsigned)n_tiles, (unsigned)p.n_chunks), 32 * TW, 0, s>>>(p);
     } else {
         const int64_t warps = n_tiles * p.T;
         pc_kernel<A, B><<<(unsigned)((warps + WPB - 1) / WPB), 32 * WPB, 0, s>>>(p);
@@ -352,12 +574,28 @@ PcParams params_for(int a, int b, int64_t W, int64_t H, int64_t T)
     return p;
 }
 
-// one group over prepared pointers; zeroes counts and regions first when it ends at K5
+int64_t n_chunks(int64_t T) { return (T + KF_PC_CHUNK - 1) / KF_PC_CHUNK; }
+// bytes of the IIR chunk states: one FP32 plane per chunk (pitch round_up(W, 8)), 256-aligned
+size_t state_bytes(int64_t W, int64_t H, int64_t T)
+{
+    return ((size_t)(n_chunks(T) * H * ws_pitch(W)) * sizeof(float) + 255) / 256 * 256;
+}
+bool holds_iir(int a, int b) { return a <= 1 && 1 <= b; }
+
+// one group over prepared pointers; zeroes counts and regions first when it ends at K5;
+// `state`: the chunk-state planes (groups holding K2)
+size_t slot_bytes(int64_t T) { return ((size_t)T * NSLOT * NCNT * sizeof(int32_t) + 255) / 256 * 256; }
+
 kf_status run_group(kf_ctx *ctx, int a, int b, const uint32_t *in, int64_t in_pitch, void *out, int64_t out_pitch,
-                    int64_t W, int64_t H, int64_t T, int32_t *counts, int32_t *regions, cudaStream_t s)
+                    int64_t W, int64_t H, int64_t T, int32_t *counts, int32_t *regions, float *state, int32_t *slots,
+                    cudaStream_t s)
 {
     if (T == 0) return KF_OK;
     PcParams p = params_for(a, b, W, H, T);
+    p.state = state;
+    p.state_pitch = ws_pitch(W);
+    p.n_chunks = (int)n_chunks(T);
+    p.decay_chunk = (float)pow(1.0 - 0.25, (double)KF_PC_CHUNK);
     p.in = in;
     p.in_pitch = in_pitch;
     p.in_fstride = in_pitch * H;
@@ -366,15 +604,21 @@ kf_status run_group(kf_ctx *ctx, int a, int b, const uint32_t *in, int64_t in_pi
     p.out_fstride = out_pitch * H;
     p.counts = counts;
     p.regions = regions;
+    p.slots = slots;
     if (b == 4) {
-        cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)T, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(regions, 0, sizeof(int32_t) * 3 * NREG * (size_t)T, s);
+        const cudaError_t e = cudaMemsetAsync(slots, 0, sizeof(int32_t) * NSLOT * NCNT * (size_t)T, s);
         if (e != cudaSuccess) return fail(ctx, (int)e);
     }
     const int64_t n_tiles = (int64_t)p.tiles_x * p.tiles_y;
-    const bool temporal = a <= 1 && 1 <= b;
+    const bool temporal = holds_iir(a, b);
     if ((temporal ? n_tiles : (n_tiles * T + WPB - 1) / WPB) > 0x7fffffffLL) return KF_EINVAL;
-    const int e = launch_group(a, b, p, s);
+    if (temporal && (p.n_chunks > 65535 || (H + TS - 1) / TS > 65535)) return KF_EINVAL;
+    int e = launch_group(a, b, p, s);
+    if (!e && b == 4) {
+        const int64_t n = T * NCNT;
+        pc_sums_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(slots, (int)T, counts, regions);
+        e = (int)cudaGetLastError();
+    }
     return e ? fail(ctx, e) : KF_OK;
 }
 
@@ -393,6 +637,15 @@ kf_status kf_pc_traffic(kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_
             const int out = TS - 2 * halo_of(a, i);
             const double read_factor = (double)TS * TS / ((double)out * out);
             tot += px * (map_bytes(a - 1) * read_factor + map_bytes(i));
+            if (holds_iir(a, i)) {
+                // the chunked recursion: the local pass reads all but the last chunk and writes
+                // their end states; the carry reads frame 0 and those states and writes every
+                // chunk's start state; the group reads the start states with its halo
+                const double hw = (double)W * H, nc = (double)n_chunks(T);
+                tot += (nc - 1) * KF_PC_CHUNK * hw * map_bytes(a - 1) + (nc - 1) * hw * 4.0;
+                tot += hw * map_bytes(a - 1) + (nc - 1) * hw * 4.0 + nc * hw * 4.0;
+                tot += nc * hw * 4.0 * read_factor;
+            }
             a = i + 1;
         }
     }
@@ -426,7 +679,7 @@ kf_status kf_pc_workspace_bytes(kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H
     const int n_cuts = __builtin_popcount(cuts);
     const size_t plane = (size_t)(ws_pitch(W) * H * T) * sizeof(float);
     const size_t plane_a = (plane + 255) / 256 * 256;
-    *bytes = n_cuts == 0 ? 0 : (n_cuts == 1 ? plane_a : 2 * plane_a);
+    *bytes = state_bytes(W, H, T) + slot_bytes(T) + (n_cuts == 0 ? 0 : (n_cuts == 1 ? plane_a : 2 * plane_a));
     return KF_OK;
 }
 
@@ -447,8 +700,10 @@ kf_status kf_pc_run(kf_ctx *ctx, uint32_t cuts, const kf_pc_video *video, const 
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t W = video->W, H = video->H, T = video->T, wp = ws_pitch(W);
     const size_t plane_a = ((size_t)(wp * H * T) * sizeof(float) + 255) / 256 * 256;
-    float *planes[2] = {static_cast<float *>(workspace),
-                        workspace ? reinterpret_cast<float *>(static_cast<char *>(workspace) + plane_a) : nullptr};
+    float *state = static_cast<float *>(workspace);
+    int32_t *slots = reinterpret_cast<int32_t *>(static_cast<char *>(workspace) + state_bytes(W, H, T));
+    char *maps = reinterpret_cast<char *>(slots) + slot_bytes(T);
+    float *planes[2] = {reinterpret_cast<float *>(maps), reinterpret_cast<float *>(maps + plane_a)};
     const uint32_t *in = reinterpret_cast<const uint32_t *>(video->rgba);
     int64_t in_pitch = video->pitch;
     int a = 0, k = 0;
@@ -457,7 +712,7 @@ kf_status kf_pc_run(kf_ctx *ctx, uint32_t cuts, const kf_pc_video *video, const 
         const bool last = i == KF_PC_STAGES - 1;
         void *o = last ? static_cast<void *>(out->mask) : static_cast<void *>(planes[k % 2]);
         const int64_t op = last ? out->mask_pitch : wp;
-        st = run_group(ctx, a, i, in, in_pitch, o, op, W, H, T, out->counts, out->regions, s);
+        st = run_group(ctx, a, i, in, in_pitch, o, op, W, H, T, out->counts, out->regions, state, slots, s);
         if (st != KF_OK) return st;
         in = reinterpret_cast<const uint32_t *>(planes[k % 2]);
         in_pitch = wp;
@@ -467,8 +722,16 @@ kf_status kf_pc_run(kf_ctx *ctx, uint32_t cuts, const kf_pc_video *video, const 
     return KF_OK;
 }
 
+kf_status kf_pc_group_workspace_bytes(kf_ctx *ctx, int a, int b, int64_t W, int64_t H, int64_t T, size_t *bytes)
+{
+    if (!ctx || !bytes || a < 0 || b < a || b >= KF_PC_STAGES || W <= 0 || H <= 0 || T < 0) return KF_EINVAL;
+    *bytes = (holds_iir(a, b) ? state_bytes(W, H, T) : 0) + (b == 4 ? slot_bytes(T) : 0);
+    return KF_OK;
+}
+
 kf_status kf_pc_run_group(kf_ctx *ctx, int a, int b, const kf_pc_video *video, const float *in, int64_t in_pitch,
-                          float *out, int64_t out_pitch, const kf_pc_out *out_mask, void *stream)
+                          float *out, int64_t out_pitch, const kf_pc_out *out_mask, void *workspace,
+                          size_t workspace_bytes, void *stream)
 {
     if (!ctx || a < 0 || b < a || b >= KF_PC_STAGES) return KF_EINVAL;
     // geometry from the video descriptor (its rgba is only read when a == 0)
@@ -487,6 +750,11 @@ kf_status kf_pc_run_group(kf_ctx *ctx, int a, int b, const kf_pc_video *video, c
     } else if (!out || out_pitch < W || !aligned(out, 4)) {
         return KF_EINVAL;
     }
+    const size_t need = (holds_iir(a, b) ? state_bytes(W, H, T) : 0) + (b == 4 ? slot_bytes(T) : 0);
+    if (need) {
+        if (!workspace || !aligned(workspace, 256)) return KF_EINVAL;
+        if (workspace_bytes < need) return KF_ENOMEM;
+    }
     const int dev = kf::ctx_device(ctx);
     if (dev < 0) return KF_ESTATE;
     if (cudaSetDevice(dev) != cudaSuccess) return KF_ECUDA;
@@ -494,8 +762,12 @@ kf_status kf_pc_run_group(kf_ctx *ctx, int a, int b, const kf_pc_video *video, c
     const int64_t sp = a == 0 ? video->pitch : in_pitch;
     void *dst = b == 4 ? static_cast<void *>(out_mask->mask) : static_cast<void *>(out);
     const int64_t dp = b == 4 ? out_mask->mask_pitch : out_pitch;
+    float *state = holds_iir(a, b) ? static_cast<float *>(workspace) : nullptr;
+    int32_t *slots = b == 4 ? reinterpret_cast<int32_t *>(static_cast<char *>(workspace) +
+                                                          (holds_iir(a, b) ? state_bytes(W, H, T) : 0))
+                            : nullptr;
     return run_group(ctx, a, b, src, sp, dst, dp, W, H, T, b == 4 ? out_mask->counts : nullptr,
-                     b == 4 ? out_mask->regions : nullptr, static_cast<cudaStream_t>(stream));
+                     b == 4 ? out_mask->regions : nullptr, state, slots, static_cast<cudaStream_t>(stream));
 }
 
 kf_status kf_pc_kalman(kf_ctx *ctx, const int32_t *regions, int64_t T, int n_tracks, double *states, int32_t *status,

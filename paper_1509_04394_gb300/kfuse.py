@@ -116,7 +116,8 @@ def _lib():
             "kf_pc_plan": (i32, [P, i64, i64, i64, P, P]),
             "kf_pc_workspace_bytes": (i32, [P, u32, i64, i64, i64, P]),
             "kf_pc_run": (i32, [P, u32, P, P, P, ctypes.c_size_t, P]),
-            "kf_pc_run_group": (i32, [P, i32, i32, P, P, i64, P, i64, P, P]),
+            "kf_pc_run_group": (i32, [P, i32, i32, P, P, i64, P, i64, P, P, ctypes.c_size_t, P]),
+            "kf_pc_group_workspace_bytes": (i32, [P, i32, i32, i64, i64, i64, P]),
             "kf_pc_kalman": (i32, [P, P, i64, i32, P, P, P]),
             "kf_kernel_times": (i32, [P, P, P]),
         }
@@ -138,7 +139,7 @@ def exported_symbols() -> list[str]:
             "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups",
             "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_grad", "kf_costmodel_get",
             "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times", "kf_pc_traffic", "kf_pc_plan",
-            "kf_pc_workspace_bytes", "kf_pc_run", "kf_pc_run_group", "kf_pc_kalman"]
+            "kf_pc_workspace_bytes", "kf_pc_run", "kf_pc_run_group", "kf_pc_kalman", "kf_pc_group_workspace_bytes"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -598,10 +599,18 @@ def kf_pc_run(ctx, cuts: int, frames, W: int, mask, counts, regions, workspace=N
            ctx)
 
 
-def kf_pc_run_group(ctx, a: int, b: int, W: int, frames=None, inp=None, out=None, mask_out=None, T=None, H=None,
+def kf_pc_group_workspace_bytes(ctx, a: int, b: int, W: int, H: int, T: int) -> int:
+    n = ctypes.c_size_t()
+    _check("kf_pc_group_workspace_bytes", _lib().kf_pc_group_workspace_bytes(ctx, int(a), int(b), int(W), int(H), int(T),
+                                                                               ctypes.byref(n)), ctx)
+    return n.value
+
+
+def kf_pc_run_group(ctx, a: int, b: int, W: int, frames=None, inp=None, out=None, mask_out=None, workspace=None,
                     stream=None) -> None:
     """One group [a..b]: input RGBA frames (a == 0) or an FP32 map [T, H, pitch]; output an
-    FP32 map [T, H, pitch] (b < 4) or (mask, counts, regions) (b == 4)."""
+    FP32 map [T, H, pitch] (b < 4) or (mask, counts, regions) (b == 4). A group holding the
+    IIR filter (a <= 1 <= b) needs `workspace` (kf_pc_group_workspace_bytes)."""
     if frames is not None:
         v = _pc_video(frames, W)
     else:
@@ -611,8 +620,10 @@ def kf_pc_run_group(ctx, a: int, b: int, W: int, frames=None, inp=None, out=None
     op_ = 0 if out is None else out.data_ptr()
     opitch = 0 if out is None else int(out.shape[2])
     mo = None if mask_out is None else _pc_out(*mask_out)
+    ws = 0 if workspace is None else workspace.data_ptr()
+    nb = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check("kf_pc_run_group", _lib().kf_pc_run_group(ctx, int(a), int(b), ctypes.byref(v), ip, ipitch, op_, opitch,
-                                                       ctypes.byref(mo) if mo is not None else None,
+                                                       ctypes.byref(mo) if mo is not None else None, ws, nb,
                                                        _stream(stream)), ctx)
 
 

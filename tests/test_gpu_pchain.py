@@ -73,7 +73,7 @@ def normwise(a, b):
     return np.max(np.abs(a - b)) / den if den > 0 else np.max(np.abs(a))
 
 
-@pytest.mark.parametrize("shape", [(5, 96, 128), (4, 61, 83), (3, 33, 29)])
+@pytest.mark.parametrize("shape", [(5, 96, 128), (4, 61, 83), (3, 33, 29), (70, 40, 50)])
 def test_every_stage_map_matches_the_oracle(dev, shape):
     T, H, W = shape
     fr = rgba_video(T, H, W, seed=3, pitch=W + 4)
@@ -83,30 +83,34 @@ def test_every_stage_map_matches_the_oracle(dev, shape):
     P = (W + 7) // 8 * 8
     cur = None
     names = ["Y", "y", "G", "M"]
+    ws = torch.empty(K.kf_pc_group_workspace_bytes(ctx.h, 1, 1, W, H, T), dtype=torch.uint8, device=dev)
     for s in range(4):
         out = torch.full((T, H, P), float("nan"), dtype=torch.float32, device=dev)
-        K.kf_pc_run_group(ctx.h, s, s, W, frames=fd if s == 0 else None, inp=cur, out=out)
+        K.kf_pc_run_group(ctx.h, s, s, W, frames=fd if s == 0 else None, inp=cur, out=out,
+                          workspace=ws if s == 1 else None)
         got = out[:, :, :W].cpu().numpy().astype(np.float64) / K.PC_SCALE[s]
         ref = maps[names[s]]
         err = max(normwise(got[t], ref[t]) for t in range(T))
         assert err <= (1e-12 if s == 0 else TOL), (names[s], err)
         cur = out
     mask, counts, regions = outputs(dev, T, H, W)
-    K.kf_pc_run_group(ctx.h, 4, 4, W, inp=cur, mask_out=(mask, counts, regions))
+    ws5 = torch.empty(K.kf_pc_group_workspace_bytes(ctx.h, 4, 4, W, H, T), dtype=torch.uint8, device=dev)
+    K.kf_pc_run_group(ctx.h, 4, 4, W, inp=cur, mask_out=(mask, counts, regions), workspace=ws5)
     m = mask.cpu().numpy()
     assert np.all(m[:, :, W:] == 7), "columns past W must be untouched"
     check_mask(m[:, :, :W], counts.cpu().numpy(), regions.cpu().numpy(), maps["M"])
 
 
-def test_all_16_partitions_are_bit_identical(dev):
-    T, H, W = 4, 70, 90
+@pytest.mark.parametrize("T", [4, 33, 65])
+def test_all_16_partitions_are_bit_identical(dev, T):
+    """T = 33 and 65: the IIR recursion spans two and three chunks."""
+    H, W = 70, 90
     fr = rgba_video(T, H, W, seed=4)
     ctx = K.Context(0, harris=False)
     fd = torch.from_numpy(fr).to(dev)
     res = {}
     for cuts in range(16):
-        ws_b = K.kf_pc_workspace_bytes(ctx.h, cuts, W, H, T)
-        ws = torch.empty(ws_b, dtype=torch.uint8, device=dev) if ws_b else None
+        ws = torch.empty(K.kf_pc_workspace_bytes(ctx.h, cuts, W, H, T), dtype=torch.uint8, device=dev)
         mask, counts, regions = outputs(dev, T, H, W)
         K.kf_pc_run(ctx.h, cuts, fd, W, mask, counts, regions, ws)
         res[cuts] = (mask.cpu().numpy(), counts.cpu().numpy(), regions.cpu().numpy())
@@ -120,7 +124,7 @@ def test_all_16_partitions_are_bit_identical(dev):
 
 
 @pytest.mark.parametrize("T,H,W", [(1, 1, 1), (2, 1, 7), (3, 7, 1), (2, 5, 5), (3, 29, 31), (2, 30, 30), (1, 64, 64),
-                                   (3, 100, 57)])
+                                   (3, 100, 57), (40, 9, 33)])
 def test_ragged_and_degenerate_frames(dev, T, H, W):
     rng = np.random.default_rng(H * 1000 + W)
     fr = rng.integers(0, 256, (T, H, W, 4), dtype=np.uint8)
@@ -128,8 +132,7 @@ def test_ragged_and_degenerate_frames(dev, T, H, W):
     fd = torch.from_numpy(fr).to(dev)
     _, _, _, maps = op.chain_volume(fr, keep_maps=True)
     for cuts in (0, 0b0010, 0b1111):
-        ws_b = K.kf_pc_workspace_bytes(ctx.h, cuts, W, H, T)
-        ws = torch.empty(ws_b, dtype=torch.uint8, device=dev) if ws_b else None
+        ws = torch.empty(K.kf_pc_workspace_bytes(ctx.h, cuts, W, H, T), dtype=torch.uint8, device=dev)
         mask, counts, regions = outputs(dev, T, H, W)
         K.kf_pc_run(ctx.h, cuts, fd, W, mask, counts, regions, ws)
         m = mask.cpu().numpy()
@@ -143,7 +146,8 @@ def test_kalman_matches_the_oracle_on_the_gpu_region_sums(dev):
     ctx = K.Context(0, harris=False)
     fd = torch.from_numpy(fr).to(dev)
     mask, counts, regions = outputs(dev, T, H, W)
-    K.kf_pc_run(ctx.h, 0, fd, W, mask, counts, regions, None)
+    ws = torch.empty(K.kf_pc_workspace_bytes(ctx.h, 0, W, H, T), dtype=torch.uint8, device=dev)
+    K.kf_pc_run(ctx.h, 0, fd, W, mask, counts, regions, ws)
     states = torch.zeros((T, 16, 4), dtype=torch.float64, device=dev)
     status = torch.full((T, 16), -1, dtype=torch.int32, device=dev)
     K.kf_pc_kalman(ctx.h, regions, states, status)

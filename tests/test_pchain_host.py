@@ -33,6 +33,12 @@ def expected_bytes(cuts, W, H, T):
         halo = sum(1 for s in (2, 3) if a <= s <= b)
         out = 32 - 2 * halo
         tot += W * H * T * (in_b[a] * 32 * 32 / out ** 2 + out_b[b])
+        if a <= 1 <= b:  # the chunked IIR recursion (chunks of 32 frames)
+            nc = -(-T // 32)
+            hw = W * H
+            tot += (nc - 1) * 32 * hw * in_b[a] + (nc - 1) * hw * 4        # local end states
+            tot += hw * in_b[a] + (nc - 1) * hw * 4 + nc * hw * 4          # carry
+            tot += nc * hw * 4 * 32 * 32 / out ** 2                          # start states, with halo
     return tot + T * 4 * (1 + 3 * 16)
 
 
@@ -52,11 +58,21 @@ def test_plan_is_full_fusion_and_orders_the_papers_partitions(hctx):
 
 
 def test_workspace_sizes(hctx):
-    plane = -(-(1024 * 512 * 3 * 4) // 256) * 256  # pitch round_up(1020, 8) = 1024
-    assert K.kf_pc_workspace_bytes(hctx, 0, 1020, 512, 3) == 0
-    assert K.kf_pc_workspace_bytes(hctx, 0b0010, 1020, 512, 3) == plane
+    T = 70  # three chunks of 32 frames
+    plane = -(-(1024 * 512 * T * 4) // 256) * 256  # pitch round_up(1020, 8) = 1024
+    state = -(-(3 * 512 * 1024 * 4) // 256) * 256
+    slots = -(-(T * 32 * 49 * 4) // 256) * 256  # 32 partial copies of the 49 per-frame sums
+    assert K.kf_pc_workspace_bytes(hctx, 0, 1020, 512, T) == state + slots
+    assert K.kf_pc_workspace_bytes(hctx, 0b0010, 1020, 512, T) == state + slots + plane
     for c in (0b0011, 0b1111):
-        assert K.kf_pc_workspace_bytes(hctx, c, 1020, 512, 3) == 2 * plane
+        assert K.kf_pc_workspace_bytes(hctx, c, 1020, 512, T) == state + slots + 2 * plane
+    for a, b in [(0, 1), (1, 1), (1, 3)]:
+        assert K.kf_pc_group_workspace_bytes(hctx, a, b, 1020, 512, T) == state
+    assert K.kf_pc_group_workspace_bytes(hctx, 0, 4, 1020, 512, T) == state + slots
+    for a, b in [(2, 4), (4, 4)]:
+        assert K.kf_pc_group_workspace_bytes(hctx, a, b, 1020, 512, T) == slots
+    for a, b in [(0, 0), (2, 3), (3, 3)]:
+        assert K.kf_pc_group_workspace_bytes(hctx, a, b, 1020, 512, T) == 0
 
 
 def test_argument_rejection(hctx):
@@ -69,8 +85,12 @@ def test_argument_rejection(hctx):
     assert L.kf_pc_run(hctx, 0, K.ctypes.byref(v), None, None, 0, None) == K.KF_EINVAL
     # region sums would pass 2^31: rejected before any launch
     big = K.kf_pc_video(16, 40000, 40000, 1, 40000)
-    assert L.kf_pc_run_group(hctx, 1, 2, K.ctypes.byref(big), 16, 40000, 16, 40000, None, None) == K.KF_EINVAL
+    assert L.kf_pc_run_group(hctx, 1, 2, K.ctypes.byref(big), 16, 40000, 16, 40000, None, 256, 1 << 40,
+                             None) == K.KF_EINVAL
     ok = K.kf_pc_video(16, 64, 32, 2, 64)
-    assert L.kf_pc_run_group(hctx, 1, 2, K.ctypes.byref(ok), 16, 64, 16, 64, None, None) == K.KF_ESTATE
+    assert L.kf_pc_run_group(hctx, 2, 3, K.ctypes.byref(ok), 16, 64, 16, 64, None, None, 0, None) == K.KF_ESTATE
+    # a group holding the IIR filter without its chunk-state workspace
+    assert L.kf_pc_run_group(hctx, 1, 2, K.ctypes.byref(ok), 16, 64, 16, 64, None, None, 0, None) == K.KF_EINVAL
+    assert L.kf_pc_run_group(hctx, 1, 2, K.ctypes.byref(ok), 16, 64, 16, 64, None, 256, 16, None) == K.KF_ENOMEM
     assert L.kf_pc_kalman(hctx, 16, 5, 16, 16, 16, None) == K.KF_ESTATE
     assert L.kf_pc_kalman(hctx, 16, -1, 16, 16, 16, None) == K.KF_EINVAL
