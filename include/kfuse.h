@@ -379,7 +379,7 @@ kf_status kf_run_static(kf_ctx *ctx, uint32_t cuts, const kf_video *video, const
  * frames that run in parallel: the filter is linear, so a pass over the input gives each
  * chunk's end state from zero, a carry pass per pixel turns those into the true state
  * before every chunk (in chunk order), and a group holding K2 runs each (tile, chunk) as
- * one block of 4 warps from that state, 8 rows' states per warp in registers. The result
+ * one block of 8 warps from that state, 4 rows' states per warp in registers. The result
  * is the recursion evaluated in this fixed chunked order (the same in every partition);
  * other groups run one warp per (tile, frame). */
 #define KF_PC_STAGES 5
@@ -388,11 +388,11 @@ kf_status kf_run_static(kf_ctx *ctx, uint32_t cuts, const kf_video *video, const
 typedef struct {
     const uint8_t *rgba;  /* device, T x H rows of `pitch` pixels of 4 bytes (R, G, B, A) */
     int64_t W, H, T;
-    int64_t pitch;        /* pixels per row, >= W; rgba 16-byte aligned */
+    int64_t pitch;        /* pixels per row, >= W, a multiple of 4; rgba 16-byte aligned */
 } kf_pc_video;
 typedef struct {
-    uint8_t *mask;        /* device, T x H x mask_pitch bytes */
-    int64_t mask_pitch;   /* >= W */
+    uint8_t *mask;        /* device, T x H x mask_pitch bytes, 16-byte aligned */
+    int64_t mask_pitch;   /* >= W, a multiple of 4 */
     int32_t *counts;      /* device, [T], written (no pre-zeroing needed) */
     int32_t *regions;     /* device, [T][KF_PC_REGIONS][3] (count, sum x, sum y), written */
 } kf_pc_out;
@@ -412,7 +412,8 @@ kf_status kf_pc_run(kf_ctx *ctx, uint32_t cuts, const kf_pc_video *video, const 
                     size_t workspace_bytes, void *stream);
 /* One group [a..b] (0-based stages, a <= b <= 4) over explicit maps. in: a == 0 the RGBA
  * frames (video), else an FP32 map [T][H][in_pitch] of stage a-1. out: b == 4 the mask
- * outputs (out_mask), else an FP32 map [T][H][out_pitch] of stage b. A group holding K2
+ * outputs (out_mask), else an FP32 map [T][H][out_pitch] of stage b. Maps: 16-byte
+ * aligned, pitches (elements) multiples of 4. A group holding K2
  * or ending at K5 needs a workspace of kf_pc_group_workspace_bytes (256-byte aligned):
  * the chunk states and the partial sums; other groups none. */
 kf_status kf_pc_group_workspace_bytes(kf_ctx *ctx, int a, int b, int64_t W, int64_t H, int64_t T, size_t *bytes);

@@ -3,15 +3,15 @@
 // any contiguous group of them fused into one kernel (Sec. V-B, Eq. 2), and K6, the
 // Kalman filter over feature positions, after the kernel-to-kernel dependency.
 //
-// A group (0-based stages A..B) works on 32 x 32 tiles of its input (lane = column); a
-// group with K3 and K4 has a 2-pixel halo and writes the inner 28 x 28 (30 x 30 with one
-// of them). Horizontal taps are warp shuffles. pc_kernel<A, B>, for groups without K2:
-// one warp per (tile, frame) streams the 32 rows in registers. pc_temporal_kernel<A, B>,
-// for groups holding K2 (the IIR filter, a recursion over frames): one block of 4 warps
-// per tile walks every frame of the video in order, each warp keeping the filter state of
-// its 8 rows in registers and loading the next frame's rows while it computes this one;
-// the spatial stages exchange rows through shared memory. No filter state goes through
-// memory.
+// A group (0-based stages A..B) runs pc_tile_kernel<A, B>: one block of 8 warps per tile
+// of its input, 128 columns (4 per lane, 16-byte loads and stores) x 32 rows, each warp
+// owning 4 rows for the point stages; K3 and K4 read neighbouring rows through shared
+// memory and neighbouring columns by one shuffle per side. A group with K3 and K4 has a
+// 2-row halo (its column halo is rounded up to one lane, 4 columns) and writes 120 x 28.
+// Groups holding K2 (the IIR filter, a recursion over frames) run each tile over a chunk
+// of frames from the chunk's start state (see the chunked recursion below), keeping each
+// pixel's filter state in registers and loading the next frame's rows while computing
+// this one; other groups run one (tile, frame) per block.
 //
 // Clamp-to-edge per stage: the group's input is read at clamped coordinates, which is
 // the clamp of K1..K3's inputs (point stages commute with it). K4 reads K3's output at
@@ -36,8 +36,11 @@ int ctx_device(const kf_ctx *ctx);  // kf_api.cu
 namespace {
 
 constexpr unsigned FULLM = 0xffffffffu;
-constexpr int TS = 32;   // tile side: 32 lanes x 32 streamed rows of the group's input
-constexpr int WPB = 4;   // warps per block of the per-frame groups
+constexpr int TS = 32;   // tile rows of the group's input
+constexpr int C4 = 4;    // columns per lane
+constexpr int TX = 32 * C4;  // tile columns
+constexpr int TW = 8;        // warps per tile
+constexpr int RW = TS / TW;  // rows per warp
 constexpr int NREG = KF_PC_REGIONS;
 constexpr int GRIDN = 4;  // regions per side
 constexpr float ALPHA = 0.25f;
@@ -68,8 +71,11 @@ struct PcParams {
 // ---- the stages (one definition each, used by every group)
 __device__ __forceinline__ float k1_gray(uint32_t rgba)
 {
-    const float r = (float)(rgba & 0xffu), g = (float)((rgba >> 8) & 0xffu), b = (float)((rgba >> 16) & 0xffu);
-    return fmaf(29.0f, b, fmaf(150.0f, g, 77.0f * r));  // integer <= 65280: exact
+    // 77 R + 150 G + 29 B in integers (<= 65280), placed under the exponent of 2^23 and
+    // 2^23 subtracted: exact, and no conversion unit (a 4-byte dot product, __dp4a,
+    // measured 15-20 % slower for the whole chain on this part)
+    const uint32_t y = 77u * (rgba & 0xffu) + 150u * ((rgba >> 8) & 0xffu) + 29u * ((rgba >> 16) & 0xffu);
+    return __uint_as_float(0x4B000000u | y) - 8388608.0f;
 }
 __device__ __forceinline__ float k2_iir(float prev, float Y) { return fmaf(ALPHA, Y - prev, prev); }
 // [1 2 1] of three neighbours (the centre weighted 2)
@@ -77,288 +83,271 @@ __device__ __forceinline__ float tap121(float l, float c, float r) { return fmaf
 
 template <int A, int B> struct Group {
     static constexpr bool H1 = A <= 1 && 1 <= B, H2 = A <= 2 && 2 <= B, H3 = A <= 3 && 3 <= B, H4 = B == 4;
-    static constexpr int HALO = (H2 ? 1 : 0) + (H3 ? 1 : 0);
-    static constexpr int OUT = TS - 2 * HALO;  // output tile side
+    static constexpr int HALO = (H2 ? 1 : 0) + (H3 ? 1 : 0);  // rows (and needed columns) each side
+    static constexpr int HC = HALO ? 4 : 0;   // column halo, rounded to whole lanes (16-byte rows)
+    static constexpr int OUTW = TX - 2 * HC;  // output tile: OUTW x OUTH
+    static constexpr int OUTH = TS - 2 * HALO;
     static constexpr bool TEMPORAL = H1;
+    // resident blocks per SM the register budget targets (measured: the fused filter with
+    // spatial stages keeps its states and the next frame's rows in registers, so fewer)
+    static constexpr int MIN_BLOCKS = (H1 && HALO) ? 3 : 4;
 };
 
-// Groups without K2: one warp per (tile, frame).
+// One block of TW = 8 warps per tile of TX = 128 columns (4 per lane) x TS = 32 rows of
+// the group's input, over one frame, or over one chunk of CHUNK frames for a group holding
+// K2. Warp w owns tile rows 4w .. 4w+3 for the point stages (and their IIR states, 16 per
+// lane); K3 and K4 read the neighbouring rows through shared memory (y' then G'), with two
+// block barriers per frame; horizontal taps are one shuffle per side per row.
 template <int A, int B>
-__global__ void __launch_bounds__(32 * WPB) pc_kernel(const PcParams p)
+__global__ void __launch_bounds__(32 * TW, Group<A, B>::MIN_BLOCKS) pc_tile_kernel(const PcParams p)
 {
     using G = Group<A, B>;
-    static_assert(!G::TEMPORAL, "groups holding the IIR filter run pc_temporal_kernel");
-    constexpr int HALO = G::HALO, OUT = G::OUT;
-    __shared__ int acc[WPB][NREG][3];  // this frame's region sums of the warp (B == 4)
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-    const int64_t n_tiles = (int64_t)p.tiles_x * p.tiles_y;
-    if (gw >= n_tiles * p.T) return;  // warp-uniform; no block barriers below
-    const int64_t tile = gw % n_tiles;
-    const int f_begin = (int)(gw / n_tiles), f_end = f_begin + 1;
-    const int W = p.W, H = p.H;
-    const int tx = (int)(tile % p.tiles_x), ty = (int)(tile / p.tiles_x);
-    const int x = tx * OUT - HALO + lane;  // this lane's input column
-    const int xc = min(max(x, 0), W - 1);
-    const int y0 = ty * OUT - HALO;         // the tile's first input row
-    const bool out_col = lane >= HALO && lane < TS - HALO && x < W;
-    const bool edge_tile = (tx * OUT - HALO < 0) || (tx * OUT - HALO + TS > W);
-    const int src_lane = lane + (xc - x);   // the lane holding the clamped column
-    const int rxl = (GRIDN * xc) / W;      // region column of this lane
-    if constexpr (G::H4) {
-        if (lane < NREG) acc[wib][lane][0] = acc[wib][lane][1] = acc[wib][lane][2] = 0;
-        __syncwarp();
-    }
-
-    uint32_t buf[TS];  // input rows of the next frame to process
-    auto load = [&](int f, uint32_t (&v)[TS]) {
-        const uint32_t *base = p.in + (int64_t)f * p.in_fstride + xc;
-#pragma unroll
-        for (int r = 0; r < TS; ++r) v[r] = __ldg(base + (int64_t)min(max(y0 + r, 0), H - 1) * p.in_pitch);
-    };
-    load(f_begin, buf);
-
-    for (int f = f_begin; f < f_end; ++f) {
-        uint32_t cur[TS];
-#pragma unroll
-        for (int r = 0; r < TS; ++r) cur[r] = buf[r];
-        if (f + 1 < f_end) load(f + 1, buf);  // in flight while this frame computes
-        float *outf = static_cast<float *>(p.out) + (int64_t)f * p.out_fstride;
-        uint8_t *outm = static_cast<uint8_t *>(p.out) + (int64_t)f * p.out_fstride;
-        [[maybe_unused]] float hy[TS], Gv[TS], D[TS], S[TS];
-        [[maybe_unused]] unsigned count = 0;
-
-        // the output row o of the group's last stage (tile row, global row y0 + o)
-        auto emit = [&](int o, float v) {
-            const int gy = y0 + o;
-            if (gy >= H) return;  // rows past the frame (warp-uniform)
-            if constexpr (!G::H4) {
-                if (out_col) outf[(int64_t)gy * p.out_pitch + x] = v;
-            } else {
-                const bool m = out_col && v > TAU;
-                if (out_col) outm[(int64_t)gy * p.out_pitch + x] = (uint8_t)m;
-                count += __popc(__ballot_sync(FULLM, m));
-                if (m) {
-                    const int rg = ((GRIDN * gy) / H) * GRIDN + rxl;
-                    atomicAdd(&acc[wib][rg][0], 1);
-                    atomicAdd(&acc[wib][rg][1], x);
-                    atomicAdd(&acc[wib][rg][2], gy);
-                }
-            }
-        };
-        // K4 (+ K5) at tile row o from D, S of rows o-1, o, o+1; at the frame's first and
-        // last rows the missing neighbour is the row itself (clamp on G')
-        auto sobel_out = [&](int o, float Dm, float Dc, float Dp, float Sm, float Sc, float Sp) {
-            const int gy = y0 + o;
-            const float dm = gy - 1 < 0 ? Dc : Dm, dp = gy + 1 > H - 1 ? Dc : Dp;
-            const float sm = gy - 1 < 0 ? Sc : Sm, sp = gy + 1 > H - 1 ? Sc : Sp;
-            const float gx = tap121(dm, Dc, dp);
-            const float gyv = sp - sm;
-            emit(o, fabsf(gx) + fabsf(gyv));
-        };
-        // K3's output row q of the tile: the column clamp, then the Sobel's row partials
-        auto push_G = [&](int q, float g) {
-            if constexpr (G::H2)
-                if (edge_tile) g = __shfl_sync(FULLM, g, src_lane);
-            Gv[q] = g;
-            const float gl = __shfl_up_sync(FULLM, g, 1), gr = __shfl_down_sync(FULLM, g, 1);
-            D[q] = gr - gl;
-            S[q] = tap121(gl, g, gr);
-        };
-
-#pragma unroll
-        for (int r = 0; r < TS; ++r) {
-            const uint32_t v = cur[r];
-            if constexpr (A == 0) {
-                emit(r, k1_gray(v));  // K1 alone (a group from K1 on that holds K2 is temporal)
-            } else if constexpr (A == 2) {
-                const float yv = __uint_as_float(v);
-                // ---- K3: horizontal [1 2 1], then vertical [1 2 1] one row behind
-                hy[r] = tap121(__shfl_up_sync(FULLM, yv, 1), yv, __shfl_down_sync(FULLM, yv, 1));
-                if (r >= 2) {
-                    const int q = r - 1;
-                    const float g = tap121(hy[q - 1], hy[q], hy[q + 1]);
-                    if constexpr (B == 2) {
-                        emit(q, g);
-                    } else {
-                        push_G(q, g);
-                        // output rows 2..29: G rows 1..30 exist
-                        if (q >= 3) sobel_out(q - 1, D[q - 2], D[q - 1], D[q], S[q - 2], S[q - 1], S[q]);
-                    }
-                }
-            } else if constexpr (A == 3) {
-                push_G(r, __uint_as_float(v));
-                if (r >= 2) sobel_out(r - 1, D[r - 2], D[r - 1], D[r], S[r - 2], S[r - 1], S[r]);
-            } else {
-                emit(r, __uint_as_float(v));  // K5 alone on M'
-            }
-        }
-
-        if constexpr (G::H4) {
-            __syncwarp();
-            int32_t *sl = p.slots + ((int64_t)f * NSLOT + (int)(gw % NSLOT)) * NCNT;
-            if (lane == 0 && count) atomicAdd(sl, (int)count);
-            if (lane < NREG) {
-                int *a = acc[wib][lane];
-                if (a[0]) {
-                    atomicAdd(sl + 1 + 3 * lane + 0, a[0]);
-                    atomicAdd(sl + 1 + 3 * lane + 1, a[1]);
-                    atomicAdd(sl + 1 + 3 * lane + 2, a[2]);
-                    a[0] = a[1] = a[2] = 0;
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
-// Groups holding K2: one block of 4 warps per tile walks every frame of the video in
-// order. Warp w owns tile rows 8w .. 8w+7 for the point stages (its 8 IIR states per lane
-// stay in registers; the next frame's 8 input rows are loaded while this frame computes),
-// then the spatial stages read neighbouring rows through shared memory (y', then G'), two
-// block barriers per frame. Four warps per tile give the recursion 4x the warps of one
-// warp per tile.
-constexpr int TW = 4;        // warps per tile
-constexpr int RW = TS / TW;  // rows per warp
-
-template <int A, int B>
-__global__ void __launch_bounds__(32 * TW) pc_temporal_kernel(const PcParams p)
-{
-    // blockIdx.y: the chunk of CHUNK frames; the filter starts from the state the carry
-    // pass left for the frame before the chunk (at clamped coordinates, like the input)
-    using G = Group<A, B>;
-    static_assert(G::TEMPORAL, "groups holding the IIR filter");
-    constexpr int HALO = G::HALO, OUT = G::OUT;
-    __shared__ float ys[TS][TS];  // y' of the tile (B >= 2)
-    __shared__ float gs[TS][TS];  // G' of the tile (B >= 3)
+    constexpr int HALO = G::HALO, HC = G::HC, OUTW = G::OUTW, OUTH = G::OUTH;
+    __shared__ float4 ys[TS][32];  // y' rows of the tile (groups with K3)
+    __shared__ float4 gs[TS][32];  // G' rows of the tile (groups with K3 and K4)
     __shared__ int acc[TW][NREG][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int tile = blockIdx.x;
     const int W = p.W, H = p.H;
     const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
-    const int x = tx * OUT - HALO + lane;
-    const int xc = min(max(x, 0), W - 1);
-    const int y0 = ty * OUT - HALO;
-    const bool out_col = lane >= HALO && lane < TS - HALO && x < W;
-    const bool edge_tile = (tx * OUT - HALO < 0) || (tx * OUT - HALO + TS > W);
-    const int src_lane = lane + (xc - x);
-    const int rxl = (GRIDN * xc) / W;
-    const int r0 = RW * w;  // this warp's first tile row
-    const int f0 = blockIdx.y * CHUNK, f1 = min(f0 + CHUNK, p.T);
+    const int xt = tx * OUTW - HC;  // the tile's first input column (a multiple of 4)
+    const int x0 = xt + C4 * lane;  // this lane's first column
+    const int y0 = ty * OUTH - HALO;
+    const int r0 = RW * w;
+    // the lane's columns: clamped sources, and which are outputs
+    const bool lane_inside = x0 >= 0 && x0 + C4 <= W;
+    int xc[C4];
+    unsigned out_bits = 0;
+#pragma unroll
+    for (int e = 0; e < C4; ++e) {
+        xc[e] = min(max(x0 + e, 0), W - 1);
+        const int col = C4 * lane + e;
+        out_bits |= (col >= HC && col < TX - HC && x0 + e < W) ? (1u << e) : 0u;
+    }
+    const bool edge_tile = xt < 0 || xt + TX > W;
+    const bool rows_inside = y0 >= 0 && y0 + TS <= H;
+    [[maybe_unused]] const int rxl[C4] = {(GRIDN * xc[0]) / W, (GRIDN * xc[1]) / W, (GRIDN * xc[2]) / W,
+                                          (GRIDN * xc[3]) / W};
+    int f0, f1;
+    if constexpr (G::TEMPORAL) {
+        f0 = blockIdx.y * CHUNK;
+        f1 = min(f0 + CHUNK, p.T);
+    } else {
+        f0 = blockIdx.y;
+        f1 = f0 + 1;
+    }
     if constexpr (G::H4) {
         if (lane < NREG) acc[w][lane][0] = acc[w][lane][1] = acc[w][lane][2] = 0;
         __syncwarp();
     }
-    uint32_t buf[RW];
-    auto load = [&](int f) {
-        const uint32_t *base = p.in + (int64_t)f * p.in_fstride + xc;
-#pragma unroll
-        for (int i = 0; i < RW; ++i) buf[i] = __ldg(base + (int64_t)min(max(y0 + r0 + i, 0), H - 1) * p.in_pitch);
+    // 16-byte loads of one input row (4 columns), clamped columns at a frame edge
+    auto load_row = [&](const uint32_t *plane, int64_t pitch, int r) {
+        const uint32_t *row = plane + (int64_t)min(max(y0 + r, 0), H - 1) * pitch;
+        uint4 v;
+        if (lane_inside) {
+            v = __ldg(reinterpret_cast<const uint4 *>(row + x0));
+        } else {
+            v.x = __ldg(row + xc[0]);
+            v.y = __ldg(row + xc[1]);
+            v.z = __ldg(row + xc[2]);
+            v.w = __ldg(row + xc[3]);
+        }
+        return v;
     };
-    float st[RW];
-    {
-        const float *s0 = p.state + (int64_t)blockIdx.y * H * p.state_pitch + xc;
+    uint4 buf[RW];
+    auto load = [&](int f) {
+        const uint32_t *plane = p.in + (int64_t)f * p.in_fstride;
 #pragma unroll
-        for (int i = 0; i < RW; ++i) st[i] = s0[(int64_t)min(max(y0 + r0 + i, 0), H - 1) * p.state_pitch];
+        for (int i = 0; i < RW; ++i) buf[i] = load_row(plane, p.in_pitch, r0 + i);
+    };
+    [[maybe_unused]] float st[RW][C4];  // IIR states of this warp's rows (TEMPORAL)
+    if constexpr (G::TEMPORAL) {
+        const uint32_t *s0 = reinterpret_cast<const uint32_t *>(p.state) + (int64_t)blockIdx.y * H * p.state_pitch;
+#pragma unroll
+        for (int i = 0; i < RW; ++i) {
+            const uint4 v = load_row(s0, p.state_pitch, r0 + i);
+            st[i][0] = __uint_as_float(v.x);
+            st[i][1] = __uint_as_float(v.y);
+            st[i][2] = __uint_as_float(v.z);
+            st[i][3] = __uint_as_float(v.w);
+        }
     }
     load(f0);
     for (int f = f0; f < f1; ++f) {
-        uint32_t cur[RW];
-#pragma unroll
-        for (int i = 0; i < RW; ++i) cur[i] = buf[i];
-        if (f + 1 < f1) load(f + 1);
         float *outf = static_cast<float *>(p.out) + (int64_t)f * p.out_fstride;
         uint8_t *outm = static_cast<uint8_t *>(p.out) + (int64_t)f * p.out_fstride;
         [[maybe_unused]] unsigned count = 0;
-        auto emit = [&](int o, float v) {  // tile row o (warp-uniform)
+        // one output row of the group's last stage: 4 values of tile row o
+        auto emit = [&](int o, const float (&v)[C4]) {
             const int gy = y0 + o;
-            if (gy >= H) return;
+            if (!rows_inside && gy >= H) return;  // warp-uniform
             if constexpr (!G::H4) {
-                if (out_col) outf[(int64_t)gy * p.out_pitch + x] = v;
+                float *row = outf + (int64_t)gy * p.out_pitch + x0;
+                if (out_bits == 0xfu) {
+                    *reinterpret_cast<float4 *>(row) = make_float4(v[0], v[1], v[2], v[3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < C4; ++e) if (out_bits >> e & 1) row[e] = v[e];
+                }
             } else {
-                const bool m = out_col && v > TAU;
-                if (out_col) outm[(int64_t)gy * p.out_pitch + x] = (uint8_t)m;
-                count += __popc(__ballot_sync(FULLM, m));
-                if (m) {
-                    const int rg = ((GRIDN * gy) / H) * GRIDN + rxl;
-                    atomicAdd(&acc[w][rg][0], 1);
-                    atomicAdd(&acc[w][rg][1], x);
-                    atomicAdd(&acc[w][rg][2], gy);
+                unsigned bits = 0;
+#pragma unroll
+                for (int e = 0; e < C4; ++e) bits |= (v[e] > TAU) ? (1u << e) : 0u;
+                bits &= out_bits;
+                uint8_t *row = outm + (int64_t)gy * p.out_pitch + x0;
+                if (out_bits == 0xfu) {
+                    *reinterpret_cast<uint32_t *>(row) = (bits & 1u) | (bits & 2u) << 7 | (bits & 4u) << 14 | (bits & 8u) << 21;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < C4; ++e) if (out_bits >> e & 1) row[e] = (uint8_t)(bits >> e & 1);
+                }
+                count += __popc(bits);
+                if (bits) {
+                    const int ry = ((GRIDN * gy) / H) * GRIDN;
+#pragma unroll
+                    for (int e = 0; e < C4; ++e) {
+                        if (bits >> e & 1) {
+                            const int rg = ry + rxl[e];
+                            atomicAdd(&acc[w][rg][0], 1);
+                            atomicAdd(&acc[w][rg][1], x0 + e);
+                            atomicAdd(&acc[w][rg][2], gy);
+                        }
+                    }
                 }
             }
         };
-        // ---- K1, K2 on this warp's rows
+        // horizontal [1 2 1] of a row held 4 columns per lane (one shuffle per side)
+        auto h121 = [&](const float4 v, float (&o)[C4]) {
+            const float l = __shfl_up_sync(FULLM, v.w, 1), r = __shfl_down_sync(FULLM, v.x, 1);
+            o[0] = tap121(l, v.x, v.y);
+            o[1] = tap121(v.x, v.y, v.z);
+            o[2] = tap121(v.y, v.z, v.w);
+            o[3] = tap121(v.z, v.w, r);
+        };
+
+        // ---- the point stages on this warp's rows: K1, K2 (or the group's loaded input)
+        [[maybe_unused]] float pv[RW][C4];
 #pragma unroll
         for (int i = 0; i < RW; ++i) {
-            const float Y = A == 0 ? k1_gray(cur[i]) : __uint_as_float(cur[i]);
-            st[i] = k2_iir(st[i], Y);
-            if constexpr (B == 1) emit(r0 + i, st[i]);
-            else ys[r0 + i][lane] = st[i];
+            const uint32_t u[C4] = {buf[i].x, buf[i].y, buf[i].z, buf[i].w};
+#pragma unroll
+            for (int e = 0; e < C4; ++e) {
+                float v = (A == 0) ? k1_gray(u[e]) : __uint_as_float(u[e]);
+                if constexpr (G::TEMPORAL) {
+                    st[i][e] = k2_iir(st[i][e], v);
+                    v = st[i][e];
+                }
+                pv[i][e] = v;
+            }
         }
-        if constexpr (B >= 2) {
+        if (f + 1 < f1) load(f + 1);  // the next frame's rows, in flight during this frame's spatial stages
+        if constexpr (B <= 1 || A == 4) {
+            // point groups: K1 alone, K1 K2, K2 alone, or K5 alone (on M')
+#pragma unroll
+            for (int i = 0; i < RW; ++i) emit(r0 + i, pv[i]);
+        } else if constexpr (A <= 2) {
+            // ---- K3 (then K4, K5) with the rows of the whole tile from shared memory
+#pragma unroll
+            for (int i = 0; i < RW; ++i) ys[r0 + i][lane] = make_float4(pv[i][0], pv[i][1], pv[i][2], pv[i][3]);
             __syncthreads();
-            // ---- K3 on rows q of this warp with both neighbours in the tile (1..30)
-            float hy[RW + 2];
+            // rows streamed top to bottom: G' of row q as soon as hy of row q+1 exists
+            float hy[3][C4];  // hy of rows q-1, q, q+1 (rolling)
 #pragma unroll
             for (int i = 0; i < RW + 2; ++i) {
                 const int r = r0 - 1 + i;
-                if (r >= 0 && r < TS) {  // warp-uniform
-                    const float yv = ys[r][lane];
-                    hy[i] = tap121(__shfl_up_sync(FULLM, yv, 1), yv, __shfl_down_sync(FULLM, yv, 1));
-                }
-            }
 #pragma unroll
-            for (int i = 0; i < RW; ++i) {
-                const int q = r0 + i;
-                if (q < 1 || q > TS - 2) continue;
-                float g = tap121(hy[i], hy[i + 1], hy[i + 2]);
+                for (int e = 0; e < C4; ++e) { hy[0][e] = hy[1][e]; hy[1][e] = hy[2][e]; }
+                if (r >= 0 && r < TS) h121(ys[r][lane], hy[2]);  // warp-uniform
+                const int q = r - 1;
+                if (i < 2 || q < 1 || q > TS - 2) continue;
+                float g[C4];
+#pragma unroll
+                for (int e = 0; e < C4; ++e) g[e] = tap121(hy[0][e], hy[1][e], hy[2][e]);
                 if constexpr (B == 2) {
                     emit(q, g);
                 } else {
-                    if (edge_tile) g = __shfl_sync(FULLM, g, src_lane);
-                    gs[q][lane] = g;
+                    if (edge_tile) {  // out-of-frame columns of G' take the edge column's value
+                        if (xt < 0) {
+                            const int sl = (0 - xt) / C4, se = (0 - xt) % C4;
+                            const float ev = __shfl_sync(FULLM, se == 0 ? g[0] : se == 1 ? g[1] : se == 2 ? g[2] : g[3], sl);
+#pragma unroll
+                            for (int e = 0; e < C4; ++e) if (x0 + e < 0) g[e] = ev;
+                        }
+                        if (xt + TX > W) {
+                            const int sl = (W - 1 - xt) / C4, se = (W - 1 - xt) % C4;
+                            const float ev = __shfl_sync(FULLM, se == 0 ? g[0] : se == 1 ? g[1] : se == 2 ? g[2] : g[3], sl);
+#pragma unroll
+                            for (int e = 0; e < C4; ++e) if (x0 + e >= W) g[e] = ev;
+                        }
+                    }
+                    gs[q][lane] = make_float4(g[0], g[1], g[2], g[3]);
                 }
             }
             if constexpr (B >= 3) {
                 __syncthreads();
-                // ---- K4 (+ K5) on output rows o of this warp (2..29)
-                float Dv[RW + 2], Sv[RW + 2];
+            }
+        } else {  // A == 3: K4 (+ K5) on the loaded G' rows
 #pragma unroll
-                for (int i = 0; i < RW + 2; ++i) {
-                    const int r = r0 - 1 + i;
-                    if (r >= 1 && r <= TS - 2) {
-                        const float g = gs[r][lane];
-                        const float gl = __shfl_up_sync(FULLM, g, 1), gr = __shfl_down_sync(FULLM, g, 1);
-                        Dv[i] = gr - gl;
-                        Sv[i] = tap121(gl, g, gr);
+            for (int i = 0; i < RW; ++i) gs[r0 + i][lane] = make_float4(pv[i][0], pv[i][1], pv[i][2], pv[i][3]);
+            __syncthreads();
+        }
+        if constexpr (G::H3) {
+            // ---- K4 (+ K5) on output rows 2..29 (1..30 when the group starts at K4)
+            constexpr int lo = HALO, hi = TS - HALO;
+            float Dv[3][C4], Sv[3][C4];  // rows o-1, o, o+1 (rolling)
+#pragma unroll
+            for (int i = 0; i < RW + 2; ++i) {
+                const int r = r0 - 1 + i;
+#pragma unroll
+                for (int e = 0; e < C4; ++e) {
+                    Dv[0][e] = Dv[1][e]; Dv[1][e] = Dv[2][e];
+                    Sv[0][e] = Sv[1][e]; Sv[1][e] = Sv[2][e];
+                }
+                if (r >= lo - 1 && r <= hi) {  // warp-uniform
+                    const float4 g = gs[r][lane];
+                    const float gl = __shfl_up_sync(FULLM, g.w, 1), gr = __shfl_down_sync(FULLM, g.x, 1);
+                    const float gv[C4 + 2] = {gl, g.x, g.y, g.z, g.w, gr};
+#pragma unroll
+                    for (int e = 0; e < C4; ++e) {
+                        Dv[2][e] = gv[e + 2] - gv[e];
+                        Sv[2][e] = tap121(gv[e], gv[e + 1], gv[e + 2]);
                     }
                 }
+                const int o = r - 1;
+                if (i < 2 || o < lo || o >= hi) continue;
+                // rows o-1, o+1; at the frame's first and last rows the row itself (clamp on G')
+                const bool top = !rows_inside && y0 + o - 1 < 0, bot = !rows_inside && y0 + o + 1 > H - 1;
+                float m[C4];
 #pragma unroll
-                for (int i = 0; i < RW; ++i) {
-                    const int o = r0 + i;
-                    if (o < 2 || o > TS - 3) continue;
-                    const int gy = y0 + o;
-                    const float dm = gy - 1 < 0 ? Dv[i + 1] : Dv[i], dp = gy + 1 > H - 1 ? Dv[i + 1] : Dv[i + 2];
-                    const float sm = gy - 1 < 0 ? Sv[i + 1] : Sv[i], sp = gy + 1 > H - 1 ? Sv[i + 1] : Sv[i + 2];
-                    emit(o, fabsf(tap121(dm, Dv[i + 1], dp)) + fabsf(sp - sm));
+                for (int e = 0; e < C4; ++e) {
+                    const float dc = Dv[1][e], sc = Sv[1][e];
+                    const float dm = top ? dc : Dv[0][e], dp = bot ? dc : Dv[2][e];
+                    const float sm = top ? sc : Sv[0][e], sp = bot ? sc : Sv[2][e];
+                    m[e] = fabsf(tap121(dm, dc, dp)) + fabsf(sp - sm);
                 }
+                emit(o, m);
             }
         }
         if constexpr (G::H4) {
-            __syncwarp();
-            int32_t *sl = p.slots + ((int64_t)f * NSLOT + (int)((blockIdx.x * TW + w) % NSLOT)) * NCNT;
+            count = __reduce_add_sync(FULLM, count);
+            __syncwarp();  // the lanes' shared-memory region sums are visible
+            const int64_t slot = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * TW + w;
+            int32_t *sl = p.slots + ((int64_t)f * NSLOT + (int)(slot % NSLOT)) * NCNT;
             if (lane == 0 && count) atomicAdd(sl, (int)count);
             if (lane < NREG) {
-                int *a = acc[w][lane];
-                if (a[0]) {
-                    atomicAdd(sl + 1 + 3 * lane + 0, a[0]);
-                    atomicAdd(sl + 1 + 3 * lane + 1, a[1]);
-                    atomicAdd(sl + 1 + 3 * lane + 2, a[2]);
-                    a[0] = a[1] = a[2] = 0;
+                int *a2 = acc[w][lane];
+                if (a2[0]) {
+                    atomicAdd(sl + 1 + 3 * lane + 0, a2[0]);
+                    atomicAdd(sl + 1 + 3 * lane + 1, a2[1]);
+                    atomicAdd(sl + 1 + 3 * lane + 2, a2[2]);
+                    a2[0] = a2[1] = a2[2] = 0;
                 }
             }
             __syncwarp();
         }
+        // before the next frame rewrites ys (read by K3 above when no second barrier follows
+        // K3) or gs (written from the input rows when the group starts at K4)
+        if constexpr ((G::H2 && B == 2) || A == 3) __syncthreads();
     }
 }
 
@@ -369,32 +358,34 @@ __global__ void __launch_bounds__(32 * TW) pc_temporal_kernel(const PcParams p)
 // s_0 = Y_0 (so that y_0 = Y_0), s_k = (1 - ALPHA)^CHUNK s_{k-1} + l_end(k-1); (3) every
 // group holding K2 runs each chunk from its s_k. The states are one FP32 plane per chunk;
 // pass (2) overwrites l_end(k-1) with s_{k-1} in place.
+constexpr int LW = 4, LR = TS / LW;  // local pass: warps per block, rows per warp (1 column per lane)
+
 template <int A0>  // 0: RGBA frames, 1: Y' map
-__global__ void __launch_bounds__(32 * TW) pc_iir_local_kernel(const PcParams p)
+__global__ void __launch_bounds__(32 * LW) pc_iir_local_kernel(const PcParams p)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int x = blockIdx.x * TS + lane;
-    const int y = blockIdx.z * TS + RW * w;
+    const int x = blockIdx.x * 32 + lane;
+    const int y = blockIdx.z * TS + LR * w;
     const int k = blockIdx.y;  // chunk (all but the last)
     if (x >= p.W) return;      // no block barriers here
     const int f0 = k * CHUNK;
-    float l[RW];
+    float l[LR];
 #pragma unroll
-    for (int i = 0; i < RW; ++i) l[i] = 0.0f;
+    for (int i = 0; i < LR; ++i) l[i] = 0.0f;
     const uint32_t *base = p.in + x;
-    const int nrows = min(RW, p.H - y);
+    const int nrows = min(LR, p.H - y);
 #pragma unroll 4
     for (int f = f0; f < f0 + CHUNK; ++f) {  // unrolled: later frames' loads issue early
         const uint32_t *fr = base + (int64_t)f * p.in_fstride;
-        uint32_t v[RW];
+        uint32_t v[LR];
 #pragma unroll
-        for (int i = 0; i < RW; ++i) v[i] = i < nrows ? __ldg(fr + (int64_t)(y + i) * p.in_pitch) : 0u;
+        for (int i = 0; i < LR; ++i) v[i] = i < nrows ? __ldg(fr + (int64_t)(y + i) * p.in_pitch) : 0u;
 #pragma unroll
-        for (int i = 0; i < RW; ++i) l[i] = k2_iir(l[i], A0 == 0 ? k1_gray(v[i]) : __uint_as_float(v[i]));
+        for (int i = 0; i < LR; ++i) l[i] = k2_iir(l[i], A0 == 0 ? k1_gray(v[i]) : __uint_as_float(v[i]));
     }
     float *o = p.state + (int64_t)k * p.H * p.state_pitch + x;
 #pragma unroll
-    for (int i = 0; i < RW; ++i)
+    for (int i = 0; i < LR; ++i)
         if (y + i < p.H) o[(int64_t)(y + i) * p.state_pitch] = l[i];
 }
 
@@ -441,59 +432,76 @@ __global__ void pc_sums_kernel(const int32_t *slots, int T, int32_t *counts, int
 // K6: one thread per track walks the frames. The constant-velocity model is the same per
 // axis and starts from the same covariance, so the x and y axes share one symmetric 2 x 2
 // covariance (P00 position, P01, P11 velocity) -- the block structure of the 4 x 4 filter.
-__global__ void pc_kalman_kernel(const int32_t *regions, int T, int n, double *states, int32_t *status)
+// The block stages KF_FRAMES frames of region sums in shared memory at a time (coalesced),
+// so the walk's dependent chain never waits on a global load.
+constexpr int KF_TRACKS = 32;  // tracks per block
+constexpr int KF_FRAMES = 64;  // frames staged per round
+
+__global__ void __launch_bounds__(KF_TRACKS) pc_kalman_kernel(const int32_t *regions, int T, int n, double *states,
+                                                               int32_t *status)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+    __shared__ int32_t zs[KF_FRAMES][KF_TRACKS][3];
+    const int k0 = blockIdx.x * KF_TRACKS, k = k0 + threadIdx.x;
+    const int nb = min(KF_TRACKS, n - k0);  // tracks of this block
     bool started = false;
     double px = 0, py = 0, vx = 0, vy = 0, P00 = 0, P01 = 0, P11 = 0;
-    for (int t = 0; t < T; ++t) {
-        const int32_t *rg = regions + ((int64_t)t * n + k) * 3;
-        const int cnt = rg[0];
-        const double zx = cnt > 0 ? (double)rg[1] / cnt : 0.0, zy = cnt > 0 ? (double)rg[2] / cnt : 0.0;
-        int s;
-        if (!started) {
-            if (cnt > 0) {
-                started = true;
-                px = zx;
-                py = zy;
-                vx = vy = 0.0;
-                P00 = KR;
-                P01 = 0.0;
-                P11 = KP0;
-                s = 1;
-            } else {
-                s = 0;
-            }
-        } else {
-            // predict: state by F, P by F P F' + Q with Q = q [[1/3, 1/2], [1/2, 1]]
-            px += vx;
-            py += vy;
-            const double a = P00 + 2.0 * P01 + P11 + KQ / 3.0, b = P01 + P11 + KQ / 2.0, c = P11 + KQ;
-            P00 = a;
-            P01 = b;
-            P11 = c;
-            if (cnt > 0) {
-                const double Sd = P00 + KR, k0 = P00 / Sd, k1 = P01 / Sd;
-                const double ex = zx - px, ey = zy - py;
-                px += k0 * ex;
-                vx += k1 * ex;
-                py += k0 * ey;
-                vy += k1 * ey;
-                P11 -= k1 * P01;
-                P01 *= 1.0 - k0;
-                P00 *= 1.0 - k0;
-                s = 1;
-            } else {
-                s = 2;
-            }
+    for (int t0 = 0; t0 < T; t0 += KF_FRAMES) {
+        const int nt = min(KF_FRAMES, T - t0);
+        __syncthreads();  // the previous round's values are consumed
+        for (int i = threadIdx.x; i < nt * nb * 3; i += KF_TRACKS) {
+            const int t = i / (nb * 3), j = i - t * nb * 3;
+            zs[t][j / 3][j % 3] = regions[((int64_t)(t0 + t) * n + k0) * 3 + j];
         }
-        double *o = states + ((int64_t)t * n + k) * 4;
-        o[0] = px;
-        o[1] = py;
-        o[2] = vx;
-        o[3] = vy;
-        status[(int64_t)t * n + k] = s;
+        __syncthreads();
+        if (k >= n) continue;
+        for (int t = 0; t < nt; ++t) {
+            const int cnt = zs[t][threadIdx.x][0];
+            const double inv_c = cnt > 0 ? 1.0 / cnt : 0.0;
+            const double zx = zs[t][threadIdx.x][1] * inv_c, zy = zs[t][threadIdx.x][2] * inv_c;
+            int s;
+            if (!started) {
+                if (cnt > 0) {
+                    started = true;
+                    px = zx;
+                    py = zy;
+                    vx = vy = 0.0;
+                    P00 = KR;
+                    P01 = 0.0;
+                    P11 = KP0;
+                    s = 1;
+                } else {
+                    s = 0;
+                }
+            } else {
+                // predict: state by F, P by F P F' + Q with Q = q [[1/3, 1/2], [1/2, 1]]
+                px += vx;
+                py += vy;
+                const double a = P00 + 2.0 * P01 + P11 + KQ / 3.0, b = P01 + P11 + KQ / 2.0, c = P11 + KQ;
+                P00 = a;
+                P01 = b;
+                P11 = c;
+                if (cnt > 0) {
+                    const double inv_s = 1.0 / (P00 + KR), g0 = P00 * inv_s, g1 = P01 * inv_s;
+                    const double ex = zx - px, ey = zy - py;
+                    px += g0 * ex;
+                    vx += g1 * ex;
+                    py += g0 * ey;
+                    vy += g1 * ey;
+                    P11 -= g1 * P01;
+                    P01 *= 1.0 - g0;
+                    P00 *= 1.0 - g0;
+                    s = 1;
+                } else {
+                    s = 2;
+                }
+            }
+            double *o = states + ((int64_t)(t0 + t) * n + k) * 4;
+            o[0] = px;
+            o[1] = py;
+            o[2] = vx;
+            o[3] = vy;
+            status[(int64_t)(t0 + t) * n + k] = s;
+        }
     }
 }
 
@@ -504,14 +512,13 @@ int launch_one(const PcParams &p, cudaStream_t s)
     const int64_t n_tiles = (int64_t)p.tiles_x * p.tiles_y;
     if constexpr (G::TEMPORAL) {
         // the chunk states first: local ends, then the carry (in place)
-        const dim3 lg((unsigned)((p.W + TS - 1) / TS), (unsigned)(p.n_chunks - 1), (unsigned)((p.H + TS - 1) / TS));
-        if (p.n_chunks > 1) pc_iir_local_kernel<A><<<lg, 32 * TW, 0, s>>>(p);
+        const dim3 lg((unsigned)((p.W + 31) / 32), (unsigned)(p.n_chunks - 1), (unsigned)((p.H + TS - 1) / TS));
+        if (p.n_chunks > 1) pc_iir_local_kernel<A><<<lg, 32 * LW, 0, s>>>(p);
         const int64_t px = (int64_t)p.W * p.H;
         pc_iir_carry_kernel<A><<<(unsigned)((px + 255) / 256), 256, 0, s>>>(p);
-        pc_temporal_kernel<A, B><<<dim3((unsigned)n_tiles, (unsigned)p.n_chunks), 32 * TW, 0, s>>>(p);
+        pc_tile_kernel<A, B><<<dim3((unsigned)n_tiles, (unsigned)p.n_chunks), 32 * TW, 0, s>>>(p);
     } else {
-        const int64_t warps = n_tiles * p.T;
-        pc_kernel<A, B><<<(unsigned)((warps + WPB - 1) / WPB), 32 * WPB, 0, s>>>(p);
+        pc_tile_kernel<A, B><<<dim3((unsigned)n_tiles, (unsigned)p.T), 32 * TW, 0, s>>>(p);
     }
     return (int)cudaGetLastError();
 }
@@ -549,15 +556,16 @@ bool sums_fit(int64_t W, int64_t H) { return (W > H ? W : H) * (W * H / 16 + W +
 
 kf_status check_video(const kf_pc_video *v)
 {
-    if (!v || !v->rgba || v->W <= 0 || v->H <= 0 || v->T < 0 || v->pitch < v->W || !aligned(v->rgba, 16)) return KF_EINVAL;
+    if (!v || !v->rgba || v->W <= 0 || v->H <= 0 || v->T < 0 || v->pitch < v->W || v->pitch % 4 || !aligned(v->rgba, 16))
+        return KF_EINVAL;
     if (v->W > (1 << 24) || v->H > (1 << 24) || v->T > 0x7fffffff || v->W * v->H > 0x7fffffffLL) return KF_EINVAL;
     if (!sums_fit(v->W, v->H)) return KF_EINVAL;
     return KF_OK;
 }
 kf_status check_out(const kf_pc_out *o, int64_t W)
 {
-    if (!o || !o->mask || o->mask_pitch < W || !o->counts || !o->regions || !aligned(o->counts, 4) ||
-        !aligned(o->regions, 4))
+    if (!o || !o->mask || o->mask_pitch < W || o->mask_pitch % 4 || !aligned(o->mask, 16) || !o->counts || !o->regions ||
+        !aligned(o->counts, 4) || !aligned(o->regions, 4))
         return KF_EINVAL;
     return KF_OK;
 }
@@ -565,12 +573,13 @@ kf_status check_out(const kf_pc_out *o, int64_t W)
 PcParams params_for(int a, int b, int64_t W, int64_t H, int64_t T)
 {
     PcParams p{};
-    const int out = TS - 2 * halo_of(a, b);
+    const int halo = halo_of(a, b), hc = halo ? 4 : 0;
+    const int outw = TX - 2 * hc, outh = TS - 2 * halo;
     p.W = (int)W;
     p.H = (int)H;
     p.T = (int)T;
-    p.tiles_x = (int)((W + out - 1) / out);
-    p.tiles_y = (int)((H + out - 1) / out);
+    p.tiles_x = (int)((W + outw - 1) / outw);
+    p.tiles_y = (int)((H + outh - 1) / outh);
     return p;
 }
 
@@ -611,7 +620,7 @@ kf_status run_group(kf_ctx *ctx, int a, int b, const uint32_t *in, int64_t in_pi
     }
     const int64_t n_tiles = (int64_t)p.tiles_x * p.tiles_y;
     const bool temporal = holds_iir(a, b);
-    if ((temporal ? n_tiles : (n_tiles * T + WPB - 1) / WPB) > 0x7fffffffLL) return KF_EINVAL;
+    if (n_tiles > 0x7fffffffLL || (!temporal && T > 65535)) return KF_EINVAL;
     if (temporal && (p.n_chunks > 65535 || (H + TS - 1) / TS > 65535)) return KF_EINVAL;
     int e = launch_group(a, b, p, s);
     if (!e && b == 4) {
@@ -634,8 +643,8 @@ kf_status kf_pc_traffic(kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_
     int a = 0;
     for (int i = 0; i < KF_PC_STAGES; ++i) {
         if (i == KF_PC_STAGES - 1 || (cuts >> i & 1)) {
-            const int out = TS - 2 * halo_of(a, i);
-            const double read_factor = (double)TS * TS / ((double)out * out);
+            const int halo = halo_of(a, i), hc = halo ? 4 : 0;
+            const double read_factor = (double)TX * TS / ((double)(TX - 2 * hc) * (TS - 2 * halo));
             tot += px * (map_bytes(a - 1) * read_factor + map_bytes(i));
             if (holds_iir(a, i)) {
                 // the chunked recursion: the local pass reads all but the last chunk and writes
@@ -741,13 +750,13 @@ kf_status kf_pc_run_group(kf_ctx *ctx, int a, int b, const kf_pc_video *video, c
     if (a == 0) {
         const kf_status st = check_video(video);
         if (st != KF_OK) return st;
-    } else if (!in || in_pitch < W || !aligned(in, 4)) {
+    } else if (!in || in_pitch < W || in_pitch % 4 || !aligned(in, 16)) {
         return KF_EINVAL;
     }
     if (b == 4) {
         const kf_status st = check_out(out_mask, W);
         if (st != KF_OK) return st;
-    } else if (!out || out_pitch < W || !aligned(out, 4)) {
+    } else if (!out || out_pitch < W || out_pitch % 4 || !aligned(out, 16)) {
         return KF_EINVAL;
     }
     const size_t need = (holds_iir(a, b) ? state_bytes(W, H, T) : 0) + (b == 4 ? slot_bytes(T) : 0);
@@ -780,8 +789,8 @@ kf_status kf_pc_kalman(kf_ctx *ctx, const int32_t *regions, int64_t T, int n_tra
     const int dev = kf::ctx_device(ctx);
     if (dev < 0) return KF_ESTATE;
     if (cudaSetDevice(dev) != cudaSuccess) return KF_ECUDA;
-    pc_kalman_kernel<<<(n_tracks + 63) / 64, 64, 0, static_cast<cudaStream_t>(stream)>>>(regions, (int)T, n_tracks,
-                                                                                           states, status);
+    pc_kalman_kernel<<<(n_tracks + KF_TRACKS - 1) / KF_TRACKS, KF_TRACKS, 0, static_cast<cudaStream_t>(stream)>>>(
+        regions, (int)T, n_tracks, states, status);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? KF_OK : fail(ctx, (int)e);
 }

@@ -1,7 +1,7 @@
 """Host-side checks of the paper's own chain (CPU only): the traffic model restated
-plainly for every partition (tile 32 x 32, halo = number of spatial stages in the
-group), the planner's choice, workspace sizes, and argument rejection on a host-only
-context."""
+plainly for every partition (tiles of 128 x 32 input, row halo = number of spatial
+stages in the group, column halo one lane of 4), the planner's choice, workspace sizes,
+and argument rejection on a host-only context."""
 import itertools
 
 import pytest
@@ -31,14 +31,15 @@ def expected_bytes(cuts, W, H, T):
     tot = 0.0
     for a, b in groups_of(cuts):
         halo = sum(1 for s in (2, 3) if a <= s <= b)
-        out = 32 - 2 * halo
-        tot += W * H * T * (in_b[a] * 32 * 32 / out ** 2 + out_b[b])
+        hc = 4 if halo else 0  # tiles of 128 x 32 input; the column halo is one lane (4 columns)
+        rf = 128 * 32 / ((128 - 2 * hc) * (32 - 2 * halo))
+        tot += W * H * T * (in_b[a] * rf + out_b[b])
         if a <= 1 <= b:  # the chunked IIR recursion (chunks of 32 frames)
             nc = -(-T // 32)
             hw = W * H
             tot += (nc - 1) * 32 * hw * in_b[a] + (nc - 1) * hw * 4        # local end states
             tot += hw * in_b[a] + (nc - 1) * hw * 4 + nc * hw * 4          # carry
-            tot += nc * hw * 4 * 32 * 32 / out ** 2                          # start states, with halo
+            tot += nc * hw * 4 * rf                                          # start states, with halo
     return tot + T * 4 * (1 + 3 * 16)
 
 
@@ -87,6 +88,8 @@ def test_argument_rejection(hctx):
     big = K.kf_pc_video(16, 40000, 40000, 1, 40000)
     assert L.kf_pc_run_group(hctx, 1, 2, K.ctypes.byref(big), 16, 40000, 16, 40000, None, 256, 1 << 40,
                              None) == K.KF_EINVAL
+    odd = K.kf_pc_video(16, 62, 32, 2, 62)  # pitch not a multiple of 4 pixels
+    assert L.kf_pc_run(hctx, 0, K.ctypes.byref(odd), None, None, 0, None) == K.KF_EINVAL
     ok = K.kf_pc_video(16, 64, 32, 2, 64)
     assert L.kf_pc_run_group(hctx, 2, 3, K.ctypes.byref(ok), 16, 64, 16, 64, None, None, 0, None) == K.KF_ESTATE
     # a group holding the IIR filter without its chunk-state workspace
