@@ -422,8 +422,8 @@ kf_status kf_pc_run_group(kf_ctx *ctx, int a, int b, const kf_pc_video *video, c
                           size_t workspace_bytes, void *stream);
 /* K6 over [T][n_tracks][3] region sums (device): states [T][n_tracks][4] (FP64, device) and
  * status [T][n_tracks] (0 not started, 1 updated, 2 predicted only). One thread per track
- * walks the frames; the x and y axes share one 2 x 2 covariance (the model is the same
- * per axis), which is the 4 x 4 filter's exact block structure. */
+ * walks the frames in FP32; the x and y axes share one 2 x 2 covariance (the model is the
+ * same per axis), which is the 4 x 4 filter's exact block structure. */
 kf_status kf_pc_kalman(kf_ctx *ctx, const int32_t *regions, int64_t T, int n_tracks, double *states, int32_t *status,
                        void *stream);
 

@@ -433,7 +433,9 @@ __global__ void pc_sums_kernel(const int32_t *slots, int T, int32_t *counts, int
 // axis and starts from the same covariance, so the x and y axes share one symmetric 2 x 2
 // covariance (P00 position, P01, P11 velocity) -- the block structure of the 4 x 4 filter.
 // The block stages KF_FRAMES frames of region sums in shared memory at a time (coalesced),
-// so the walk's dependent chain never waits on a global load.
+// so the walk's dependent chain never waits on a global load. The filter runs in FP32
+// (stored as FP64): its chain of dependent operations per frame is the kernel's whole
+// cost, and FP64 made it ten times longer on this part.
 constexpr int KF_TRACKS = 32;  // tracks per block
 constexpr int KF_FRAMES = 64;  // frames staged per round
 
@@ -444,7 +446,7 @@ __global__ void __launch_bounds__(KF_TRACKS) pc_kalman_kernel(const int32_t *reg
     const int k0 = blockIdx.x * KF_TRACKS, k = k0 + threadIdx.x;
     const int nb = min(KF_TRACKS, n - k0);  // tracks of this block
     bool started = false;
-    double px = 0, py = 0, vx = 0, vy = 0, P00 = 0, P01 = 0, P11 = 0;
+    float px = 0, py = 0, vx = 0, vy = 0, P00 = 0, P01 = 0, P11 = 0;
     for (int t0 = 0; t0 < T; t0 += KF_FRAMES) {
         const int nt = min(KF_FRAMES, T - t0);
         __syncthreads();  // the previous round's values are consumed
@@ -456,18 +458,18 @@ __global__ void __launch_bounds__(KF_TRACKS) pc_kalman_kernel(const int32_t *reg
         if (k >= n) continue;
         for (int t = 0; t < nt; ++t) {
             const int cnt = zs[t][threadIdx.x][0];
-            const double inv_c = cnt > 0 ? 1.0 / cnt : 0.0;
-            const double zx = zs[t][threadIdx.x][1] * inv_c, zy = zs[t][threadIdx.x][2] * inv_c;
+            const float inv_c = cnt > 0 ? 1.0f / (float)cnt : 0.0f;
+            const float zx = (float)zs[t][threadIdx.x][1] * inv_c, zy = (float)zs[t][threadIdx.x][2] * inv_c;
             int s;
             if (!started) {
                 if (cnt > 0) {
                     started = true;
                     px = zx;
                     py = zy;
-                    vx = vy = 0.0;
-                    P00 = KR;
-                    P01 = 0.0;
-                    P11 = KP0;
+                    vx = vy = 0.0f;
+                    P00 = (float)KR;
+                    P01 = 0.0f;
+                    P11 = (float)KP0;
                     s = 1;
                 } else {
                     s = 0;
@@ -476,20 +478,20 @@ __global__ void __launch_bounds__(KF_TRACKS) pc_kalman_kernel(const int32_t *reg
                 // predict: state by F, P by F P F' + Q with Q = q [[1/3, 1/2], [1/2, 1]]
                 px += vx;
                 py += vy;
-                const double a = P00 + 2.0 * P01 + P11 + KQ / 3.0, b = P01 + P11 + KQ / 2.0, c = P11 + KQ;
+                const float a = P00 + 2.0f * P01 + P11 + (float)(KQ / 3.0), b = P01 + P11 + (float)(KQ / 2.0), c = P11 + (float)KQ;
                 P00 = a;
                 P01 = b;
                 P11 = c;
                 if (cnt > 0) {
-                    const double inv_s = 1.0 / (P00 + KR), g0 = P00 * inv_s, g1 = P01 * inv_s;
-                    const double ex = zx - px, ey = zy - py;
+                    const float inv_s = 1.0f / (P00 + (float)KR), g0 = P00 * inv_s, g1 = P01 * inv_s;
+                    const float ex = zx - px, ey = zy - py;
                     px += g0 * ex;
                     vx += g1 * ex;
                     py += g0 * ey;
                     vy += g1 * ey;
                     P11 -= g1 * P01;
-                    P01 *= 1.0 - g0;
-                    P00 *= 1.0 - g0;
+                    P01 *= 1.0f - g0;
+                    P00 *= 1.0f - g0;
                     s = 1;
                 } else {
                     s = 2;

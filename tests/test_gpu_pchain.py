@@ -4,7 +4,7 @@ Each stage map of the unfused sequence against the FP64 oracle (Y' exact; y', G'
 within 1e-5 normwise), masks under the exemption rule (pixels whose oracle response is
 within the tolerance of the threshold may differ), counts and region sums consistent
 with the mask, all 16 partitions bit-identical to each other, ragged and degenerate
-sizes, and the Kalman filter against the oracle's on the GPU's own region sums."""
+sizes, and the Kalman filter (FP32) against the oracle's (FP64) on the GPU's own region sums."""
 import numpy as np
 import pytest
 
@@ -159,7 +159,11 @@ def test_kalman_matches_the_oracle_on_the_gpu_region_sums(dev):
     reg = regions.cpu().numpy().astype(np.int64)
     s_o, st_o = op.kalman(reg)
     np.testing.assert_array_equal(status.cpu().numpy(), st_o)
-    np.testing.assert_allclose(states.cpu().numpy(), s_o, rtol=1e-9, atol=1e-9)
+    # FP32 filter against the FP64 oracle: each step rounds at ~1e-7 of the coordinates
+    # (up to W = 160 px here, ~2e-5 px) and the stable filter carries a few steps' worth:
+    # positions within 5e-3 px, velocities within 1e-3 px/frame
+    np.testing.assert_allclose(states.cpu().numpy()[..., :2], s_o[..., :2], rtol=0, atol=5e-3)
+    np.testing.assert_allclose(states.cpu().numpy()[..., 2:], s_o[..., 2:], rtol=0, atol=1e-3)
     assert (st_o == 1).sum() > T  # the regions do see features
     # a track with gaps: drop every third frame's measurements of region 5
     reg2 = reg.copy()
@@ -168,4 +172,5 @@ def test_kalman_matches_the_oracle_on_the_gpu_region_sums(dev):
     K.kf_pc_kalman(ctx.h, r2, states, status)
     s_o2, st_o2 = op.kalman(reg2)
     np.testing.assert_array_equal(status.cpu().numpy(), st_o2)
-    np.testing.assert_allclose(states.cpu().numpy(), s_o2, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(states.cpu().numpy()[..., :2], s_o2[..., :2], rtol=0, atol=5e-3)
+    np.testing.assert_allclose(states.cpu().numpy()[..., 2:], s_o2[..., 2:], rtol=0, atol=1e-3)
