@@ -32,6 +32,7 @@ from synth import video as sv  # noqa: E402
 
 METRIC = "fused-chain Mpixel/s & HBM roofline fraction vs unfused, 800×600×1000 u8"
 UNIT = "Mpixel/s"
+E2E_CHUNK = 100  # frames per chunk of the pipelined host-to-host call
 SPEC = sv.HSDV_800x600x1000
 WORKLOAD = "Harris 8-stage chain, 1000 frames x 800 rows x 600 cols u8, 64 blobs + 32 patches, seed 3"
 
@@ -370,20 +371,24 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                      max(3, args.steps // 4), 1)
     del ws, ws16
 
-    # end to end through the public call: pinned host frames in; mask, counts and tracks out
-    mask_h = torch.empty_like(frames_pin, device="cpu").pin_memory()
-    outs_d = (counts, n_pts, idx, uu, vv, st)
-    outs_h = [torch.empty_like(t, device="cpu").pin_memory() for t in outs_d]
+    # end to end through the public call: pinned host frames in; mask, counts and tracks
+    # out. kf_track_host runs the step in chunks of E2E_CHUNK frames with the copy in of
+    # one chunk, the hot path of the previous one and the copy out of the one before on
+    # three streams.
+    host = dict(frames=frames_pin, mask=torch.empty_like(frames_pin).pin_memory(),
+                counts=torch.empty_like(counts, device="cpu").pin_memory(),
+                n_points=torch.empty_like(n_pts, device="cpu").pin_memory(),
+                idx=torch.empty_like(idx, device="cpu").pin_memory(), u=torch.empty_like(uu, device="cpu").pin_memory(),
+                v=torch.empty_like(vv, device="cpu").pin_memory(), status=torch.empty_like(st, device="cpu").pin_memory())
+    devb = dict(frames=frames, mask=mask, counts=counts, n_points=n_pts, idx=idx, u=uu, v=vv, status=st)
 
     def e2e_step():
-        frames.copy_(frames_pin, non_blocking=True)
-        step()
-        mask_h.copy_(mask, non_blocking=True)
-        for hst, d in zip(outs_h, outs_d):
-            hst.copy_(d, non_blocking=True)
+        K.kf_track_host(ctx.h, host, devb, W, KP, ws_track, chunk=E2E_CHUNK, stream=stream)
     ms_e2e = timed(e2e_step, max(3, args.steps // 2), 1)
+    e2e_same = bool(torch.equal(host["mask"], mask.cpu()) and torch.equal(host["idx"], idx.cpu())
+                    and torch.equal(host["u"], uu.cpu()))
     h2d = frames_pin.numel()
-    d2h = mask_h.numel() + sum(t.numel() * t.element_size() for t in outs_h)
+    d2h = sum(t.numel() * t.element_size() for k, t in host.items() if k != "frames")
     tracked = int(n_pts.sum())
 
     line = {
@@ -420,7 +425,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "unfused_f16": {"value": world * px / (ms_unf16 / 1000) / 1e6, "ms_per_step": ms_unf16,
                         "hbm_frac": 50 * px / (ms_unf16 / 1000) / 1e9 / hbm_peak},
         "e2e": {"value": world * px / (ms_e2e / 1000) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e},
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e, "chunk_frames": E2E_CHUNK,
+                "call": "kf_track_host (copy in, hot path, copy out overlapped on three streams)",
+                "results_equal_device_step": e2e_same},
         "gpu_launches": sum(k["launches"] for k in kernels.values()),  # counted by the library's event pairs
         "device_error": dev_err,
         "clocks": clocks,
@@ -524,6 +531,103 @@ def run_pchain(args):
         out["sizes"].append(row)
         del fr, mask
         torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
+ST_BETAS = (4096, 16384, 65536)
+ST_SIDES = (8, 16, 32, 64, 128)
+
+
+def run_stbox(args):
+    """Spatio-temporal boxes against Eq. 6: the group K1, Kt (temporal binomial, reach n),
+    K3, K4, K5 on 1024 x 1024 x 1000 RGBA video, run over boxes x * x * t. For each output
+    volume beta = x^2 t the sides x in ST_SIDES with t = beta / x^2 are timed (CUDA events,
+    inputs larger than L2), next to Sec. VI-D's bytes for the tiling, Eq. 3's data
+    utilisation and Eq. 6's optimum; then a free sweep over (x, t) for the best box."""
+    import torch
+    from paper_1509_04394_gb300 import build as kbuild
+    from paper_1509_04394_gb300 import kfuse as K
+    kbuild.build()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    ctx = K.Context(0, harris=False)
+    hbm_peak, peak_kind = peaks()
+    T, H, W = args.pc_frames, args.pc_size or 1024, args.pc_size or 1024
+    fr = pchain_video(dev, H, W, T, 40)
+    mask = torch.zeros((T, H, W), dtype=torch.uint8, device=dev)
+    counts = torch.zeros(T, dtype=torch.int32, device=dev)
+    px = T * H * W
+    smem_cap = 227 * 1024
+
+    def time_box(n, x, t):
+        run = lambda: K.kf_st_run(ctx.h, fr, W, mask, counts, n, x, t, stream)  # noqa: E731
+        if args.pc_once:
+            run()
+            torch.cuda.synchronize()
+            return None
+        for _ in range(args.warmup):
+            run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    def row(n, x, t):
+        ms = time_box(n, x, t)
+        model, clipped = K.kf_st_traffic(W, H, T, x, t, n)
+        r = {"x": x, "t": t, "smem_bytes": K.kf_st_smem_bytes(n, x), "model_bytes_per_px": model / px,
+             "clipped_bytes_per_px": clipped / px, "du_eq3": x * x * t / ((x + 4) ** 2 * (t + n))}
+        if ms is not None:
+            r.update({"ms": ms, "value": px / (ms / 1000) / 1e6, "hbm_frac": clipped / (ms / 1000) / 1e9 / hbm_peak})
+        return r
+
+    out = {"workload": f"spatio-temporal group (gray, temporal binomial, 3x3 Gaussian, Sobel, threshold) on "
+                       f"{W}x{H}x{T} RGBA (64 generated frames, cycled)", "unit": "Mpixel/s",
+           "peak_hbm_gbs": hbm_peak, "peak_kind": peak_kind, "l2": "inputs larger than L2 (4.2 GB frames)",
+           "reaches": []}
+    first = {}
+
+    def same_as_first(n):  # every box shape gives the same masks and counts (or it is a bug)
+        if args.pc_once:
+            return None
+        if n not in first:
+            first[n] = (mask.clone(), counts.clone())
+            return True
+        return bool(torch.equal(first[n][0], mask) and torch.equal(first[n][1], counts))
+
+    for n in (2, 4):
+        rec = {"n": n, "dx": 2, "dt": n, "fixed_beta": [], "sweep": []}
+        for beta in ST_BETAS:
+            x6, t6 = K.kf_st_box_eq6(beta, n)
+            rows = []
+            for x in ST_SIDES:
+                t = beta // (x * x)
+                if t < 1 or K.kf_st_smem_bytes(n, x) > smem_cap:
+                    continue
+                rows.append(row(n, x, t))
+                rows[-1]["identical_to_first_box"] = same_as_first(n)
+            timed_rows = [r for r in rows if "ms" in r]
+            best = min(timed_rows, key=lambda r: r["ms"]) if timed_rows else None
+            least = min(rows, key=lambda r: r["clipped_bytes_per_px"])
+            rec["fixed_beta"].append({"beta": beta, "eq6_x": x6, "eq6_t": t6, "boxes": rows,
+                                      "fastest_x": best["x"] if best else None,
+                                      "least_traffic_x": least["x"]})
+        for x in (16, 32, 48, 64, 96):
+            if K.kf_st_smem_bytes(n, x) > smem_cap:
+                continue
+            for t in (4, 8, 16, 32, 64):
+                rec["sweep"].append(row(n, x, t))
+                rec["sweep"][-1]["identical_to_first_box"] = same_as_first(n)
+        timed = [r for r in rec["sweep"] if "ms" in r]
+        if timed:
+            b = min(timed, key=lambda r: r["ms"])
+            rec["best"] = {"x": b["x"], "t": b["t"], "ms": b["ms"], "value": b["value"], "hbm_frac": b["hbm_frac"]}
+        out["reaches"].append(rec)
+        first.pop(n, None)
     print(json.dumps(out), flush=True)
 
 
@@ -672,6 +776,8 @@ def main():
     ap.add_argument("--pc-frames", type=int, default=1000, help="frames per size (--pchain)")
     ap.add_argument("--pc-size", type=int, default=0, help="one square size instead of the three (--pchain)")
     ap.add_argument("--pc-once", action="store_true", help="run each partition once, untimed (profiler case)")
+    ap.add_argument("--stbox", action="store_true", help="spatio-temporal boxes against Eq. 6 (uses --pc-frames, "
+                    "--pc-size, --pc-once)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -679,6 +785,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.pchain:
         run_pchain(args)
+    elif args.stbox:
+        run_stbox(args)
     elif args.costmodel:
         run_costmodel(args)
     elif args.batch48:

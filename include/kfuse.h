@@ -232,6 +232,22 @@ kf_status kf_track_workspace_bytes(const kf_ctx *ctx, int64_t W, int64_t H, int6
  * >= kf_track_workspace_bytes, 256-byte aligned. W*H must be below 2^31. */
 kf_status kf_track(kf_ctx *ctx, const kf_video *video, const kf_corners *out, const kf_tracks *tracks,
                    void *workspace, size_t workspace_bytes, void *stream);
+/* kf_track from host memory to host memory, pipelined (the paper has no counterpart; a
+ * serving path for video that arrives in host memory). The frames go in and the results
+ * come back in chunks of `chunk` frames on the context's own streams (one copy-in, two
+ * compute used in turn, one copy-out): the copy in of chunk k, the hot path over chunks
+ * k-1 and k-2 and the copies out of earlier chunks overlap. Chunks below ~100 frames of
+ * 800x600 leave the SMs partly idle (a chunk's fused chain has 22 warps of work per
+ * frame). host_video / host_out / host_tracks: host buffers of the same shapes and
+ * pitches as the device ones (page-locked, e.g. cudaHostAlloc, for the copies to be
+ * asynchronous; pageable memory still gives correct results, without overlap). video /
+ * out / tracks / workspace: device buffers as for kf_track (video holds all T frames; LK
+ * of a chunk's first frame reads the previous chunk's last). Asynchronous: `stream` waits
+ * for the last copy out, and the copies start after the work queued on `stream` before
+ * the call; the host buffers must stay valid until then. */
+kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corners *host_out,
+                        const kf_tracks *host_tracks, const kf_video *video, const kf_corners *out,
+                        const kf_tracks *tracks, void *workspace, size_t workspace_bytes, int64_t chunk, void *stream);
 
 /* ------------------------------------------------------------------ batches */
 /* Many independent videos of different sizes and lengths through the fully fused chain
@@ -426,6 +442,42 @@ kf_status kf_pc_run_group(kf_ctx *ctx, int a, int b, const kf_pc_video *video, c
  * same per axis), which is the 4 x 4 filter's exact block structure. */
 kf_status kf_pc_kalman(kf_ctx *ctx, const int32_t *regions, int64_t T, int n_tracks, double *states, int32_t *status,
                        void *stream);
+
+/* ------------------------------------------------------------------ spatio-temporal boxes */
+/* A fused group with a temporal reach, run over boxes of x * x pixels by t frames: the
+ * input box of Alg. 2 (Sec. VI-C), the data utilisation of Eq. 3 and the box shape of
+ * Eq. 5 / Eq. 6 (Sec. VI-E). The paper gives no stage with a finite temporal reach; the
+ * group is the paper's chain with its IIR filter replaced by a finite one, over the same
+ * RGBA input (kf_pc_video):
+ *   K1  g = 77 R + 150 G + 29 B
+ *   Kt  z_t = sum_{k=0..n} C(n, k) g_{max(t-n+k, 0)}, n in {1, 2, 4} (temporal reach n)
+ *   K3  G = sum w(dy) w(dx) z(clamp(p + d)), w = [1 2 1]
+ *   K4  M = |Sobel_x G| + |Sobel_y G|, indices clamped on G
+ *   K5  mask = M > 261120 * 2^n (u8 0/1), i.e. M / (65280 * 2^n * 16) > 0.25; per frame
+ *       the mask count
+ * all in exact 32-bit integers. One-sided reaches dx = 2 (spatial, both sides), dt = n
+ * (temporal, past side). */
+/* Shared memory of one box: RGBA staging of one frame ((x + 8) x (x + 4) x 4 bytes), a
+ * ring of n + 1 16-bit gray planes of the same extent, the smoothed plane (x + 2) x
+ * (x + 4) x 4 bytes. Boxes above 227 KB are rejected by kf_st_run. x a multiple of 8. */
+kf_status kf_st_smem_bytes(int n, int x, size_t *bytes);
+/* Sec. VI-D's fused transfer for boxes x * x * t: model_bytes = B ((x + 4)^2 (t + n) * 4 +
+ * x^2 t) with B = W H T / (x^2 t) (halos never clipped); clipped_bytes = the input
+ * extents of the tiling's boxes clipped to the volume (4 bytes a pixel) + W H T mask
+ * bytes. Either pointer may be NULL. */
+kf_status kf_st_traffic(int64_t W, int64_t H, int64_t T, int x, int t, int n, double *model_bytes,
+                        double *clipped_bytes);
+/* Eq. 6 for this group's reaches (dx = 2, dt = n) and output volume beta = x^2 t:
+ * x = (2 beta dx / dt)^(1/3), t = beta / x^2. */
+kf_status kf_st_box_eq6(double beta, int n, double *x, double *t);
+/* The group over the whole video in boxes of x * x * t (x a multiple of 8, t >= 1), one
+ * block per box, frames streamed through shared memory in time order (the temporal halo
+ * stays on chip for the box). mask: device, T x H x mask_pitch bytes (16-byte aligned,
+ * mask_pitch >= W, a multiple of 4; the pitch padding is not written); counts: device
+ * [T], written. A copy wait that runs out records KF_DEVERR_TIMEOUT. Asynchronous on
+ * `stream`. */
+kf_status kf_st_run(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64_t mask_pitch, int32_t *counts, int n,
+                    int x, int t, void *stream);
 
 /* ------------------------------------------------------------------ kernel timing */
 /* Per-kernel device time of the library's own launches (instrumentation; the paper

@@ -389,6 +389,17 @@ kf_status kf_create(int device, kf_ctx **out)
 kf_status kf_destroy(kf_ctx *ctx)
 {
     if (ctx) kf::costmodel_free(ctx);
+    if (ctx && ctx->s_in) {
+        cudaSetDevice(ctx->device);
+        cudaStreamDestroy(ctx->s_in);
+        cudaStreamDestroy(ctx->s_out);
+        for (int i = 0; i < kf_ctx::N_RING; ++i) cudaStreamDestroy(ctx->s_comp[i]);
+        for (int i = 0; i < kf_ctx::N_RING; ++i) {
+            cudaEventDestroy(ctx->ev_in[i]);
+            cudaEventDestroy(ctx->ev_comp[i]);
+        }
+        cudaEventDestroy(ctx->ev_edge);
+    }
     if (ctx && (!ctx->timed.empty() || !ctx->spare_events.empty())) {
         cudaSetDevice(ctx->device);
         for (const kf_ctx::Timed &t : ctx->timed) {
@@ -632,8 +643,10 @@ kf_status kf_track_workspace_bytes(const kf_ctx *ctx, int64_t W, int64_t H, int6
     return KF_OK;
 }
 
-kf_status kf_track(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf_tracks *tr, void *ws, size_t ws_bytes,
-                   void *stream)
+namespace {
+
+kf_status check_track_args(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf_tracks *tr, void *ws,
+                           size_t ws_bytes)
 {
     if (!ctx) return KF_EINVAL;
     if (ctx->device < 0) return KF_ESTATE;
@@ -653,27 +666,37 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf
     kf_track_workspace_bytes(ctx, v->W, v->H, v->T, &need);
     if (!ws || !aligned(ws, 256)) return KF_EINVAL;
     if (ws_bytes < need) return KF_ENOMEM;
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(ctx, e);
-    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return KF_OK;
+}
+
+// The hot path over frames [t0, t1) of a video whose frames [0, t1) are on the device
+// (LK of frame t0 reads frame t0 - 1): the chain with corner lists over the frame range,
+// then selection and LK from frame t0 on.
+kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf_tracks *tr, void *ws, int64_t t0,
+                      int64_t t1, cudaStream_t s)
+{
+    const int64_t n = t1 - t0;
+    if (n <= 0) return KF_OK;
     int *cand_count = static_cast<int *>(ws);
     auto *cand = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + round_up(4 * v->T, 256));
     const int64_t cap = kf::cand_capacity(v->W, v->H);
-    e = cudaMemsetAsync(cand_count, 0, sizeof(int) * (size_t)v->T, s);
+    cudaError_t e = cudaMemsetAsync(cand_count + t0, 0, sizeof(int) * (size_t)n, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     // the fusable set of the chain: one fused kernel, which also lists each frame's corners
+    const int64_t fstride = v->pitch * v->H, mstride = o->mask_pitch * v->H;
     kf_map fin{}, fout{};
-    fin.plane[0] = const_cast<uint8_t *>(v->frames);
+    fin.plane[0] = const_cast<uint8_t *>(v->frames) + t0 * fstride;
     fin.channels = 1;
     fin.dtype = KF_DT_U8;
     fin.pitch = v->pitch;
-    fin.frame_stride = v->pitch * v->H;
-    fout.plane[0] = o->mask;
+    fin.frame_stride = fstride;
+    fout.plane[0] = o->mask + t0 * mstride;
     fout.channels = 1;
     fout.dtype = KF_DT_U8;
     fout.pitch = o->mask_pitch;
-    fout.frame_stride = o->mask_pitch * v->H;
-    kf_status st = launch_group(ctx, 1, kf::NSTAGES, fin, fout, v->W, v->H, v->T, o->counts, s, cand, cand_count, cap);
+    fout.frame_stride = mstride;
+    kf_status st = launch_group(ctx, 1, kf::NSTAGES, fin, fout, v->W, v->H, n, o->counts + t0, s, cand + t0 * cap,
+                                cand_count + t0, cap);
     if (st != KF_OK) return st;
     // the tracking set, after the kernel-to-kernel dependency
     kf::TrackVideo tv{};
@@ -691,19 +714,108 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf
     tv.u = tr->u;
     tv.v = tr->v;
     tv.frame_begin = 0;
+    tv.first_frame = t0;
     {
         TimedLaunch tl(ctx, KF_KT_SELECT, s);
-        const int r = kf::launch_select(tv, nullptr, 1, v->T, tr->K, stream);
+        const int r = kf::launch_select(tv, nullptr, 1, n, tr->K, s);
         if (r) return cuda_fail(ctx, (cudaError_t)r);
         tl.done();
     }
     {
         TimedLaunch tl(ctx, KF_KT_LK, s);
-        const int r = kf::launch_lk(tv, nullptr, 1, v->T, tr->K, stream);
+        const int r = kf::launch_lk(tv, nullptr, 1, n, tr->K, s);
         if (r) return cuda_fail(ctx, (cudaError_t)r);
         tl.done();
     }
     return KF_OK;
+}
+
+// the context's copy streams and event ring (created on first use)
+kf_status copy_streams(kf_ctx *c)
+{
+    if (c->s_in) return KF_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking);
+    for (int i = 0; e == cudaSuccess && i < kf_ctx::N_RING; ++i) {
+        e = cudaStreamCreateWithFlags(&c->s_comp[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_edge, cudaEventDisableTiming);
+    return e == cudaSuccess ? KF_OK : cuda_fail(c, e);
+}
+
+}  // namespace
+
+kf_status kf_track(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf_tracks *tr, void *ws, size_t ws_bytes,
+                   void *stream)
+{
+    kf_status st = check_track_args(ctx, v, o, tr, ws, ws_bytes);
+    if (st != KF_OK || v->T == 0) return st;
+    const cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    return track_range(ctx, v, o, tr, ws, 0, v->T, static_cast<cudaStream_t>(stream));
+}
+
+kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corners *host_out,
+                        const kf_tracks *host_tracks, const kf_video *video, const kf_corners *out,
+                        const kf_tracks *tracks, void *workspace, size_t workspace_bytes, int64_t chunk, void *stream)
+{
+    kf_status st = check_track_args(ctx, video, out, tracks, workspace, workspace_bytes);
+    if (st != KF_OK) return st;
+    if (!host_video || !host_out || !host_tracks || chunk < 1) return KF_EINVAL;
+    const int64_t T = video->T, H = video->H, K = tracks->K;
+    if (host_video->W != video->W || host_video->H != H || host_video->T != T || host_video->pitch != video->pitch ||
+        host_out->mask_pitch != out->mask_pitch || host_tracks->K != K)
+        return KF_EINVAL;
+    if (T == 0) return KF_OK;
+    if (!host_video->frames || !host_out->mask || !host_out->counts || !host_tracks->n_points || !host_tracks->idx ||
+        !host_tracks->u || !host_tracks->v || !host_tracks->status)
+        return KF_EINVAL;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    if ((st = copy_streams(ctx)) != KF_OK) return st;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the internal streams start after what the caller queued before this call
+    e = cudaEventRecord(ctx->ev_edge, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_in, ctx->ev_edge, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ctx->ev_edge, 0);
+    for (int i = 0; e == cudaSuccess && i < kf_ctx::N_RING; ++i) e = cudaStreamWaitEvent(ctx->s_comp[i], ctx->ev_edge, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    const int64_t fstride = video->pitch * H, mstride = out->mask_pitch * H;
+    for (int64_t t0 = 0, k = 0; t0 < T && e == cudaSuccess; t0 += chunk, ++k) {
+        const int64_t t1 = t0 + chunk < T ? t0 + chunk : T, n = t1 - t0;
+        const int r = (int)(k % kf_ctx::N_RING);
+        cudaEvent_t ein = ctx->ev_in[r], ecomp = ctx->ev_comp[r];
+        const cudaStream_t cs = ctx->s_comp[r];
+        // copy in (s_in), compute (two streams in turn), copy out (s_out). Chunks touch
+        // disjoint frames of every buffer, and a chunk's tracking reads only input frames
+        // copied in before it, so consecutive chunks' kernels may overlap: the next chunk's
+        // launch fills the SMs while the previous one drains its last wave.
+        e = cudaMemcpyAsync(const_cast<uint8_t *>(video->frames) + t0 * fstride, host_video->frames + t0 * fstride,
+                            (size_t)(n * fstride), cudaMemcpyHostToDevice, ctx->s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ein, ctx->s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ein, 0);
+        if (e != cudaSuccess) break;
+        st = track_range(ctx, video, out, tracks, workspace, t0, t1, cs);
+        if (st != KF_OK) return st;
+        e = cudaEventRecord(ecomp, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ecomp, 0);
+        auto d2h = [&](void *dst, const void *src, size_t bytes) {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s_out);
+        };
+        d2h(host_out->mask + t0 * mstride, out->mask + t0 * mstride, (size_t)(n * mstride));
+        d2h(host_out->counts + t0, out->counts + t0, sizeof(int32_t) * (size_t)n);
+        d2h(host_tracks->n_points + t0, tracks->n_points + t0, sizeof(int32_t) * (size_t)n);
+        d2h(host_tracks->idx + t0 * K, tracks->idx + t0 * K, sizeof(int32_t) * (size_t)(n * K));
+        d2h(host_tracks->u + t0 * K, tracks->u + t0 * K, sizeof(float) * (size_t)(n * K));
+        d2h(host_tracks->v + t0 * K, tracks->v + t0 * K, sizeof(float) * (size_t)(n * K));
+        d2h(host_tracks->status + t0 * K, tracks->status + t0 * K, sizeof(int32_t) * (size_t)(n * K));
+    }
+    // the caller's stream ends after the last copy out
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_edge, ctx->s_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_edge, 0);
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e);
 }
 
 kf_status kf_set_kernel_timing(kf_ctx *ctx, int on)

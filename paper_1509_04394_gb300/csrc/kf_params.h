@@ -91,6 +91,7 @@ struct TrackVideo {
     int32_t *n_points, *idx, *status;
     float *u, *v;
     int64_t frame_begin;
+    int64_t first_frame;  // one video processed from this frame on (kernel frame 0 = first_frame)
 };
 
 // Strip geometry of a group with accumulated horizontal radius rxt: input strips start

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) select_kernel(const TrackVideo
     __shared__ unsigned nsel;
     __shared__ int digit_s, rank_s, count_s;
     const TrackVideo &vd = video_of(one, vids, n_videos, blockIdx.x);
-    const int frame = (int)(blockIdx.x - vd.frame_begin);
+    const int frame = (int)(blockIdx.x - vd.frame_begin + vd.first_frame);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cap = vd.cand_cap;
     int32_t *n_points = vd.n_points, *idx_out = vd.idx;
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(LK_THREADS) lk_kernel(const TrackVideo one, co
         i = (int)(gid % K);
     }
     const TrackVideo &vd = video_of(one, vids, n_videos, min(gframe, total_frames - 1));
-    const int frame = (int)(gframe - vd.frame_begin);
+    const int frame = (int)(gframe - vd.frame_begin + vd.first_frame);
     const bool valid = gframe < total_frames && frame > 0 && i < vd.n_points[frame];
     if (!__any_sync(FULLM, valid)) return;  // warp-uniform
     const int W = vd.W, H = vd.H;
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(LK_THREADS) lk_kernel(const TrackVideo one, co
         const long long oq = __shfl_sync(FULLM, (long long)o, src);
         const TrackVideo &vq = video_of(one, vids, n_videos, gf);
         float s[5];
-        lk_sums_clamped(vq, (int)(gf - vq.frame_begin), q, s);
+        lk_sums_clamped(vq, (int)(gf - vq.frame_begin + vq.first_frame), q, s);
         if ((lane & 15) == 0 && (lane < 16 || has_b)) store_step(vq, oq, s[0], s[1], s[2], s[3], s[4]);
     }
 }

@@ -94,6 +94,7 @@ def _lib():
             "kf_run_static": (i32, [P, u32, P, P, P]),
             "kf_track_workspace_bytes": (i32, [P, i64, i64, i64, P]),
             "kf_track": (i32, [P, P, P, P, P, ctypes.c_size_t, P]),
+            "kf_track_host": (i32, [P, P, P, P, P, P, P, P, ctypes.c_size_t, i64, P]),
             "kf_batch_workspace_bytes": (i32, [P, P, i32, i32, P]),
             "kf_batch_create": (i32, [P, P, P, P, i32, P, ctypes.c_size_t, P]),
             "kf_batch_run": (i32, [P, P]),
@@ -120,6 +121,10 @@ def _lib():
             "kf_pc_group_workspace_bytes": (i32, [P, i32, i32, i64, i64, i64, P]),
             "kf_pc_kalman": (i32, [P, P, i64, i32, P, P, P]),
             "kf_kernel_times": (i32, [P, P, P]),
+            "kf_st_smem_bytes": (i32, [i32, i32, P]),
+            "kf_st_traffic": (i32, [i64, i64, i64, i32, i32, i32, P, P]),
+            "kf_st_box_eq6": (i32, [dbl, i32, P, P]),
+            "kf_st_run": (i32, [P, P, P, i64, P, i32, i32, i32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -139,7 +144,8 @@ def exported_symbols() -> list[str]:
             "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups",
             "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_grad", "kf_costmodel_get",
             "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times", "kf_pc_traffic", "kf_pc_plan",
-            "kf_pc_workspace_bytes", "kf_pc_run", "kf_pc_run_group", "kf_pc_kalman", "kf_pc_group_workspace_bytes"]
+            "kf_pc_workspace_bytes", "kf_pc_run", "kf_pc_run_group", "kf_pc_kalman", "kf_pc_group_workspace_bytes",
+            "kf_track_host", "kf_st_smem_bytes", "kf_st_traffic", "kf_st_box_eq6", "kf_st_run"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -286,6 +292,26 @@ def kf_track(ctx, frames, W: int, mask, counts, K: int, n_points, idx, u, v, sta
     ws_bytes = workspace.numel() * workspace.element_size()
     _check("kf_track", _lib().kf_track(ctx, ctypes.byref(vid), ctypes.byref(o), ctypes.byref(tr), workspace.data_ptr(),
                                        ws_bytes, _stream(stream)), ctx)
+
+
+def kf_track_host(ctx, host, dev, W: int, K: int, workspace, chunk: int = 100, stream=None) -> None:
+    """kf_track from host tensors to host tensors, pipelined in chunks of `chunk` frames.
+    host, dev: dicts of tensors (host: pinned CPU, dev: CUDA) with keys frames [T, H, P]
+    u8, mask [T, H, MP] u8, counts [T] i32, n_points [T] i32, idx / status [T, K] i32,
+    u / v [T, K] f32."""
+    def structs(d):
+        T, H, P = d["frames"].shape
+        vid = kf_video(d["frames"].data_ptr(), int(W), int(H), int(T), int(P))
+        o = kf_corners(d["mask"].data_ptr(), int(d["mask"].shape[2]), d["counts"].data_ptr())
+        tr = kf_tracks(int(K), d["n_points"].data_ptr(), d["idx"].data_ptr(), d["u"].data_ptr(), d["v"].data_ptr(),
+                       d["status"].data_ptr())
+        return vid, o, tr
+    hv, ho, ht = structs(host)
+    dv, do, dt = structs(dev)
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("kf_track_host", _lib().kf_track_host(ctx, ctypes.byref(hv), ctypes.byref(ho), ctypes.byref(ht),
+                                                 ctypes.byref(dv), ctypes.byref(do), ctypes.byref(dt),
+                                                 workspace.data_ptr(), ws_bytes, int(chunk), _stream(stream)), ctx)
 
 
 def _videos(frames_list, W_list):
@@ -632,3 +658,34 @@ def kf_pc_kalman(ctx, regions, states, status, stream=None) -> None:
     T, N, _ = regions.shape
     _check("kf_pc_kalman", _lib().kf_pc_kalman(ctx, regions.data_ptr(), int(T), int(N), states.data_ptr(),
                                                status.data_ptr(), _stream(stream)), ctx)
+
+
+# ---------------------------------------------------------------- spatio-temporal boxes
+ST_TAPS = (1, 2, 4)
+
+
+def kf_st_smem_bytes(n: int, x: int) -> int:
+    b = ctypes.c_size_t()
+    _check("kf_st_smem_bytes", _lib().kf_st_smem_bytes(int(n), int(x), ctypes.byref(b)))
+    return b.value
+
+
+def kf_st_traffic(W: int, H: int, T: int, x: int, t: int, n: int) -> tuple[float, float]:
+    """(model bytes, clipped bytes) of the box tiling."""
+    m, c = ctypes.c_double(), ctypes.c_double()
+    _check("kf_st_traffic", _lib().kf_st_traffic(int(W), int(H), int(T), int(x), int(t), int(n), ctypes.byref(m),
+                                                 ctypes.byref(c)))
+    return m.value, c.value
+
+
+def kf_st_box_eq6(beta: float, n: int) -> tuple[float, float]:
+    x, t = ctypes.c_double(), ctypes.c_double()
+    _check("kf_st_box_eq6", _lib().kf_st_box_eq6(float(beta), int(n), ctypes.byref(x), ctypes.byref(t)))
+    return x.value, t.value
+
+
+def kf_st_run(ctx, frames, W: int, mask, counts, n: int, x: int, t: int, stream=None) -> None:
+    """frames [T, H, pitch, 4] u8 RGBA; mask [T, H, mask_pitch] u8; counts [T] int32 (CUDA)."""
+    v = _pc_video(frames, W)
+    _check("kf_st_run", _lib().kf_st_run(ctx, ctypes.byref(v), mask.data_ptr(), int(mask.shape[2]), counts.data_ptr(),
+                                         int(n), int(x), int(t), _stream(stream)), ctx)

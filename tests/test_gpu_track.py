@@ -182,3 +182,38 @@ def test_kernel_timing_counts_every_launch(dev):
     K.kf_set_kernel_timing(ctx.h, False)
     K.kf_track(ctx.h, frames, 160, mask, counts, 16, n, idx, u, v, st, ws)
     assert all(c == 0 for c, _ in K.kf_kernel_times(ctx.h).values())
+
+
+@pytest.mark.parametrize("chunk", [1, 3, 7, 100])
+def test_host_pipelined_call_equals_kf_track(dev, chunk):
+    """kf_track_host (host frames in, host results out, chunks overlapped on copy
+    streams) gives what kf_track gives, bit for bit, in host and device buffers."""
+    T, H, W, Kp = 9, 80, 150, 32
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=8, n_blobs=8, n_patches=6), pitch=sv.pitch_for(W))
+    ref = run_track(dev, fr, W, Kp)
+    ctx = K.Context(0)
+    P = fr.shape[2]
+
+    def bufs(device, pin):
+        d = dict(frames=torch.zeros((T, H, P), dtype=torch.uint8, device=device),
+                 mask=torch.full((T, H, P), 5, dtype=torch.uint8, device=device),
+                 counts=torch.full((T,), -1, dtype=torch.int32, device=device),
+                 n_points=torch.full((T,), -1, dtype=torch.int32, device=device),
+                 idx=torch.full((T, Kp), -1, dtype=torch.int32, device=device),
+                 u=torch.zeros((T, Kp), dtype=torch.float32, device=device),
+                 v=torch.zeros((T, Kp), dtype=torch.float32, device=device),
+                 status=torch.full((T, Kp), -1, dtype=torch.int32, device=device))
+        return {k: t.pin_memory() for k, t in d.items()} if pin else d
+    host, devb = bufs("cpu", True), bufs(dev, False)
+    host["frames"].copy_(torch.from_numpy(fr))
+    ws = torch.empty(K.kf_track_workspace_bytes(ctx.h, W, H, T), dtype=torch.uint8, device=dev)
+    K.kf_track_host(ctx.h, host, devb, W, Kp, ws, chunk=chunk)
+    torch.cuda.synchronize()
+    assert K.kf_device_error(ctx.h) == 0
+    names = dict(mask="mask", counts="counts", n_points="n", idx="idx", u="u", v="v", status="st")
+    for k, r in names.items():
+        got, exp = host[k].numpy(), ref[r]
+        if k == "mask":  # the pitch padding is not written by either call
+            got, exp = got[..., :W], exp[..., :W]
+        assert np.array_equal(got, exp), k
+        assert np.array_equal(host[k].numpy(), devb[k].cpu().numpy()), k

@@ -1,0 +1,46 @@
+"""Host side of the spatio-temporal box calls against the reference (CPU only; the
+library loads without a GPU): Sec. VI-D's box traffic with and without clipping, Eq. 6
+for the group's reaches, shared-memory feasibility and argument checks."""
+import pytest
+
+from oracle import partition as opart
+from oracle import stbox as ost
+from paper_1509_04394_gb300 import build as kbuild
+from paper_1509_04394_gb300 import kfuse as K
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    kbuild.build()
+
+
+@pytest.mark.parametrize("W,H,T,x,t,n", [(1024, 1024, 1000, 32, 16, 2), (800, 600, 97, 64, 5, 4), (13, 9, 7, 8, 3, 1),
+                                         (256, 256, 1000, 16, 64, 2)])
+def test_traffic_equals_the_reference(W, H, T, x, t, n):
+    model, clipped = K.kf_st_traffic(W, H, T, x, t, n)
+    assert model == pytest.approx(ost.box_model_bytes(W, H, T, x, t, n), rel=1e-12)
+    assert clipped == 4 * ost.box_exact_reads(W, H, T, x, t, n) + W * H * T
+
+
+@pytest.mark.parametrize("beta", [4096.0, 16384.0, 65536.0, 1e6])
+@pytest.mark.parametrize("n", ost.TAPS)
+def test_eq6_equals_the_reference(beta, n):
+    x, t = K.kf_st_box_eq6(beta, n)
+    xr, tr = opart.eq6_box(beta, ost.DX, n)
+    assert x == pytest.approx(xr, rel=1e-12) and t == pytest.approx(tr, rel=1e-12)
+
+
+def test_smem_grows_with_the_box_and_the_ring():
+    for n in ost.TAPS:
+        b = [K.kf_st_smem_bytes(n, x) for x in (8, 16, 32, 64)]
+        assert b == sorted(b)
+        # staging + (n + 1) gray planes + the smoothed plane, each at least its raw size
+        x = 64
+        assert b[3] >= (x + 8) * (x + 4) * (4 + 2 * (n + 1)) + (x + 2) * (x + 4) * 4
+    assert K.kf_st_smem_bytes(4, 64) > K.kf_st_smem_bytes(2, 64) > K.kf_st_smem_bytes(1, 64)
+
+
+@pytest.mark.parametrize("n,x", [(3, 16), (2, 12), (2, 4), (0, 8)])
+def test_bad_arguments_are_rejected(n, x):
+    with pytest.raises(K.KfuseError):
+        K.kf_st_smem_bytes(n, x)
