@@ -373,22 +373,34 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # end to end through the public call: pinned host frames in; mask, counts and tracks
     # out. kf_track_host runs the step in chunks of E2E_CHUNK frames with the copy in of
-    # one chunk, the hot path of the previous one and the copy out of the one before on
-    # three streams.
-    host = dict(frames=frames_pin, mask=torch.empty_like(frames_pin).pin_memory(),
+    # one chunk, the hot path of the previous ones and the copy out of earlier ones on
+    # separate streams. The headline delivers the mask bit-packed (stored by the device
+    # straight into the pinned host buffer); the byte-mask form is reported beside it.
+    S = ((W * H + 7) // 8 + 15) // 16 * 16
+    host = dict(frames=frames_pin, mask=torch.empty((T, S), dtype=torch.uint8).pin_memory(),
                 counts=torch.empty_like(counts, device="cpu").pin_memory(),
                 n_points=torch.empty_like(n_pts, device="cpu").pin_memory(),
                 idx=torch.empty_like(idx, device="cpu").pin_memory(), u=torch.empty_like(uu, device="cpu").pin_memory(),
                 v=torch.empty_like(vv, device="cpu").pin_memory(), status=torch.empty_like(st, device="cpu").pin_memory())
+    host_b = dict(host, mask=torch.empty_like(frames_pin).pin_memory())
     devb = dict(frames=frames, mask=mask, counts=counts, n_points=n_pts, idx=idx, u=uu, v=vv, status=st)
 
     def e2e_step():
-        K.kf_track_host(ctx.h, host, devb, W, KP, ws_track, chunk=E2E_CHUNK, stream=stream)
+        K.kf_track_host(ctx.h, host, devb, W, KP, ws_track, chunk=E2E_CHUNK, stream=stream, mask_format=K.KF_MASK_BITS)
+
+    def e2e_bytes_step():
+        K.kf_track_host(ctx.h, host_b, devb, W, KP, ws_track, chunk=E2E_CHUNK, stream=stream,
+                        mask_format=K.KF_MASK_BYTES)
     ms_e2e = timed(e2e_step, max(3, args.steps // 2), 1)
-    e2e_same = bool(torch.equal(host["mask"], mask.cpu()) and torch.equal(host["idx"], idx.cpu())
-                    and torch.equal(host["u"], uu.cpu()))
+    m_bits = np.packbits(mask[:, :, :W].reshape(T, -1).cpu().numpy(), axis=1, bitorder="little")
+    e2e_same = bool(np.array_equal(host["mask"].numpy()[:, :m_bits.shape[1]], m_bits)
+                    and torch.equal(host["idx"], idx.cpu()) and torch.equal(host["u"], uu.cpu()))
+    ms_e2e_b = timed(e2e_bytes_step, max(3, args.steps // 2), 1)
+    e2e_same_b = bool(torch.equal(host_b["mask"], mask.cpu()) and torch.equal(host_b["idx"], idx.cpu()))
     h2d = frames_pin.numel()
-    d2h = sum(t.numel() * t.element_size() for k, t in host.items() if k != "frames")
+    d2h_tracks = sum(t.numel() * t.element_size() for k, t in host.items() if k not in ("frames", "mask"))
+    d2h = T * ((W * H + 7) // 8) + d2h_tracks
+    d2h_b = host_b["mask"].numel() + d2h_tracks
     tracked = int(n_pts.sum())
 
     line = {
@@ -426,8 +438,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                         "hbm_frac": 50 * px / (ms_unf16 / 1000) / 1e9 / hbm_peak},
         "e2e": {"value": world * px / (ms_e2e / 1000) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e, "chunk_frames": E2E_CHUNK,
-                "call": "kf_track_host (copy in, hot path, copy out overlapped on three streams)",
+                "call": "kf_track_host, KF_MASK_BITS (copy in, hot path on two streams, mask packed 8 px/byte "
+                        "into pinned host memory by the device, tracks copied out)",
                 "results_equal_device_step": e2e_same},
+        "e2e_byte_mask": {"value": world * px / (ms_e2e_b / 1000) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                          "d2h_bytes_per_step": int(d2h_b), "ms_per_step": ms_e2e_b,
+                          "call": "kf_track_host, KF_MASK_BYTES", "results_equal_device_step": e2e_same_b},
         "gpu_launches": sum(k["launches"] for k in kernels.values()),  # counted by the library's event pairs
         "device_error": dev_err,
         "clocks": clocks,
@@ -535,7 +551,7 @@ def run_pchain(args):
 
 
 ST_BETAS = (4096, 16384, 65536)
-ST_SIDES = (8, 16, 32, 64, 128)
+ST_SIDES = (8, 16, 32, 48, 64, 96)
 
 
 def run_stbox(args):
@@ -557,7 +573,6 @@ def run_stbox(args):
     mask = torch.zeros((T, H, W), dtype=torch.uint8, device=dev)
     counts = torch.zeros(T, dtype=torch.int32, device=dev)
     px = T * H * W
-    smem_cap = 227 * 1024
 
     def time_box(n, x, t):
         run = lambda: K.kf_st_run(ctx.h, fr, W, mask, counts, n, x, t, stream)  # noqa: E731
@@ -579,7 +594,7 @@ def run_stbox(args):
     def row(n, x, t):
         ms = time_box(n, x, t)
         model, clipped = K.kf_st_traffic(W, H, T, x, t, n)
-        r = {"x": x, "t": t, "smem_bytes": K.kf_st_smem_bytes(n, x), "model_bytes_per_px": model / px,
+        r = {"x": x, "t": t, "beta": x * x * t, "smem_bytes": K.kf_st_smem_bytes(n, x), "model_bytes_per_px": model / px,
              "clipped_bytes_per_px": clipped / px, "du_eq3": x * x * t / ((x + 4) ** 2 * (t + n))}
         if ms is not None:
             r.update({"ms": ms, "value": px / (ms / 1000) / 1e6, "hbm_frac": clipped / (ms / 1000) / 1e9 / hbm_peak})
@@ -606,7 +621,7 @@ def run_stbox(args):
             rows = []
             for x in ST_SIDES:
                 t = beta // (x * x)
-                if t < 1 or K.kf_st_smem_bytes(n, x) > smem_cap:
+                if t < 1:
                     continue
                 rows.append(row(n, x, t))
                 rows[-1]["identical_to_first_box"] = same_as_first(n)
@@ -617,8 +632,6 @@ def run_stbox(args):
                                       "fastest_x": best["x"] if best else None,
                                       "least_traffic_x": least["x"]})
         for x in (16, 32, 48, 64, 96):
-            if K.kf_st_smem_bytes(n, x) > smem_cap:
-                continue
             for t in (4, 8, 16, 32, 64):
                 rec["sweep"].append(row(n, x, t))
                 rec["sweep"][-1]["identical_to_first_box"] = same_as_first(n)

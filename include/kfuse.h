@@ -242,12 +242,23 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *video, const kf_corners *out, co
  * pitches as the device ones (page-locked, e.g. cudaHostAlloc, for the copies to be
  * asynchronous; pageable memory still gives correct results, without overlap). video /
  * out / tracks / workspace: device buffers as for kf_track (video holds all T frames; LK
- * of a chunk's first frame reads the previous chunk's last). Asynchronous: `stream` waits
- * for the last copy out, and the copies start after the work queued on `stream` before
- * the call; the host buffers must stay valid until then. */
+ * of a chunk's first frame reads the previous chunk's last). mask_format: KF_MASK_BYTES,
+ * host_out->mask like the device mask (same mask_pitch); or KF_MASK_BITS, the mask
+ * packed for transfer, 8 pixels a byte: frame f's pixel (y, x), i = y W + x, is bit i % 8
+ * of byte f * host_out->mask_pitch + i / 8 (mask_pitch = bytes per frame, >= ceil(W H /
+ * 8), a multiple of 16; bits past W H are 0). With KF_MASK_BITS the device stores the
+ * packed frames straight into host_out->mask, which must be host memory the device can
+ * address (cudaHostGetDevicePointer succeeds: cudaHostAlloc, cudaHostRegister with
+ * cudaHostRegisterMapped, or any memory on systems whose devices translate host
+ * addresses; else KF_EINVAL); the device mask is written as well. Asynchronous: `stream` waits for the
+ * last copy out, and the copies start after the work queued on `stream` before the call;
+ * the host buffers must stay valid until then. */
+#define KF_MASK_BYTES 0
+#define KF_MASK_BITS 1
 kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corners *host_out,
                         const kf_tracks *host_tracks, const kf_video *video, const kf_corners *out,
-                        const kf_tracks *tracks, void *workspace, size_t workspace_bytes, int64_t chunk, void *stream);
+                        const kf_tracks *tracks, void *workspace, size_t workspace_bytes, int64_t chunk, int mask_format,
+                        void *stream);
 
 /* ------------------------------------------------------------------ batches */
 /* Many independent videos of different sizes and lengths through the fully fused chain
@@ -457,9 +468,10 @@ kf_status kf_pc_kalman(kf_ctx *ctx, const int32_t *regions, int64_t T, int n_tra
  *       the mask count
  * all in exact 32-bit integers. One-sided reaches dx = 2 (spatial, both sides), dt = n
  * (temporal, past side). */
-/* Shared memory of one box: RGBA staging of one frame ((x + 8) x (x + 4) x 4 bytes), a
- * ring of n + 1 16-bit gray planes of the same extent, the smoothed plane (x + 2) x
- * (x + 4) x 4 bytes. Boxes above 227 KB are rejected by kf_st_run. x a multiple of 8. */
+/* Shared memory of one box: RGBA staging of one frame ((x + 8) x (x + 4) x 4 bytes), the
+ * temporal map Kt of the same extent (4 bytes a pixel), the smoothed map (x + 2) x (x + 4)
+ * x 4 bytes and the gray values of the n previous frames (2 bytes a pixel each). Box
+ * sides x in {8, 16, 32, 48, 64, 96}; others are rejected. */
 kf_status kf_st_smem_bytes(int n, int x, size_t *bytes);
 /* Sec. VI-D's fused transfer for boxes x * x * t: model_bytes = B ((x + 4)^2 (t + n) * 4 +
  * x^2 t) with B = W H T / (x^2 t) (halos never clipped); clipped_bytes = the input
@@ -470,9 +482,9 @@ kf_status kf_st_traffic(int64_t W, int64_t H, int64_t T, int x, int t, int n, do
 /* Eq. 6 for this group's reaches (dx = 2, dt = n) and output volume beta = x^2 t:
  * x = (2 beta dx / dt)^(1/3), t = beta / x^2. */
 kf_status kf_st_box_eq6(double beta, int n, double *x, double *t);
-/* The group over the whole video in boxes of x * x * t (x a multiple of 8, t >= 1), one
- * block per box, frames streamed through shared memory in time order (the temporal halo
- * stays on chip for the box). mask: device, T x H x mask_pitch bytes (16-byte aligned,
+/* The group over the whole video in boxes of x * x * t (x as for kf_st_smem_bytes, t >=
+ * 1), one block per box, frames streamed through shared memory in time order (the
+ * temporal halo stays on chip for the box). mask: device, T x H x mask_pitch bytes (16-byte aligned,
  * mask_pitch >= W, a multiple of 4; the pitch padding is not written); counts: device
  * [T], written. A copy wait that runs out records KF_DEVERR_TIMEOUT. Asynchronous on
  * `stream`. */

@@ -730,6 +730,50 @@ kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const
     return KF_OK;
 }
 
+// Bit-packing of the chain's masks for transfer: frame f's H * W pixels in raster order,
+// pixel i as bit i % 8 of byte i / 8, 32 pixels (one 32-bit word) per thread, written to
+// dst + f * dst_stride (a multiple of 16 bytes; the last word's bits past H * W are 0).
+__global__ void __launch_bounds__(256) pack_mask_kernel(const uint8_t *__restrict__ mask, int64_t pitch, int64_t fstride,
+                                                        int W, int H, int64_t n_frames, int64_t words, uint8_t *dst,
+                                                        int64_t dst_stride)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= words) return;
+    const int64_t p0 = i * 32, npx = (int64_t)W * H;
+    const int y0 = (int)(p0 / W), x0 = (int)(p0 - (int64_t)y0 * W);
+    const bool fast = x0 + 32 <= W && (x0 & 7) == 0 && (pitch & 7) == 0;
+    for (int64_t f = blockIdx.y; f < n_frames; f += gridDim.y) {
+        const uint8_t *fm = mask + f * fstride;
+        uint32_t bits = 0;
+        if (fast) {
+            const uint2 *src = reinterpret_cast<const uint2 *>(fm + (int64_t)y0 * pitch + x0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint2 v = src[q];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t w = h ? v.y : v.x;  // 4 pixels; any nonzero byte is a set pixel
+                    w |= w >> 4;
+                    w |= w >> 2;
+                    w |= w >> 1;
+                    w &= 0x01010101u;
+                    bits |= ((w | (w >> 7) | (w >> 14) | (w >> 21)) & 0xfu) << (8 * q + 4 * h);
+                }
+            }
+        } else {
+            int y = y0, xx = x0;
+            for (int b = 0; b < 32 && p0 + b < npx; ++b) {
+                bits |= (uint32_t)(fm[(int64_t)y * pitch + xx] != 0) << b;
+                if (++xx == W) {
+                    xx = 0;
+                    ++y;
+                }
+            }
+        }
+        reinterpret_cast<uint32_t *>(dst + f * dst_stride)[i] = bits;
+    }
+}
+
 // the context's copy streams and event ring (created on first use)
 kf_status copy_streams(kf_ctx *c)
 {
@@ -759,14 +803,20 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf
 
 kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corners *host_out,
                         const kf_tracks *host_tracks, const kf_video *video, const kf_corners *out,
-                        const kf_tracks *tracks, void *workspace, size_t workspace_bytes, int64_t chunk, void *stream)
+                        const kf_tracks *tracks, void *workspace, size_t workspace_bytes, int64_t chunk, int mask_format,
+                        void *stream)
 {
     kf_status st = check_track_args(ctx, video, out, tracks, workspace, workspace_bytes);
     if (st != KF_OK) return st;
     if (!host_video || !host_out || !host_tracks || chunk < 1) return KF_EINVAL;
+    if (mask_format != KF_MASK_BYTES && mask_format != KF_MASK_BITS) return KF_EINVAL;
     const int64_t T = video->T, H = video->H, K = tracks->K;
+    const bool bits = mask_format == KF_MASK_BITS;
+    const int64_t packed = (video->W * H + 7) / 8;
     if (host_video->W != video->W || host_video->H != H || host_video->T != T || host_video->pitch != video->pitch ||
-        host_out->mask_pitch != out->mask_pitch || host_tracks->K != K)
+        host_tracks->K != K)
+        return KF_EINVAL;
+    if (bits ? (host_out->mask_pitch < packed || host_out->mask_pitch % 16) : host_out->mask_pitch != out->mask_pitch)
         return KF_EINVAL;
     if (T == 0) return KF_OK;
     if (!host_video->frames || !host_out->mask || !host_out->counts || !host_tracks->n_points || !host_tracks->idx ||
@@ -774,6 +824,16 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
         return KF_EINVAL;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
+    // packed masks are stored by the device into the page-locked host buffer directly
+    uint8_t *host_bits = nullptr;
+    if (bits) {
+        void *d = nullptr;
+        if (cudaHostGetDevicePointer(&d, host_out->mask, 0) != cudaSuccess || (uintptr_t)d % 16) {
+            cudaGetLastError();
+            return KF_EINVAL;
+        }
+        host_bits = static_cast<uint8_t *>(d);
+    }
     if ((st = copy_streams(ctx)) != KF_OK) return st;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the internal streams start after what the caller queued before this call
@@ -799,12 +859,21 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
         if (e != cudaSuccess) break;
         st = track_range(ctx, video, out, tracks, workspace, t0, t1, cs);
         if (st != KF_OK) return st;
+        if (bits) {
+            const int64_t words = (packed + 3) / 4;
+            const dim3 grid((unsigned)((words + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
+            pack_mask_kernel<<<grid, 256, 0, cs>>>(out->mask + t0 * mstride, out->mask_pitch, mstride, (int)video->W,
+                                                   (int)H, n, words, host_bits + t0 * host_out->mask_pitch,
+                                                   host_out->mask_pitch);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) break;
+        }
         e = cudaEventRecord(ecomp, cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ecomp, 0);
         auto d2h = [&](void *dst, const void *src, size_t bytes) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s_out);
         };
-        d2h(host_out->mask + t0 * mstride, out->mask + t0 * mstride, (size_t)(n * mstride));
+        if (!bits) d2h(host_out->mask + t0 * mstride, out->mask + t0 * mstride, (size_t)(n * mstride));
         d2h(host_out->counts + t0, out->counts + t0, sizeof(int32_t) * (size_t)n);
         d2h(host_tracks->n_points + t0, tracks->n_points + t0, sizeof(int32_t) * (size_t)n);
         d2h(host_tracks->idx + t0 * K, tracks->idx + t0 * K, sizeof(int32_t) * (size_t)(n * K));

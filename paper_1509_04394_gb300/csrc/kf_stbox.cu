@@ -8,16 +8,18 @@
 // smoothing weights (1,2,1)x(1,2,1), unnormalised Sobel), so the chain is computed
 // exactly in 32-bit integers and M > 0.25 is M_int > 261120 * 2^n.
 //
-// One block per box. The box's frames stream through shared memory in time order: a TMA
-// copy brings the (x + 8) x (x + 4) RGBA pixels of the next frame (the box with its
-// two-pixel spatial halo, widened to 16-byte column boundaries) into a staging plane while
-// the block computes the current frame; the block turns it into a 16-bit gray plane in a
-// ring of n + 1 planes. So the temporal halo -- the n frames before the current one -- stays
-// on chip for the whole box and each input frame of the box is read once: a box reads
-// (x + 4)^2 (t + n) pixels (plus the column widening) and writes x^2 t mask bytes.
-// Per frame, pass B forms the smoothed map G over (x + 2) x (x + 4) from the ring (4
-// columns per thread, a 3-row vertical window in registers), pass C the Sobel magnitude,
-// threshold and mask stores over x * x (4 columns per thread, 4 mask bytes per store).
+// One block per box, the box side X a compile-time constant. The box's frames stream
+// through shared memory in time order: a TMA copy brings the (X + 8) x (X + 4) RGBA pixels
+// of the next frame (the box with its two-pixel spatial halo, widened to 16-byte column
+// boundaries) into a staging plane while the block computes the current frame. Each
+// thread converts the same pixel pairs in every frame, so the gray values of the n
+// previous frames -- the temporal halo -- stay on chip for the whole box in a ring only
+// that thread touches, and each input frame of the box is read once: a box reads
+// (X + 4)^2 (t + n) pixels (plus the column widening) and writes X^2 t mask bytes.
+// Per frame: K1 + Kt write the temporal map Z; pass B forms the smoothed map G over
+// (X + 2) x (X + 4) (4 columns per thread, a 3-row vertical window in registers); pass C
+// the Sobel magnitude, threshold and mask stores over X * X (4 columns per thread, 4 mask
+// bytes per store).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -40,12 +42,8 @@ struct StParams {
     int32_t *counts;
     int *err;
     int W, H, T;
-    int x, t;              // box: x * x pixels, t frames
+    int t;                 // box depth in frames (the side is the kernel's X)
     int boxes_x, boxes_y;  // boxes per frame row / column
-    int seg;               // rows per work item of passes B and C
-    int thr_shift;         // n
-    // shared memory layout (bytes from the 128-aligned base)
-    int off_ring, off_g, off_bar;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -86,48 +84,67 @@ __device__ __forceinline__ uint32_t gray_of(uint32_t rgba)
 }
 
 // binomial weight C(N, k)
-template <int N> __device__ __forceinline__ int binom(int k);
-template <> __device__ __forceinline__ int binom<1>(int) { return 1; }
-template <> __device__ __forceinline__ int binom<2>(int k) { return k == 1 ? 2 : 1; }
-template <> __device__ __forceinline__ int binom<4>(int k) { return k == 2 ? 6 : (k == 1 || k == 3) ? 4 : 1; }
-
-template <int N>
-__global__ void __launch_bounds__(256) st_box_kernel(const __grid_constant__ StParams p)
+template <int N> __host__ __device__ constexpr int binom(int k)
 {
+    return N == 1 ? 1 : N == 2 ? (k == 1 ? 2 : 1) : (k == 2 ? 6 : (k == 1 || k == 3) ? 4 : 1);
+}
+
+// Launch shape of a box side X: threads per block and rows per work item of passes B / C.
+// Launch shape of a box side X: threads per block (about ten pixel pairs of a staged
+// frame per thread) and rows per work item of passes B and C.
+template <int X> struct BoxCfg {
+    static constexpr int THREADS = X <= 16 ? 32 : X <= 32 ? 64 : X <= 48 ? 128 : X <= 64 ? 256 : 512;
+    static constexpr int SEG = X <= 16 ? 4 : 8;
+    static constexpr int SR = X + 4, SC = X + 8, GW = X + 4;  // staged rows / columns; G columns
+    static constexpr int PAIRS = SR * (SC / 2);                 // pixel pairs of a staged frame
+    static constexpr int STAGE_BYTES = SR * SC * 4;
+    __host__ __device__ static constexpr int up(int v) { return (v + 127) / 128 * 128; }
+    static constexpr int OFF_Z = up(STAGE_BYTES);
+    static constexpr int OFF_G = OFF_Z + up(SR * SC * 4);
+    static constexpr int OFF_RING = OFF_G + up((X + 2) * GW * 4);
+    template <int N> __host__ __device__ static constexpr int off_bar() { return OFF_RING + up(N * PAIRS * 4); }
+    template <int N> __host__ __device__ static constexpr int smem() { return off_bar<N>() + 8 + 128; }  // + base alignment slack
+};
+
+template <int N, int X>
+__global__ void __launch_bounds__(BoxCfg<X>::THREADS) st_box_kernel(const __grid_constant__ StParams p)
+{
+    using C = BoxCfg<X>;
+    constexpr int SR = C::SR, SC = C::SC, GW = C::GW, TH = C::THREADS, SEG = C::SEG;
     extern __shared__ __align__(128) unsigned char st_smem[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)st_smem + 127) & ~(uintptr_t)127);
-    const int x = p.x, SR = x + 4, SC = x + 8;  // staging / ring plane: rows, columns
     const uint32_t *stage = reinterpret_cast<const uint32_t *>(base);
-    uint16_t *ring = reinterpret_cast<uint16_t *>(base + p.off_ring);
-    int32_t *G = reinterpret_cast<int32_t *>(base + p.off_g);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + p.off_bar);
-    const int GW = x + 4;           // G plane columns (x + 2 used)
-    const int plane = SR * SC;      // u16 elements per ring plane
+    int32_t *Z = reinterpret_cast<int32_t *>(base + C::OFF_Z);
+    int32_t *G = reinterpret_cast<int32_t *>(base + C::OFF_G);
+    uint32_t *ring = reinterpret_cast<uint32_t *>(base + C::OFF_RING);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + C::template off_bar<N>());
 
     const int b = blockIdx.x;
     const int nb_xy = p.boxes_x * p.boxes_y;
     const int bt = b / nb_xy, bxy = b - bt * nb_xy;
     const int by = bxy / p.boxes_x, bx = bxy - by * p.boxes_x;
-    const int x0 = bx * x, y0 = by * x, t0 = bt * p.t;
+    const int x0 = bx * X, y0 = by * X, t0 = bt * p.t;
     const int t_end = min(t0 + p.t, p.T);
-    const int n_planes = t_end - (t0 - N);  // the n frames before the box, then its own
+    const int n_planes = t_end - (t0 - N);  // the N frames before the box, then its own
     const int tid = threadIdx.x;
-    const unsigned stage_bytes = (unsigned)(SR * SC * 4);
 
     if (tid == 0) {
         bar_init(bar);
-        bar_expect(bar, stage_bytes);
+        bar_expect(bar, C::STAGE_BYTES);
         tma_frame(base, &p.tmap, x0 - 4, y0 - 2, max(t0 - N, 0), bar);
     }
     __syncthreads();
 
-    // staging index of a clamped image coordinate (the clamped pixel always lies in the box)
-    const bool inner_x = x0 - 4 >= 0 && x0 + x + 4 <= p.W;
-    const bool inner_y = y0 - 2 >= 0 && y0 + x + 2 <= p.H;
-    const int thr = 261120 << p.thr_shift;
-    const int gcols = GW / 4, ocols = x / 4;
-    const int segs_b = (x + 2 + p.seg - 1) / p.seg, segs_c = (x + p.seg - 1) / p.seg;
-
+    const bool inner = x0 - 4 >= 0 && x0 + X + 4 <= p.W && y0 - 2 >= 0 && y0 + X + 2 <= p.H;
+    const int thr = 261120 << N;
+    // G plane rows / columns that lie inside the frame (G row / column j is image row
+    // y0-1+j / column x0-1+j): K4 clamps its own input to them
+    const int gr_lo = y0 == 0 ? 1 : 0, gr_hi = min(X + 1, p.H - y0);
+    const int g_lo = x0 == 0 ? 1 : 0, g_hi = min(X + 1, p.W - x0);
+    // The pixel pairs a thread converts are the same in every frame (pair i by thread
+    // i % THREADS), so the gray values of their N previous frames -- the temporal halo --
+    // sit in a ring that only that thread touches: pair i of frame q in ring[(q % N) *
+    // PAIRS + i]. No barrier guards it.
     for (int pl = 0; pl < n_planes; ++pl) {
         const bool ok = bar_wait(bar, (unsigned)(pl & 1));
         if (__syncthreads_or(!ok)) {
@@ -137,12 +154,14 @@ __global__ void __launch_bounds__(256) st_box_kernel(const __grid_constant__ StP
             }
             return;
         }
-        // the staged frame -> gray ring slot pl % (N + 1), two pixels per step
-        uint16_t *slot = ring + (pl % (N + 1)) * plane;
-        for (int i = tid; i < SR * (SC / 2); i += blockDim.x) {
+        // K1 + Kt: the staged frame -> gray pairs -> the temporal binomial into Z
+        const bool out_frame = pl >= N;
+        const int slot0 = pl % N;  // the ring slot of plane pl - N, overwritten by plane pl
+#pragma unroll 2
+        for (int i = tid; i < C::PAIRS; i += TH) {
             const int r = i / (SC / 2), c = 2 * (i - r * (SC / 2));
             uint32_t a, bb;
-            if (inner_x && inner_y) {
+            if (inner) {
                 const uint2 w = *reinterpret_cast<const uint2 *>(stage + r * SC + c);
                 a = w.x;
                 bb = w.y;
@@ -153,46 +172,51 @@ __global__ void __launch_bounds__(256) st_box_kernel(const __grid_constant__ StP
                 a = stage[ry * SC + ca];
                 bb = stage[ry * SC + cb];
             }
-            *reinterpret_cast<uint32_t *>(slot + r * SC + c) = gray_of(a) | (gray_of(bb) << 16);
+            const uint32_t g = gray_of(a) | (gray_of(bb) << 16);
+            if (out_frame) {
+                int lo = (int)(g & 0xffffu), hi = (int)(g >> 16);
+#pragma unroll
+                for (int k = 0; k < N; ++k) {  // plane pl - N + k, weight C(N, k)
+                    int sl = slot0 + k;
+                    sl = sl >= N ? sl - N : sl;
+                    const uint32_t q = ring[sl * C::PAIRS + i];
+                    lo += binom<N>(k) * (int)(q & 0xffffu);
+                    hi += binom<N>(k) * (int)(q >> 16);
+                }
+                *reinterpret_cast<int2 *>(Z + r * SC + c) = make_int2(lo, hi);
+            }
+            ring[slot0 * C::PAIRS + i] = g;
         }
         __syncthreads();
         if (tid == 0 && pl + 1 < n_planes) {
-            bar_expect(bar, stage_bytes);
+            bar_expect(bar, C::STAGE_BYTES);
             tma_frame(base, &p.tmap, x0 - 4, y0 - 2, max(t0 - N + pl + 1, 0), bar);
         }
-        if (pl < N) continue;  // a frame of the temporal halo only
+        if (!out_frame) continue;  // a frame of the temporal halo only
         const int f = t0 - N + pl;
 
-        // pass B: G over rows 0..x+1 (image y0-1..), columns 0..x+3 (image x0-1..)
-        for (int it = tid; it < gcols * segs_b; it += blockDim.x) {
-            const int g = 4 * (it % gcols), r0 = (it / gcols) * p.seg, r1 = min(r0 + p.seg, x + 2);
+        // pass B (K3): G over rows 0..X+1, columns 0..X+3 from Z (Z column j is image
+        // column x0-4+j, Z row i image row y0-2+i)
+        constexpr int GCOLS = GW / 4, SEGS_B = (X + 2 + SEG - 1) / SEG;
+        for (int it = tid; it < GCOLS * SEGS_B; it += TH) {
+            const int g = 4 * (it % GCOLS), r0 = (it / GCOLS) * SEG;
             int hm2[4] = {0, 0, 0, 0}, hm1[4] = {0, 0, 0, 0};
-            for (int i = r0; i < r1 + 2; ++i) {  // ring rows i (image y0-2+i)
-                int z[6];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) z[j] = 0;
-#pragma unroll
-                for (int k = 0; k <= N; ++k) {
-                    const uint16_t *row = ring + ((pl - N + k) % (N + 1)) * plane + i * SC + g + 2;
-                    const uint32_t *w = reinterpret_cast<const uint32_t *>(row);
-                    const int wk = binom<N>(k);
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const uint32_t v = w[j];
-                        z[2 * j] += wk * (int)(v & 0xffffu);
-                        z[2 * j + 1] += wk * (int)(v >> 16);
-                    }
-                }
+#pragma unroll 1
+            for (int q = 0; q < SEG + 2; ++q) {
+                const int i = min(r0 + q, SR - 1);  // rows past the plane only feed unstored G rows
+                const int2 z01 = *reinterpret_cast<const int2 *>(Z + i * SC + g + 2);
+                const int4 z25 = *reinterpret_cast<const int4 *>(Z + i * SC + g + 4);
+                const int z[6] = {z01.x, z01.y, z25.x, z25.y, z25.z, z25.w};
                 int h[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) h[c] = z[c] + 2 * z[c + 1] + z[c + 2];
-                if (i >= r0 + 2) {
+                if (q >= 2 && r0 + q - 2 < X + 2) {
                     int4 o;
                     o.x = hm2[0] + 2 * hm1[0] + h[0];
                     o.y = hm2[1] + 2 * hm1[1] + h[1];
                     o.z = hm2[2] + 2 * hm1[2] + h[2];
                     o.w = hm2[3] + 2 * hm1[3] + h[3];
-                    *reinterpret_cast<int4 *>(G + (i - 2) * GW + g) = o;
+                    *reinterpret_cast<int4 *>(G + (r0 + q - 2) * GW + g) = o;
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -203,24 +227,34 @@ __global__ void __launch_bounds__(256) st_box_kernel(const __grid_constant__ StP
         }
         __syncthreads();
 
-        // pass C: Sobel magnitude, threshold, mask and count over the box's x * x outputs
+        // pass C (K4, K5): Sobel magnitude, threshold, mask and count over X * X outputs
+        constexpr int OCOLS = X / 4, SEGS_C = (X + SEG - 1) / SEG;
         int count = 0;
         uint8_t *mframe = p.mask + (int64_t)f * p.mask_fstride;
-        for (int it = tid; it < ocols * segs_c; it += blockDim.x) {
-            const int o = 4 * (it % ocols), r0 = (it / ocols) * p.seg, r1 = min(r0 + p.seg, x);
+        for (int it = tid; it < OCOLS * SEGS_C; it += TH) {
+            const int o = 4 * (it % OCOLS), r0 = (it / OCOLS) * SEG;
+            const bool clamp_cols = o < g_lo || o + 5 > g_hi;
             int dxm2[4] = {0, 0, 0, 0}, dxm1[4] = {0, 0, 0, 0}, sxm2[4] = {0, 0, 0, 0}, sxm1[4] = {0, 0, 0, 0};
-            for (int gr = r0; gr < r1 + 2; ++gr) {  // G rows gr (output row gr - 1 centre)
-                const int4 a = *reinterpret_cast<const int4 *>(G + gr * GW + o);
-                const int2 c2 = *reinterpret_cast<const int2 *>(G + gr * GW + o + 4);
-                const int v[6] = {a.x, a.y, a.z, a.w, c2.x, c2.y};
+#pragma unroll 1
+            for (int q = 0; q < SEG + 2; ++q) {  // G row r0+q; output row r0+q-2 centred on r0+q-1
+                const int32_t *grow = G + min(max(r0 + q, gr_lo), gr_hi) * GW;
+                int v[6];
+                if (!clamp_cols) {
+                    const int4 a = *reinterpret_cast<const int4 *>(grow + o);
+                    const int2 c2 = *reinterpret_cast<const int2 *>(grow + o + 4);
+                    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = c2.x; v[5] = c2.y;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) v[j] = grow[min(max(o + j, g_lo), g_hi)];
+                }
                 int dx[4], sx[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     dx[c] = v[c + 2] - v[c];
                     sx[c] = v[c] + 2 * v[c + 1] + v[c + 2];
                 }
-                if (gr >= r0 + 2) {
-                    const int r = gr - 2;  // output row (image y0 + r)
+                const int r = r0 + q - 2;
+                if (q >= 2 && r < X) {
                     uint32_t bits = 0;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -254,35 +288,42 @@ __global__ void __launch_bounds__(256) st_box_kernel(const __grid_constant__ StP
     }
 }
 
-// shared memory plan of a box side and temporal reach
-struct StSmem {
-    int off_ring, off_g, off_bar, total;
-};
-StSmem st_plan(int x, int n)
+// the supported box sides and the kernel of (n, x); nullptr if not supported
+using BoxKernel = void (*)(StParams);
+template <int N> BoxKernel box_kernel_n(int x)
 {
-    auto up = [](int v, int a) { return (v + a - 1) / a * a; };
-    StSmem s;
-    const int SR = x + 4, SC = x + 8;
-    s.off_ring = up(SR * SC * 4, 128);
-    s.off_g = up(s.off_ring + (n + 1) * SR * SC * 2, 128);
-    s.off_bar = up(s.off_g + (x + 2) * (x + 4) * 4, 128);
-    s.total = s.off_bar + 8 + 128;  // + alignment slack of the dynamic base
-    return s;
+    switch (x) {
+    case 8: return st_box_kernel<N, 8>;
+    case 16: return st_box_kernel<N, 16>;
+    case 32: return st_box_kernel<N, 32>;
+    case 48: return st_box_kernel<N, 48>;
+    case 64: return st_box_kernel<N, 64>;
+    case 96: return st_box_kernel<N, 96>;
+    default: return nullptr;
+    }
 }
+BoxKernel box_kernel(int n, int x)
+{
+    return n == 1 ? box_kernel_n<1>(x) : n == 2 ? box_kernel_n<2>(x) : n == 4 ? box_kernel_n<4>(x) : nullptr;
+}
+int box_threads(int x) { return x <= 16 ? 32 : x <= 32 ? 64 : x <= 48 ? 128 : x <= 64 ? 256 : 512; }
+template <int N> int box_smem_n(int x)
+{
+    switch (x) {
+    case 8: return BoxCfg<8>::smem<N>();
+    case 16: return BoxCfg<16>::smem<N>();
+    case 32: return BoxCfg<32>::smem<N>();
+    case 48: return BoxCfg<48>::smem<N>();
+    case 64: return BoxCfg<64>::smem<N>();
+    case 96: return BoxCfg<96>::smem<N>();
+    default: return 0;
+    }
+}
+int box_smem(int n, int x) { return n == 1 ? box_smem_n<1>(x) : n == 2 ? box_smem_n<2>(x) : box_smem_n<4>(x); }
 
 bool valid_n(int n) { return n == 1 || n == 2 || n == 4; }
 
 }  // namespace
-
-// launch configuration of a box: threads and rows per work item
-void st_config(int x, int *threads, int *seg)
-{
-    int th = (x * x / 32 + 31) / 32 * 32;
-    th = th < 32 ? 32 : (th > 256 ? 256 : th);
-    int s = (x * (x / 4) + th - 1) / th;
-    *threads = th;
-    *seg = s < 2 ? 2 : s;
-}
 
 }  // namespace kf
 
@@ -313,8 +354,8 @@ extern "C" {
 
 kf_status kf_st_smem_bytes(int n, int x, size_t *bytes)
 {
-    if (!bytes || !kf::valid_n(n) || x < 8 || x > 248 || x % 8) return KF_EINVAL;
-    *bytes = (size_t)kf::st_plan(x, n).total;
+    if (!bytes || !kf::box_kernel(n, x)) return KF_EINVAL;
+    *bytes = (size_t)kf::box_smem(n, x);
     return KF_OK;
 }
 
@@ -351,14 +392,16 @@ kf_status kf_st_box_eq6(double beta, int n, double *x, double *t)
 kf_status kf_st_run(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64_t mask_pitch, int32_t *counts, int n,
                     int x, int t, void *stream)
 {
-    if (!ctx || !video || !kf::valid_n(n) || x < 8 || x % 8 || t < 1) return KF_EINVAL;
+    if (!ctx || !video || t < 1) return KF_EINVAL;
+    const kf::BoxKernel kern = kf::box_kernel(n, x);
+    if (!kern) return KF_EINVAL;
     const int64_t W = video->W, H = video->H, T = video->T;
     if (W < 1 || H < 1 || T < 0 || W > 0x7fffffff || H > 0x7fffffff || T > 0x7fffffff) return KF_EINVAL;
     if (T == 0) return KF_OK;
     if (!video->rgba || !mask || !counts || (uintptr_t)video->rgba % 16 || (uintptr_t)mask % 16) return KF_EINVAL;
     if (video->pitch < W || video->pitch % 4 || mask_pitch < W || mask_pitch % 4) return KF_EINVAL;
-    const kf::StSmem sm = kf::st_plan(x, n);
-    if (sm.total > kf::ST_MAX_SMEM) return KF_EINVAL;
+    const int smem = kf::box_smem(n, x);
+    if (smem > kf::ST_MAX_SMEM) return KF_EINVAL;
     const int64_t bxn = (W + x - 1) / x, byn = (H + x - 1) / x, btn = (T + t - 1) / t;
     if (bxn * byn * btn > 0x7fffffff) return KF_EINVAL;
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -383,23 +426,16 @@ kf_status kf_st_run(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64_
     p.W = (int)W;
     p.H = (int)H;
     p.T = (int)T;
-    p.x = x;
     p.t = t;
     p.boxes_x = (int)bxn;
     p.boxes_y = (int)byn;
-    p.thr_shift = n;
-    p.off_ring = sm.off_ring;
-    p.off_g = sm.off_g;
-    p.off_bar = sm.off_bar;
-    int threads = 0;
-    kf::st_config(x, &threads, &p.seg);
+    const int threads = kf::box_threads(x);
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)T, s);
     if (e != cudaSuccess) return st_fail(ctx, e);
-    void (*kern)(StParams) = n == 1 ? kf::st_box_kernel<1> : (n == 2 ? kf::st_box_kernel<2> : kf::st_box_kernel<4>);
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm.total);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return st_fail(ctx, e);
-    kern<<<(unsigned)(bxn * byn * btn), threads, sm.total, s>>>(p);
+    kern<<<(unsigned)(bxn * byn * btn), threads, smem, s>>>(p);
     e = cudaGetLastError();
     return e == cudaSuccess ? KF_OK : st_fail(ctx, e);
 }

@@ -94,7 +94,7 @@ def _lib():
             "kf_run_static": (i32, [P, u32, P, P, P]),
             "kf_track_workspace_bytes": (i32, [P, i64, i64, i64, P]),
             "kf_track": (i32, [P, P, P, P, P, ctypes.c_size_t, P]),
-            "kf_track_host": (i32, [P, P, P, P, P, P, P, P, ctypes.c_size_t, i64, P]),
+            "kf_track_host": (i32, [P, P, P, P, P, P, P, P, ctypes.c_size_t, i64, i32, P]),
             "kf_batch_workspace_bytes": (i32, [P, P, i32, i32, P]),
             "kf_batch_create": (i32, [P, P, P, P, i32, P, ctypes.c_size_t, P]),
             "kf_batch_run": (i32, [P, P]),
@@ -294,24 +294,31 @@ def kf_track(ctx, frames, W: int, mask, counts, K: int, n_points, idx, u, v, sta
                                        ws_bytes, _stream(stream)), ctx)
 
 
-def kf_track_host(ctx, host, dev, W: int, K: int, workspace, chunk: int = 100, stream=None) -> None:
+KF_MASK_BYTES, KF_MASK_BITS = 0, 1
+
+
+def kf_track_host(ctx, host, dev, W: int, K: int, workspace, chunk: int = 100, stream=None,
+                  mask_format: int = KF_MASK_BYTES) -> None:
     """kf_track from host tensors to host tensors, pipelined in chunks of `chunk` frames.
     host, dev: dicts of tensors (host: pinned CPU, dev: CUDA) with keys frames [T, H, P]
-    u8, mask [T, H, MP] u8, counts [T] i32, n_points [T] i32, idx / status [T, K] i32,
-    u / v [T, K] f32."""
-    def structs(d):
+    u8, mask [T, H, MP] u8 (KF_MASK_BITS: host mask [T, S] u8, S >= ceil(W H / 8) a
+    multiple of 16), counts [T] i32, n_points [T] i32, idx / status [T, K] i32, u / v
+    [T, K] f32."""
+    def structs(d, packed=False):
         T, H, P = d["frames"].shape
         vid = kf_video(d["frames"].data_ptr(), int(W), int(H), int(T), int(P))
-        o = kf_corners(d["mask"].data_ptr(), int(d["mask"].shape[2]), d["counts"].data_ptr())
+        mp = int(d["mask"].shape[1]) if packed else int(d["mask"].shape[2])
+        o = kf_corners(d["mask"].data_ptr(), mp, d["counts"].data_ptr())
         tr = kf_tracks(int(K), d["n_points"].data_ptr(), d["idx"].data_ptr(), d["u"].data_ptr(), d["v"].data_ptr(),
                        d["status"].data_ptr())
         return vid, o, tr
-    hv, ho, ht = structs(host)
+    hv, ho, ht = structs(host, mask_format == KF_MASK_BITS)
     dv, do, dt = structs(dev)
     ws_bytes = workspace.numel() * workspace.element_size()
     _check("kf_track_host", _lib().kf_track_host(ctx, ctypes.byref(hv), ctypes.byref(ho), ctypes.byref(ht),
                                                  ctypes.byref(dv), ctypes.byref(do), ctypes.byref(dt),
-                                                 workspace.data_ptr(), ws_bytes, int(chunk), _stream(stream)), ctx)
+                                                 workspace.data_ptr(), ws_bytes, int(chunk), int(mask_format),
+                                                 _stream(stream)), ctx)
 
 
 def _videos(frames_list, W_list):

@@ -207,7 +207,7 @@ def test_host_pipelined_call_equals_kf_track(dev, chunk):
     host, devb = bufs("cpu", True), bufs(dev, False)
     host["frames"].copy_(torch.from_numpy(fr))
     ws = torch.empty(K.kf_track_workspace_bytes(ctx.h, W, H, T), dtype=torch.uint8, device=dev)
-    K.kf_track_host(ctx.h, host, devb, W, Kp, ws, chunk=chunk)
+    K.kf_track_host(ctx.h, host, devb, W, Kp, ws, chunk=chunk, mask_format=K.KF_MASK_BYTES)
     torch.cuda.synchronize()
     assert K.kf_device_error(ctx.h) == 0
     names = dict(mask="mask", counts="counts", n_points="n", idx="idx", u="u", v="v", status="st")
@@ -217,3 +217,45 @@ def test_host_pipelined_call_equals_kf_track(dev, chunk):
             got, exp = got[..., :W], exp[..., :W]
         assert np.array_equal(got, exp), k
         assert np.array_equal(host[k].numpy(), devb[k].cpu().numpy()), k
+
+
+@pytest.mark.parametrize("W,chunk", [(150, 4), (600, 3), (37, 100)])
+def test_host_call_with_bit_packed_masks(dev, W, chunk):
+    """KF_MASK_BITS: the host receives each frame's mask as H * W bits in raster order
+    (LSB first), stored by the device into the pinned buffer; the rest as with bytes."""
+    T, H, Kp = 7, 40, 16
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=9, n_blobs=6, n_patches=4), pitch=sv.pitch_for(W))
+    ref = run_track(dev, fr, W, Kp)
+    ctx = K.Context(0)
+    P = fr.shape[2]
+    S = ((W * H + 7) // 8 + 15) // 16 * 16
+    devb = dict(frames=torch.zeros((T, H, P), dtype=torch.uint8, device=dev),
+                mask=torch.zeros((T, H, P), dtype=torch.uint8, device=dev),
+                counts=torch.zeros(T, dtype=torch.int32, device=dev),
+                n_points=torch.full((T,), -1, dtype=torch.int32, device=dev),
+                idx=torch.full((T, Kp), -1, dtype=torch.int32, device=dev), u=torch.zeros((T, Kp), device=dev),
+                v=torch.zeros((T, Kp), device=dev), status=torch.full((T, Kp), -1, dtype=torch.int32, device=dev))
+    host = {k: torch.empty_like(t, device="cpu").pin_memory() for k, t in devb.items()}
+    host["mask"] = torch.full((T, S), 0xAB, dtype=torch.uint8).pin_memory()
+    host["frames"].copy_(torch.from_numpy(fr))
+    ws = torch.empty(K.kf_track_workspace_bytes(ctx.h, W, H, T), dtype=torch.uint8, device=dev)
+    K.kf_track_host(ctx.h, host, devb, W, Kp, ws, chunk=chunk, mask_format=K.KF_MASK_BITS)
+    torch.cuda.synchronize()
+    assert K.kf_device_error(ctx.h) == 0
+    exp = np.packbits(ref["mask"][..., :W].reshape(T, -1), axis=1, bitorder="little")
+    got = host["mask"].numpy()
+    nbytes = (W * H + 7) // 8
+    np.testing.assert_array_equal(got[:, :nbytes], exp)
+    words = (nbytes + 3) // 4 * 4
+    assert (got[:, nbytes:words] == 0).all() and (got[:, words:] == 0xAB).all()
+    for k, r in dict(counts="counts", n_points="n", idx="idx", u="u", v="v", status="st").items():
+        assert np.array_equal(host[k].numpy(), ref[r]), k
+    # a pageable host mask: rejected before any work where the device cannot address it;
+    # where it can (address translation of system memory), the same packed mask arrives
+    host["mask"] = torch.zeros((T, S), dtype=torch.uint8)
+    try:
+        K.kf_track_host(ctx.h, host, devb, W, Kp, ws, chunk=chunk, mask_format=K.KF_MASK_BITS)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(host["mask"].numpy()[:, :nbytes], exp)
+    except K.KfuseError:
+        pass

@@ -32,15 +32,16 @@ def test_eq6_equals_the_reference(beta, n):
 
 def test_smem_grows_with_the_box_and_the_ring():
     for n in ost.TAPS:
-        b = [K.kf_st_smem_bytes(n, x) for x in (8, 16, 32, 64)]
-        assert b == sorted(b)
-        # staging + (n + 1) gray planes + the smoothed plane, each at least its raw size
+        b = [K.kf_st_smem_bytes(n, x) for x in (8, 16, 32, 48, 64, 96)]
+        assert b == sorted(b) and b[-1] <= 227 * 1024
+        # staging and temporal planes (4 bytes a pixel each), the ring of n frames (2 bytes
+        # a pixel each) and the smoothed plane, each at least its raw size
         x = 64
-        assert b[3] >= (x + 8) * (x + 4) * (4 + 2 * (n + 1)) + (x + 2) * (x + 4) * 4
+        assert b[4] >= (x + 8) * (x + 4) * (8 + 2 * n) + (x + 2) * (x + 4) * 4
     assert K.kf_st_smem_bytes(4, 64) > K.kf_st_smem_bytes(2, 64) > K.kf_st_smem_bytes(1, 64)
 
 
-@pytest.mark.parametrize("n,x", [(3, 16), (2, 12), (2, 4), (0, 8)])
+@pytest.mark.parametrize("n,x", [(3, 16), (2, 12), (2, 4), (0, 8), (2, 128), (1, 24)])
 def test_bad_arguments_are_rejected(n, x):
     with pytest.raises(K.KfuseError):
         K.kf_st_smem_bytes(n, x)
