@@ -778,8 +778,13 @@ __global__ void __launch_bounds__(256) pack_mask_kernel(const uint8_t *__restric
 kf_status copy_streams(kf_ctx *c)
 {
     if (c->s_in) return KF_OK;
-    cudaError_t e = cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking);
+    // the copy-out stream at the highest priority: its mask-packing kernels then take SM
+    // slots as soon as blocks of the compute streams retire, instead of queueing behind
+    // the next chunks' kernels
+    int lo_prio = 0, hi_prio = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_out, cudaStreamNonBlocking, hi_prio);
     for (int i = 0; e == cudaSuccess && i < kf_ctx::N_RING; ++i) {
         e = cudaStreamCreateWithFlags(&c->s_comp[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming);
@@ -843,15 +848,20 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
     for (int i = 0; e == cudaSuccess && i < kf_ctx::N_RING; ++i) e = cudaStreamWaitEvent(ctx->s_comp[i], ctx->ev_edge, 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     const int64_t fstride = video->pitch * H, mstride = out->mask_pitch * H;
-    for (int64_t t0 = 0, k = 0; t0 < T && e == cudaSuccess; t0 += chunk, ++k) {
-        const int64_t t1 = t0 + chunk < T ? t0 + chunk : T, n = t1 - t0;
+    // the first chunk is a quarter of the others, so the hot path starts sooner
+    const int64_t first = chunk / 4 > 0 ? chunk / 4 : 1;
+    int64_t t1 = 0;
+    for (int64_t t0 = 0, k = 0; t0 < T && e == cudaSuccess; t0 = t1, ++k) {
+        const int64_t len = k == 0 ? first : chunk;
+        t1 = t0 + len < T ? t0 + len : T;
+        const int64_t n = t1 - t0;
         const int r = (int)(k % kf_ctx::N_RING);
         cudaEvent_t ein = ctx->ev_in[r], ecomp = ctx->ev_comp[r];
         const cudaStream_t cs = ctx->s_comp[r];
-        // copy in (s_in), compute (two streams in turn), copy out (s_out). Chunks touch
-        // disjoint frames of every buffer, and a chunk's tracking reads only input frames
-        // copied in before it, so consecutive chunks' kernels may overlap: the next chunk's
-        // launch fills the SMs while the previous one drains its last wave.
+        // copy in (s_in), compute (the compute streams in turn), copy out (s_out). Chunks
+        // touch disjoint frames of every buffer, and a chunk's tracking reads only input
+        // frames copied in before it, so consecutive chunks' kernels may overlap: the next
+        // chunks' launches fill the SMs while the previous one drains its last wave.
         e = cudaMemcpyAsync(const_cast<uint8_t *>(video->frames) + t0 * fstride, host_video->frames + t0 * fstride,
                             (size_t)(n * fstride), cudaMemcpyHostToDevice, ctx->s_in);
         if (e == cudaSuccess) e = cudaEventRecord(ein, ctx->s_in);
@@ -859,17 +869,18 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
         if (e != cudaSuccess) break;
         st = track_range(ctx, video, out, tracks, workspace, t0, t1, cs);
         if (st != KF_OK) return st;
-        if (bits) {
-            const int64_t words = (packed + 3) / 4;
-            const dim3 grid((unsigned)((words + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
-            pack_mask_kernel<<<grid, 256, 0, cs>>>(out->mask + t0 * mstride, out->mask_pitch, mstride, (int)video->W,
-                                                   (int)H, n, words, host_bits + t0 * host_out->mask_pitch,
-                                                   host_out->mask_pitch);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) break;
-        }
         e = cudaEventRecord(ecomp, cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ecomp, 0);
+        if (e == cudaSuccess && bits) {
+            // on the copy-out stream: its stores to host memory do not hold up the next
+            // chunks' kernels on the compute streams
+            const int64_t words = (packed + 3) / 4;
+            const dim3 grid((unsigned)((words + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
+            pack_mask_kernel<<<grid, 256, 0, ctx->s_out>>>(out->mask + t0 * mstride, out->mask_pitch, mstride,
+                                                           (int)video->W, (int)H, n, words,
+                                                           host_bits + t0 * host_out->mask_pitch, host_out->mask_pitch);
+            e = cudaGetLastError();
+        }
         auto d2h = [&](void *dst, const void *src, size_t bytes) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s_out);
         };

@@ -26,7 +26,7 @@ struct kf_ctx {
     std::vector<Timed> timed;
     std::vector<cudaEvent_t> spare_events;
     // kf_track_host: the copy-in, compute and copy-out streams and their event rings (owned)
-    static constexpr int N_RING = 2;
+    static constexpr int N_RING = 3;
     cudaStream_t s_in = nullptr, s_out = nullptr, s_comp[N_RING] = {};
     cudaEvent_t ev_in[N_RING] = {}, ev_comp[N_RING] = {}, ev_edge = nullptr;
 };

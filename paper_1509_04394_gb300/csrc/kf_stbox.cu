@@ -94,7 +94,9 @@ template <int N> __host__ __device__ constexpr int binom(int k)
 // frame per thread) and rows per work item of passes B and C.
 template <int X> struct BoxCfg {
     static constexpr int THREADS = X <= 16 ? 32 : X <= 32 ? 64 : X <= 48 ? 128 : X <= 64 ? 256 : 512;
-    static constexpr int SEG = X <= 16 ? 4 : 8;
+    // rows per work item: as many items as threads, about, in each pass
+    static constexpr int SEG_B = (X + 2 + THREADS / ((X + 4) / 4) - 1) / (THREADS / ((X + 4) / 4));
+    static constexpr int SEG_C = (X + THREADS / (X / 4) - 1) / (THREADS / (X / 4));
     static constexpr int SR = X + 4, SC = X + 8, GW = X + 4;  // staged rows / columns; G columns
     static constexpr int PAIRS = SR * (SC / 2);                 // pixel pairs of a staged frame
     static constexpr int STAGE_BYTES = SR * SC * 4;
@@ -106,11 +108,168 @@ template <int X> struct BoxCfg {
     template <int N> __host__ __device__ static constexpr int smem() { return off_bar<N>() + 8 + 128; }  // + base alignment slack
 };
 
+// Per-box constants shared by the passes.
+struct BoxPos {
+    int x0, y0;          // the box's first column / row
+    bool inner;          // the staged frame needs no clamping
+    int gr_lo, gr_hi;    // G plane rows inside the frame (G row j is image row y0-1+j)
+    int g_lo, g_hi;      // G plane columns inside the frame (G column j is image column x0-1+j)
+};
+
+// K1 + Kt: the staged frame (pl-th plane of the box) -> gray pairs -> the temporal binomial
+// into Z (output planes only); the thread's ring keeps the gray of its pairs' last N frames.
+template <int N, int X>
+__device__ __forceinline__ void convert_frame(const StParams &p, const BoxPos &b, const uint32_t *stage, uint32_t *ring,
+                                              int32_t *Z, int pl)
+{
+    using C = BoxCfg<X>;
+    constexpr int SC = C::SC;
+    const bool out_frame = pl >= N;
+    const int slot0 = pl % N;  // the ring slot of plane pl - N, overwritten by plane pl
+#pragma unroll 2
+    for (int i = threadIdx.x; i < C::PAIRS; i += C::THREADS) {
+        const int r = i / (SC / 2), c = 2 * (i - r * (SC / 2));
+        uint32_t a, bb;
+        if (b.inner) {
+            const uint2 w = *reinterpret_cast<const uint2 *>(stage + r * SC + c);
+            a = w.x;
+            bb = w.y;
+        } else {
+            const int ry = min(max(b.y0 - 2 + r, 0), p.H - 1) - (b.y0 - 2);
+            const int ca = min(max(b.x0 - 4 + c, 0), p.W - 1) - (b.x0 - 4);
+            const int cb = min(max(b.x0 - 3 + c, 0), p.W - 1) - (b.x0 - 4);
+            a = stage[ry * SC + ca];
+            bb = stage[ry * SC + cb];
+        }
+        const uint32_t g = gray_of(a) | (gray_of(bb) << 16);
+        if (out_frame) {
+            int lo = (int)(g & 0xffffu), hi = (int)(g >> 16);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {  // plane pl - N + k, weight C(N, k)
+                int sl = slot0 + k;
+                sl = sl >= N ? sl - N : sl;
+                const uint32_t q = ring[sl * C::PAIRS + i];
+                lo += binom<N>(k) * (int)(q & 0xffffu);
+                hi += binom<N>(k) * (int)(q >> 16);
+            }
+            *reinterpret_cast<int2 *>(Z + r * SC + c) = make_int2(lo, hi);
+        }
+        ring[slot0 * C::PAIRS + i] = g;
+    }
+}
+
+// pass B (K3): G over rows 0..X+1, columns 0..X+3 from Z (Z column j is image column
+// x0-4+j, Z row i image row y0-2+i); work items of SEG_B rows x 4 columns
+template <int X>
+__device__ __forceinline__ void pass_b(const int32_t *Z, int32_t *G)
+{
+    using C = BoxCfg<X>;
+    constexpr int SR = C::SR, SC = C::SC, GW = C::GW, SEG = C::SEG_B;
+    constexpr int GCOLS = GW / 4, SEGS = (X + 2 + SEG - 1) / SEG;
+    for (int it = threadIdx.x; it < GCOLS * SEGS; it += C::THREADS) {
+        const int g = 4 * (it % GCOLS), r0 = (it / GCOLS) * SEG;
+        int hm2[4] = {0, 0, 0, 0}, hm1[4] = {0, 0, 0, 0};
+#pragma unroll 1
+        for (int q = 0; q < SEG + 2; ++q) {
+            const int i = min(r0 + q, SR - 1);  // rows past the plane only feed unstored G rows
+            const int2 z01 = *reinterpret_cast<const int2 *>(Z + i * SC + g + 2);
+            const int4 z25 = *reinterpret_cast<const int4 *>(Z + i * SC + g + 4);
+            const int z[6] = {z01.x, z01.y, z25.x, z25.y, z25.z, z25.w};
+            int h[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) h[c] = z[c] + 2 * z[c + 1] + z[c + 2];
+            if (q >= 2 && r0 + q - 2 < X + 2) {
+                int4 o;
+                o.x = hm2[0] + 2 * hm1[0] + h[0];
+                o.y = hm2[1] + 2 * hm1[1] + h[1];
+                o.z = hm2[2] + 2 * hm1[2] + h[2];
+                o.w = hm2[3] + 2 * hm1[3] + h[3];
+                *reinterpret_cast<int4 *>(G + (r0 + q - 2) * GW + g) = o;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                hm2[c] = hm1[c];
+                hm1[c] = h[c];
+            }
+        }
+    }
+}
+
+// pass C (K4, K5): Sobel magnitude, threshold, mask and count of frame f over X * X
+// outputs; work items of SEG_C rows x 4 columns. K4 clamps its own input: G rows and
+// columns outside the frame read the nearest G inside it.
+template <int N, int X>
+__device__ __forceinline__ void pass_c(const StParams &p, const BoxPos &b, const int32_t *G, int f)
+{
+    using C = BoxCfg<X>;
+    constexpr int GW = C::GW, SEG = C::SEG_C;
+    constexpr int OCOLS = X / 4, SEGS = (X + SEG - 1) / SEG;
+    const int thr = 261120 << N;
+    int count = 0;
+    uint8_t *mframe = p.mask + (int64_t)f * p.mask_fstride;
+    for (int it = threadIdx.x; it < OCOLS * SEGS; it += C::THREADS) {
+        const int o = 4 * (it % OCOLS), r0 = (it / OCOLS) * SEG;
+        const bool clamp_cols = o < b.g_lo || o + 5 > b.g_hi;
+        int dxm2[4] = {0, 0, 0, 0}, dxm1[4] = {0, 0, 0, 0}, sxm2[4] = {0, 0, 0, 0}, sxm1[4] = {0, 0, 0, 0};
+#pragma unroll 1
+        for (int q = 0; q < SEG + 2; ++q) {  // G row r0+q; output row r0+q-2 centred on r0+q-1
+            const int32_t *grow = G + min(max(r0 + q, b.gr_lo), b.gr_hi) * GW;
+            int v[6];
+            if (!clamp_cols) {
+                const int4 a = *reinterpret_cast<const int4 *>(grow + o);
+                const int2 c2 = *reinterpret_cast<const int2 *>(grow + o + 4);
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = c2.x; v[5] = c2.y;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 6; ++j) v[j] = grow[min(max(o + j, b.g_lo), b.g_hi)];
+            }
+            int dx[4], sx[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                dx[c] = v[c + 2] - v[c];
+                sx[c] = v[c] + 2 * v[c + 1] + v[c + 2];
+            }
+            const int r = r0 + q - 2;
+            if (q >= 2 && r < X) {
+                uint32_t bits = 0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int gx = dxm2[c] + 2 * dxm1[c] + dx[c];
+                    const int gy = sx[c] - sxm2[c];
+                    bits |= (uint32_t)(abs(gx) + abs(gy) > thr) << (8 * c);
+                }
+                const int yy = b.y0 + r, xx = b.x0 + o;
+                if (yy < p.H && xx < p.W) {
+                    uint8_t *dst = mframe + (int64_t)yy * p.mask_pitch + xx;
+                    if (xx + 4 <= p.W) {
+                        *reinterpret_cast<uint32_t *>(dst) = bits;
+                    } else {
+                        bits &= (1u << (8 * (p.W - xx))) - 1u;
+                        for (int c = 0; c < p.W - xx; ++c) dst[c] = (uint8_t)(bits >> (8 * c));
+                    }
+                    count += __popc(bits);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                dxm2[c] = dxm1[c];
+                dxm1[c] = dx[c];
+                sxm2[c] = sxm1[c];
+                sxm1[c] = sx[c];
+            }
+        }
+    }
+    count = __reduce_add_sync(0xffffffffu, count);
+    if ((threadIdx.x & 31) == 0 && count) atomicAdd(p.counts + f, count);
+}
+
+// Two barriers per frame: phase A runs pass C of the previous output frame, then waits
+// for the staged frame and converts it; phase B issues the next frame's copy and runs
+// pass B. The copy of frame pl+1 thus overlaps pass B of pl and pass C of pl.
 template <int N, int X>
 __global__ void __launch_bounds__(BoxCfg<X>::THREADS) st_box_kernel(const __grid_constant__ StParams p)
 {
     using C = BoxCfg<X>;
-    constexpr int SR = C::SR, SC = C::SC, GW = C::GW, TH = C::THREADS, SEG = C::SEG;
     extern __shared__ __align__(128) unsigned char st_smem[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)st_smem + 127) & ~(uintptr_t)127);
     const uint32_t *stage = reinterpret_cast<const uint32_t *>(base);
@@ -119,173 +278,51 @@ __global__ void __launch_bounds__(BoxCfg<X>::THREADS) st_box_kernel(const __grid
     uint32_t *ring = reinterpret_cast<uint32_t *>(base + C::OFF_RING);
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + C::template off_bar<N>());
 
-    const int b = blockIdx.x;
     const int nb_xy = p.boxes_x * p.boxes_y;
-    const int bt = b / nb_xy, bxy = b - bt * nb_xy;
+    const int bt = blockIdx.x / nb_xy, bxy = blockIdx.x - bt * nb_xy;
     const int by = bxy / p.boxes_x, bx = bxy - by * p.boxes_x;
-    const int x0 = bx * X, y0 = by * X, t0 = bt * p.t;
+    BoxPos b;
+    b.x0 = bx * X;
+    b.y0 = by * X;
+    const int t0 = bt * p.t;
     const int t_end = min(t0 + p.t, p.T);
     const int n_planes = t_end - (t0 - N);  // the N frames before the box, then its own
-    const int tid = threadIdx.x;
+    b.inner = b.x0 - 4 >= 0 && b.x0 + X + 4 <= p.W && b.y0 - 2 >= 0 && b.y0 + X + 2 <= p.H;
+    b.gr_lo = b.y0 == 0 ? 1 : 0;
+    b.gr_hi = min(X + 1, p.H - b.y0);
+    b.g_lo = b.x0 == 0 ? 1 : 0;
+    b.g_hi = min(X + 1, p.W - b.x0);
 
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         bar_init(bar);
         bar_expect(bar, C::STAGE_BYTES);
-        tma_frame(base, &p.tmap, x0 - 4, y0 - 2, max(t0 - N, 0), bar);
+        tma_frame(base, &p.tmap, b.x0 - 4, b.y0 - 2, max(t0 - N, 0), bar);
     }
     __syncthreads();
 
-    const bool inner = x0 - 4 >= 0 && x0 + X + 4 <= p.W && y0 - 2 >= 0 && y0 + X + 2 <= p.H;
-    const int thr = 261120 << N;
-    // G plane rows / columns that lie inside the frame (G row / column j is image row
-    // y0-1+j / column x0-1+j): K4 clamps its own input to them
-    const int gr_lo = y0 == 0 ? 1 : 0, gr_hi = min(X + 1, p.H - y0);
-    const int g_lo = x0 == 0 ? 1 : 0, g_hi = min(X + 1, p.W - x0);
     // The pixel pairs a thread converts are the same in every frame (pair i by thread
     // i % THREADS), so the gray values of their N previous frames -- the temporal halo --
-    // sit in a ring that only that thread touches: pair i of frame q in ring[(q % N) *
+    // sit in a ring that only that thread touches: pair i of plane q in ring[(q % N) *
     // PAIRS + i]. No barrier guards it.
     for (int pl = 0; pl < n_planes; ++pl) {
+        if (pl > N) pass_c<N, X>(p, b, G, t0 - N + pl - 1);
         const bool ok = bar_wait(bar, (unsigned)(pl & 1));
+        if (ok) convert_frame<N, X>(p, b, stage, ring, Z, pl);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
+            if (threadIdx.x == 0) {
                 atomicOr(p.err, ST_DEVERR_TIMEOUT);
                 bar_wait(bar, (unsigned)(pl & 1));  // the copy in flight, once more (bounded)
             }
             return;
         }
-        // K1 + Kt: the staged frame -> gray pairs -> the temporal binomial into Z
-        const bool out_frame = pl >= N;
-        const int slot0 = pl % N;  // the ring slot of plane pl - N, overwritten by plane pl
-#pragma unroll 2
-        for (int i = tid; i < C::PAIRS; i += TH) {
-            const int r = i / (SC / 2), c = 2 * (i - r * (SC / 2));
-            uint32_t a, bb;
-            if (inner) {
-                const uint2 w = *reinterpret_cast<const uint2 *>(stage + r * SC + c);
-                a = w.x;
-                bb = w.y;
-            } else {
-                const int ry = min(max(y0 - 2 + r, 0), p.H - 1) - (y0 - 2);
-                const int ca = min(max(x0 - 4 + c, 0), p.W - 1) - (x0 - 4);
-                const int cb = min(max(x0 - 3 + c, 0), p.W - 1) - (x0 - 4);
-                a = stage[ry * SC + ca];
-                bb = stage[ry * SC + cb];
-            }
-            const uint32_t g = gray_of(a) | (gray_of(bb) << 16);
-            if (out_frame) {
-                int lo = (int)(g & 0xffffu), hi = (int)(g >> 16);
-#pragma unroll
-                for (int k = 0; k < N; ++k) {  // plane pl - N + k, weight C(N, k)
-                    int sl = slot0 + k;
-                    sl = sl >= N ? sl - N : sl;
-                    const uint32_t q = ring[sl * C::PAIRS + i];
-                    lo += binom<N>(k) * (int)(q & 0xffffu);
-                    hi += binom<N>(k) * (int)(q >> 16);
-                }
-                *reinterpret_cast<int2 *>(Z + r * SC + c) = make_int2(lo, hi);
-            }
-            ring[slot0 * C::PAIRS + i] = g;
-        }
-        __syncthreads();
-        if (tid == 0 && pl + 1 < n_planes) {
+        if (threadIdx.x == 0 && pl + 1 < n_planes) {
             bar_expect(bar, C::STAGE_BYTES);
-            tma_frame(base, &p.tmap, x0 - 4, y0 - 2, max(t0 - N + pl + 1, 0), bar);
+            tma_frame(base, &p.tmap, b.x0 - 4, b.y0 - 2, max(t0 - N + pl + 1, 0), bar);
         }
-        if (!out_frame) continue;  // a frame of the temporal halo only
-        const int f = t0 - N + pl;
-
-        // pass B (K3): G over rows 0..X+1, columns 0..X+3 from Z (Z column j is image
-        // column x0-4+j, Z row i image row y0-2+i)
-        constexpr int GCOLS = GW / 4, SEGS_B = (X + 2 + SEG - 1) / SEG;
-        for (int it = tid; it < GCOLS * SEGS_B; it += TH) {
-            const int g = 4 * (it % GCOLS), r0 = (it / GCOLS) * SEG;
-            int hm2[4] = {0, 0, 0, 0}, hm1[4] = {0, 0, 0, 0};
-#pragma unroll 1
-            for (int q = 0; q < SEG + 2; ++q) {
-                const int i = min(r0 + q, SR - 1);  // rows past the plane only feed unstored G rows
-                const int2 z01 = *reinterpret_cast<const int2 *>(Z + i * SC + g + 2);
-                const int4 z25 = *reinterpret_cast<const int4 *>(Z + i * SC + g + 4);
-                const int z[6] = {z01.x, z01.y, z25.x, z25.y, z25.z, z25.w};
-                int h[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) h[c] = z[c] + 2 * z[c + 1] + z[c + 2];
-                if (q >= 2 && r0 + q - 2 < X + 2) {
-                    int4 o;
-                    o.x = hm2[0] + 2 * hm1[0] + h[0];
-                    o.y = hm2[1] + 2 * hm1[1] + h[1];
-                    o.z = hm2[2] + 2 * hm1[2] + h[2];
-                    o.w = hm2[3] + 2 * hm1[3] + h[3];
-                    *reinterpret_cast<int4 *>(G + (r0 + q - 2) * GW + g) = o;
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    hm2[c] = hm1[c];
-                    hm1[c] = h[c];
-                }
-            }
-        }
+        if (pl >= N) pass_b<X>(Z, G);
         __syncthreads();
-
-        // pass C (K4, K5): Sobel magnitude, threshold, mask and count over X * X outputs
-        constexpr int OCOLS = X / 4, SEGS_C = (X + SEG - 1) / SEG;
-        int count = 0;
-        uint8_t *mframe = p.mask + (int64_t)f * p.mask_fstride;
-        for (int it = tid; it < OCOLS * SEGS_C; it += TH) {
-            const int o = 4 * (it % OCOLS), r0 = (it / OCOLS) * SEG;
-            const bool clamp_cols = o < g_lo || o + 5 > g_hi;
-            int dxm2[4] = {0, 0, 0, 0}, dxm1[4] = {0, 0, 0, 0}, sxm2[4] = {0, 0, 0, 0}, sxm1[4] = {0, 0, 0, 0};
-#pragma unroll 1
-            for (int q = 0; q < SEG + 2; ++q) {  // G row r0+q; output row r0+q-2 centred on r0+q-1
-                const int32_t *grow = G + min(max(r0 + q, gr_lo), gr_hi) * GW;
-                int v[6];
-                if (!clamp_cols) {
-                    const int4 a = *reinterpret_cast<const int4 *>(grow + o);
-                    const int2 c2 = *reinterpret_cast<const int2 *>(grow + o + 4);
-                    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = c2.x; v[5] = c2.y;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) v[j] = grow[min(max(o + j, g_lo), g_hi)];
-                }
-                int dx[4], sx[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    dx[c] = v[c + 2] - v[c];
-                    sx[c] = v[c] + 2 * v[c + 1] + v[c + 2];
-                }
-                const int r = r0 + q - 2;
-                if (q >= 2 && r < X) {
-                    uint32_t bits = 0;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int gx = dxm2[c] + 2 * dxm1[c] + dx[c];
-                        const int gy = sx[c] - sxm2[c];
-                        bits |= (uint32_t)(abs(gx) + abs(gy) > thr) << (8 * c);
-                    }
-                    const int yy = y0 + r, xx = x0 + o;
-                    if (yy < p.H && xx < p.W) {
-                        uint8_t *dst = mframe + (int64_t)yy * p.mask_pitch + xx;
-                        if (xx + 4 <= p.W) {
-                            *reinterpret_cast<uint32_t *>(dst) = bits;
-                        } else {
-                            bits &= (1u << (8 * (p.W - xx))) - 1u;
-                            for (int c = 0; c < p.W - xx; ++c) dst[c] = (uint8_t)(bits >> (8 * c));
-                        }
-                        count += __popc(bits);
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    dxm2[c] = dxm1[c];
-                    dxm1[c] = dx[c];
-                    sxm2[c] = sxm1[c];
-                    sxm1[c] = sx[c];
-                }
-            }
-        }
-        count = __reduce_add_sync(0xffffffffu, count);
-        if ((tid & 31) == 0 && count) atomicAdd(p.counts + f, count);
     }
+    if (n_planes > N) pass_c<N, X>(p, b, G, t_end - 1);
 }
 
 // the supported box sides and the kernel of (n, x); nullptr if not supported
