@@ -771,6 +771,70 @@ def run_costmodel(args):
           flush=True)
 
 
+def run_dagplan(args):
+    """Recompute instead of store: on the learned-cost-model workload (400 random DAGs,
+    1080x1920, groups timed on a prefix of the video, MLP trained on 300 DAGs), each of
+    the 100 held-out DAGs is planned by the MLP over contiguous partitions and over plans
+    with inlined (recomputed) nodes; both plans and the measured-best contiguous partition
+    run end to end (CUDA events), and the plans' bits are compared."""
+    import torch
+    from paper_1509_04394_gb300 import build as kbuild
+    from paper_1509_04394_gb300 import costmodel as cm
+    from paper_1509_04394_gb300 import kfuse as K
+    from synth import dags as sd
+    kbuild.build()
+    dev = torch.device("cuda:0")
+    W, H, T = 1920, 1080, args.cm_frames
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=5), pitch=W)
+    f = torch.from_numpy(fr).to(dev)
+    ctx = K.kf_create(0)
+    meas = [cm.measure(ctx, sd.to_array(sd.random_dag(4000 + s)), f, W, 4000 + s) for s in range(400)]
+    X, y = cm.dataset(meas[:300])
+    K.kf_costmodel_train(ctx, X, y, steps=4000, lr=3e-3, seed=1)
+    out_a = torch.empty((T, H, W), dtype=torch.float32, device=dev)
+    out_b = torch.empty((T, H, W), dtype=torch.float32, device=dev)
+
+    def run_ms(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rows = []
+    for m in meas[300:]:
+        dag = K.kf_dag_create(ctx, m.rows)
+        ws = torch.empty(K.kf_dag_workspace_bytes(dag, W, H, T), dtype=torch.uint8, device=dev)
+        plans = cm.plan_costs(ctx, m)
+        cuts_x, xm, pred_x = K.kf_dag_plan_recompute(dag, W, H, T, model=ctx)
+        t_best = run_ms(lambda: K.kf_dag_run(dag, plans["measured"], f, W, out_a, ws))
+        t_mlp = run_ms(lambda: K.kf_dag_run(dag, plans["mlp"], f, W, out_a, ws))
+        t_x = run_ms(lambda: K.kf_dag_run_x(dag, cuts_x, xm, f, W, out_b, ws))
+        rows.append({"seed": m.seed, "n": m.n, "inlined": bin(xm).count("1"), "best_contiguous_ms": t_best,
+                     "mlp_contiguous_ms": t_mlp, "mlp_recompute_ms": t_x, "same_bits": bool(torch.equal(out_a, out_b))})
+        K.kf_dag_destroy(dag)
+        del ws
+    changed = [r for r in rows if r["inlined"]]
+    r_x = np.array([r["mlp_recompute_ms"] / r["mlp_contiguous_ms"] for r in rows])
+    r_best = np.array([r["mlp_recompute_ms"] / r["best_contiguous_ms"] for r in rows])
+    r_c = np.array([r["mlp_recompute_ms"] / r["mlp_contiguous_ms"] for r in changed]) if changed else np.array([1.0])
+    print(json.dumps({"workload": f"100 held-out random DAGs (12-24 stages), 1080x1920 u8, {T} frames",
+                      "dags": len(rows), "plans_with_inlined_nodes": len(changed),
+                      "mean_inlined_nodes_where_used": float(np.mean([r["inlined"] for r in changed])) if changed else 0,
+                      "recompute_over_contiguous_mlp": {"mean": float(r_x.mean()), "median": float(np.median(r_x))},
+                      "recompute_over_contiguous_mlp_where_inlined": {"mean": float(r_c.mean()),
+                                                                      "median": float(np.median(r_c)),
+                                                                      "min": float(r_c.min()), "max": float(r_c.max())},
+                      "recompute_over_measured_best_contiguous": {"mean": float(r_best.mean()),
+                                                                  "median": float(np.median(r_best)),
+                                                                  "faster": int(np.sum(r_best < 1.0))},
+                      "all_bits_equal": all(r["same_bits"] for r in rows), "per_dag": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -789,6 +853,7 @@ def main():
     ap.add_argument("--pc-frames", type=int, default=1000, help="frames per size (--pchain)")
     ap.add_argument("--pc-size", type=int, default=0, help="one square size instead of the three (--pchain)")
     ap.add_argument("--pc-once", action="store_true", help="run each partition once, untimed (profiler case)")
+    ap.add_argument("--dagplan", action="store_true", help="recompute-vs-store DAG plans (learned costs)")
     ap.add_argument("--stbox", action="store_true", help="spatio-temporal boxes against Eq. 6 (uses --pc-frames, "
                     "--pc-size, --pc-once)")
     args = ap.parse_args()
@@ -800,6 +865,8 @@ def main():
         run_pchain(args)
     elif args.stbox:
         run_stbox(args)
+    elif args.dagplan:
+        run_dagplan(args)
     elif args.costmodel:
         run_costmodel(args)
     elif args.batch48:

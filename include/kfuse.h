@@ -337,6 +337,35 @@ kf_status kf_dag_run(kf_dag *dag, uint32_t cuts, const kf_video *video, float *o
 kf_status kf_dag_time_groups(kf_dag *dag, const kf_video *video, float *out, int64_t out_pitch, void *workspace,
                              size_t workspace_bytes, int reps, void *stream, float *ms);
 
+/* Plans beyond contiguous partitions: recompute instead of store (the ordering
+ * restriction of Sec. VII (a) relaxed for nodes that are cheaper to recompute than to
+ * read back). A plan is (cuts, inline_mask): the contiguous ranges of `cuts`, and the
+ * inlined nodes (bit j-1 = node j; never the output node n) that are never stored -- every
+ * group that needs an inlined node computes it itself, with its inlined inputs, from the
+ * stored maps and the frame. A group thus computes its range (less inlined nodes only
+ * later groups need) plus the inlined nodes it needs, and stores the output and every
+ * range node not inlined from which a path through inlined nodes reaches a later stage.
+ * With inline_mask 0 this is the contiguous partition of kf_dag_run. */
+#define KF_DAG_EXACT_INLINE 12
+/* Sec. VI-D traffic of a plan over the executor's 32 x 16 tile (as kf_dag_group_info)
+ * and the largest shared-memory bytes per block of its groups (max_onchip may be NULL). */
+kf_status kf_dag_xplan_traffic(const kf_dag *dag, uint32_t cuts, uint32_t inline_mask, int64_t W, int64_t H, int64_t T,
+                               double *bytes, double *max_onchip);
+/* The cheapest plan whose groups fit onchip_limit bytes of shared memory per block (<= 0
+ * or above the executor's 200 KiB: the executor's limit). Cost of a group: its traffic
+ * (model NULL), or the learned model's predicted time from the features of the group's
+ * own program (`model` a context whose cost model is trained or set; else KF_ESTATE).
+ * Search: for every inline set the exact dynamic program over cut points (a group's cost
+ * depends only on its range and the inline set); over inline sets exhaustively when the
+ * DAG has at most KF_DAG_EXACT_INLINE + 1 stages, else by hill climbing over single-node
+ * toggles from the best contiguous partition (never worse than it). *cost: bytes or ms.
+ * KF_ESMEM if nothing fits. */
+kf_status kf_dag_plan_recompute(const kf_dag *dag, int64_t W, int64_t H, int64_t T, double onchip_limit, kf_ctx *model,
+                                uint32_t *cuts, uint32_t *inline_mask, double *cost);
+/* Run plan (cuts, inline_mask) on `stream`, like kf_dag_run. */
+kf_status kf_dag_run_x(kf_dag *dag, uint32_t cuts, uint32_t inline_mask, const kf_video *video, float *out,
+                       int64_t out_pitch, void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------------ learned cost model */
 /* A 3-layer MLP (width 64, ReLU, FP32) predicting a fused group's runtime from its
  * KF_NFEAT features, in place of the execution-time estimate C_i of the partition model

@@ -18,6 +18,13 @@ group member computes, read by a member) its tile grown by its halo h_e on every
 4 bytes per stored node. Halos: a stored node needs 0; a member or external input needs
 the largest (halo of a consumer member + that consumer's radius) over its consumers in
 the group; a member no stored node depends on is not computed.
+
+On-chip bytes of a group (the executor's shared memory per block, the feasibility test
+of Sec. VII (c)): the group's tiles are held in equal slots of (TX + 2 h_max)(TY + 2
+h_max) floats, h_max the largest halo in the group; the external inputs are loaded
+first (in node order), then the computed members run in node order, each taking a free
+slot (or a new one) for its tile, and an input's slot is freed after its last consumer
+in the group has taken its own; the group needs as many slots as were ever taken.
 """
 from __future__ import annotations
 
@@ -117,6 +124,32 @@ def group_traffic(rows, a: int, b: int, X: set[int]) -> tuple[float, set[int], d
     t = sum((TX + 2 * h) * (TY + 2 * h) * (1 if e == 0 else 4) for e, h in ext.items())
     t += TX * TY * 4 * len(outs)
     return float(t), outs, {**halo, **{e: h for e, h in ext.items()}}
+
+
+def onchip_bytes(rows, a: int, b: int, X: set[int]) -> int:
+    """Shared-memory bytes per block of the group of range [a, b]."""
+    _, _, halo = group_traffic(rows, a, b, X)
+    members = group_members(rows, a, b, X)
+    live = {j for j in members if halo[j] >= 0}
+    ext = sorted(e for e in halo if e not in members)
+    cons = consumers(rows)
+    last = {}
+    for j in list(ext) + sorted(live):
+        cs = [c for c in cons[j] if c in live]
+        if cs:
+            last[j] = max(cs)
+    hmax = max([0] + [halo[j] for j in list(ext) + sorted(live)])
+    free, slots, taken = [], {}, 0
+    for e in ext:
+        slots[e] = free.pop() if free else taken
+        taken = max(taken, slots[e] + 1)
+    for j in sorted(live):
+        slots[j] = free.pop() if free else taken
+        taken = max(taken, slots[j] + 1)
+        for i in inputs(rows, j):
+            if last.get(i) == j and i in slots:
+                free.append(slots.pop(i))
+    return taken * (TX + 2 * hmax) * (TY + 2 * hmax) * 4
 
 
 def valid(rows, cuts: int, X: set[int]) -> bool:

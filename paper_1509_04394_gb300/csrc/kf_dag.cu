@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/kfuse.h"
@@ -148,29 +149,73 @@ struct GroupPlan {
 
 int stage_radius(const kf_gstage &s) { return s.kind == KF_G_STENCIL ? s.radius : (s.kind == KF_G_MAX3 ? 1 : 0); }
 
-// group of nodes [a, b] (1-based, inclusive)
-GroupPlan plan_group(const kf_dag *d, int a, int b)
+// Node masks: bit j-1 stands for node j (1..n).
+inline bool has(uint32_t m, int j) { return j >= 1 && (m >> (j - 1) & 1u); }
+uint32_t range_mask(int a, int b) { return (b >= 32 ? ~0u : ((1u << b) - 1u)) & ~((1u << (a - 1)) - 1u); }
+
+// The group of range [a, b] when the nodes of X are inlined (recomputed by every group
+// that needs them instead of being stored): the range's nodes that are not inlined or
+// are needed by a range node, plus, transitively, the inlined inputs of its members.
+uint32_t members_of(const kf_dag *d, int a, int b, uint32_t X)
+{
+    uint32_t m = 0;
+    for (int j = b; j >= a; --j) {
+        bool need = !has(X, j);
+        for (int c : d->cons[j]) need = need || has(m, c);
+        if (need) m |= 1u << (j - 1);
+    }
+    for (int j = b; j >= 1; --j) {  // inputs are lower-numbered: one descending sweep closes the set
+        if (!has(m, j)) continue;
+        const kf_gstage &s = d->st[j - 1];
+        for (int in : {s.in1, s.kind == KF_G_PRODUCT ? s.in2 : 0})
+            if (in >= 1 && has(X, in)) m |= 1u << (in - 1);
+    }
+    return m;
+}
+
+// The range nodes the group stores: the output, and every node not inlined from which a
+// path through inlined nodes reaches a stage after the range.
+uint32_t stores_of(const kf_dag *d, int a, int b, uint32_t X)
+{
+    const int n = d->n;
+    // reach[j]: the highest stage reachable from j through inlined intermediates
+    std::vector<int> reach(n + 1, 0);
+    for (int j = n; j >= 1; --j) {
+        int r = 0;
+        for (int c : d->cons[j]) r = std::max(r, has(X, c) ? std::max(c, reach[c]) : c);
+        reach[j] = r;
+    }
+    uint32_t m = 0;
+    for (int j = a; j <= b; ++j)
+        if (j == n || (!has(X, j) && reach[j] > b)) m |= 1u << (j - 1);
+    return m;
+}
+
+// program of a group computing the nodes of `members` and storing those of `outs`
+GroupPlan plan_members(const kf_dag *d, uint32_t members, uint32_t outs)
 {
     GroupPlan g;
     const int n = d->n;
     g.halo.assign(n + 1, -1);
-    auto is_output = [&](int j) {
-        if (j == n) return true;
+    int top = 0;
+    for (int j = n; j >= 1; --j)
+        if (has(members, j)) {
+            top = j;
+            break;
+        }
+    for (int j = top; j >= 1; --j) {
+        if (!has(members, j)) continue;
+        int h = has(outs, j) ? 0 : -1;
         for (int c : d->cons[j])
-            if (c > b) return true;
-        return false;
-    };
-    for (int j = b; j >= a; --j) {
-        int h = is_output(j) ? 0 : -1;
-        for (int c : d->cons[j])
-            if (c >= a && c <= b && g.halo[c] >= 0) h = std::max(h, g.halo[c] + stage_radius(d->st[c - 1]));
+            if (has(members, c) && g.halo[c] >= 0) h = std::max(h, g.halo[c] + stage_radius(d->st[c - 1]));
         g.halo[j] = h;
-        if (is_output(j)) g.outs.push_back(j);
+        if (has(outs, j)) g.outs.push_back(j);
     }
-    for (int e = 0; e < a; ++e) {
+    for (int e = 0; e < top; ++e) {
+        if (has(members, e)) continue;
         int h = -1;
         for (int c : d->cons[e])
-            if (c >= a && c <= b && g.halo[c] >= 0) h = std::max(h, g.halo[c] + stage_radius(d->st[c - 1]));
+            if (has(members, c) && g.halo[c] >= 0) h = std::max(h, g.halo[c] + stage_radius(d->st[c - 1]));
         if (h >= 0) {
             g.ext.push_back(e);
             g.ext_h.push_back(h);
@@ -179,11 +224,11 @@ GroupPlan plan_group(const kf_dag *d, int a, int b)
     }
     // last consumer in the group of every live node
     std::vector<int> last(n + 1, -1);
-    for (int j = 0; j <= b; ++j)
+    for (int j = 0; j <= top; ++j)
         for (int c : d->cons[j])
-            if (c >= a && c <= b && g.halo[c] >= 0) last[j] = std::max(last[j], c);
+            if (has(members, c) && g.halo[c] >= 0) last[j] = std::max(last[j], c);
     int hmax = 0;
-    for (int j = 0; j <= b; ++j) hmax = std::max(hmax, g.halo[j]);
+    for (int j = 0; j <= top; ++j) hmax = std::max(hmax, g.halo[j]);
     const int slot_floats = (DAG_TX + 2 * hmax) * (DAG_TY + 2 * hmax);
     std::vector<int> slot_of(n + 1, -1);
     std::vector<int> free_slots;
@@ -205,8 +250,8 @@ GroupPlan plan_group(const kf_dag *d, int a, int b)
         op.halo = g.ext_h[i];
         op.out_slot = slot_of[op.node] = take();
     }
-    for (int j = a; j <= b; ++j) {
-        if (g.halo[j] < 0) continue;  // dead node: nothing in or after the group reads it
+    for (int j = 1; j <= top; ++j) {
+        if (!has(members, j) || g.halo[j] < 0) continue;  // not a member, or nothing stored depends on it
         const kf_gstage &s = d->st[j - 1];
         DagOp &op = g.prog.ops[nops++];
         op = DagOp{};
@@ -220,7 +265,7 @@ GroupPlan plan_group(const kf_dag *d, int a, int b)
         op.in1_halo = g.halo[s.in1];
         op.in2_slot = s.kind == KF_G_PRODUCT ? slot_of[s.in2] : 0;
         op.in2_halo = s.kind == KF_G_PRODUCT ? g.halo[s.in2] : 0;
-        op.store = is_output(j) ? 1 : 0;
+        op.store = has(outs, j) ? 1 : 0;
         op.out_slot = slot_of[j] = take();
         // free the inputs whose last in-group consumer is this stage (after writing j's slot)
         for (int in : {s.in1, s.kind == KF_G_PRODUCT ? s.in2 : -1})
@@ -236,6 +281,18 @@ GroupPlan plan_group(const kf_dag *d, int a, int b)
     g.smem_bytes = (double)n_slots * slot_floats * sizeof(float);
     g.feasible = g.smem_bytes <= DAG_SMEM_LIMIT;
     return g;
+}
+
+// group of nodes [a, b] (1-based, inclusive) of a contiguous partition
+GroupPlan plan_group(const kf_dag *d, int a, int b) { return plan_members(d, range_mask(a, b), stores_of(d, a, b, 0)); }
+
+// Sec. VI-D over the executor's tile: halo'd input boxes in, stored maps out (bytes per tile)
+double tile_traffic(const GroupPlan &g)
+{
+    double per_box = 0;
+    for (size_t i = 0; i < g.ext.size(); ++i)
+        per_box += (DAG_TX + 2.0 * g.ext_h[i]) * (DAG_TY + 2.0 * g.ext_h[i]) * (g.ext[i] == 0 ? 1.0 : 4.0);
+    return per_box + (double)DAG_TX * DAG_TY * 4.0 * g.outs.size();
 }
 
 int group_index(int n, int a0, int b0) { return a0 * n - a0 * (a0 - 1) / 2 + (b0 - a0); }  // 0-based first/last
@@ -270,14 +327,13 @@ kf_status launch_plan(const GroupPlan &g, const kf_video *v, float *maps, const 
 }
 
 // features of a fused group for the learned cost model (per output pixel where relevant)
-void features(const kf_dag *d, int a, int b, int64_t W, int64_t H, int64_t T, float *f)
+void features_of(const kf_dag *d, const GroupPlan &g, uint32_t members, int64_t W, int64_t H, int64_t T, float *f)
 {
-    const GroupPlan g = plan_group(d, a, b);
     const double tile = (double)DAG_TX * DAG_TY;
     int n_st = 0, n_sten = 0, sum_r = 0, hmax = 0;
     double compute = 0;
-    for (int j = a; j <= b; ++j) {
-        if (g.halo[j] < 0) continue;
+    for (int j = 1; j <= d->n; ++j) {
+        if (!has(members, j) || g.halo[j] < 0) continue;
         const kf_gstage &s = d->st[j - 1];
         const int r = stage_radius(s);
         ++n_st;
@@ -305,6 +361,84 @@ void features(const kf_dag *d, int a, int b, int64_t W, int64_t H, int64_t T, fl
     f[10] = (float)g.outs.size();
     f[11] = (float)std::log((double)W * H * T);
 }
+
+void features(const kf_dag *d, int a, int b, int64_t W, int64_t H, int64_t T, float *f)
+{
+    features_of(d, plan_group(d, a, b), range_mask(a, b), W, H, T, f);
+}
+
+// traffic (bytes) of the plan (cuts, X) and the largest on-chip bytes of its groups
+double xplan_traffic(const kf_dag *d, uint32_t cuts, uint32_t X, double tiles, double *max_onchip)
+{
+    double t = 0, m = 0;
+    int a = 1;
+    for (int b = 1; b <= d->n; ++b) {
+        if (b < d->n && !(cuts >> (b - 1) & 1)) continue;
+        const GroupPlan g = plan_members(d, members_of(d, a, b, X), stores_of(d, a, b, X));
+        t += tiles * tile_traffic(g);
+        m = std::max(m, g.smem_bytes);
+        a = b + 1;
+    }
+    *max_onchip = m;
+    return t;
+}
+
+// Cost of a group under the planner's model: Sec. VI-D traffic, or the learned model's
+// predicted time (memoised per group program: members and stores fix it).
+struct PlanCost {
+    const kf_dag *d;
+    int64_t W, H, T;
+    double tiles, limit;
+    kf_ctx *model;  // nullptr: traffic
+    std::unordered_map<uint64_t, double> memo;
+    double operator()(int a, int b, uint32_t X)
+    {
+        const uint32_t mem = members_of(d, a, b, X), outs = stores_of(d, a, b, X);
+        const uint64_t key = (uint64_t)mem << 32 | outs;
+        auto it = memo.find(key);
+        if (it != memo.end()) return it->second;
+        const GroupPlan g = plan_members(d, mem, outs);
+        double c = INFINITY;
+        if (g.smem_bytes <= limit) {
+            if (!model) {
+                c = tiles * tile_traffic(g);
+            } else {
+                float f[KF_NFEAT], ms = 0.f;
+                features_of(d, g, mem, W, H, T, f);
+                if (kf_costmodel_predict(model, f, 1, &ms) == KF_OK) c = ms;
+            }
+        }
+        memo.emplace(key, c);
+        return c;
+    }
+};
+
+// The cheapest contiguous partition for a fixed inline set X (each group's cost depends
+// only on its range and X, so the dynamic program over cut points is exact).
+double best_cuts(const kf_dag *d, uint32_t X, PlanCost &cost, uint32_t *cuts)
+{
+    const int n = d->n;
+    std::vector<double> best(n + 1, INFINITY);
+    std::vector<int> from(n + 1, -1);
+    best[0] = 0;
+    for (int j = 1; j <= n; ++j)
+        for (int i = 0; i < j; ++i) {
+            if (!std::isfinite(best[i])) continue;
+            const double c = best[i] + cost(i + 1, j, X);
+            if (c < best[j]) {
+                best[j] = c;
+                from[j] = i;
+            }
+        }
+    uint32_t m = 0;
+    if (std::isfinite(best[n]))
+        for (int j = n; j > 0; j = from[j])
+            if (from[j] > 0) m |= 1u << (from[j] - 1);
+    *cuts = m;
+    return best[n];
+}
+
+bool valid_inline(const kf_dag *d, uint32_t X) { return d->n >= 32 || (X >> (d->n - 1)) == 0; }
 
 }  // namespace
 
@@ -349,14 +483,7 @@ kf_status kf_dag_group_info(const kf_dag *d, int first, int last, int64_t W, int
     const GroupPlan g = plan_group(d, first + 1, last + 1);
     if (features_out) features(d, first + 1, last + 1, W, H, T, features_out);
     if (onchip_bytes) *onchip_bytes = g.smem_bytes;
-    if (traffic_bytes) {  // Sec. VI-D over the executor's tile: halo'd input boxes in, outputs out
-        const double boxes = (double)W * H * T / ((double)DAG_TX * DAG_TY);
-        double per_box = 0;
-        for (size_t i = 0; i < g.ext.size(); ++i)
-            per_box += (DAG_TX + 2.0 * g.ext_h[i]) * (DAG_TY + 2.0 * g.ext_h[i]) * (g.ext[i] == 0 ? 1.0 : 4.0);
-        per_box += (double)DAG_TX * DAG_TY * 4.0 * g.outs.size();
-        *traffic_bytes = boxes * per_box;
-    }
+    if (traffic_bytes) *traffic_bytes = (double)W * H * T / ((double)DAG_TX * DAG_TY) * tile_traffic(g);
     return KF_OK;
 }
 
@@ -455,6 +582,102 @@ kf_status kf_dag_time_groups(kf_dag *d, const kf_video *v, float *out, int64_t o
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+}
+
+kf_status kf_dag_xplan_traffic(const kf_dag *d, uint32_t cuts, uint32_t inline_mask, int64_t W, int64_t H, int64_t T,
+                               double *bytes, double *max_onchip)
+{
+    if (!d || !bytes || W <= 0 || H <= 0 || T <= 0 || !valid_inline(d, inline_mask)) return KF_EINVAL;
+    if (d->n < 32 && (cuts >> (d->n - 1))) return KF_EINVAL;
+    double m = 0;
+    *bytes = xplan_traffic(d, cuts, inline_mask, (double)W * H * T / ((double)DAG_TX * DAG_TY), &m);
+    if (max_onchip) *max_onchip = m;
+    return KF_OK;
+}
+
+kf_status kf_dag_plan_recompute(const kf_dag *d, int64_t W, int64_t H, int64_t T, double onchip_limit, kf_ctx *model,
+                                uint32_t *cuts, uint32_t *inline_mask, double *cost_out)
+{
+    if (!d || !cuts || !inline_mask || W <= 0 || H <= 0 || T <= 0) return KF_EINVAL;
+    if (model) {  // a model that is not trained (or set) predicts nothing
+        float f[KF_NFEAT] = {}, ms = 0.f;
+        if (kf_costmodel_predict(model, f, 1, &ms) != KF_OK) return KF_ESTATE;
+    }
+    const int n = d->n;
+    PlanCost cost{d, W, H, T, (double)W * H * T / ((double)DAG_TX * DAG_TY),
+                  onchip_limit > 0 && onchip_limit < DAG_SMEM_LIMIT ? onchip_limit : DAG_SMEM_LIMIT, model, {}};
+    uint32_t best_c = 0, best_x = 0;
+    double best = best_cuts(d, 0, cost, &best_c);
+    if (n - 1 <= KF_DAG_EXACT_INLINE) {
+        // every inline set of the n - 1 non-output nodes in increasing order; only a
+        // strictly cheaper plan replaces the best, so the contiguous plan wins ties
+        for (uint32_t X = 1; X < (1u << (n - 1)); ++X) {
+            uint32_t c = 0;
+            const double t = best_cuts(d, X, cost, &c);
+            if (t < best) {
+                best = t;
+                best_c = c;
+                best_x = X;
+            }
+        }
+    } else {
+        // hill climbing over single-node toggles from the contiguous optimum
+        for (bool improved = true; improved;) {
+            improved = false;
+            uint32_t step_x = best_x, step_c = best_c;
+            double step = best;
+            for (int j = 1; j < n; ++j) {
+                uint32_t c = 0;
+                const uint32_t X = best_x ^ (1u << (j - 1));
+                const double t = best_cuts(d, X, cost, &c);
+                if (t < step) {
+                    step = t;
+                    step_x = X;
+                    step_c = c;
+                }
+            }
+            if (step < best) {
+                best = step;
+                best_x = step_x;
+                best_c = step_c;
+                improved = true;
+            }
+        }
+    }
+    if (!std::isfinite(best)) return KF_ESMEM;
+    *cuts = best_c;
+    *inline_mask = best_x;
+    if (cost_out) *cost_out = best;
+    return KF_OK;
+}
+
+kf_status kf_dag_run_x(kf_dag *d, uint32_t cuts, uint32_t inline_mask, const kf_video *v, float *out, int64_t out_pitch,
+                       void *ws, size_t ws_bytes, void *stream)
+{
+    if (!d || !v || !out || !valid_inline(d, inline_mask)) return KF_EINVAL;
+    if (d->device < 0) return KF_ESTATE;
+    if (d->n < 32 && (cuts >> (d->n - 1))) return KF_EINVAL;
+    if (v->W <= 0 || v->H <= 0 || v->T <= 0 || !v->frames || v->pitch < v->W || out_pitch < v->W) return KF_EINVAL;
+    if (v->T > 65535 || v->H > (1 << 30)) return KF_EINVAL;
+    size_t need = 0;
+    kf_dag_workspace_bytes(d, v->W, v->H, v->T, &need);
+    if (!ws || ws_bytes < need) return KF_ENOMEM;
+    std::vector<GroupPlan> plans;
+    int a = 1;
+    for (int b = 1; b <= d->n; ++b) {  // every group checked before anything is enqueued
+        if (b < d->n && !(cuts >> (b - 1) & 1)) continue;
+        plans.push_back(plan_members(d, members_of(d, a, b, inline_mask), stores_of(d, a, b, inline_mask)));
+        if (!plans.back().feasible) return KF_ESMEM;
+        a = b + 1;
+    }
+    if (cudaSetDevice(d->device) != cudaSuccess) return KF_ECUDA;
+    const Geo geo = geo_of(d, v->W, v->H, v->T);
+    for (const GroupPlan &g : plans) {
+        const kf_status st =
+            launch_plan(g, v, static_cast<float *>(ws), geo, out, out_pitch, d->n, static_cast<cudaStream_t>(stream));
+        if (st != KF_OK) return st;
+    }
+    return KF_OK;
 }
 
 }  // extern "C"

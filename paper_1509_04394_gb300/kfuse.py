@@ -125,6 +125,9 @@ def _lib():
             "kf_st_traffic": (i32, [i64, i64, i64, i32, i32, i32, P, P]),
             "kf_st_box_eq6": (i32, [dbl, i32, P, P]),
             "kf_st_run": (i32, [P, P, P, i64, P, i32, i32, i32, P]),
+            "kf_dag_xplan_traffic": (i32, [P, u32, u32, i64, i64, i64, P, P]),
+            "kf_dag_plan_recompute": (i32, [P, i64, i64, i64, dbl, P, P, P, P]),
+            "kf_dag_run_x": (i32, [P, u32, u32, P, P, i64, P, ctypes.c_size_t, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -145,7 +148,8 @@ def exported_symbols() -> list[str]:
             "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_grad", "kf_costmodel_get",
             "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times", "kf_pc_traffic", "kf_pc_plan",
             "kf_pc_workspace_bytes", "kf_pc_run", "kf_pc_run_group", "kf_pc_kalman", "kf_pc_group_workspace_bytes",
-            "kf_track_host", "kf_st_smem_bytes", "kf_st_traffic", "kf_st_box_eq6", "kf_st_run"]
+            "kf_track_host", "kf_st_smem_bytes", "kf_st_traffic", "kf_st_box_eq6", "kf_st_run",
+            "kf_dag_xplan_traffic", "kf_dag_plan_recompute", "kf_dag_run_x"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -422,6 +426,32 @@ def kf_dag_run(dag, cuts: int, frames, W: int, out, workspace, stream=None) -> N
     v = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
     _check("kf_dag_run", _lib().kf_dag_run(dag, cuts, ctypes.byref(v), out.data_ptr(), int(out.shape[2]),
                                            workspace.data_ptr(), workspace.numel(), _stream(stream)))
+
+
+def kf_dag_xplan_traffic(dag, cuts: int, inline_mask: int, W, H, T) -> tuple[float, float]:
+    """(traffic bytes, largest on-chip bytes per block) of plan (cuts, inline_mask)."""
+    b, m = ctypes.c_double(), ctypes.c_double()
+    _check("kf_dag_xplan_traffic", _lib().kf_dag_xplan_traffic(dag, int(cuts), int(inline_mask), int(W), int(H), int(T),
+                                                               ctypes.byref(b), ctypes.byref(m)))
+    return b.value, m.value
+
+
+def kf_dag_plan_recompute(dag, W, H, T, onchip_limit: float = 0.0, model=None) -> tuple[int, int, float]:
+    """(cuts, inline_mask, cost) of the cheapest plan: cost = traffic bytes, or the
+    learned model's predicted ms when `model` (a context with a trained model) is given."""
+    c, x, b = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_double()
+    _check("kf_dag_plan_recompute", _lib().kf_dag_plan_recompute(dag, int(W), int(H), int(T), float(onchip_limit), model,
+                                                                 ctypes.byref(c), ctypes.byref(x), ctypes.byref(b)))
+    return c.value, x.value, b.value
+
+
+def kf_dag_run_x(dag, cuts: int, inline_mask: int, frames, W: int, out, workspace, stream=None) -> None:
+    """kf_dag_run with inlined (recomputed) nodes."""
+    T, H, P = frames.shape
+    v = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
+    _check("kf_dag_run_x", _lib().kf_dag_run_x(dag, int(cuts), int(inline_mask), ctypes.byref(v), out.data_ptr(),
+                                               int(out.shape[2]), workspace.data_ptr(), workspace.numel(),
+                                               _stream(stream)))
 
 
 def group_index(n: int, a: int, b: int) -> int:

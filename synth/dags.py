@@ -55,3 +55,23 @@ def random_dag(seed: int, n_min: int = 12, n_max: int = 24) -> list[GStage]:
 def to_array(stages: list[GStage]):
     """(kind, in1, in2, radius, a, b) rows for the C ABI / the oracle."""
     return [(KIND_CODE[s.kind], s.in1, s.in2, s.radius, s.a, s.b) for s in stages]
+
+
+def deep_dag(seed: int, n_min: int = 14, n_max: int = 24) -> list[GStage]:
+    """A DAG whose fused halos outgrow shared memory: stencils of radius 2-3 make up half
+    the stages, and products take their second input from the first quarter of the DAG
+    (long skip connections), so early point stages are read far downstream."""
+    u = uniforms(seed, 11, 1 + 8 * n_max)
+    n = n_min + int(u[0] * (n_max - n_min + 1))
+    stages: list[GStage] = []
+    for i in range(1, n + 1):
+        v = u[1 + 8 * (i - 1): 1 + 8 * i]
+        k = v[0]
+        kind = "affine" if k < 0.2 else "abs" if k < 0.3 else "product" if k < 0.5 else "stencil" if k < 0.95 else "max3"
+        in1 = i - 1 if v[1] < 0.8 else int(v[2] * i)
+        in2 = int(v[3] * max(1, i // 4)) if kind == "product" else -1
+        radius = 2 + int(v[4] * 2) if kind == "stencil" else (1 if kind == "max3" else 0)
+        a = -1.5 + 3.0 * v[5]
+        b = -1.0 + 2.0 * v[6]
+        stages.append(GStage(kind, in1, in2, radius, a, b))
+    return stages

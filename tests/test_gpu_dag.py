@@ -74,3 +74,38 @@ def test_group_timing_covers_every_group(dev):
             t = ms[K.group_index(n, a, b)]
             assert (t > 0) == (onchip <= 200 * 1024), (a, b, t, onchip)
     K.kf_dag_destroy(dag)
+
+
+@pytest.mark.parametrize("seed,shape,deep", [(11, (2, 40, 70), False), (12, (2, 64, 96), True), (13, (1, 9, 13), True),
+                                             (14, (2, 50, 33), False)])
+def test_plans_with_recomputed_nodes_give_the_same_bits(dev, seed, shape, deep):
+    """Plans that recompute inlined nodes in their consumer groups compute every node by
+    the same formula: bit-identical to the unfused run, including the planner's own plans
+    (traffic and a tight on-chip limit)."""
+    T, H, W = shape
+    rows = sd.to_array(sd.deep_dag(5000 + seed) if deep else sd.random_dag(seed))
+    n = len(rows)
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=seed, n_blobs=4, n_patches=2), pitch=sv.pitch_for(W))
+    ctx = K.Context(0, harris=False)
+    dag = K.kf_dag_create(ctx.h, rows)
+    f = torch.from_numpy(fr).to(dev)
+    ws = torch.empty(K.kf_dag_workspace_bytes(dag, W, H, T), dtype=torch.uint8, device=dev)
+    P = sv.pitch_for(W)
+    ref = torch.full((T, H, P), float("nan"), dtype=torch.float32, device=dev)
+    K.kf_dag_run(dag, (1 << (n - 1)) - 1, f, W, ref, ws)
+    rng = np.random.default_rng(seed)
+    plans = [(int(rng.integers(0, 1 << (n - 1))), int(rng.integers(0, 1 << (n - 1)))) for _ in range(6)]
+    plans.append(K.kf_dag_plan_recompute(dag, W, H, T)[:2])
+    plans.append(K.kf_dag_plan_recompute(dag, W, H, T, 30000)[:2])
+    ran = 0
+    for cuts, xm in plans:
+        out = torch.full((T, H, P), float("nan"), dtype=torch.float32, device=dev)
+        try:
+            K.kf_dag_run_x(dag, cuts, xm, f, W, out, ws)
+        except K.KfuseError as e:
+            assert e.status == K.KF_ESMEM
+            continue
+        ran += 1
+        assert torch.equal(out[:, :, :W], ref[:, :, :W]), (cuts, xm)
+    assert ran >= 2
+    K.kf_dag_destroy(dag)
