@@ -267,11 +267,13 @@ __device__ __forceinline__ void pass_c(const StParams &p, const BoxPos &b, const
 // for the staged frame and converts it; phase B issues the next frame's copy and runs
 // pass B. The copy of frame pl+1 thus overlaps pass B of pl and pass C of pl.
 template <int N, int X>
-__global__ void __launch_bounds__(BoxCfg<X>::THREADS) st_box_kernel(const __grid_constant__ StParams p)
+__global__ void __launch_bounds__(BoxCfg<X>::THREADS, 2) st_box_kernel(const __grid_constant__ StParams p)
 {
     using C = BoxCfg<X>;
     extern __shared__ __align__(128) unsigned char st_smem[];
-    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)st_smem + 127) & ~(uintptr_t)127);
+    // 128-byte aligned start (TMA destination), offset within the shared window so that
+    // every pointer below stays a shared-memory pointer
+    unsigned char *base = st_smem + ((128u - (smem_addr(st_smem) & 127u)) & 127u);
     const uint32_t *stage = reinterpret_cast<const uint32_t *>(base);
     int32_t *Z = reinterpret_cast<int32_t *>(base + C::OFF_Z);
     int32_t *G = reinterpret_cast<int32_t *>(base + C::OFF_G);
