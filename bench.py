@@ -374,8 +374,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # end to end through the public call: pinned host frames in; mask, counts and tracks
     # out. kf_track_host runs the step in chunks of E2E_CHUNK frames with the copy in of
     # one chunk, the hot path of the previous ones and the copy out of earlier ones on
-    # separate streams. The headline delivers the mask bit-packed (stored by the device
-    # straight into the pinned host buffer); the byte-mask form is reported beside it.
+    # separate streams. The headline delivers the mask bit-packed (packed on the device,
+    # 8 pixels a byte, and copied out); the byte-mask form is reported beside it.
     S = ((W * H + 7) // 8 + 15) // 16 * 16
     host = dict(frames=frames_pin, mask=torch.empty((T, S), dtype=torch.uint8).pin_memory(),
                 counts=torch.empty_like(counts, device="cpu").pin_memory(),
@@ -438,8 +438,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                         "hbm_frac": 50 * px / (ms_unf16 / 1000) / 1e9 / hbm_peak},
         "e2e": {"value": world * px / (ms_e2e / 1000) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e, "chunk_frames": E2E_CHUNK,
-                "call": "kf_track_host, KF_MASK_BITS (copy in, hot path on two streams, mask packed 8 px/byte "
-                        "into pinned host memory by the device, tracks copied out)",
+                "call": "kf_track_host, KF_MASK_BITS (copy in, hot path on three streams, mask packed 8 px/byte "
+                        "on the device, packed mask and tracks copied out)",
                 "results_equal_device_step": e2e_same},
         "e2e_byte_mask": {"value": world * px / (ms_e2e_b / 1000) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                           "d2h_bytes_per_step": int(d2h_b), "ms_per_step": ms_e2e_b,

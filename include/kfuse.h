@@ -246,11 +246,10 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *video, const kf_corners *out, co
  * host_out->mask like the device mask (same mask_pitch); or KF_MASK_BITS, the mask
  * packed for transfer, 8 pixels a byte: frame f's pixel (y, x), i = y W + x, is bit i % 8
  * of byte f * host_out->mask_pitch + i / 8 (mask_pitch = bytes per frame, >= ceil(W H /
- * 8), a multiple of 16; bits past W H are 0). With KF_MASK_BITS the device stores the
- * packed frames straight into host_out->mask, which must be host memory the device can
- * address (cudaHostGetDevicePointer succeeds: cudaHostAlloc, cudaHostRegister with
- * cudaHostRegisterMapped, or any memory on systems whose devices translate host
- * addresses; else KF_EINVAL); the device mask is written as well. Asynchronous: `stream` waits for the
+ * 8), a multiple of 16; bits past W H are 0). With KF_MASK_BITS the chunks are packed
+ * on the device into a staging ring the context owns (3 chunks of packed frames,
+ * allocated on first use and grown when a call needs more) and copied out from there;
+ * the device mask is written as well. Asynchronous: `stream` waits for the
  * last copy out, and the copies start after the work queued on `stream` before the call;
  * the host buffers must stay valid until then. */
 #define KF_MASK_BYTES 0

@@ -400,6 +400,10 @@ kf_status kf_destroy(kf_ctx *ctx)
         }
         cudaEventDestroy(ctx->ev_edge);
     }
+    if (ctx && ctx->pack_buf) {
+        cudaSetDevice(ctx->device);
+        cudaFree(ctx->pack_buf);
+    }
     if (ctx && (!ctx->timed.empty() || !ctx->spare_events.empty())) {
         cudaSetDevice(ctx->device);
         for (const kf_ctx::Timed &t : ctx->timed) {
@@ -829,15 +833,22 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
         return KF_EINVAL;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
-    // packed masks are stored by the device into the page-locked host buffer directly
-    uint8_t *host_bits = nullptr;
+    // packed masks: staged per chunk in a device ring of N_RING chunks (owned by the
+    // context, grown on demand) and copied out from there
     if (bits) {
-        void *d = nullptr;
-        if (cudaHostGetDevicePointer(&d, host_out->mask, 0) != cudaSuccess || (uintptr_t)d % 16) {
-            cudaGetLastError();
-            return KF_EINVAL;
+        const size_t need = (size_t)kf_ctx::N_RING * (size_t)chunk * (size_t)host_out->mask_pitch;
+        if (need > ctx->pack_bytes) {
+            e = cudaDeviceSynchronize();  // the old ring may still be in use by an earlier call
+            if (e == cudaSuccess && ctx->pack_buf) e = cudaFree(ctx->pack_buf);
+            ctx->pack_buf = nullptr;
+            ctx->pack_bytes = 0;
+            if (e == cudaSuccess) e = cudaMalloc(&ctx->pack_buf, need);
+            if (e != cudaSuccess) {
+                ctx->pack_buf = nullptr;
+                return cuda_fail(ctx, e);
+            }
+            ctx->pack_bytes = need;
         }
-        host_bits = static_cast<uint8_t *>(d);
     }
     if ((st = copy_streams(ctx)) != KF_OK) return st;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -871,20 +882,25 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
         if (st != KF_OK) return st;
         e = cudaEventRecord(ecomp, cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ecomp, 0);
-        if (e == cudaSuccess && bits) {
-            // on the copy-out stream: its stores to host memory do not hold up the next
-            // chunks' kernels on the compute streams
-            const int64_t words = (packed + 3) / 4;
-            const dim3 grid((unsigned)((words + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
-            pack_mask_kernel<<<grid, 256, 0, ctx->s_out>>>(out->mask + t0 * mstride, out->mask_pitch, mstride,
-                                                           (int)video->W, (int)H, n, words,
-                                                           host_bits + t0 * host_out->mask_pitch, host_out->mask_pitch);
-            e = cudaGetLastError();
-        }
         auto d2h = [&](void *dst, const void *src, size_t bytes) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s_out);
         };
-        if (!bits) d2h(host_out->mask + t0 * mstride, out->mask + t0 * mstride, (size_t)(n * mstride));
+        if (bits) {
+            // packed on the copy-out stream into ring slot r (the slot's previous chunk was
+            // copied out earlier on the same stream), then copied out
+            uint8_t *slot = ctx->pack_buf + (size_t)r * (size_t)chunk * (size_t)host_out->mask_pitch;
+            const int64_t words = (packed + 3) / 4;
+            const dim3 grid((unsigned)((words + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
+            if (e == cudaSuccess) {
+                pack_mask_kernel<<<grid, 256, 0, ctx->s_out>>>(out->mask + t0 * mstride, out->mask_pitch, mstride,
+                                                               (int)video->W, (int)H, n, words, slot,
+                                                               host_out->mask_pitch);
+                e = cudaGetLastError();
+            }
+            d2h(host_out->mask + t0 * host_out->mask_pitch, slot, (size_t)(n * host_out->mask_pitch));
+        } else {
+            d2h(host_out->mask + t0 * mstride, out->mask + t0 * mstride, (size_t)(n * mstride));
+        }
         d2h(host_out->counts + t0, out->counts + t0, sizeof(int32_t) * (size_t)n);
         d2h(host_tracks->n_points + t0, tracks->n_points + t0, sizeof(int32_t) * (size_t)n);
         d2h(host_tracks->idx + t0 * K, tracks->idx + t0 * K, sizeof(int32_t) * (size_t)(n * K));

@@ -29,4 +29,7 @@ struct kf_ctx {
     static constexpr int N_RING = 3;
     cudaStream_t s_in = nullptr, s_out = nullptr, s_comp[N_RING] = {};
     cudaEvent_t ev_in[N_RING] = {}, ev_comp[N_RING] = {}, ev_edge = nullptr;
+    // kf_track_host with packed masks: device staging of the packed chunks (owned)
+    uint8_t *pack_buf = nullptr;
+    size_t pack_bytes = 0;
 };
