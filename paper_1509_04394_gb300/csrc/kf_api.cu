@@ -897,7 +897,11 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
                                                                host_out->mask_pitch);
                 e = cudaGetLastError();
             }
-            d2h(host_out->mask + t0 * host_out->mask_pitch, slot, (size_t)(n * host_out->mask_pitch));
+            // the packed words of each frame only; the rest of the host frame stride is untouched
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(host_out->mask + t0 * host_out->mask_pitch, (size_t)host_out->mask_pitch, slot,
+                                      (size_t)host_out->mask_pitch, (size_t)(4 * words), (size_t)n, cudaMemcpyDeviceToHost,
+                                      ctx->s_out);
         } else {
             d2h(host_out->mask + t0 * mstride, out->mask + t0 * mstride, (size_t)(n * mstride));
         }
