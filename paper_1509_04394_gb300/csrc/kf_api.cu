@@ -838,7 +838,8 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
     if (bits) {
         const size_t need = (size_t)kf_ctx::N_RING * (size_t)chunk * (size_t)host_out->mask_pitch;
         if (need > ctx->pack_bytes) {
-            e = cudaDeviceSynchronize();  // the old ring may still be in use by an earlier call
+            // the old ring may still be in use by an earlier call's copy-out stream
+            e = ctx->s_out ? cudaStreamSynchronize(ctx->s_out) : cudaSuccess;
             if (e == cudaSuccess && ctx->pack_buf) e = cudaFree(ctx->pack_buf);
             ctx->pack_buf = nullptr;
             ctx->pack_bytes = 0;

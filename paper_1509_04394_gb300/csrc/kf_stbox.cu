@@ -78,9 +78,15 @@ __device__ __forceinline__ void tma_frame(void *dst, const CUtensorMap *map, int
         : "memory");
 }
 
-__device__ __forceinline__ uint32_t gray_of(uint32_t rgba)
+// K1 for two RGBA pixels at once: the R, G and B bytes of both gathered into 16-bit
+// halves by byte permutes, so one multiply-add chain gives both gray values (each at
+// most 65280, so the halves never carry into each other): lo = gray(a), hi = gray(b).
+__device__ __forceinline__ uint32_t gray_pair(uint32_t a, uint32_t b)
 {
-    return 77u * (rgba & 0xffu) + 150u * ((rgba >> 8) & 0xffu) + 29u * ((rgba >> 16) & 0xffu);
+    const uint32_t u = __byte_perm(a, b, 0x5140);  // a.R, b.R, a.G, b.G
+    const uint32_t v = __byte_perm(a, b, 0x0062);  // a.B, b.B
+    const uint32_t r = __byte_perm(u, 0u, 0x4140), g = __byte_perm(u, 0u, 0x4342), bl = __byte_perm(v, 0u, 0x4140);
+    return 77u * r + 150u * g + 29u * bl;
 }
 
 // binomial weight C(N, k)
@@ -126,9 +132,11 @@ __device__ __forceinline__ void convert_frame(const StParams &p, const BoxPos &b
     constexpr int SC = C::SC;
     const bool out_frame = pl >= N;
     const int slot0 = pl % N;  // the ring slot of plane pl - N, overwritten by plane pl
+    // pair i = threadIdx.x + k THREADS sits at row r, column c; walked without divisions
+    constexpr int PR = SC / 2, R_STEP = C::THREADS / PR, C_STEP = 2 * (C::THREADS - R_STEP * PR);
+    int r = threadIdx.x / PR, c = 2 * (threadIdx.x - r * PR);
 #pragma unroll 2
     for (int i = threadIdx.x; i < C::PAIRS; i += C::THREADS) {
-        const int r = i / (SC / 2), c = 2 * (i - r * (SC / 2));
         uint32_t a, bb;
         if (b.inner) {
             const uint2 w = *reinterpret_cast<const uint2 *>(stage + r * SC + c);
@@ -141,7 +149,7 @@ __device__ __forceinline__ void convert_frame(const StParams &p, const BoxPos &b
             a = stage[ry * SC + ca];
             bb = stage[ry * SC + cb];
         }
-        const uint32_t g = gray_of(a) | (gray_of(bb) << 16);
+        const uint32_t g = gray_pair(a, bb);
         if (out_frame) {
             int lo = (int)(g & 0xffffu), hi = (int)(g >> 16);
 #pragma unroll
@@ -155,6 +163,12 @@ __device__ __forceinline__ void convert_frame(const StParams &p, const BoxPos &b
             *reinterpret_cast<int2 *>(Z + r * SC + c) = make_int2(lo, hi);
         }
         ring[slot0 * C::PAIRS + i] = g;
+        c += C_STEP;
+        r += R_STEP;
+        if (c >= SC) {
+            c -= SC;
+            ++r;
+        }
     }
 }
 
