@@ -250,9 +250,11 @@ __device__ __forceinline__ void products(const Rows<2> &i, Rows<3> &p)
 
 // Stage 6: 5x5 box sum. Horizontal: the four 5-wide windows of a lane's columns share
 // the pair sums A = x-2 + x-1, B = x0 + x1, Cp = x2 + x3, D = x4 + x5 and E = B + Cp
-// (11 adds for 4 outputs). Vertical: the five newest rows, oldest first, from a 5-slot
-// register ring addressed by the compile-time loop phase (the row loop is unrolled by 5,
-// so no register is ever moved); the order is by age, the same in every partition.
+// (11 adds for 4 outputs). Vertical: each row's sum with the row before it is kept (a
+// 5-slot ring addressed by the compile-time loop phase: the row loop is unrolled by 5,
+// so no register is ever moved), and the window of rows t-4..t is
+// ((r[t-4] + r[t-3]) + (r[t-2] + r[t-1])) + r[t]: 3 adds a value instead of 4, in an
+// order fixed by the rows' ages alone, the same in every partition and chunk height.
 // Output row = input row - 2.
 __device__ __forceinline__ void box_h(const float (&x)[C], float (&o)[C])
 {
@@ -266,43 +268,49 @@ __device__ __forceinline__ void box_h(const float (&x)[C], float (&o)[C])
     o[3] = x[1] + (Cp + D);
 }
 struct BoxV {
-    float ring[5][3][C];
-    // slot of the row pushed at phase PH is PH; the row pushed k steps earlier is (PH - k) mod 5
+    float pair[5][3][C];  // slot PH: the row pushed at phase PH plus the row before it
+    float last[3][C];     // the newest row
+    // the first row of a frame: the rows above it clamp to it
+    __device__ __forceinline__ void fill(const Rows<3> &h)
+    {
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                last[m][c] = h.v[m][c];
+#pragma unroll
+                for (int s = 0; s < 5; ++s) pair[s][m][c] = h.v[m][c] + h.v[m][c];
+            }
+    }
+    // rows past the frame's end clamp to the last one
+    template <int PH>
+    __device__ __forceinline__ void newest(Rows<3> &h) const
+    {
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int c = 0; c < C; ++c) h.v[m][c] = last[m][c];
+    }
     template <int PH>
     __device__ __forceinline__ void put(const Rows<3> &h)
     {
 #pragma unroll
         for (int m = 0; m < 3; ++m)
 #pragma unroll
-            for (int c = 0; c < C; ++c) ring[PH][m][c] = h.v[m][c];
+            for (int c = 0; c < C; ++c) {
+                pair[PH][m][c] = last[m][c] + h.v[m][c];
+                last[m][c] = h.v[m][c];
+            }
     }
-    __device__ __forceinline__ void fill(const Rows<3> &h)
-    {
-#pragma unroll
-        for (int s = 0; s < 5; ++s)
-#pragma unroll
-            for (int m = 0; m < 3; ++m)
-#pragma unroll
-                for (int c = 0; c < C; ++c) ring[s][m][c] = h.v[m][c];
-    }
-    template <int PH>
-    __device__ __forceinline__ void newest(Rows<3> &h) const
-    {
-        constexpr int s = (PH + 4) % 5;  // slot written by the previous push
-#pragma unroll
-        for (int m = 0; m < 3; ++m)
-#pragma unroll
-            for (int c = 0; c < C; ++c) h.v[m][c] = ring[s][m][c];
-    }
+    // after put<PH>: pair (PH + 4) % 5 = r[t-2] + r[t-1], pair (PH + 2) % 5 = r[t-4] + r[t-3]
     template <int PH>
     __device__ __forceinline__ void sum(Rows<3> &o) const
     {
-        constexpr int s0 = (PH + 1) % 5, s1 = (PH + 2) % 5, s2 = (PH + 3) % 5, s3 = (PH + 4) % 5;
+        constexpr int p1 = (PH + 4) % 5, p3 = (PH + 2) % 5;
 #pragma unroll
         for (int m = 0; m < 3; ++m)
 #pragma unroll
-            for (int c = 0; c < C; ++c)
-                o.v[m][c] = (((ring[s0][m][c] + ring[s1][m][c]) + ring[s2][m][c]) + ring[s3][m][c]) + ring[PH][m][c];
+            for (int c = 0; c < C; ++c) o.v[m][c] = (pair[p3][m][c] + pair[p1][m][c]) + last[m][c];
     }
 };
 
