@@ -773,10 +773,11 @@ def run_costmodel(args):
 
 def run_dagplan(args):
     """Recompute instead of store: on the learned-cost-model workload (400 random DAGs,
-    1080x1920, groups timed on a prefix of the video, MLP trained on 300 DAGs), each of
-    the 100 held-out DAGs is planned by the MLP over contiguous partitions and over plans
-    with inlined (recomputed) nodes; both plans and the measured-best contiguous partition
-    run end to end (CUDA events), and the plans' bits are compared."""
+    1080x1920, groups timed on a prefix of the video), each of the 100 held-out DAGs is
+    planned over contiguous partitions and over plans with inlined (recomputed) nodes by
+    two MLPs -- one trained on the 300 training DAGs' contiguous groups, one also on 60
+    sampled groups with inlined nodes per training DAG -- and the plans, with the
+    measured-best contiguous partition, run end to end (CUDA events); bits compared."""
     import torch
     from paper_1509_04394_gb300 import build as kbuild
     from paper_1509_04394_gb300 import costmodel as cm
@@ -787,10 +788,15 @@ def run_dagplan(args):
     W, H, T = 1920, 1080, args.cm_frames
     fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=5), pitch=W)
     f = torch.from_numpy(fr).to(dev)
-    ctx = K.kf_create(0)
-    meas = [cm.measure(ctx, sd.to_array(sd.random_dag(4000 + s)), f, W, 4000 + s) for s in range(400)]
-    X, y = cm.dataset(meas[:300])
-    K.kf_costmodel_train(ctx, X, y, steps=4000, lr=3e-3, seed=1)
+    ctx_c, ctx_x = K.kf_create(0), K.kf_create(0)
+    meas = [cm.measure(ctx_c, sd.to_array(sd.random_dag(4000 + s)), f, W, 4000 + s) for s in range(400)]
+    Xc, yc = cm.dataset(meas[:300])
+    inl = [cm.measure_inlined(ctx_c, m.rows, f, W, 9000 + m.seed) for m in meas[:300]]
+    Xi = np.concatenate([x for x, _ in inl])
+    yi = np.concatenate([y for _, y in inl])
+    K.kf_costmodel_train(ctx_c, Xc, yc, steps=4000, lr=3e-3, seed=1)
+    K.kf_costmodel_train(ctx_x, np.concatenate([Xc, Xi]).astype(np.float32), np.concatenate([yc, yi]), steps=4000,
+                         lr=3e-3, seed=1)
     out_a = torch.empty((T, H, W), dtype=torch.float32, device=dev)
     out_b = torch.empty((T, H, W), dtype=torch.float32, device=dev)
 
@@ -807,48 +813,55 @@ def run_dagplan(args):
 
     rows = []
     for m in meas[300:]:
-        dag = K.kf_dag_create(ctx, m.rows)
+        dag = K.kf_dag_create(ctx_c, m.rows)
         ws = torch.empty(K.kf_dag_workspace_bytes(dag, W, H, T), dtype=torch.uint8, device=dev)
-        plans = cm.plan_costs(ctx, m)
-        cuts_x, xm, pred_x = K.kf_dag_plan_recompute(dag, W, H, T, model=ctx)
-        t_best = run_ms(lambda: K.kf_dag_run(dag, plans["measured"], f, W, out_a, ws))
-        t_mlp = run_ms(lambda: K.kf_dag_run(dag, plans["mlp"], f, W, out_a, ws))
-        t_x = run_ms(lambda: K.kf_dag_run_x(dag, cuts_x, xm, f, W, out_b, ws))
-        same = bool(torch.equal(out_a, out_b))
+        best_cuts = cm.plan_costs(ctx_c, m)["measured"]
+        t_best = run_ms(lambda: K.kf_dag_run(dag, best_cuts, f, W, out_a, ws))
+        r = {"seed": m.seed, "n": m.n, "best_contiguous_ms": t_best}
+        same = True
+        for name, ctx in (("mlp", ctx_c), ("mlp_inl", ctx_x)):
+            cont = cm.plan_costs(ctx, m)["mlp"]
+            cx, xm, _ = K.kf_dag_plan_recompute(dag, W, H, T, model=ctx)
+            r[name + "_contiguous_ms"] = run_ms(lambda: K.kf_dag_run(dag, cont, f, W, out_a, ws))
+            r[name + "_recompute_ms"] = run_ms(lambda: K.kf_dag_run_x(dag, cx, xm, f, W, out_b, ws))
+            r[name + "_inlined"] = bin(xm).count("1")
+            same = same and bool(torch.equal(out_a, out_b))
         # measured search: inline one node at a time on top of the measured-best partition
         best_j, t_j = 0, t_best
         for j in range(1, m.n):
             try:
-                t = run_ms(lambda: K.kf_dag_run_x(dag, plans["measured"], 1 << (j - 1), f, W, out_b, ws), reps=2)
+                t = run_ms(lambda: K.kf_dag_run_x(dag, best_cuts, 1 << (j - 1), f, W, out_b, ws), reps=2)
             except K.KfuseError:
                 continue
             same = same and bool(torch.equal(out_a, out_b))
             if t < t_j:
                 best_j, t_j = j, t
-        rows.append({"seed": m.seed, "n": m.n, "inlined": bin(xm).count("1"), "best_contiguous_ms": t_best,
-                     "mlp_contiguous_ms": t_mlp, "mlp_recompute_ms": t_x, "measured_one_inlined_ms": t_j,
-                     "measured_inlined_node": best_j, "same_bits": same})
+        r["measured_one_inlined_ms"], r["measured_inlined_node"] = t_j, best_j
+        r["same_bits"] = same
+        rows.append(r)
         K.kf_dag_destroy(dag)
         del ws
-    changed = [r for r in rows if r["inlined"]]
-    r_x = np.array([r["mlp_recompute_ms"] / r["mlp_contiguous_ms"] for r in rows])
-    r_best = np.array([r["mlp_recompute_ms"] / r["best_contiguous_ms"] for r in rows])
-    r_c = np.array([r["mlp_recompute_ms"] / r["mlp_contiguous_ms"] for r in changed]) if changed else np.array([1.0])
+
+    def summary(name):
+        x = np.array([q[name + "_recompute_ms"] for q in rows])
+        c = np.array([q[name + "_contiguous_ms"] for q in rows])
+        best = np.array([q["best_contiguous_ms"] for q in rows])
+        used = np.array([q[name + "_inlined"] > 0 for q in rows])
+        return {"plans_with_inlined_nodes": int(used.sum()),
+                "recompute_over_own_contiguous": {"mean": float((x / c).mean()),
+                                                  "mean_where_inlined": float((x / c)[used].mean()) if used.any() else 1.0,
+                                                  "min": float((x / c).min()), "max": float((x / c).max())},
+                "recompute_over_measured_best_contiguous": {"mean": float((x / best).mean()),
+                                                            "faster": int(np.sum(x < best))},
+                "contiguous_over_measured_best": float((c / best).mean())}
     print(json.dumps({"workload": f"100 held-out random DAGs (12-24 stages), 1080x1920 u8, {T} frames",
-                      "dags": len(rows), "plans_with_inlined_nodes": len(changed),
-                      "mean_inlined_nodes_where_used": float(np.mean([r["inlined"] for r in changed])) if changed else 0,
-                      "recompute_over_contiguous_mlp": {"mean": float(r_x.mean()), "median": float(np.median(r_x))},
-                      "recompute_over_contiguous_mlp_where_inlined": {"mean": float(r_c.mean()),
-                                                                      "median": float(np.median(r_c)),
-                                                                      "min": float(r_c.min()), "max": float(r_c.max())},
-                      "recompute_over_measured_best_contiguous": {"mean": float(r_best.mean()),
-                                                                  "median": float(np.median(r_best)),
-                                                                  "faster": int(np.sum(r_best < 1.0))},
+                      "dags": len(rows), "inlined_training_samples": int(len(yi)),
+                      "mlp_contiguous_training": summary("mlp"), "mlp_with_inlined_training": summary("mlp_inl"),
                       "measured_one_inlined_over_best_contiguous": {
-                          "mean": float(np.mean([r["measured_one_inlined_ms"] / r["best_contiguous_ms"] for r in rows])),
-                          "improved_dags": int(sum(r["measured_inlined_node"] > 0 for r in rows)),
-                          "min": float(min(r["measured_one_inlined_ms"] / r["best_contiguous_ms"] for r in rows))},
-                      "all_bits_equal": all(r["same_bits"] for r in rows), "per_dag": rows}), flush=True)
+                          "mean": float(np.mean([q["measured_one_inlined_ms"] / q["best_contiguous_ms"] for q in rows])),
+                          "improved_dags": int(sum(q["measured_inlined_node"] > 0 for q in rows)),
+                          "min": float(min(q["measured_one_inlined_ms"] / q["best_contiguous_ms"] for q in rows))},
+                      "all_bits_equal": all(q["same_bits"] for q in rows), "per_dag": rows}), flush=True)
 
 
 def main():

@@ -362,6 +362,15 @@ kf_status kf_dag_xplan_traffic(const kf_dag *dag, uint32_t cuts, uint32_t inline
  * KF_ESMEM if nothing fits. */
 kf_status kf_dag_plan_recompute(const kf_dag *dag, int64_t W, int64_t H, int64_t T, double onchip_limit, kf_ctx *model,
                                 uint32_t *cuts, uint32_t *inline_mask, double *cost);
+/* Measure groups of plans with inlined nodes, for training the learned model on them:
+ * groups[3 g .. 3 g + 2] = (first, last, inline_mask) of group g (0-based stages). Runs
+ * the DAG unfused once (so every stored map exists), then each group (one warm-up, `reps`
+ * timed launches, CUDA events on `stream`): ms[g] = mean time, -1 if it exceeds the
+ * on-chip limit; features (NULL or count x KF_NFEAT) = the group's cost-model features.
+ * Synchronous. */
+kf_status kf_dag_time_xgroups(kf_dag *dag, const kf_video *video, float *out, int64_t out_pitch, void *workspace,
+                              size_t workspace_bytes, const int32_t *groups, int count, int reps, void *stream,
+                              float *ms, float *features);
 /* Run plan (cuts, inline_mask) on `stream`, like kf_dag_run. */
 kf_status kf_dag_run_x(kf_dag *dag, uint32_t cuts, uint32_t inline_mask, const kf_video *video, float *out,
                        int64_t out_pitch, void *workspace, size_t workspace_bytes, void *stream);

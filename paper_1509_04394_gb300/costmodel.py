@@ -57,6 +57,55 @@ def measure(ctx, rows, frames, W: int, seed: int, reps: int = 2) -> Measured:
     return Measured(seed, n, rows, ms, feats, traffic, onchip)
 
 
+def inlined_samples(rows, seed: int, count: int = 60) -> list[tuple[int, int, int]]:
+    """(first, last, inline_mask) groups of plans that recompute nodes: a random range
+    and a random non-empty set of the stored maps it reads (sometimes with one of their
+    own stored inputs, or one of its own nodes), drawn from a seeded generator."""
+    n = len(rows)
+    rng = np.random.default_rng(seed)
+
+    def inputs(j):
+        kind, i1, i2 = rows[j - 1][0], rows[j - 1][1], rows[j - 1][2]
+        return [i1, i2] if kind == 3 else [i1]
+    out, tries = [], 0
+    while len(out) < count and tries < 20 * count:
+        tries += 1
+        a = int(rng.integers(1, n + 1))
+        b = int(rng.integers(a, n + 1))
+        ext = sorted({i for j in range(a, b + 1) for i in inputs(j) if 0 < i < a})
+        if not ext:
+            continue
+        pick = [e for e in ext if rng.random() < 0.5] or [ext[int(rng.integers(len(ext)))]]
+        X = set(pick)
+        if rng.random() < 0.3:
+            deeper = sorted({i for e in pick for i in inputs(e) if i > 0})
+            if deeper:
+                X.add(deeper[int(rng.integers(len(deeper)))])
+        if rng.random() < 0.2 and b > a:
+            X.add(int(rng.integers(a, b)))  # a range node, never the output n
+        X.discard(n)
+        mask = sum(1 << (j - 1) for j in X)
+        out.append((a - 1, b - 1, mask))
+    return out
+
+
+def measure_inlined(ctx, rows, frames, W: int, seed: int, count: int = 60, reps: int = 2):
+    """(features, ms) of sampled groups with inlined nodes (feasible ones only)."""
+    import torch
+    T, H, _ = frames.shape
+    dag = K.kf_dag_create(ctx, rows)
+    try:
+        ws = torch.empty(K.kf_dag_workspace_bytes(dag, W, H, T), dtype=torch.uint8, device=frames.device)
+        out = torch.empty((T, H, W), dtype=torch.float32, device=frames.device)
+        groups = inlined_samples(rows, seed, count)
+        ms, feats = K.kf_dag_time_xgroups(dag, groups, frames, W, out, ws, reps=reps)
+        del ws, out
+    finally:
+        K.kf_dag_destroy(dag)
+    ok = ms > 0
+    return feats[ok], ms[ok].astype(np.float64)
+
+
 def dataset(ms_list: list[Measured]):
     X = np.concatenate([m.feats[m.ms > 0] for m in ms_list])
     y = np.concatenate([m.ms[m.ms > 0] for m in ms_list])

@@ -680,4 +680,49 @@ kf_status kf_dag_run_x(kf_dag *d, uint32_t cuts, uint32_t inline_mask, const kf_
     return KF_OK;
 }
 
+kf_status kf_dag_time_xgroups(kf_dag *d, const kf_video *v, float *out, int64_t out_pitch, void *ws, size_t ws_bytes,
+                              const int32_t *groups, int count, int reps, void *stream, float *ms, float *features)
+{
+    if (!d || !v || !groups || count < 0 || !ms || reps < 1) return KF_EINVAL;
+    const int n = d->n;
+    for (int g = 0; g < count; ++g) {
+        const int a = groups[3 * g], b = groups[3 * g + 1];
+        const uint32_t X = (uint32_t)groups[3 * g + 2];
+        if (a < 0 || b < a || b >= n || !valid_inline(d, X)) return KF_EINVAL;
+    }
+    // materialise every node once (no fusion), so that any group finds its inputs
+    kf_status st = kf_dag_run(d, n > 1 ? (uint32_t)((1ull << (n - 1)) - 1) : 0u, v, out, out_pitch, ws, ws_bytes, stream);
+    if (st != KF_OK) return st;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Geo geo = geo_of(d, v->W, v->H, v->T);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return KF_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return KF_ECUDA;
+    }
+    for (int g = 0; g < count && st == KF_OK; ++g) {
+        const int a = groups[3 * g] + 1, b = groups[3 * g + 1] + 1;
+        const uint32_t X = (uint32_t)groups[3 * g + 2];
+        const uint32_t mem = members_of(d, a, b, X);
+        const GroupPlan gp = plan_members(d, mem, stores_of(d, a, b, X));
+        if (features) features_of(d, gp, mem, v->W, v->H, v->T, features + (size_t)g * KF_NFEAT);
+        if (!gp.feasible) {
+            ms[g] = -1.0f;
+            continue;
+        }
+        st = launch_plan(gp, v, static_cast<float *>(ws), geo, out, out_pitch, n, s);  // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == KF_OK; ++r) st = launch_plan(gp, v, static_cast<float *>(ws), geo, out, out_pitch, n, s);
+        cudaEventRecord(e1, s);
+        float t = 0;
+        if (st == KF_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+            st = KF_ECUDA;
+        ms[g] = t / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 }  // extern "C"

@@ -128,6 +128,7 @@ def _lib():
             "kf_dag_xplan_traffic": (i32, [P, u32, u32, i64, i64, i64, P, P]),
             "kf_dag_plan_recompute": (i32, [P, i64, i64, i64, dbl, P, P, P, P]),
             "kf_dag_run_x": (i32, [P, u32, u32, P, P, i64, P, ctypes.c_size_t, P]),
+            "kf_dag_time_xgroups": (i32, [P, P, P, i64, P, ctypes.c_size_t, P, i32, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -149,7 +150,7 @@ def exported_symbols() -> list[str]:
             "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times", "kf_pc_traffic", "kf_pc_plan",
             "kf_pc_workspace_bytes", "kf_pc_run", "kf_pc_run_group", "kf_pc_kalman", "kf_pc_group_workspace_bytes",
             "kf_track_host", "kf_st_smem_bytes", "kf_st_traffic", "kf_st_box_eq6", "kf_st_run",
-            "kf_dag_xplan_traffic", "kf_dag_plan_recompute", "kf_dag_run_x"]
+            "kf_dag_xplan_traffic", "kf_dag_plan_recompute", "kf_dag_run_x", "kf_dag_time_xgroups"]
 
 
 def _check(call: str, status: int, ctx=None):
@@ -452,6 +453,22 @@ def kf_dag_run_x(dag, cuts: int, inline_mask: int, frames, W: int, out, workspac
     _check("kf_dag_run_x", _lib().kf_dag_run_x(dag, int(cuts), int(inline_mask), ctypes.byref(v), out.data_ptr(),
                                                int(out.shape[2]), workspace.data_ptr(), workspace.numel(),
                                                _stream(stream)))
+
+
+def kf_dag_time_xgroups(dag, groups, frames, W: int, out, workspace, reps: int = 2, stream=None):
+    """groups: [(first, last, inline_mask)] -> (ms [G], features [G, KF_NFEAT])."""
+    import numpy as np
+    T, H, P = frames.shape
+    v = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
+    g = np.ascontiguousarray(np.array(groups, dtype=np.int32).reshape(-1, 3))
+    G = g.shape[0]
+    ms = np.zeros(G, dtype=np.float32)
+    feats = np.zeros((G, KF_NFEAT), dtype=np.float32)
+    _check("kf_dag_time_xgroups", _lib().kf_dag_time_xgroups(dag, ctypes.byref(v), out.data_ptr(), int(out.shape[2]),
+                                                             workspace.data_ptr(), workspace.numel(),
+                                                             g.ctypes.data, int(G), int(reps), _stream(stream),
+                                                             ms.ctypes.data, feats.ctypes.data))
+    return ms, feats
 
 
 def group_index(n: int, a: int, b: int) -> int:

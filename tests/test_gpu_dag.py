@@ -109,3 +109,29 @@ def test_plans_with_recomputed_nodes_give_the_same_bits(dev, seed, shape, deep):
         assert torch.equal(out[:, :, :W], ref[:, :, :W]), (cuts, xm)
     assert ran >= 2
     K.kf_dag_destroy(dag)
+
+
+def test_timing_groups_with_inlined_nodes(dev):
+    """kf_dag_time_xgroups: a time for every feasible group, and with no inlined node
+    the features of the contiguous group."""
+    from paper_1509_04394_gb300 import costmodel as cm
+    rows = sd.to_array(sd.random_dag(21, 12, 14))
+    n = len(rows)
+    T, H, W = 2, 96, 160
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=21), pitch=sv.pitch_for(W))
+    ctx = K.Context(0, harris=False)
+    dag = K.kf_dag_create(ctx.h, rows)
+    f = torch.from_numpy(fr).to(dev)
+    ws = torch.empty(K.kf_dag_workspace_bytes(dag, W, H, T), dtype=torch.uint8, device=dev)
+    out = torch.zeros((T, H, W), dtype=torch.float32, device=dev)
+    groups = cm.inlined_samples(rows, 3, 12) + [(0, n - 1, 0), (2, 5, 0)]
+    ms, feats = K.kf_dag_time_xgroups(dag, groups, f, W, out, ws, reps=2)
+    for (a, b, xm), t, ft in zip(groups, ms, feats):
+        assert t > 0 or t == -1
+        if xm == 0:
+            fi, oc, _ = K.kf_dag_group_info(dag, a, b, W, H, T)
+            np.testing.assert_array_equal(ft, np.array(fi, dtype=np.float32))
+            assert (t > 0) == (oc <= 200 * 1024)
+    with pytest.raises(K.KfuseError):  # the output node may not be inlined
+        K.kf_dag_time_xgroups(dag, [(0, 1, 1 << (n - 1))], f, W, out, ws)
+    K.kf_dag_destroy(dag)
