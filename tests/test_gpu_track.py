@@ -255,3 +255,25 @@ def test_host_call_with_bit_packed_masks(dev, W, chunk):
     K.kf_track_host(ctx.h, host, devb, W, Kp, ws, chunk=chunk, mask_format=K.KF_MASK_BITS)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(host["mask"].numpy()[:, :nbytes], exp)
+
+
+def test_host_call_rejects_bad_arguments_before_any_work(dev):
+    T, H, W, Kp = 3, 32, 64, 8
+    P = sv.pitch_for(W)
+    ctx = K.Context(0)
+    devb = dict(frames=torch.zeros((T, H, P), dtype=torch.uint8, device=dev),
+                mask=torch.zeros((T, H, P), dtype=torch.uint8, device=dev),
+                counts=torch.zeros(T, dtype=torch.int32, device=dev), n_points=torch.zeros(T, dtype=torch.int32, device=dev),
+                idx=torch.zeros((T, Kp), dtype=torch.int32, device=dev), u=torch.zeros((T, Kp), device=dev),
+                v=torch.zeros((T, Kp), device=dev), status=torch.zeros((T, Kp), dtype=torch.int32, device=dev))
+    host = {k: torch.empty_like(t, device="cpu").pin_memory() for k, t in devb.items()}
+    ws = torch.empty(K.kf_track_workspace_bytes(ctx.h, W, H, T), dtype=torch.uint8, device=dev)
+    with pytest.raises(K.KfuseError):  # unknown mask format
+        K.kf_track_host(ctx.h, host, devb, W, Kp, ws, chunk=2, mask_format=7)
+    with pytest.raises(K.KfuseError):  # empty chunks
+        K.kf_track_host(ctx.h, host, devb, W, Kp, ws, chunk=0)
+    packed = dict(host, mask=torch.zeros((T, 8), dtype=torch.uint8).pin_memory())  # < ceil(W H / 8) bytes a frame
+    with pytest.raises(K.KfuseError):
+        K.kf_track_host(ctx.h, packed, devb, W, Kp, ws, chunk=2, mask_format=K.KF_MASK_BITS)
+    torch.cuda.synchronize()
+    assert K.kf_device_error(ctx.h) == 0
