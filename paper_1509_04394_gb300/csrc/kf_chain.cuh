@@ -198,15 +198,16 @@ __device__ __forceinline__ float lo16_to_float(uint32_t x) { return __uint_as_fl
 __device__ __forceinline__ float hi16_to_float(uint32_t x) { return __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7632)) - 8388608.0f; }
 
 // Stage 4: Sobel. Per row: Dx = g(x+1) - g(x-1), Sx = g(x-1) + 2 g(x) + g(x+1);
-// then Ix = Dx(r-1) + 2 Dx(r) + Dx(r+1) = (1,1)^2 pass of Dx, Iy = Sx(r+1) - Sx(r-1) =
-// (1,-1) then (1,1) pass of Sx. Output row = input row - 1.
+// then Ix = Dx(r-1) + 2 Dx(r) + Dx(r+1) = (1,1)^2 pass of Dx, Iy = Sx(r+1) - Sx(r-1)
+// directly from the Sx of two rows before (one subtraction; the values are integers
+// below 2^24, so every form gives the same bits). Output row = input row - 1.
 struct SobelV {
     float d[2][C];  // Dx passes
-    float s[2][C];  // Sx passes
+    float s[2][C];  // Sx of the previous row and of the one before it
     __device__ __forceinline__ void fill(const float (&dx)[C], const float (&sx)[C])
     {
 #pragma unroll
-        for (int c = 0; c < C; ++c) { d[0][c] = dx[c]; d[1][c] = 2.0f * dx[c]; s[0][c] = sx[c]; s[1][c] = 0.0f; }
+        for (int c = 0; c < C; ++c) { d[0][c] = dx[c]; d[1][c] = 2.0f * dx[c]; s[0][c] = sx[c]; s[1][c] = sx[c]; }
     }
     __device__ __forceinline__ void replay(float (&dx)[C], float (&sx)[C])
     {
@@ -220,9 +221,8 @@ struct SobelV {
             const float a = dx[c] + d[0][c];
             ix[c] = a + d[1][c];
             d[0][c] = dx[c]; d[1][c] = a;
-            const float p = sx[c] - s[0][c];
-            iy[c] = p + s[1][c];
-            s[0][c] = sx[c]; s[1][c] = p;
+            iy[c] = sx[c] - s[1][c];
+            s[1][c] = s[0][c]; s[0][c] = sx[c];
         }
     }
 };
