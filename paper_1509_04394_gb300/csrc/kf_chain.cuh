@@ -327,9 +327,10 @@ __device__ __forceinline__ void harris(const Rows<3> &s, float (&r)[C])
 }
 
 // Stage 8: threshold + 3x3 non-maximum suppression. Horizontal max of 3, then the
-// vertical max of 3 as two (max, max) passes; the centre row is one row behind.
+// vertical max of the row and the two before it (one 3-input max); the centre row is one
+// row behind.
 struct NmsV {
-    float p[2][C];  // max passes
+    float p[2][C];  // horizontal maxima of the previous row and of the one before it
     float rc[C];    // R of the previous row (the centre of the output row)
     __device__ __forceinline__ void fill(const float (&mh)[C], const float (&r)[C])
     {
@@ -348,11 +349,10 @@ struct NmsV {
         unsigned bits = 0;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const float m1 = fmaxf(mh[c], p[0][c]);
-            const float m9 = fmaxf(m1, p[1][c]);
+            const float m9 = fmaxf(fmaxf(mh[c], p[0][c]), p[1][c]);
             centre[c] = rc[c];
             bits |= ((centre[c] > thr) & (centre[c] >= m9)) ? (1u << c) : 0u;
-            p[0][c] = mh[c]; p[1][c] = m1; rc[c] = r[c];
+            p[1][c] = p[0][c]; p[0][c] = mh[c]; rc[c] = r[c];
         }
         return bits;
     }
