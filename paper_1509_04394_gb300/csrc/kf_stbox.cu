@@ -363,7 +363,18 @@ BoxKernel box_kernel(int n, int x)
 {
     return n == 1 ? box_kernel_n<1>(x) : n == 2 ? box_kernel_n<2>(x) : n == 4 ? box_kernel_n<4>(x) : nullptr;
 }
-int box_threads(int x) { return x <= 16 ? 32 : x <= 32 ? 64 : x <= 48 ? 128 : x <= 64 ? 256 : 512; }
+int box_threads(int x)
+{
+    switch (x) {
+    case 8: return BoxCfg<8>::THREADS;
+    case 16: return BoxCfg<16>::THREADS;
+    case 32: return BoxCfg<32>::THREADS;
+    case 48: return BoxCfg<48>::THREADS;
+    case 64: return BoxCfg<64>::THREADS;
+    case 96: return BoxCfg<96>::THREADS;
+    default: return 0;
+    }
+}
 template <int N> int box_smem_n(int x)
 {
     switch (x) {
