@@ -45,3 +45,18 @@ def test_smem_grows_with_the_box_and_the_ring():
 def test_bad_arguments_are_rejected(n, x):
     with pytest.raises(K.KfuseError):
         K.kf_st_smem_bytes(n, x)
+
+
+@pytest.mark.parametrize("n", [2, 4])
+@pytest.mark.parametrize("beta", [4096, 16384, 65536])
+def test_least_traffic_box_is_the_grid_point_nearest_eq6(n, beta):
+    """On the benchmark's 1024 x 1024 x 1000 volume, among the box sides 8..96 with
+    t = beta / x^2, the box of least clipped traffic is one of the grid points next to
+    Eq. 6's x (the model's optimum; clipping at the volume's edges moves it little)."""
+    sides = [x for x in (8, 16, 32, 48, 64, 96) if beta // (x * x) >= 1]
+    clipped = {x: K.kf_st_traffic(1024, 1024, 1000, x, beta // (x * x), n)[1] for x in sides}
+    best = min(clipped, key=clipped.get)
+    x6, _ = K.kf_st_box_eq6(beta, n)
+    below = max([x for x in sides if x <= x6], default=min(sides))
+    above = min([x for x in sides if x >= x6], default=max(sides))
+    assert best in (below, above)
