@@ -520,6 +520,15 @@ kf_status kf_st_traffic(int64_t W, int64_t H, int64_t T, int x, int t, int n, do
 /* Eq. 6 for this group's reaches (dx = 2, dt = n) and output volume beta = x^2 t:
  * x = (2 beta dx / dt)^(1/3), t = beta / x^2. */
 kf_status kf_st_box_eq6(double beta, int n, double *x, double *t);
+/* The supported box nearest Eq. 6 for output volume beta (>= 1): the side closest in
+ * ratio to Eq. 6's x, t = beta / x^2 rounded (at least 1). */
+kf_status kf_st_plan_eq6(double beta, int n, int *x, int *t);
+/* The measured choice: runs kf_st_run once per candidate box (boxes[2 i], boxes[2 i + 1]
+ * = x, t; one warm-up, `reps` timed runs, CUDA events on `stream`) and returns the
+ * fastest box and its mean time. Every run writes mask and counts (the last one's stay).
+ * Synchronous. */
+kf_status kf_st_tune(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64_t mask_pitch, int32_t *counts, int n,
+                     const int *boxes, int count, int reps, void *stream, int *best_x, int *best_t, float *best_ms);
 /* The group over the whole video in boxes of x * x * t (x as for kf_st_smem_bytes, t >=
  * 1), one block per box, frames streamed through shared memory in time order (the
  * temporal halo stays on chip for the box). mask: device, T x H x mask_pitch bytes (16-byte aligned,

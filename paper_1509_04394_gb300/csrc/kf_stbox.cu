@@ -508,4 +508,68 @@ kf_status kf_st_run(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64_
     return e == cudaSuccess ? KF_OK : st_fail(ctx, e);
 }
 
+kf_status kf_st_plan_eq6(double beta, int n, int *x, int *t)
+{
+    if (!(beta >= 1) || !kf::valid_n(n) || !x || !t) return KF_EINVAL;
+    double xe = 0, te = 0;
+    kf_st_box_eq6(beta, n, &xe, &te);
+    static const int sides[] = {8, 16, 32, 48, 64, 96};
+    int best = 8;
+    double best_r = INFINITY;
+    for (int sd : sides) {  // nearest supported side by ratio
+        const double r = sd > xe ? sd / xe : xe / sd;
+        if (r < best_r) {
+            best_r = r;
+            best = sd;
+        }
+    }
+    *x = best;
+    const double tt = beta / ((double)best * best);
+    *t = tt < 1.0 ? 1 : (int)llround(tt);
+    return KF_OK;
+}
+
+kf_status kf_st_tune(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64_t mask_pitch, int32_t *counts, int n,
+                     const int *boxes, int count, int reps, void *stream, int *best_x, int *best_t, float *best_ms)
+{
+    if (!ctx || !video || !boxes || count < 1 || reps < 1 || !best_x || !best_t) return KF_EINVAL;
+    if (ctx->device < 0) return KF_ESTATE;
+    for (int i = 0; i < count; ++i)
+        if (!kf::box_kernel(n, boxes[2 * i]) || boxes[2 * i + 1] < 1) return KF_EINVAL;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return st_fail(ctx, e);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return KF_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return KF_ECUDA;
+    }
+    int bx = 0, bt = 0;
+    float best = INFINITY;
+    kf_status st = KF_OK;
+    for (int i = 0; i < count && st == KF_OK; ++i) {
+        const int x = boxes[2 * i], t = boxes[2 * i + 1];
+        st = kf_st_run(ctx, video, mask, mask_pitch, counts, n, x, t, stream);  // warm-up
+        if (st != KF_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == KF_OK; ++r) st = kf_st_run(ctx, video, mask, mask_pitch, counts, n, x, t, stream);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = KF_ECUDA;
+        float ms = 0;
+        if (st == KF_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / reps < best) {
+            best = ms / reps;
+            bx = x;
+            bt = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != KF_OK) return st;
+    *best_x = bx;
+    *best_t = bt;
+    if (best_ms) *best_ms = best;
+    return KF_OK;
+}
+
 }  // extern "C"

@@ -125,6 +125,8 @@ def _lib():
             "kf_st_traffic": (i32, [i64, i64, i64, i32, i32, i32, P, P]),
             "kf_st_box_eq6": (i32, [dbl, i32, P, P]),
             "kf_st_run": (i32, [P, P, P, i64, P, i32, i32, i32, P]),
+            "kf_st_plan_eq6": (i32, [dbl, i32, P, P]),
+            "kf_st_tune": (i32, [P, P, P, i64, P, i32, P, i32, i32, P, P, P, P]),
             "kf_dag_xplan_traffic": (i32, [P, u32, u32, i64, i64, i64, P, P]),
             "kf_dag_plan_recompute": (i32, [P, i64, i64, i64, dbl, P, P, P, P]),
             "kf_dag_run_x": (i32, [P, u32, u32, P, P, i64, P, ctypes.c_size_t, P]),
@@ -149,7 +151,7 @@ def exported_symbols() -> list[str]:
             "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_grad", "kf_costmodel_get",
             "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times", "kf_pc_traffic", "kf_pc_plan",
             "kf_pc_workspace_bytes", "kf_pc_run", "kf_pc_run_group", "kf_pc_kalman", "kf_pc_group_workspace_bytes",
-            "kf_track_host", "kf_st_smem_bytes", "kf_st_traffic", "kf_st_box_eq6", "kf_st_run",
+            "kf_track_host", "kf_st_smem_bytes", "kf_st_traffic", "kf_st_box_eq6", "kf_st_run", "kf_st_plan_eq6", "kf_st_tune",
             "kf_dag_xplan_traffic", "kf_dag_plan_recompute", "kf_dag_run_x", "kf_dag_time_xgroups"]
 
 
@@ -743,3 +745,21 @@ def kf_st_run(ctx, frames, W: int, mask, counts, n: int, x: int, t: int, stream=
     v = _pc_video(frames, W)
     _check("kf_st_run", _lib().kf_st_run(ctx, ctypes.byref(v), mask.data_ptr(), int(mask.shape[2]), counts.data_ptr(),
                                          int(n), int(x), int(t), _stream(stream)), ctx)
+
+
+def kf_st_plan_eq6(beta: float, n: int) -> tuple[int, int]:
+    """The supported box (x, t) nearest Eq. 6 for output volume beta."""
+    x, t = ctypes.c_int(), ctypes.c_int()
+    _check("kf_st_plan_eq6", _lib().kf_st_plan_eq6(float(beta), int(n), ctypes.byref(x), ctypes.byref(t)))
+    return x.value, t.value
+
+
+def kf_st_tune(ctx, frames, W: int, mask, counts, n: int, boxes, reps: int = 3, stream=None) -> tuple[int, int, float]:
+    """The fastest of the candidate boxes [(x, t), ...] on this video: (x, t, ms)."""
+    v = _pc_video(frames, W)
+    arr = (ctypes.c_int * (2 * len(boxes)))(*[int(a) for xt in boxes for a in xt])
+    bx, bt, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check("kf_st_tune", _lib().kf_st_tune(ctx, ctypes.byref(v), mask.data_ptr(), int(mask.shape[2]), counts.data_ptr(),
+                                           int(n), arr, len(boxes), int(reps), _stream(stream), ctypes.byref(bx),
+                                           ctypes.byref(bt), ctypes.byref(ms)), ctx)
+    return bx.value, bt.value, ms.value

@@ -102,3 +102,21 @@ def test_full_size_sampled_frames(dev):
         assert cnt[f] == co[-1]
     # every count equals its mask's
     np.testing.assert_array_equal(cnt, mask.view(T, -1).sum(dim=1, dtype=torch.int64).cpu().numpy())
+
+
+def test_box_tuner_returns_the_fastest_candidate_and_the_same_results(dev):
+    T, H, W, n = 20, 96, 128, 2
+    fr = rgba_video(T, H, W, seed=31)
+    ctx = K.Context(0)
+    frames = torch.from_numpy(fr).to(dev)
+    mask = torch.zeros((T, H, W), dtype=torch.uint8, device=dev)
+    counts = torch.zeros(T, dtype=torch.int32, device=dev)
+    boxes = [(16, 8), (32, 4), (32, 16), (64, 2)]
+    x, t, ms = K.kf_st_tune(ctx.h, frames, W, mask, counts, n, boxes, reps=2)
+    assert (x, t) in boxes and ms > 0
+    torch.cuda.synchronize()
+    m, c = run(dev, fr, W, n, x, t)
+    np.testing.assert_array_equal(mask.cpu().numpy(), m)
+    np.testing.assert_array_equal(counts.cpu().numpy(), c)
+    with pytest.raises(K.KfuseError):  # an unsupported side
+        K.kf_st_tune(ctx.h, frames, W, mask, counts, n, [(24, 4)])

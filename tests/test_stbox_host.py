@@ -60,3 +60,16 @@ def test_least_traffic_box_is_the_grid_point_nearest_eq6(n, beta):
     below = max([x for x in sides if x <= x6], default=min(sides))
     above = min([x for x in sides if x >= x6], default=max(sides))
     assert best in (below, above)
+
+
+@pytest.mark.parametrize("beta", [1, 100, 4096, 16384, 65536, 1e6])
+@pytest.mark.parametrize("n", ost.TAPS)
+def test_eq6_plan_is_the_nearest_supported_side(beta, n):
+    x, t = K.kf_st_plan_eq6(beta, n)
+    x6, _ = opart.eq6_box(beta, ost.DX, n)
+    sides = (8, 16, 32, 48, 64, 96)
+    ratio = lambda s: max(s / x6, x6 / s)  # noqa: E731
+    assert x in sides and ratio(x) == min(ratio(s) for s in sides)
+    assert t == max(1, round(beta / (x * x)))
+    with pytest.raises(K.KfuseError):
+        K.kf_st_plan_eq6(0.5, n)
