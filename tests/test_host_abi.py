@@ -39,6 +39,27 @@ def test_library_exports_every_declared_function():
     assert sorted(K.exported_symbols()) == names
 
 
+def declared_arity():
+    """Parameter count of every function kfuse.h declares."""
+    src = open(os.path.join(ROOT, "include", "kfuse.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(kf_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    arity = declared_arity()
+    assert len(arity) == len(declared_functions())
+    L = K._lib()
+    for name, n in arity.items():
+        f = getattr(L, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+
+
 def test_version_and_status_strings():
     assert K.kf_version() == (1, 0)
     L = K._lib()
