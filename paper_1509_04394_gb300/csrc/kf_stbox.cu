@@ -95,7 +95,6 @@ template <int N> __host__ __device__ constexpr int binom(int k)
     return N == 1 ? 1 : N == 2 ? (k == 1 ? 2 : 1) : (k == 2 ? 6 : (k == 1 || k == 3) ? 4 : 1);
 }
 
-// Launch shape of a box side X: threads per block and rows per work item of passes B / C.
 // Launch shape of a box side X: threads per block (about ten pixel pairs of a staged
 // frame per thread) and rows per work item of passes B and C.
 template <int X> struct BoxCfg {
@@ -104,7 +103,7 @@ template <int X> struct BoxCfg {
     static constexpr int SEG_B = (X + 2 + THREADS / ((X + 4) / 4) - 1) / (THREADS / ((X + 4) / 4));
     static constexpr int SEG_C = (X + THREADS / (X / 4) - 1) / (THREADS / (X / 4));
     // row loops of passes B and C fully unrolled (compile-time register windows) where the
-    // register budget allows it without spilling; measured 13 % faster at X = 64
+    // register budget allows it without spilling; measured 15 % faster at X = 64
     static constexpr int UNROLL_B = X >= 32 && X <= 64 ? SEG_B + 2 : 1;
     static constexpr int UNROLL_C = X >= 32 && X <= 64 ? SEG_C + 2 : 1;
     static constexpr int SR = X + 4, SC = X + 8, GW = X + 4;  // staged rows / columns; G columns
