@@ -316,14 +316,20 @@ __global__ void __launch_bounds__(32 * TW, Group<A, B>::MIN_BLOCKS) pc_tile_kern
                 const int o = r - 1;
                 if (i < 2 || o < lo || o >= hi) continue;
                 // rows o-1, o+1; at the frame's first and last rows the row itself (clamp on G')
-                const bool top = !rows_inside && y0 + o - 1 < 0, bot = !rows_inside && y0 + o + 1 > H - 1;
                 float m[C4];
+                if (rows_inside) {  // warp-uniform: tiles away from the frame's top and bottom
 #pragma unroll
-                for (int e = 0; e < C4; ++e) {
-                    const float dc = Dv[1][e], sc = Sv[1][e];
-                    const float dm = top ? dc : Dv[0][e], dp = bot ? dc : Dv[2][e];
-                    const float sm = top ? sc : Sv[0][e], sp = bot ? sc : Sv[2][e];
-                    m[e] = fabsf(tap121(dm, dc, dp)) + fabsf(sp - sm);
+                    for (int e = 0; e < C4; ++e)
+                        m[e] = fabsf(tap121(Dv[0][e], Dv[1][e], Dv[2][e])) + fabsf(Sv[2][e] - Sv[0][e]);
+                } else {
+                    const bool top = y0 + o - 1 < 0, bot = y0 + o + 1 > H - 1;
+#pragma unroll
+                    for (int e = 0; e < C4; ++e) {
+                        const float dc = Dv[1][e], sc = Sv[1][e];
+                        const float dm = top ? dc : Dv[0][e], dp = bot ? dc : Dv[2][e];
+                        const float sm = top ? sc : Sv[0][e], sp = bot ? sc : Sv[2][e];
+                        m[e] = fabsf(tap121(dm, dc, dp)) + fabsf(sp - sm);
+                    }
                 }
                 emit(o, m);
             }
