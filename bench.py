@@ -28,6 +28,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1509_04394_gb300 import shard  # noqa: E402
 from synth import video as sv  # noqa: E402
 
 METRIC = "fused-chain Mpixel/s & HBM roofline fraction vs unfused, 800×600×1000 u8"
@@ -117,7 +118,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ ranks
 def max_over_ranks(ms: float, world: int, device=None) -> float:
-    """The slowest rank's time (replicas: every rank processes its own volume)."""
+    """The slowest rank's time (every rank processes its own frame range)."""
     if world <= 1:
         return ms
     import torch
@@ -133,11 +134,15 @@ def job_rate(pixels_per_rank: int, world: int, ms: float) -> float:
 
 
 # ------------------------------------------------------------------ workload
-def make_video(rank: int, T: int | None = None):
+def make_video(rank: int = 0, world: int = 1, T: int | None = None):
+    """Rank `rank`'s frames of one video of world x T frames (T defaults to the workload's
+    1000): the T frames it owns and, before them, the one frame that the tracking of its
+    first owned frame reads (none for rank 0). Returns (frames [n, H, P], P, owned)."""
     P = sv.pitch_for(SPEC.W)
-    spec = SPEC if rank == 0 else sv.VideoSpec(**{**SPEC.__dict__, "seed": SPEC.seed + 1000 * rank})
-    frames, _ = sv.generate(spec, pitch=P, frames=range(T or spec.T))
-    return frames, P
+    T = T or SPEC.T
+    s0, t0, t1 = shard.span(world * T, world, rank)
+    frames, _ = sv.generate(SPEC, pitch=P, frames=range(s0, t1))
+    return frames, P, t1 - t0
 
 
 def run_profile(args):
@@ -147,7 +152,7 @@ def run_profile(args):
     from paper_1509_04394_gb300 import build as kbuild
     from paper_1509_04394_gb300 import kfuse as K
     kbuild.build()
-    frames_h, P = make_video(0, args.profile)
+    frames_h, P, _ = make_video(0, 1, args.profile)
     T, H, W = frames_h.shape[0], SPEC.H, SPEC.W
     dev = torch.device("cuda:0")
     frames = torch.from_numpy(frames_h).to(dev)
@@ -195,7 +200,7 @@ def cpu_oracle_rate(frames: np.ndarray, W: int, budget_s: float = 12.0) -> dict:
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
-    frames, P = make_video(0)
+    frames, P, _ = make_video()
     from oracle import chain as oc
     T, H, W = SPEC.T, SPEC.H, SPEC.W
     per_step = 25  # frames of the workload per timed step (24 tracked frame pairs)
@@ -236,8 +241,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if world > 1:
         dist.barrier()
 
-    frames_h, P = make_video(rank)
-    T, H, W = SPEC.T, SPEC.H, SPEC.W
+    frames_h, P, owned = make_video(rank, world)  # this rank's frame range of one video
+    T, H, W = frames_h.shape[0], SPEC.H, SPEC.W
     KP = 256  # tracked points per frame
     frames_pin = torch.from_numpy(frames_h).pin_memory()
     frames = frames_pin.to(dev)
@@ -303,7 +308,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     clocks = clk.summary(t_soak, t_b)
     dev_err = K.kf_device_error(ctx.h)
 
-    px = T * H * W
+    px = owned * H * W  # pixels this rank owns (the halo frame before them is not counted)
     value = job_rate(px, world, ms)
     hbm_peak, peak_kind = peaks()
     n_corners = int(counts.sum())
@@ -411,8 +416,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    f"top-{KP} corner selection + LK tracking per frame pair", "partition_cuts": cuts,
                    "groups": n_groups, "chunk_rows": 200, "cols_per_lane": 4,
                    "l2": "inputs larger than L2 (480 MB frames, 480 MB mask), no flush",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "frames_per_s": world * T / (ms / 1000),
+                   "parallelism": (f"frame shards x{world} of one {world * owned}-frame video, merged on the host"
+                                   if world > 1 else "single GPU")},
+        "frames_per_s": world * owned / (ms / 1000),
         "tracked_points_per_s": world * tracked / (ms / 1000),
         "chain_only": {"value": world * px / (ms_chain / 1000) / 1e6, "ms_per_step": ms_chain,
                        "kernel": "group_kernel<1,8> (full fusion, no corner lists), timed alone by kf_run",

@@ -1,6 +1,7 @@
-"""The benchmark's multi-GPU path is replicas (weak scaling, no collective on the data
-path): each rank times its own volume, rank 0 reports the slowest rank's time and the
-whole job's pixels over it. The rank logic runs here as two gloo processes on the CPU."""
+"""The benchmark's multi-GPU path shards one video by frame range (weak scaling, no
+collective on the data path): each rank times its own frames, rank 0 reports the slowest
+rank's time and the whole job's pixels over it. The rank logic runs here as two gloo
+processes on the CPU."""
 import os
 import socket
 
