@@ -1,6 +1,7 @@
 """Pins of the random-DAG oracle and generator (CPU only): binomial weights, impulse
 responses and border clamps of the stencil, 3x3 maximum by brute force, saturation of
-the product, and the generator's topological order."""
+the product, node 0 as the frame over full scale, and the generator's topological
+order."""
 import itertools
 
 import numpy as np
@@ -48,6 +49,12 @@ def test_pointwise_stages():
     np.testing.assert_array_equal(od.stage(1, x, None, 0, -1.5, 0.25), -1.5 * x + 0.25)
     np.testing.assert_array_equal(od.stage(2, x, None, 0, 0, 0), np.abs(x))
     np.testing.assert_array_equal(od.stage(3, x, z, 0, 0, 0), [[-8.0, 1.0], [16.0, -16.0]])
+
+
+def test_node_zero_is_the_frame_in_units_of_full_scale():
+    nodes = od.run_frame([(1, 0, -1, 0, 1.0, 0.0)], np.array([[0, 51, 255]], dtype=np.uint8))
+    np.testing.assert_array_equal(nodes[0], [[0.0, 0.2, 1.0]])
+    np.testing.assert_array_equal(nodes[1], nodes[0])
 
 
 def test_random_dags_are_topological_and_sized():

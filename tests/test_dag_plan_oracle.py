@@ -1,6 +1,6 @@
 """Pins of the recompute-vs-store plan reference (CPU only): Sec. VI-D's serial and fused
 transfer for a chain of point stages, a three-stage DAG worked by hand with and without
-recomputing its first node, stores and members by their definitions, and the brute
+recomputing its first node, a 3x3 maximum's halo by hand, stores and members by their definitions, and the brute
 force's minimum against every plan listed by hand."""
 import pytest
 
@@ -43,6 +43,16 @@ def test_hand_worked_recompute():
     assert not odp.valid(rows, 0, {3})
     assert odp.group_members(rows, 1, 2, {2}) == {1}
     assert odp.group_members(rows, 3, 3, {2}) == {2, 3}
+
+
+def test_hand_worked_max3():
+    # 1 = 3x3 max(frame), 2 = affine(1): the max reads the frame with a halo of 1
+    rows = [(MAX3, 0, -1, 1, 0, 0), (AFF, 1, -1, 0, 1.0, 0.0)]
+    fused = (odp.TX + 2) * (odp.TY + 2) * 1 + TILE * 4
+    assert odp.plan_traffic(rows, 0, set(), odp.TX, odp.TY, 1) == fused
+    assert odp.plan_traffic(rows, 1, set(), odp.TX, odp.TY, 1) == fused + TILE * 4 * 2
+    # frame slot, node 1's slot; node 2 reuses the frame's: 2 slots of (TX + 2)(TY + 2)
+    assert odp.onchip_bytes(rows, 1, 2, set()) == 2 * (odp.TX + 2) * (odp.TY + 2) * 4
 
 
 def test_inlined_node_not_needed_by_its_range_is_not_computed_there():

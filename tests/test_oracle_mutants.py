@@ -1,9 +1,12 @@
 """Mutation check of the oracle's pins (CPU only). Each case plants one plausible mistake
-in a copy of the C oracle -- a wrong tap, sign, index or operand, a dropped term or
-stage, a wrong border, threshold or tie rule, a wrong frame -- builds the copy in a
-temporary directory, and runs the pins of test_oracle_pins.py against it: at least one
-pin must fail for every mutant. The unchanged copy, run the same way, passes every pin.
-The oracle itself is never modified."""
+in a copy of an oracle -- a wrong tap, sign, index or operand, a dropped term or stage,
+a wrong border, threshold or tie rule, a wrong frame, a one-sided halo -- and runs that
+oracle's pins against the copy: at least one pin must fail for every mutant. The C
+oracle's copies are built in a temporary directory; a Python oracle's copy is executed
+as a fresh module and swapped in for the pin module's reference to it. The unchanged
+copies, run the same way, pass every pin. The oracles themselves are never modified.
+Changes that cannot alter any result are not listed (e.g. in the plan reference, every
+external input of a group is stored by an earlier group by construction)."""
 import concurrent.futures as cf
 import inspect
 import itertools
@@ -70,9 +73,11 @@ MUTANTS = {
 }
 
 
-def _pin_calls():
-    """Every pin with each of its parameter sets, in source order (cheap pins first)."""
-    fns = [f for n, f in inspect.getmembers(pins, inspect.isfunction) if n.startswith("test_")]
+def _pin_calls(module=pins):
+    """Every pin of `module` with each of its parameter sets, in source order (cheap pins
+    first)."""
+    fns = [f for n, f in inspect.getmembers(module, inspect.isfunction)
+           if n.startswith("test_") and f.__module__ == module.__name__]
     fns.sort(key=lambda f: f.__code__.co_firstlineno)
     calls = []
     for f in fns:
@@ -138,3 +143,158 @@ def test_unchanged_copy_passes_every_pin(builds, monkeypatch):
 @pytest.mark.parametrize("name", list(MUTANTS))
 def test_every_planted_mistake_fails_a_pin(builds, monkeypatch, name):
     assert _failing_pin(monkeypatch, builds[name]) is not None, f"no pin catches: {name}"
+
+
+# ------------------------------------------------------------------ the Python oracles
+# module: (pin modules and the name each binds the module to, {name: (text, replacement)})
+PY_MUTANTS = {
+    "pchain": (["test_pchain_oracle:op"], {
+        "gray takes blue for green": ("150.0 * c[..., 1]", "150.0 * c[..., 2]"),
+        "gray scale off": ("(256.0 * 255.0)", "(255.0 * 255.0)"),
+        "IIR weights swapped": ("return y_prev + alpha * (g - y_prev)", "return g + alpha * (y_prev - g)"),
+        "IIR first frame scaled": ("return g.copy()", "return alpha * g"),
+        "Gaussian weights do not sum to one": ("w = {-1: 0.25, 0: 0.5, 1: 0.25}", "w = {-1: 0.25, 0: 0.25, 1: 0.25}"),
+        "gradient one-sided": ("gx += s[d] * (_shift(G, d, 1) - _shift(G, d, -1))",
+                               "gx += s[d] * (_shift(G, d, 1) - _shift(G, d, 0))"),
+        "gradient y along x": ("gy += s[d] * (_shift(G, 1, d) - _shift(G, -1, d))",
+                               "gy += s[d] * (_shift(G, d, 1) - _shift(G, d, -1))"),
+        "L2 magnitude instead of L1": ("np.abs(gx) + np.abs(gy)", "np.hypot(gx, gy)"),
+        "threshold not strict": ("mask = M > tau\n", "mask = M >= tau\n"),
+        "regions transposed": ("r = (GRID * y // H) * GRID + (GRID * x // W)",
+                               "r = (GRID * x // W) * GRID + (GRID * y // H)"),
+        "region sums swapped": ("regions[r, 1] += x\n        regions[r, 2] += y",
+                                "regions[r, 1] += y\n        regions[r, 2] += x"),
+        "Kalman half-step transition": ("F = np.block([[I2, I2], [np.zeros((2, 2)), I2]])",
+                                        "F = np.block([[I2, 0.5 * I2], [np.zeros((2, 2)), I2]])"),
+        "Kalman process noise off": ("I2 / 3.0, I2 / 2.0", "I2 / 2.0, I2 / 2.0"),
+        "Kalman prediction adds no noise": ("P = F @ P @ F.T + Q", "P = F @ P @ F.T"),
+        "Kalman innovation reversed": ("s = s + K @ (z - Hm @ s)", "s = s + K @ (Hm @ s - z)"),
+        "Kalman covariance not updated": ("P = (np.eye(4) - K @ Hm) @ P", "P = P"),
+        "centroid transposed": ("z = np.array([sx / cnt, sy / cnt])", "z = np.array([sy / cnt, sx / cnt])"),
+    }),
+    "stbox": (["test_stbox_oracle:ost"], {
+        "gray takes blue for green": ("150 * c[..., 1]", "150 * c[..., 2]"),
+        "temporal window one frame late": ("comb(n, k) * g[max(t - n + k, 0)]", "comb(n, k) * g[max(t - n + k - 1, 0)]"),
+        "temporal weights linear": ("comb(n, k) * g[max(t - n + k, 0)]", "(k + 1) * g[max(t - n + k, 0)]"),
+        "Gaussian box weights": ("w = {-1: 1, 0: 2, 1: 1}", "w = {-1: 1, 0: 1, 1: 1}"),
+        "Prewitt weights": ("s = {-1: 1, 0: 2, 1: 1}", "s = {-1: 1, 0: 1, 1: 1}"),
+        "gradient y along x": ("gy += s[d] * (_shift(G, 1, d) - _shift(G, -1, d))",
+                               "gy += s[d] * (_shift(G, d, 1) - _shift(G, d, -1))"),
+        "threshold scale doubled": ("return 261120 << n", "return 261120 << (n + 1)"),
+        "threshold not strict": ("masks[t] = M > thr", "masks[t] = M >= thr"),
+        "model halo one-sided": ("(x + 2 * DX) ** 2 * (t + n) * bytes_in", "(x + DX) ** 2 * (t + n) * bytes_in"),
+        "model temporal halo two-sided": ("(t + n) * bytes_in", "(t + 2 * n) * bytes_in"),
+        "clipped reads on the future side": ("ct = sum(spans(T, t, n, 0))", "ct = sum(spans(T, t, 0, n))"),
+        "clipped reads not clipped at the end": ("min(s + b + r_hi, N) - max(s - r_lo, 0)",
+                                                 "s + b + r_hi - max(s - r_lo, 0)"),
+        "utilisation temporal halo two-sided": ("return x * x * t / ((x + 2 * DX) ** 2 * (t + n))",
+                                                "return x * x * t / ((x + 2 * DX) ** 2 * (t + 2 * n))"),
+    }),
+    "partition": (["test_partition_oracle:op", "test_stbox_oracle:opart"], {
+        "cut bit read off by one": ("if cuts >> i & 1:", "if cuts >> (i + 1) & 1:"),
+        "one cut point too few": ("repeat=n - 1", "repeat=n - 2"),
+        "halo is the maximum radius": ("return (sum(s.rx for s in stages[a:b + 1]), sum(s.ry",
+                                       "return (max(s.rx for s in stages[a:b + 1]), sum(s.ry"),
+        "spatial halo one-sided": ("(x + 2 * Rx) * (y + 2 * Ry) * (t + Rt) * stages[a].in_bytes",
+                                   "(x + Rx) * (y + Ry) * (t + Rt) * stages[a].in_bytes"),
+        "temporal halo two-sided": ("(t + Rt) * stages[a].in_bytes", "(t + 2 * Rt) * stages[a].in_bytes"),
+        "group reads the last stage's input": ("stages[a].in_bytes", "stages[b].in_bytes"),
+        "group writes the first stage's output": ("x * y * t * stages[b].out_bytes", "x * y * t * stages[a].out_bytes"),
+        "on-chip rows one-sided": ("(2 * s.ry + 1) * s.in_bytes", "(s.ry + 1) * s.in_bytes"),
+        "feasible if any group fits": ("return all(group_onchip(stages, a, b, box) <= onchip_limit",
+                                       "return any(group_onchip(stages, a, b, box) <= onchip_limit"),
+        "utilisation temporal halo two-sided": ("* (t + rt))", "* (t + 2 * rt))"),
+        "Eq. 6 without its factor 2": ("x = (2.0 * beta * dx / dt) ** (1.0 / 3.0)",
+                                       "x = (beta * dx / dt) ** (1.0 / 3.0)"),
+        "brute force keeps the worst": ("if best is None or c < best[1]:", "if best is None or c > best[1]:"),
+        "Sobel writes one map": ('Stage("sobel", 1, 1, 0, 1 * e, 2 * e)', 'Stage("sobel", 1, 1, 0, 1 * e, 1 * e)'),
+    }),
+    "dag": (["test_dag_oracle:od"], {
+        "binomial weights unnormalised": ("/ 4.0 ** r", "/ 2.0 ** r"),
+        "binomial row shifted": ("comb(2 * r, r + k)", "comb(2 * r, k + 1)"),
+        "affine bias scaled": ("return a * a_in + b", "return a * (a_in + b)"),
+        "product squares its first input": ("np.clip(a_in * b_in, -16.0, 16.0)", "np.clip(a_in * a_in, -16.0, 16.0)"),
+        "stencil not separable": ("out += w[iy] * w[ix] * _shift(a_in, dy, dx)",
+                                  "out += w[iy] * w[iy] * _shift(a_in, dy, dx)"),
+        "max over the diagonal only": ("out = np.maximum(out, _shift(a_in, dy, dx))",
+                                       "out = np.maximum(out, _shift(a_in, dy, dy))"),
+        "frames wrap instead of clamping": ("xs = np.clip(np.arange(W) + dx, 0, W - 1)", "xs = (np.arange(W) + dx) % W"),
+        "node 0 divides by 256": ("frame_u8.astype(np.float64) / 255.0", "frame_u8.astype(np.float64) / 256.0"),
+        "second input read from the first": ("nodes[i2] if i2 >= 0 else None", "nodes[i1] if i2 >= 0 else None"),
+    }),
+    "mlp": (["test_mlp_oracle:mlp"], {
+        "ReLU gate dropped in layer 2": ("dz2 = np.outer(dy, w3) * (z2 > 0)", "dz2 = np.outer(dy, w3)"),
+        "back-propagation through W2 transposed": ("dz1 = (dz2 @ W2) * (z1 > 0)", "dz1 = (dz2 @ W2.T) * (z1 > 0)"),
+        "loss derivative without its 2": ("dy = 2.0 * (y - t) / n", "dy = (y - t) / n"),
+        "output bias gradient averaged": ("g_b3 = dy.sum()", "g_b3 = dy.mean()"),
+        "W2 gradient from pre-activations": ("g_W2 = dz2.T @ h1", "g_W2 = dz2.T @ z1"),
+        "forward subtracts the first bias": ("h1 = np.maximum(x @ W1.T + b1, 0.0)", "h1 = np.maximum(x @ W1.T - b1, 0.0)"),
+    }),
+    "dag_plan": (["test_dag_plan_oracle:odp"], {
+        "3x3 max has no radius": ("return r if kind == 4 else (1 if kind == 5 else 0)", "return r if kind == 4 else 0"),
+        "product's second input dropped": ("return [i1, i2] if kind == 3 and i2 != i1 else [i1]", "return [i1]"),
+        "stored when read by the range's last stage": ("if c > b:", "if c >= b:"),
+        "halo ignores the consumer's radius": ("h = max(h, halo[c] + radius(rows[c - 1]))", "h = max(h, halo[c])"),
+        "input halo one-sided": ("(TX + 2 * h) * (TY + 2 * h) * (1 if e == 0 else 4)",
+                                 "(TX + h) * (TY + h) * (1 if e == 0 else 4)"),
+        "frame read as a float map": ("(1 if e == 0 else 4)", "4"),
+        "stored maps as bytes": ("t += TX * TY * 4 * len(outs)", "t += TX * TY * len(outs)"),
+        "slots never freed": ("if last.get(i) == j and i in slots:", "if False:"),
+        "slots without halo": ("return taken * (TX + 2 * hmax) * (TY + 2 * hmax) * 4", "return taken * TX * TY * 4"),
+        "brute force keeps the worst": ("if best is None or c < best[0] - 1e-9:", "if best is None or c > best[0] + 1e-9:"),
+        "range cut bit off by one": ("if b == n or (cuts >> (b - 1)) & 1:", "if b == n or (cuts >> b) & 1:"),
+    }),
+}
+
+
+def _module_from(modname: str, text: str):
+    """Execute oracle source `text` as a fresh module (relative imports resolve in the
+    oracle package); registered only while it runs, so nothing else sees it."""
+    import sys
+    import types
+    name = f"oracle._planted_{modname}"
+    m = types.ModuleType(name)
+    m.__package__ = "oracle"
+    sys.modules[name] = m
+    try:
+        exec(compile(text, f"<planted oracle/{modname}.py>", "exec"), m.__dict__)
+    finally:
+        del sys.modules[name]
+    return m
+
+
+def _py_failing_pin(monkeypatch, modname, module):
+    import importlib
+    binds, _ = PY_MUTANTS[modname]
+    pin_mods = []
+    for b in binds:
+        mod_name, alias = b.split(":")
+        pm = importlib.import_module(f"tests.{mod_name}")
+        monkeypatch.setattr(pm, alias, module)
+        pin_mods.append(pm)
+    for pm in pin_mods:
+        for name, f, kw in _pin_calls(pm):
+            try:
+                f(**kw)
+            except Exception as e:
+                return f"{pm.__name__}.{name}{kw or ''}: {type(e).__name__}"
+    return None
+
+
+def _py_source(modname):
+    import importlib
+    return open(importlib.import_module(f"oracle.{modname}").__file__).read()
+
+
+@pytest.mark.parametrize("modname", list(PY_MUTANTS))
+def test_unchanged_python_oracle_passes_every_pin(monkeypatch, modname):
+    assert _py_failing_pin(monkeypatch, modname, _module_from(modname, _py_source(modname))) is None
+
+
+@pytest.mark.parametrize("modname,name", [(m, n) for m, (_, ms) in PY_MUTANTS.items() for n in ms])
+def test_every_planted_mistake_in_a_python_oracle_fails_a_pin(monkeypatch, modname, name):
+    src = _py_source(modname)
+    old, new = PY_MUTANTS[modname][1][name]
+    assert src.count(old) == 1, f"{modname} / {name}: the planted text must occur exactly once"
+    got = _py_failing_pin(monkeypatch, modname, _module_from(modname, src.replace(old, new)))
+    assert got is not None, f"no pin catches: {modname} / {name}"

@@ -2,7 +2,9 @@
 
 Golden values come from the paper: the four partitions of three kernels (Sec. VI),
 the n(n+1)/2 candidate groups (Fig. 5), Transfer_serial = 2nBxyt (Sec. VI-D), the
-data-utilisation ratio (Eq. 3) and the closed-form box of Eq. 6.
+data-utilisation ratio (Eq. 3) and the closed-form box of Eq. 6, also as the minimiser of
+the traffic model itself; the unfused Harris chain's bytes per pixel and one fused
+group's on-chip bytes counted by hand; feasibility requires every group to fit.
 """
 import os
 
@@ -77,6 +79,39 @@ def test_eq6_is_the_minimiser_of_eq5(beta, dx, dt):
     x_num = xs[np.argmin(V)]
     assert x_cf == pytest.approx(x_num, rel=1e-3)
     assert t_cf == pytest.approx(beta / x_cf ** 2, rel=1e-12)
+
+
+@pytest.mark.parametrize("beta,dx,dt", [(48 * 1024, 1, 1), (20000, 3, 2)])
+def test_traffic_model_is_minimised_at_the_eq6_box(beta, dx, dt):
+    # one spatio-temporal stage, no output bytes: at a fixed box volume beta the model's
+    # traffic is (boxes = const / beta) x the box's input, so its minimum is Eq. 6's box
+    st = [op.Stage("st", dx, dx, dt, 1, 0)]
+    xs = np.linspace(2.0, 150.0, 60001)
+    cost = [op.group_traffic(st, 0, 0, 512, 512, 64, (x, x, beta / x ** 2)) for x in xs]
+    assert op.eq6_box(beta, dx, dt)[0] == pytest.approx(xs[int(np.argmin(cost))], rel=2e-3)
+
+
+@pytest.mark.parametrize("e,total", [(4, 98), (2, 50)])
+def test_unfused_harris_chain_bytes_per_pixel(e, total):
+    # FP32 maps: reads 1 + 4 + 4 + 4 + 8 + 12 + 12 + 4 = 49, writes 4 + 4 + 4 + 8 + 12 + 12
+    # + 4 + 1 = 49 (Sobel writes Ix and Iy, products and sums three maps, the mask one
+    # byte); 16-bit maps: 25 + 25
+    assert sum(s.in_bytes + s.out_bytes for s in op.harris_chain(e)) == total
+
+
+def test_onchip_bytes_of_the_fused_harris_chain_by_hand():
+    # halo 0+2+0+1+0+2+0+1 = 6 columns a side; rows held x bytes: convert 1 x 1, Gaussian-H
+    # 1 x 4, Gaussian-V 5 x 4, Sobel 3 x 4, products 1 x 8, box 5 x 12, Harris 1 x 12,
+    # NMS 3 x 4 = 129 bytes per column of the (116 + 12)-wide box, one frame
+    assert op.group_onchip(op.harris_chain(4), 0, 7, (116, 64, 1)) == (116 + 12) * 129
+
+
+def test_a_partition_is_feasible_only_if_every_group_fits():
+    st, box = op.harris_chain(4), (116, 64, 1)
+    small, big = op.group_onchip(st, 0, 0, box), op.group_onchip(st, 1, 7, box)
+    assert small < big
+    assert op.feasible(st, [(0, 0), (1, 7)], box, big)
+    assert not op.feasible(st, [(0, 0), (1, 7)], box, big - 1)
 
 
 def test_brute_force_prefers_full_fusion_for_the_harris_chain_on_large_boxes():

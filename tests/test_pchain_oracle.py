@@ -1,8 +1,10 @@
 """Pins of the FP64 reference of the paper's own chain (CPU only): gray weights, the IIR
 filter's step response in closed form, the 3x3 Gaussian's impulse response and border
 clamp, the gradient of ramps (interior and clamped border), threshold and region sums by
-brute force, and the Kalman filter against the steady state of the discrete algebraic
-Riccati equation (scipy's solver), noise-free tracking and pure prediction."""
+brute force, a ramp whose gradient magnitude is exactly the threshold, the Kalman model
+(one frame of constant velocity; the process noise as the integral of white acceleration
+over a frame), the filter against the steady state of the discrete algebraic Riccati
+equation (scipy's solver), noise-free tracking and pure prediction."""
 import numpy as np
 import pytest
 
@@ -71,6 +73,25 @@ def test_threshold_and_regions_by_brute_force():
     np.testing.assert_array_equal(mask, (M > op.TAU).astype(np.uint8))
 
 
+def _tau_ramp(T, H, W, blue_step):
+    """RGBA frames, constant in time and along y, whose gray value grows per column by
+    (77 * 4 + 150 * 10 + 29 * blue_step) / (256 * 255). With blue_step = 8 that is 2040 /
+    65280 = 1/32, and the Sobel magnitude of the ramp (smoothing leaves it unchanged) is
+    8 / 32 = 0.25, the threshold itself, at every column two or more from the edges."""
+    x = np.arange(W)
+    fr = np.zeros((T, H, W, 4), dtype=np.uint8)
+    fr[..., 0], fr[..., 1], fr[..., 2], fr[..., 3] = 4 * x, 10 * x, blue_step * x, 255
+    return fr
+
+
+def test_a_magnitude_exactly_at_the_threshold_is_not_marked():
+    masks, counts, _, maps = op.chain_volume(_tau_ramp(3, 5, 26, 8), keep_maps=True)
+    assert (maps["M"][:, :, 2:-2] == op.TAU).all()  # exact: every value is a small multiple of 2^-9
+    assert counts.tolist() == [0, 0, 0] and not masks.any()
+    masks, counts, _, _ = op.chain_volume(_tau_ramp(3, 5, 26, 9), keep_maps=True)  # 2069 / 65280 per column
+    assert masks[:, :, 2:-2].all() and not masks[:, :, :2].any() and not masks[:, :, -2:].any()
+
+
 def test_chain_volume_of_a_constant_video_is_empty():
     fr = np.full((3, 6, 8, 4), 120, dtype=np.uint8)
     masks, counts, regions, maps = op.chain_volume(fr, keep_maps=True)
@@ -81,6 +102,25 @@ def test_chain_volume_of_a_constant_video_is_empty():
 def _regions_of(points):
     """[T, 1, 3] region sums of one point per frame (count 1)."""
     return np.array([[[1, x, y]] for x, y in points], dtype=np.int64)
+
+
+def test_kalman_model_is_constant_velocity_with_white_acceleration():
+    F, Q, Hm, R = op.kalman_matrices()
+    s = np.array([3.0, -2.0, 0.5, 1.5])
+    np.testing.assert_array_equal(F @ s, [3.5, -0.5, 0.5, 1.5])  # one frame at constant velocity
+    np.testing.assert_array_equal(Hm @ s, [3.0, -2.0])
+    np.testing.assert_array_equal(R, op.KALMAN_R * np.eye(2))
+    # the covariance that white acceleration of intensity q adds over one frame:
+    # q * integral_0^1 Phi(u) G G' Phi(u)' du, Phi(u) = [[I, u I], [0, I]], G = [0; I]
+    # (midpoint rule; its error on these quadratic entries is 1 / (12 m^2))
+    m = 4000
+    I2, Z2 = np.eye(2), np.zeros((2, 2))
+    G = np.vstack([Z2, I2])
+    acc = np.zeros((4, 4))
+    for u in (np.arange(m) + 0.5) / m:
+        Phi = np.block([[I2, u * I2], [Z2, I2]])
+        acc += Phi @ G @ G.T @ Phi.T
+    np.testing.assert_allclose(Q, op.KALMAN_Q * acc / m, rtol=0, atol=1e-7)
 
 
 def test_kalman_converges_to_the_dare_steady_state_gain():

@@ -1,7 +1,7 @@
 """Pins of the spatio-temporal group's reference (CPU only): the temporal binomial's impulse
 response, start clamp and delay of a ramp in time; the integer chain against the FP64
 chain on real values built from the pinned stage functions of the paper's own chain; a
-brute-force evaluation with exact rationals; the clipped box reads by enumeration; and
+ramp whose gradient magnitude is exactly the threshold; a brute-force evaluation with exact rationals; the clipped box reads by enumeration; and
 Eq. 6 as the maximiser of Eq. 3 for this group's reaches."""
 from fractions import Fraction
 from math import comb
@@ -74,6 +74,24 @@ def test_integer_chain_equals_the_real_valued_chain(n):
     assert clear.mean() > 0.99
     np.testing.assert_array_equal(masks[clear], masks_r[clear])
     np.testing.assert_array_equal(counts, masks.reshape(6, -1).sum(axis=1))
+
+
+@pytest.mark.parametrize("n", ost.TAPS)
+def test_a_magnitude_exactly_at_the_threshold_is_not_marked(n):
+    # gray grows by (77 * 4 + 150 * 10 + 29 * b) per column; with b = 8 that is 2040, and
+    # the integer magnitude 2040 * 8 (Sobel) * 16 (3x3 weights) * 2^n (temporal weights)
+    # = 261120 * 2^n is the threshold itself at every column two or more from the edges
+    def ramp(b):
+        x = np.arange(26)
+        fr = np.zeros((n + 2, 5, 26, 4), dtype=np.uint8)
+        fr[..., 0], fr[..., 1], fr[..., 2], fr[..., 3] = 4 * x, 10 * x, b * x, 255
+        return fr
+    masks, counts, M = ost.chain_volume(ramp(8), n, keep_m=True)
+    assert (M[:, :, 2:-2] == 261120 * 2 ** n).all() and not masks.any() and not counts.any()
+    masks_r, M_r = ost.chain_volume_real(ramp(8), n)
+    assert (M_r[:, :, 2:-2] == ost.TAU).all() and not masks_r.any()
+    masks, _, _ = ost.chain_volume(ramp(9), n)
+    assert masks[:, :, 2:-2].all() and not masks[:, :, :2].any() and not masks[:, :, -2:].any()
 
 
 def test_brute_force_with_exact_rationals():
