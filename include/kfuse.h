@@ -21,6 +21,10 @@
  *   - A frame is H rows x W columns; x = column (positive right), y = row (positive
  *     down). Volumes hold T frames back to back.
  *   - Bad arguments are rejected with KF_EINVAL before anything is enqueued.
+ *   - Workspace sizes and runs take volumes of W, H in 1..2^30, T in 0..2^31-1 and at
+ *     most 2^46 pixels in all (a batch: its videos together); larger ones are KF_EINVAL,
+ *     so that no byte count overflows 64 bits. Calls state tighter bounds where they
+ *     have them (e.g. W * H below 2^31 for tracking).
  *   - One context per host thread; a context is not thread-safe.
  */
 #ifndef KFUSE_H

@@ -561,7 +561,7 @@ kf_status kf_map_scale(const kf_ctx *ctx, int stage, double *factor)
 
 kf_status kf_workspace_bytes(const kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_t T, size_t *bytes)
 {
-    if (!ctx || !bytes || W <= 0 || H <= 0 || T < 0) return KF_EINVAL;
+    if (!ctx || !bytes || !kf::volume_ok(W, H, T)) return KF_EINVAL;
     if (cuts >> (kf::NSTAGES - 1)) return KF_EINVAL;
     *bytes = plan_workspace(ctx, cuts, W, H, T).total;
     return KF_OK;
@@ -594,7 +594,7 @@ kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *v, const kf_corners
     if (!builtin_chain(ctx)) return KF_EUNSUPPORTED;
     if (!v || !o) return KF_EINVAL;
     if (cuts >> (kf::NSTAGES - 1)) return KF_EINVAL;
-    if (v->W <= 0 || v->H <= 0 || v->T < 0 || v->W > (1 << 30) || v->H > (1 << 30)) return KF_EINVAL;
+    if (!kf::volume_ok(v->W, v->H, v->T)) return KF_EINVAL;
     if (v->pitch < v->W || v->pitch % 16 || o->mask_pitch < v->W || o->mask_pitch % 16) return KF_EINVAL;
     if (v->T == 0) return KF_OK;  // nothing to read or write
     if (!v->frames || !o->mask || !o->counts) return KF_EINVAL;
@@ -641,8 +641,7 @@ kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *v, const kf_corners
 
 kf_status kf_track_workspace_bytes(const kf_ctx *ctx, int64_t W, int64_t H, int64_t T, size_t *bytes)
 {
-    if (!ctx || !bytes || W <= 0 || H <= 0 || T < 0 || W > (1 << 30) || H > (1 << 30) || W * H > 0x7fffffffLL)
-        return KF_EINVAL;
+    if (!ctx || !bytes || !kf::volume_ok(W, H, T) || W * H > 0x7fffffffLL) return KF_EINVAL;
     *bytes = (size_t)round_up(4 * T, 256) + (size_t)(8 * kf::cand_capacity(W, H) * T);
     return KF_OK;
 }
@@ -656,8 +655,7 @@ kf_status check_track_args(kf_ctx *ctx, const kf_video *v, const kf_corners *o, 
     if (ctx->device < 0) return KF_ESTATE;
     if (!builtin_chain(ctx)) return KF_EUNSUPPORTED;
     if (!v || !o || !tr) return KF_EINVAL;
-    if (v->W <= 0 || v->H <= 0 || v->T < 0 || v->W > (1 << 30) || v->H > (1 << 30) || v->W * v->H > 0x7fffffffLL)
-        return KF_EINVAL;
+    if (!kf::volume_ok(v->W, v->H, v->T) || v->W * v->H > 0x7fffffffLL) return KF_EINVAL;
     if (v->pitch < v->W || v->pitch % 16 || o->mask_pitch < v->W || o->mask_pitch % 16) return KF_EINVAL;
     if (tr->K < 1 || tr->K > 1024) return KF_EINVAL;
     if (v->T == 0) return KF_OK;
@@ -667,7 +665,7 @@ kf_status check_track_args(kf_ctx *ctx, const kf_video *v, const kf_corners *o, 
         !aligned(tr->idx, 4) || !aligned(tr->u, 4) || !aligned(tr->v, 4) || !aligned(tr->status, 4))
         return KF_EINVAL;
     size_t need = 0;
-    kf_track_workspace_bytes(ctx, v->W, v->H, v->T, &need);
+    if (kf_track_workspace_bytes(ctx, v->W, v->H, v->T, &need) != KF_OK) return KF_EINVAL;
     if (!ws || !aligned(ws, 256)) return KF_EINVAL;
     if (ws_bytes < need) return KF_ENOMEM;
     return KF_OK;
@@ -988,7 +986,7 @@ BatchLayout batch_layout(const kf_video *videos, int n, bool track)
 
 bool video_ok(const kf_video *v)
 {
-    return v && v->W > 0 && v->H > 0 && v->T > 0 && v->W <= (1 << 30) && v->H <= (1 << 30) && v->W * v->H <= 0x7fffffffLL &&
+    return v && v->T > 0 && kf::volume_ok(v->W, v->H, v->T) && v->W * v->H <= 0x7fffffffLL &&
            v->pitch >= v->W && v->pitch % 16 == 0 && v->frames && aligned(v->frames, 16);
 }
 
@@ -999,8 +997,13 @@ extern "C" {
 kf_status kf_batch_workspace_bytes(const kf_ctx *ctx, const kf_video *videos, int n, int track_K, size_t *bytes)
 {
     if (!ctx || !videos || n < 1 || !bytes || track_K < 0 || track_K > 1024) return KF_EINVAL;
-    for (int i = 0; i < n; ++i)
-        if (videos[i].W <= 0 || videos[i].H <= 0 || videos[i].T <= 0) return KF_EINVAL;
+    int64_t px = 0;  // the whole batch within the single-volume bound
+    for (int i = 0; i < n; ++i) {
+        const kf_video &v = videos[i];
+        if (v.T <= 0 || !kf::volume_ok(v.W, v.H, v.T)) return KF_EINVAL;
+        px += v.W * v.H * v.T;
+        if (px > ((int64_t)1 << 46)) return KF_EINVAL;
+    }
     *bytes = batch_layout(videos, n, track_K > 0).total;
     return KF_OK;
 }

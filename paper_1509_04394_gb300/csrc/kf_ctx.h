@@ -10,6 +10,15 @@
 namespace kf {
 struct CostModel;                   // kf_mlp.cu
 void costmodel_free(kf_ctx *ctx);   // kf_mlp.cu
+
+// The volumes the library sizes workspaces for: sides of 1..2^30 pixels, 0..2^31-1 frames
+// and at most 2^46 pixels in all (far beyond device memory), so that no workspace byte
+// count (a few tens of bytes per pixel at most) can overflow 64 bits.
+inline bool volume_ok(int64_t W, int64_t H, int64_t T)
+{
+    if (W <= 0 || H <= 0 || T < 0 || W > (1 << 30) || H > (1 << 30) || T > 0x7fffffffLL) return false;
+    return T == 0 || W * H <= ((int64_t)1 << 46) / T;
+}
 }  // namespace kf
 
 struct kf_ctx {

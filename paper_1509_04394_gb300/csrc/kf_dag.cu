@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/kfuse.h"
+#include "kf_ctx.h"
 
 namespace kf {
 int ctx_device(const kf_ctx *ctx);
@@ -514,7 +515,7 @@ kf_status kf_dag_plan(const kf_dag *d, const double *group_cost, uint32_t *cuts,
 
 kf_status kf_dag_workspace_bytes(const kf_dag *d, int64_t W, int64_t H, int64_t T, size_t *bytes)
 {
-    if (!d || !bytes || W <= 0 || H <= 0 || T <= 0) return KF_EINVAL;
+    if (!d || !bytes || T <= 0 || !kf::volume_ok(W, H, T)) return KF_EINVAL;
     const Geo g = geo_of(d, W, H, T);
     *bytes = (size_t)(g.plane * 4) * (size_t)(d->n + 1);
     return KF_OK;
@@ -529,7 +530,7 @@ kf_status kf_dag_run(kf_dag *d, uint32_t cuts, const kf_video *v, float *out, in
     if (v->W <= 0 || v->H <= 0 || v->T <= 0 || !v->frames || v->pitch < v->W || out_pitch < v->W) return KF_EINVAL;
     if (v->T > 65535 || v->H > (1 << 30)) return KF_EINVAL;
     size_t need = 0;
-    kf_dag_workspace_bytes(d, v->W, v->H, v->T, &need);
+    if (kf_dag_workspace_bytes(d, v->W, v->H, v->T, &need) != KF_OK) return KF_EINVAL;
     if (!ws || ws_bytes < need) return KF_ENOMEM;
     if (cudaSetDevice(d->device) != cudaSuccess) return KF_ECUDA;
     const Geo geo = geo_of(d, v->W, v->H, v->T);
@@ -660,7 +661,7 @@ kf_status kf_dag_run_x(kf_dag *d, uint32_t cuts, uint32_t inline_mask, const kf_
     if (v->W <= 0 || v->H <= 0 || v->T <= 0 || !v->frames || v->pitch < v->W || out_pitch < v->W) return KF_EINVAL;
     if (v->T > 65535 || v->H > (1 << 30)) return KF_EINVAL;
     size_t need = 0;
-    kf_dag_workspace_bytes(d, v->W, v->H, v->T, &need);
+    if (kf_dag_workspace_bytes(d, v->W, v->H, v->T, &need) != KF_OK) return KF_EINVAL;
     if (!ws || ws_bytes < need) return KF_ENOMEM;
     std::vector<GroupPlan> plans;
     int a = 1;

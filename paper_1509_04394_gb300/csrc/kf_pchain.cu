@@ -566,7 +566,8 @@ kf_status check_video(const kf_pc_video *v)
 {
     if (!v || !v->rgba || v->W <= 0 || v->H <= 0 || v->T < 0 || v->pitch < v->W || v->pitch % 4 || !aligned(v->rgba, 16))
         return KF_EINVAL;
-    if (v->W > (1 << 24) || v->H > (1 << 24) || v->T > 0x7fffffff || v->W * v->H > 0x7fffffffLL) return KF_EINVAL;
+    if (v->W > (1 << 24) || v->H > (1 << 24) || !kf::volume_ok(v->W, v->H, v->T) || v->W * v->H > 0x7fffffffLL)
+        return KF_EINVAL;
     if (!sums_fit(v->W, v->H)) return KF_EINVAL;
     return KF_OK;
 }
@@ -692,7 +693,7 @@ kf_status kf_pc_plan(kf_ctx *ctx, int64_t W, int64_t H, int64_t T, uint32_t *cut
 
 kf_status kf_pc_workspace_bytes(kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_t T, size_t *bytes)
 {
-    if (!ctx || !bytes || W <= 0 || H <= 0 || T < 0 || cuts >= 16) return KF_EINVAL;
+    if (!ctx || !bytes || !kf::volume_ok(W, H, T) || cuts >= 16) return KF_EINVAL;
     const int n_cuts = __builtin_popcount(cuts);
     const size_t plane = (size_t)(ws_pitch(W) * H * T) * sizeof(float);
     const size_t plane_a = (plane + 255) / 256 * 256;
@@ -710,7 +711,7 @@ kf_status kf_pc_run(kf_ctx *ctx, uint32_t cuts, const kf_pc_video *video, const 
     const int dev = kf::ctx_device(ctx);
     if (dev < 0) return KF_ESTATE;
     size_t need = 0;
-    kf_pc_workspace_bytes(ctx, cuts, video->W, video->H, video->T, &need);
+    if (kf_pc_workspace_bytes(ctx, cuts, video->W, video->H, video->T, &need) != KF_OK) return KF_EINVAL;
     if (need && (!workspace || !aligned(workspace, 256))) return KF_EINVAL;
     if (workspace_bytes < need) return KF_ENOMEM;
     if (cudaSetDevice(dev) != cudaSuccess) return KF_ECUDA;
@@ -741,7 +742,7 @@ kf_status kf_pc_run(kf_ctx *ctx, uint32_t cuts, const kf_pc_video *video, const 
 
 kf_status kf_pc_group_workspace_bytes(kf_ctx *ctx, int a, int b, int64_t W, int64_t H, int64_t T, size_t *bytes)
 {
-    if (!ctx || !bytes || a < 0 || b < a || b >= KF_PC_STAGES || W <= 0 || H <= 0 || T < 0) return KF_EINVAL;
+    if (!ctx || !bytes || a < 0 || b < a || b >= KF_PC_STAGES || !kf::volume_ok(W, H, T)) return KF_EINVAL;
     *bytes = (holds_iir(a, b) ? state_bytes(W, H, T) : 0) + (b == 4 ? slot_bytes(T) : 0);
     return KF_OK;
 }
@@ -752,7 +753,7 @@ kf_status kf_pc_run_group(kf_ctx *ctx, int a, int b, const kf_pc_video *video, c
 {
     if (!ctx || a < 0 || b < a || b >= KF_PC_STAGES) return KF_EINVAL;
     // geometry from the video descriptor (its rgba is only read when a == 0)
-    if (!video || video->W <= 0 || video->H <= 0 || video->T < 0 || video->T > 0x7fffffff || !sums_fit(video->W, video->H))
+    if (!video || !kf::volume_ok(video->W, video->H, video->T) || !sums_fit(video->W, video->H))
         return KF_EINVAL;
     const int64_t W = video->W, H = video->H, T = video->T;
     if (a == 0) {

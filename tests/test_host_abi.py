@@ -4,6 +4,7 @@ The library's dynamic program must find the same optimum as the oracle's brute-f
 enumeration of all 2^(n-1) partitions (Sec. VI, Fig. 5) under the traffic model of
 Sec. VI-D, on the Harris chain and on random chains of up to 12 kernels.
 """
+import ctypes
 import math
 import os
 import re
@@ -192,3 +193,41 @@ def test_map_scales(hctx):
     K.kf_set_precision(hctx, K.KF_PREC_F16)
     assert K.kf_map_scale(hctx, 2) == pytest.approx(1 / 65280)  # exact uint16 map
     assert all(K.kf_map_scale(hctx, s) == 1.0 for s in range(3, 8))  # FP16, true units
+
+
+def test_workspace_sizes_refuse_volumes_whose_byte_counts_could_overflow(hctx):
+    # every side 1..2^30, at most 2^31 - 1 frames and 2^46 pixels: the byte counts at the
+    # bound are exact (no 64-bit wrap), one step past it is refused
+    from synth import dags as sd
+    K.kf_add_harris_chain(hctx)
+    side, lim = 1 << 30, 1 << 46
+    ok = [(side, 1 << 16, 1), (1 << 13, 1 << 13, 1 << 20)]
+    bad = [(side + 1, 4, 1), (4, side + 1, 1), (4, 4, 1 << 31), (side, 1 << 16, 2), (1 << 13, 1 << 13, (1 << 20) + 1),
+           (1 << 40, 1 << 40, 1 << 40), (0, 4, 1), (4, 4, -1)]
+    dag = K.kf_dag_create(hctx, sd.to_array(sd.random_dag(1)))
+    for W, H, T in ok:
+        assert W * H * T == lim
+        assert K.kf_workspace_bytes(hctx, 127, W, H, T) >= 2 * 4 * W * H * T  # the cut maps, double buffered
+        assert K.kf_pc_workspace_bytes(hctx, 15, W, H, T) >= 2 * 4 * W * H * T
+        assert K.kf_pc_group_workspace_bytes(hctx, 0, 4, W, H, T) >= 4 * W * H
+        assert K.kf_dag_workspace_bytes(dag, W, H, T) >= 4 * W * H * T
+    for W, H, T in bad:
+        for call in (lambda: K.kf_workspace_bytes(hctx, 127, W, H, T),
+                     lambda: K.kf_pc_workspace_bytes(hctx, 15, W, H, T),
+                     lambda: K.kf_pc_group_workspace_bytes(hctx, 0, 4, W, H, T),
+                     lambda: K.kf_dag_workspace_bytes(dag, W, H, T),
+                     lambda: K.kf_track_workspace_bytes(hctx, W, H, T)):
+            with pytest.raises(K.KfuseError):
+                call()
+    # the tracking workspace also needs W * H below 2^31
+    assert K.kf_track_workspace_bytes(hctx, 1 << 15, 1 << 15, 1 << 16) > 0
+    with pytest.raises(K.KfuseError):
+        K.kf_track_workspace_bytes(hctx, 1 << 16, 1 << 15, 1)
+    # a batch within the bound as a whole
+    L = K._lib()
+    vids = (K.kf_video * 2)(K.kf_video(16, 1 << 13, 1 << 13, 1 << 19, 1 << 13), K.kf_video(16, 1 << 13, 1 << 13, 1 << 19, 1 << 13))
+    b = ctypes.c_size_t()
+    assert L.kf_batch_workspace_bytes(hctx, vids, 2, 0, ctypes.byref(b)) == K.KF_OK and b.value > 0
+    vids[1].T += 1
+    assert L.kf_batch_workspace_bytes(hctx, vids, 2, 0, ctypes.byref(b)) == K.KF_EINVAL
+    K.kf_dag_destroy(dag)
