@@ -616,6 +616,13 @@ class Context:
         except Exception:
             pass
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     def __getattr__(self, name):
         f = globals().get("kf_" + name)
         if f is None:
