@@ -1,7 +1,8 @@
 """Frame-range sharding of one video over processes, merged on the host (CPU only): the
 ranges cover the video in balanced contiguous pieces, a path with a one-frame temporal
-reach merges to the whole-video result only with the one-frame halo, and two gloo ranks
-running the oracle on their shards merge to the oracle's whole-video tracking."""
+reach merges to the whole-video result only with the one-frame halo, two gloo ranks
+running the oracle on their shards merge to the oracle's whole-video tracking, and the
+benchmark's ranks render their ranges of one video."""
 import os
 import socket
 
@@ -124,3 +125,21 @@ def test_two_ranks_merge_to_the_whole_video_tracking():
     assert int(whole["n_points"][5]) > 0  # rank 1's first owned frame tracks points
     for k in whole:
         assert np.array_equal(merged[k], whole[k]), k
+
+
+def test_benchmark_ranks_render_their_ranges_of_one_video():
+    import bench
+    from synth import video as sv
+    world, T = 3, 4
+    P = sv.pitch_for(bench.SPEC.W)
+    whole, _ = sv.generate(bench.SPEC, pitch=P, frames=range(world * T))
+    owned = []
+    for r in range(world):
+        fr, P2, own = bench.make_video(r, world, T)
+        assert P2 == P and own == T and len(fr) == T + (1 if r else 0)
+        assert np.array_equal(fr, whole[max(r * T - 1, 0):(r + 1) * T])
+        owned.append(fr[len(fr) - own:])
+    assert np.array_equal(np.concatenate(owned), whole)
+    # one rank: the single-GPU workload's own first frames
+    fr, _, own = bench.make_video(0, 1, 2)
+    assert own == 2 and np.array_equal(fr, whole[:2])
