@@ -252,7 +252,7 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *video, const kf_corners *out, co
  * of byte f * host_out->mask_pitch + i / 8 (mask_pitch = bytes per frame, >= ceil(W H /
  * 8), a multiple of 16; bits past W H up to the next 4-byte boundary are 0, the rest of
  * each frame's stride is not written). With KF_MASK_BITS the chunks are packed
- * on the device into a staging ring the context owns (3 chunks of packed frames,
+ * on the device into a staging ring the context owns (3 chunks of min(chunk, T) packed frames,
  * allocated on first use and grown when a call needs more) and copied out from there;
  * the device mask is written as well. Asynchronous: `stream` waits for the
  * last copy out, and the copies start after the work queued on `stream` before the call;

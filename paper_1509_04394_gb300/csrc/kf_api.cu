@@ -832,9 +832,11 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     // packed masks: staged per chunk in a device ring of N_RING chunks (owned by the
-    // context, grown on demand) and copied out from there
+    // context, grown on demand) and copied out from there; a chunk holds at most
+    // min(chunk, T) frames
+    const int64_t slot_frames = chunk < T ? chunk : T;
     if (bits) {
-        const size_t need = (size_t)kf_ctx::N_RING * (size_t)chunk * (size_t)host_out->mask_pitch;
+        const size_t need = (size_t)kf_ctx::N_RING * (size_t)slot_frames * (size_t)host_out->mask_pitch;
         if (need > ctx->pack_bytes) {
             // the old ring may still be in use by an earlier call's copy-out stream
             e = ctx->s_out ? cudaStreamSynchronize(ctx->s_out) : cudaSuccess;
@@ -887,7 +889,7 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
         if (bits) {
             // packed on the copy-out stream into ring slot r (the slot's previous chunk was
             // copied out earlier on the same stream), then copied out
-            uint8_t *slot = ctx->pack_buf + (size_t)r * (size_t)chunk * (size_t)host_out->mask_pitch;
+            uint8_t *slot = ctx->pack_buf + (size_t)r * (size_t)slot_frames * (size_t)host_out->mask_pitch;
             const int64_t words = (packed + 3) / 4;
             const dim3 grid((unsigned)((words + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
             if (e == cudaSuccess) {
