@@ -129,3 +129,31 @@ def test_onchip_limit_forces_cuts():
     g, _ = op.brute_force_best(st, 600, 800, 10, box, onchip_limit=full - 1)
     assert len(g) >= 2
     assert op.feasible(st, g, box, full - 1)
+
+
+def _paper_chain():
+    """The paper's K1..K5 (Table II / IV) as stages of the Sec. VI-D model: RGBA in (4
+    bytes), float maps between stages, a byte mask out; K2 reads the previous frame's
+    filtered value (one-sided temporal reach 1), K3 and K4 are 3x3 stencils."""
+    return [op.Stage("gray", 0, 0, 0, 4, 4), op.Stage("iir", 0, 0, 1, 4, 4), op.Stage("gauss3", 1, 1, 0, 4, 4),
+            op.Stage("gradient", 1, 1, 0, 4, 4), op.Stage("threshold", 0, 0, 0, 4, 1)]
+
+
+def test_paper_chain_box_traffic_by_hand():
+    st, N, M, T = _paper_chain(), 256, 256, 1000
+    px = N * M * T
+
+    def per_px(groups, box):
+        return op.partition_cost(st, groups, N, M, T, box) / px
+    none, two, full = [(i, i) for i in range(5)], [(0, 1), (2, 4)], [(0, 4)]
+    # box [8, 8, 8]: halo reads (8 + 2 rx)(8 + 2 ry)(8 + rt) / 512 of the input bytes
+    assert per_px(none, (8, 8, 8)) == pytest.approx((4 + 4) + (4 * 9 / 8 + 4) + 2 * (4 * 100 / 64 + 4) + (4 + 1))
+    assert per_px(two, (8, 8, 8)) == pytest.approx((4 * 9 / 8 + 4) + (4 * 144 / 64 + 1))
+    assert per_px(full, (8, 8, 8)) == pytest.approx(4 * 144 * 9 / (64 * 8) + 1)
+    # fused traffic falls as the box grows (Fig. 12a); without halos No Fusion's would not
+    # change (the paper's "constant"), with them it falls too, towards 2 reads + writes
+    boxes = [(8, 8, 8), (16, 16, 8), (32, 32, 16), (64, 64, 32)]
+    for groups in (two, full):
+        seq = [per_px(groups, b) for b in boxes]
+        assert all(a > b for a, b in zip(seq, seq[1:]))
+    assert per_px(full, (64, 64, 32)) < per_px(two, (64, 64, 32)) < per_px(none, (64, 64, 32))
