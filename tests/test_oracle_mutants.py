@@ -35,6 +35,23 @@ MUTANTS = {
     "Prewitt weights instead of Sobel": ("s[3] = {1.0, 2.0, 1.0};", "s[3] = {1.0, 1.0, 1.0};"),
     "Sobel y one-sided difference": ("g[(int64_t)clampi(y - 1, 0, H - 1) * W + xx]",
                                      "g[(int64_t)clampi(y, 0, H - 1) * W + xx]"),
+    "Ix without vertical smoothing": (
+        "gx += s[d + 1] * (g[(int64_t)yy * W + clampi(x + 1, 0, W - 1)] -\n"
+        "                                  g[(int64_t)yy * W + clampi(x - 1, 0, W - 1)]);",
+        "gx += s[d + 1] * (g[(int64_t)y * W + clampi(x + 1, 0, W - 1)] -\n"
+        "                                  g[(int64_t)y * W + clampi(x - 1, 0, W - 1)]);"),
+    "Gaussian-V clamps to the width": ("clampi(y + k, 0, H - 1)", "clampi(y + k, 0, H - 1 < W - 1 ? H - 1 : W - 1)"),
+    "trace is a difference": ("double tr = sxx[i] + syy[i];", "double tr = sxx[i] - syy[i];"),
+    "convert ignores pitch": ("in[(int64_t)y * pitch + x] / 255.0", "in[(int64_t)y * W + x] / 255.0"),
+    "count counts every pixel": ("count += keep;", "count += 1;"),
+    "box 3 rows instead of 5": ("for (int dy = -2; dy <= 2; ++dy)\n                for (int dx = -2; dx <= 2; ++dx)",
+                                "for (int dy = -1; dy <= 1; ++dy)\n                for (int dx = -2; dx <= 2; ++dx)"),
+    "NMS ignores the row above": ("for (int dy = -1; dy <= 1 && keep; ++dy)", "for (int dy = 0; dy <= 1 && keep; ++dy)"),
+    "volume masks at the width's stride": ("masks + (int64_t)t * H * pitch, pitch);", "masks + (int64_t)t * H * W, pitch);"),
+    "selection keeps one too few": ("int pos = n < K ? n : K;", "int pos = n < K - 1 ? n : K - 1;"),
+    "LK point coordinates swapped": ("int py = idx[i] / W, px = idx[i] % W;", "int py = idx[i] % W, px = idx[i] / W;"),
+    "LK cross term from Iy twice": ("a01 += gx * gy;", "a01 += gy * gy;"),
+    "LK v with the wrong sign": ("v[i] = -(a00 * b1 - a01 * b0) / det;", "v[i] = (a00 * b1 - a01 * b0) / det;"),
     "cross product uses Ix twice": ("pxy[i] = ix[i] * iy[i];", "pxy[i] = ix[i] * ix[i];"),
     "box 3 wide instead of 5": ("for (int dx = -2; dx <= 2; ++dx)", "for (int dx = -1; dx <= 1; ++dx)"),
     "box pads with zeros": (

@@ -45,6 +45,13 @@ def test_gauss_clamps_its_own_input_at_the_border():
     np.testing.assert_allclose(g1[0, :4], [11 / 16, 5 / 16, 1 / 16, 0], atol=1e-15)
     g = oc.gauss_v(g1)
     np.testing.assert_allclose(g[:4, 0], np.array([11, 5, 1, 0]) / 16 * 11 / 16, atol=1e-15)
+    # the bottom-left corner of a frame taller than wide: rows clamp at H - 1, columns at W - 1
+    f = np.zeros((20, 3), dtype=np.uint8)
+    f[19, 0] = 255
+    g1 = oc.gauss_h(oc.convert(f))
+    np.testing.assert_allclose(g1[19], [11 / 16, 5 / 16, 1 / 16], atol=1e-15)
+    g = oc.gauss_v(g1)
+    np.testing.assert_allclose(g[16:, 0], np.array([0, 1, 5, 11]) / 16 * 11 / 16, atol=1e-15)
 
 
 def test_gauss_passes_commute():
@@ -60,6 +67,20 @@ ALPHA, BETA = 2, 3
 def ramp(H=40, W=50):
     y, x = np.mgrid[0:H, 0:W]
     return (ALPHA * x + BETA * y).astype(np.uint8)
+
+
+def test_sobel_impulse_response_is_the_sobel_kernel():
+    # g = a unit impulse at (4, 5): Ix(y, x) = sum_dy s(dy) (g(y+dy, x+1) - g(y+dy, x-1))
+    # puts +s on column 4 and -s on column 6 (rows 3..5), Iy the same transposed
+    g = np.zeros((9, 11))
+    g[4, 5] = 1.0
+    ix, iy = oc.sobel(g)
+    exp_x = np.zeros_like(g)
+    exp_x[3:6, 4], exp_x[3:6, 6] = [1, 2, 1], [-1, -2, -1]
+    exp_y = np.zeros_like(g)
+    exp_y[3, 4:7], exp_y[5, 4:7] = [1, 2, 1], [-1, -2, -1]
+    np.testing.assert_array_equal(ix, exp_x)
+    np.testing.assert_array_equal(iy, exp_y)
 
 
 def test_sobel_on_a_ramp_gives_the_closed_form():
