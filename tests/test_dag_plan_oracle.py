@@ -65,6 +65,14 @@ def test_inlined_node_not_needed_by_its_range_is_not_computed_there():
     assert t == TILE * 1 + TILE * 4
 
 
+def test_inlined_nodes_are_recomputed_through_inlined_inputs():
+    # 1 = affine(frame), 2 = affine(1), 3 = affine(2), a cut after every stage, 1 and 2
+    # inlined: group [3] recomputes 2 and, through it, 1 from the frame
+    rows = chain(3)
+    assert odp.group_members(rows, 3, 3, {1, 2}) == {1, 2, 3}
+    assert odp.plan_traffic(rows, 0b11, {1, 2}, odp.TX, odp.TY, 1) == TILE * 1 + TILE * 4
+
+
 def test_brute_force_is_the_minimum_over_listed_plans():
     rows = [(AFF, 0, -1, 0, 2.0, 0.0), (STEN, 1, -1, 2, 0, 0), (MAX3, 2, -1, 1, 0, 0), (PROD, 3, 1, 0, 0, 0)]
     W, H, T = 64, 32, 1

@@ -106,6 +106,13 @@ def test_onchip_bytes_of_the_fused_harris_chain_by_hand():
     assert op.group_onchip(op.harris_chain(4), 0, 7, (116, 64, 1)) == (116 + 12) * 129
 
 
+def test_onchip_bytes_of_a_spatio_temporal_stage_by_hand():
+    # rx = ry = 1, rt = 2, 4-byte input: (16 + 2) columns x (8 + 2) frames (the temporal
+    # halo on the past side only) x 3 rows x 4 bytes
+    st = [op.Stage("st", 1, 1, 2, 4, 1)]
+    assert op.group_onchip(st, 0, 0, (16, 16, 8)) == 18 * 10 * 3 * 4
+
+
 def test_a_partition_is_feasible_only_if_every_group_fits():
     st, box = op.harris_chain(4), (116, 64, 1)
     small, big = op.group_onchip(st, 0, 0, box), op.group_onchip(st, 1, 7, box)

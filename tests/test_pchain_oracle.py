@@ -43,7 +43,7 @@ def test_gauss3_impulse_constant_and_corner():
     assert op.gauss3(c)[0, 0] == pytest.approx((0.5 + 0.25) * (0.5 + 0.25))
 
 
-@pytest.mark.parametrize("a,b", [(0.3, 0.0), (0.0, -0.2), (0.1, 0.05)])
+@pytest.mark.parametrize("a,b", [(0.3, 0.0), (0.0, -0.2), (0.1, 0.05), (0.1, -0.05)])
 def test_gradient_of_a_ramp(a, b):
     H, W = 9, 11
     yy, xx = np.mgrid[0:H, 0:W]
@@ -139,6 +139,34 @@ def test_kalman_converges_to_the_dare_steady_state_gain():
     step[-1, 0, 1] += 1  # x of the last measurement + 1
     s1, _ = op.kalman(step)
     np.testing.assert_allclose(s1[-1, 0] - s0[-1, 0], K_ss[:, 0], rtol=1e-9, atol=1e-12)
+
+
+def test_kalman_is_two_per_axis_filters_from_the_first_frame():
+    # the model decouples (F, Q, H, R and the start covariance act on x and y alike): each
+    # axis is a 2-state filter [position, velocity] started at its first measurement with
+    # variances (r, p0); run here as scalars from the stated model
+    q, r, p0 = op.KALMAN_Q, op.KALMAN_R, op.KALMAN_P0
+    F = np.array([[1.0, 1.0], [0.0, 1.0]])
+    Q = q * np.array([[1 / 3, 1 / 2], [1 / 2, 1.0]])
+    rng = np.random.default_rng(4)
+    pts = [(30 + 1.5 * t + rng.normal(), 60 - 0.5 * t + rng.normal()) for t in range(40)]
+    reg = np.array([[[1, round(x), round(y)]] for x, y in pts], dtype=np.int64)
+    reg[17:21, 0] = 0  # a gap: prediction only
+    states, status = op.kalman(reg)
+    for axis in (0, 1):
+        s, P = None, None
+        for t in range(40):
+            z = reg[t, 0, 1 + axis] if reg[t, 0, 0] else None
+            if s is None:
+                s, P = np.array([float(z), 0.0]), np.diag([r, p0])
+            else:
+                s, P = F @ s, F @ P @ F.T + Q
+                if z is not None:
+                    k = P[:, 0] / (P[0, 0] + r)
+                    s = s + k * (z - s[0])
+                    P = P - np.outer(k, P[0, :])
+            np.testing.assert_allclose(states[t, 0, [axis, axis + 2]], s, rtol=1e-12, atol=1e-12)
+    assert status[0, 0] == 1 and (status[17:21, 0] == 2).all()
 
 
 def test_kalman_tracks_noise_free_constant_velocity_and_predicts_gaps():
