@@ -52,6 +52,17 @@ MUTANTS = {
     "LK point coordinates swapped": ("int py = idx[i] / W, px = idx[i] % W;", "int py = idx[i] % W, px = idx[i] / W;"),
     "LK cross term from Iy twice": ("a01 += gx * gy;", "a01 += gy * gy;"),
     "LK v with the wrong sign": ("v[i] = -(a00 * b1 - a01 * b0) / det;", "v[i] = (a00 * b1 - a01 * b0) / det;"),
+    "Iy sign flipped": ("iy[(int64_t)y * W + x] = gy;", "iy[(int64_t)y * W + x] = -gy;"),
+    "Harris run with k = 0": ("kfo_harris(n, m[KFO_SXX], m[KFO_SXY], m[KFO_SYY], k, m[KFO_R]);",
+                              "kfo_harris(n, m[KFO_SXX], m[KFO_SXY], m[KFO_SYY], 0.0, m[KFO_R]);"),
+    "threshold not applied": ("int64_t count = kfo_nms(H, W, m[KFO_R], thr, mask, mask_pitch);",
+                              "int64_t count = kfo_nms(H, W, m[KFO_R], -1e300, mask, mask_pitch);"),
+    "selection shifts one too few": ("for (int i = last; i > pos; --i) idx[i] = idx[i - 1];",
+                                     "for (int i = last; i > pos + 1; --i) idx[i] = idx[i - 1];"),
+    "LK b from Ix only": ("b1 += gy * gt;", "b1 += gx * gt;"),
+    "LK determinant sign": ("double det = a00 * a11 - a01 * a01;", "double det = a00 * a11 + a01 * a01;"),
+    "LK window rows clamped to the width": ("clampi(py + dy, 0, H - 1) * W", "clampi(py + dy, 0, W - 1) * W"),
+    "previous frame smoothed along x only": ("kfo_gauss_v(H, W, g1p, gp);", "memcpy(gp, g1p, sizeof(double) * n);"),
     "cross product uses Ix twice": ("pxy[i] = ix[i] * iy[i];", "pxy[i] = ix[i] * ix[i];"),
     "box 3 wide instead of 5": ("for (int dx = -2; dx <= 2; ++dx)", "for (int dx = -1; dx <= 1; ++dx)"),
     "box pads with zeros": (
@@ -194,6 +205,10 @@ PY_MUTANTS = {
         "regions by width for rows": ("r = (GRID * y // H) * GRID + (GRID * x // W)",
                                       "r = (GRID * y // W) * GRID + (GRID * x // W)"),
         "magnitude of the sum": ("np.abs(gx) + np.abs(gy)", "np.abs(gx + gy)"),
+        "Gaussian not separable": ("out += w[dy] * w[dx] * _shift(y, dy, dx)", "out += w[dy] * w[dy] * _shift(y, dy, dx)"),
+        "count of the complement": ("return mask.astype(np.uint8), int(mask.sum()), regions",
+                                    "return mask.astype(np.uint8), int((~mask).sum()), regions"),
+        "IIR restarted every frame": ("        y = iir(y, Y)\n", "        y = iir(None, Y)\n"),
         "centroid transposed": ("z = np.array([sx / cnt, sy / cnt])", "z = np.array([sy / cnt, sx / cnt])"),
     }),
     "stbox": (["test_stbox_oracle:ost"], {
@@ -207,6 +222,7 @@ PY_MUTANTS = {
         "magnitude of the sum": ("return np.abs(gx) + np.abs(gy)", "return np.abs(gx + gy)"),
         "real-valued chain scaled twice": ("/ 2.0 ** n", "/ 2.0 ** (n + 1)"),
         "clipped reads spatial one-sided": ("cx = sum(spans(W, x, DX, DX))", "cx = sum(spans(W, x, 0, DX))"),
+        "gray ignores red": ("77 * c[..., 0] + 150", "0 * c[..., 0] + 150"),
         "threshold scale doubled": ("return 261120 << n", "return 261120 << (n + 1)"),
         "threshold not strict": ("masks[t] = M > thr", "masks[t] = M >= thr"),
         "model halo one-sided": ("(x + 2 * DX) ** 2 * (t + n) * bytes_in", "(x + DX) ** 2 * (t + n) * bytes_in"),
@@ -232,6 +248,9 @@ PY_MUTANTS = {
                                        "return any(group_onchip(stages, a, b, box) <= onchip_limit"),
         "utilisation temporal halo two-sided": ("* (t + rt))", "* (t + 2 * rt))"),
         "on-chip temporal halo two-sided": ("return (x + 2 * Rx) * (t + Rt) * sum", "return (x + 2 * Rx) * (t + 2 * Rt) * sum"),
+        "candidate groups repeat one and miss singletons": (
+            "[(a, b) for a in range(n) for b in range(a, n)]",
+            "[(a, b) for a in range(n) for b in range(a + 1, n)] + [(n - 1, n - 1)] * n"),
         "boxes ignore t": ("boxes = N * M * T / (x * y * t)", "boxes = N * M * T / (x * y)"),
         "Eq. 6 without its factor 2": ("x = (2.0 * beta * dx / dt) ** (1.0 / 3.0)",
                                        "x = (beta * dx / dt) ** (1.0 / 3.0)"),
@@ -261,6 +280,10 @@ PY_MUTANTS = {
         "output bias gradient averaged": ("g_b3 = dy.sum()", "g_b3 = dy.mean()"),
         "W2 gradient from pre-activations": ("g_W2 = dz2.T @ h1", "g_W2 = dz2.T @ z1"),
         "first bias gradient averaged": ("g_b1 = dz1.sum(0)", "g_b1 = dz1.mean(0)"),
+        "W2 unpacked transposed": ("W2 = p[o:o + WIDTH * WIDTH].reshape(WIDTH, WIDTH); o += WIDTH * WIDTH",
+                                   "W2 = p[o:o + WIDTH * WIDTH].reshape(WIDTH, WIDTH).T; o += WIDTH * WIDTH"),
+        "loss summed, not averaged": ("return float(np.mean((forward(p, x) - t) ** 2))",
+                                      "return float(np.sum((forward(p, x) - t) ** 2))"),
         "forward subtracts the first bias": ("h1 = np.maximum(x @ W1.T + b1, 0.0)", "h1 = np.maximum(x @ W1.T - b1, 0.0)"),
     }),
     "dag_plan": (["test_dag_plan_oracle:odp"], {

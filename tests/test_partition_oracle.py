@@ -34,7 +34,9 @@ def test_partition_and_candidate_group_counts():
     for ln in _read("counts.txt"):
         n, parts, groups = map(int, ln.split())
         assert len(op.all_partitions(n)) == parts
-        assert len(op.candidate_groups(n)) == groups
+        cand = op.candidate_groups(n)
+        assert len(cand) == len(set(cand)) == groups  # every contiguous range once
+        assert all(0 <= a <= b < n for a, b in cand)
         # every partition covers each kernel exactly once (Fig. 5 constraint)
         for p in op.all_partitions(n):
             cover = np.zeros(n, dtype=int)

@@ -92,6 +92,16 @@ def test_a_magnitude_exactly_at_the_threshold_is_not_marked():
     assert masks[:, :, 2:-2].all() and not masks[:, :, :2].any() and not masks[:, :, -2:].any()
 
 
+def test_chain_volume_filters_over_time():
+    # a step in time (black, then white frames): the chain's filtered map follows the IIR
+    # filter's step response 1 - (1 - alpha)^t at every pixel
+    fr = np.zeros((8, 4, 5, 4), dtype=np.uint8)
+    fr[1:, ..., :3] = 255
+    _, _, _, maps = op.chain_volume(fr, keep_maps=True)
+    for t in range(8):
+        np.testing.assert_allclose(maps["y"][t], 1.0 - (1.0 - op.ALPHA) ** t if t else 0.0, rtol=0, atol=1e-15)
+
+
 def test_chain_volume_of_a_constant_video_is_empty():
     fr = np.full((3, 6, 8, 4), 120, dtype=np.uint8)
     masks, counts, regions, maps = op.chain_volume(fr, keep_maps=True)
