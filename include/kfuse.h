@@ -156,6 +156,7 @@ kf_status kf_set_chunk_rows(kf_ctx *ctx, int rows);
 kf_status kf_add_stage(kf_ctx *ctx, const kf_stage_desc *desc, int *id);
 /* Declare the eight Harris stages in order (KF_EINVAL if stages were declared before). */
 kf_status kf_add_harris_chain(kf_ctx *ctx);
+/* Number of stages declared so far in *n (KF_EINVAL for a NULL argument). */
 kf_status kf_num_stages(const kf_ctx *ctx, int *n);
 
 /* ------------------------------------------------------------------ planning (host) */
@@ -287,6 +288,8 @@ kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners 
 /* Enqueue one run of the batch on `stream` (asynchronous): every video's mask, counts and,
  * if requested, tracks are rewritten. */
 kf_status kf_batch_run(kf_batch *batch, void *stream);
+/* Free the batch's executable graph (a run still in flight completes first) and its
+ * host state; the caller's workspace and buffers are not touched. NULL is a no-op. */
 kf_status kf_batch_destroy(kf_batch *batch);
 
 /* Autotuner of the executor's tile height: runs the fully fused chain on `video` once
@@ -317,6 +320,7 @@ typedef struct kf_dag kf_dag;
  * group runs as one fused kernel (Alg. 1: its input boxes copied to shared memory once,
  * stages on shared-memory tiles, only the maps later groups read are stored). */
 kf_status kf_dag_create(kf_ctx *ctx, const kf_gstage *stages, int n, kf_dag **out);
+/* Free a DAG made by kf_dag_create (host memory only). NULL is a no-op. */
 kf_status kf_dag_destroy(kf_dag *dag);
 /* For group [first, last] (0-based stages): KF_NFEAT cost-model features (stages,
  * stencils, largest input halo, summed radii, bytes in and out per pixel, shared memory
@@ -477,6 +481,10 @@ kf_status kf_pc_plan(kf_ctx *ctx, int64_t W, int64_t H, int64_t T, uint32_t *cut
  * H x round_up(W, 8)), 32 partial copies of the per-frame sums (T x 32 x 49 int32), then
  * up to two FP32 maps of T x H x round_up(W, 8) between groups, each part 256-aligned. */
 kf_status kf_pc_workspace_bytes(kf_ctx *ctx, uint32_t cuts, int64_t W, int64_t H, int64_t T, size_t *bytes);
+/* Run K1..K5 in partition `cuts` on `stream` (asynchronous): one fused kernel per group
+ * (plus the chunked recursion's two passes for the group holding K2), writing out->mask,
+ * counts and regions. workspace: device, >= kf_pc_workspace_bytes, 256-byte aligned
+ * (may be NULL when that is 0). */
 kf_status kf_pc_run(kf_ctx *ctx, uint32_t cuts, const kf_pc_video *video, const kf_pc_out *out, void *workspace,
                     size_t workspace_bytes, void *stream);
 /* One group [a..b] (0-based stages, a <= b <= 4) over explicit maps. in: a == 0 the RGBA
