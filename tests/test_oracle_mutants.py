@@ -223,6 +223,16 @@ PY_MUTANTS = {
         "real-valued chain scaled twice": ("/ 2.0 ** n", "/ 2.0 ** (n + 1)"),
         "clipped reads spatial one-sided": ("cx = sum(spans(W, x, DX, DX))", "cx = sum(spans(W, x, 0, DX))"),
         "gray ignores red": ("77 * c[..., 0] + 150", "0 * c[..., 0] + 150"),
+        "spatial reach 1": ("DX = 2  #", "DX = 1  #"),
+        "model writes each box twice": ("+ x * x * t * bytes_out)", "+ 2 * x * x * t * bytes_out)"),
+        "model boxes ignore t": ("B = W * H * T / (x * x * t)", "B = W * H * T / (x * x)"),
+        "count of the previous frame": ("counts[t] = int(masks[t].sum())", "counts[t] = int(masks[max(t - 1, 0)].sum())"),
+        "Sobel x one-sided": ("gx += s[d] * (_shift(G, d, 1) - _shift(G, d, -1))",
+                              "gx += s[d] * (_shift(G, d, 1) - _shift(G, d, 0))"),
+        "utilisation spatial halo one-sided": ("return x * x * t / ((x + 2 * DX) ** 2 * (t + n))",
+                                               "return x * x * t / ((x + DX) ** 2 * (t + n))"),
+        "clipped reads skip the first box": ("for s in range(0, N, b)]", "for s in range(b, N, b)]"),
+        "real-valued chain skips the Gaussian": ("M = pchain.gradient(pchain.gauss3(z))[2]", "M = pchain.gradient(z)[2]"),
         "threshold scale doubled": ("return 261120 << n", "return 261120 << (n + 1)"),
         "threshold not strict": ("masks[t] = M > thr", "masks[t] = M >= thr"),
         "model halo one-sided": ("(x + 2 * DX) ** 2 * (t + n) * bytes_in", "(x + DX) ** 2 * (t + n) * bytes_in"),
