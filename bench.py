@@ -36,6 +36,12 @@ UNIT = "Mpixel/s"
 E2E_CHUNK = 100  # frames per chunk of the pipelined host-to-host call
 SPEC = sv.HSDV_800x600x1000
 WORKLOAD = "Harris 8-stage chain, 1000 frames x 800 rows x 600 cols u8, 64 blobs + 32 patches, seed 3"
+# Algorithmic FP32 operations per output pixel of the chain, from the stage definitions
+# (an FMA counts once): the basis of the ALU roofline of the fused kernel.
+OPS_BY_STAGE = {"S1 convert": 1, "S2 Gaussian-H (2 adds, 2 FMAs)": 4, "S3 Gaussian-V": 4,
+                "S4 Sobel (Dx 1, Sx 2, Ix 2, Iy 1)": 6, "S5 products": 3, "S6 box 5x5 (3 x (4 + 4) adds)": 24,
+                "S7 Harris (det 2, trace 1, response 2)": 5, "S8 threshold + 3x3 max (2 + 2 max3, 2 compares)": 6}
+OPS_PER_PX = sum(OPS_BY_STAGE.values())
 
 
 def kernel_counters():
@@ -302,7 +308,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ms = timed(step, args.steps, args.warmup, between=lambda: K.kf_kernel_times(ctx.h))
     kt = K.kf_kernel_times(ctx.h)
     K.kf_set_kernel_timing(ctx.h, False)
+    mask_step, counts_step = mask.clone(), counts.clone()  # what the timed step wrote
     ms_chain = timed(chain, args.steps, args.warmup)
+    chain_same = bool(torch.equal(mask, mask_step) and torch.equal(counts, counts_step))
     t_b = time.time()
     clk.stop()
     clocks = clk.summary(t_soak, t_b)
@@ -325,10 +333,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # roofline is the FP32 lanes: algorithmic operations per output pixel from the stage
     # definitions (FMA = 1 op): S1 convert 1, S2/S3 Gaussian 4 + 4, S4 Sobel 6, S5
     # products 3, S6 separable 5x5 box 3 x 8, S7 Harris 5, S8 threshold + 3x3 max 6 = 53;
-    # peak = 152 SMs x 128 FP32 lanes x the SM clock measured under load.
+    # peak = the device's SMs x 128 FP32 lanes x the SM clock measured under load.
     sm_mhz = (clocks.get("sm_mhz") or 2070.0)
-    ops_per_px = 53
-    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e9  # G lane-ops / s
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    ops_per_px = OPS_PER_PX
+    alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e9  # G lane-ops / s
     alu_ach = px * ops_per_px / (dom / 1000) / 1e9
     # HBM view: frames read once, mask written once, one 8-byte key per corner, the
     # per-frame corner and candidate counts
@@ -337,12 +346,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     rec = kernel_counters() if T == 1000 else None
     traffic = rec["dram_bytes_per_launch_1000_frames"] if rec else None
     # issue view: executed warp instructions (ncu) over 152 SMs x 4 schedulers x clock
-    issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e9  # G warp-instructions / s
+    issue_peak = n_sm * 4 * sm_mhz * 1e6 / 1e9  # G warp-instructions / s
     issue = None
     if rec:
         ach = rec["warp_instructions_per_launch_1000_frames"] / (dom / 1000) / 1e9
         issue = {"achieved": ach, "peak": issue_peak, "unit": "Gwarp-inst/s", "frac": ach / issue_peak,
-                 "peak_kind": "152 SMs x 4 schedulers x SM clock",
+                 "peak_kind": f"{n_sm} SMs x 4 schedulers x SM clock",
                  "instructions_per_launch": rec["warp_instructions_per_launch_1000_frames"], "kernel": rec["kernel"]}
 
     # batched form: the same workload as one video of a persistent-kernel batch (graph replay)
@@ -422,10 +431,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "tracked_points_per_s": world * tracked / (ms / 1000),
         "chain_only": {"value": world * px / (ms_chain / 1000) / 1e6, "ms_per_step": ms_chain,
                        "kernel": "group_kernel<1,8> (full fusion, no corner lists), timed alone by kf_run",
+                       "identical_to_step": chain_same,
                        "hbm_frac": (2 * px + 4 * T) / (ms_chain / 1000) / 1e9 / hbm_peak},
         "roofline": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Gop/s",
                      "frac": alu_ach / alu_peak, "traffic": traffic,
-                     "peak_kind": "152 SMs x 128 FP32 lanes x median SM clock under load",
+                     "peak_kind": f"{n_sm} SMs (read from the device) x 128 FP32 lanes x median SM clock under load",
+                     "sm_count": n_sm, "ops_per_px_by_stage": OPS_BY_STAGE,
                      "kernel": "group_kernel<1,8> with corner lists (the step's dominant kernel, timed inside the step)",
                      "ms_per_launch": dom, "ops_per_px": ops_per_px, "algorithmic_ops_per_launch": px * ops_per_px,
                      "algorithmic_bytes_per_launch": alg_bytes},
@@ -438,7 +449,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                          "identical_results": batch_same},
         "autotuned_chunk_rows": {"best": best_rows, "chain_ms": best_ms, "candidates": [100, 200, 400, 800]},
         "unfused": {"value": world * px / (ms_unf / 1000) / 1e6, "ms_per_step": ms_unf, "kernels": 8,
-                    "hbm_frac": unf_bytes / (ms_unf / 1000) / 1e9 / hbm_peak, "bit_identical_to_fused": same,
+                    "hbm_frac": unf_bytes / (ms_unf / 1000) / 1e9 / hbm_peak,
+                    "bit_identical_to_fused": bool(same and chain_same),
                     "fused_chain_speedup": ms_unf / ms_chain},
         "unfused_f16": {"value": world * px / (ms_unf16 / 1000) / 1e6, "ms_per_step": ms_unf16,
                         "hbm_frac": 50 * px / (ms_unf16 / 1000) / 1e9 / hbm_peak},
@@ -460,6 +472,92 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _ranks(x) -> np.ndarray:
+    """Ranks 1..n of the values of x, ties given their average rank."""
+    x = np.asarray(x, dtype=np.float64)
+    order = np.argsort(x, kind="stable")
+    r = np.empty(len(x), dtype=np.float64)
+    r[order] = np.arange(1, len(x) + 1)
+    for v in np.unique(x):
+        sel = x == v
+        if sel.sum() > 1:
+            r[sel] = r[sel].mean()
+    return r
+
+
+def spearman(a, b) -> float:
+    ra, rb = _ranks(a), _ranks(b)
+    ra, rb = ra - ra.mean(), rb - rb.mean()
+    return float((ra * rb).sum() / np.sqrt((ra * ra).sum() * (rb * rb).sum()))
+
+
+def run_partitions(args):
+    """Every contiguous partition of the 8-stage chain timed on 600 frames of 192 x 432
+    (seed 2): the traffic model's choice (kf_plan) against the measured best, with the
+    model's rank among the measured times, its regret and the rank correlation between
+    predicted bytes and measured time (the check Sec. VI's model gets from Sec. VII-B's
+    measured No / Two / Full Fusion). Each timed launch starts with L2 flushed."""
+    import torch
+    from paper_1509_04394_gb300 import build as kbuild
+    from paper_1509_04394_gb300 import kfuse as K
+    kbuild.build()
+    spec = sv.PARTITIONS_192x432x600
+    T, H, W = spec.T, spec.H, spec.W
+    P = sv.pitch_for(W)
+    fr, _ = sv.generate(spec, pitch=P)
+    dev = torch.device("cuda:0")
+    frames = torch.from_numpy(fr).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = K.Context(0)
+    parts = K.kf_enumerate(ctx.h)
+    plan, plan_bytes = K.kf_plan(ctx.h, W, H, T)
+    ws_b = max(K.kf_workspace_bytes(ctx.h, c, W, H, T) for c in parts)
+    ws = torch.empty(max(ws_b, 256), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # twice the L2
+    mask = torch.zeros_like(frames)
+    counts = torch.zeros(T, dtype=torch.int32, device=dev)
+    K.kf_run(ctx.h, 0, frames, W, mask, counts, None, stream)
+    ref_mask, ref_counts = mask.clone(), counts.clone()
+    reps = max(args.steps, 5)
+    rows = []
+    for c in parts:
+        for _ in range(args.warmup):
+            K.kf_run(ctx.h, c, frames, W, mask, counts, ws, stream)
+        times = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            K.kf_run(ctx.h, c, frames, W, mask, counts, ws, stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        same = bool(torch.equal(mask, ref_mask) and torch.equal(counts, ref_counts))
+        rows.append({"cuts": c, "groups": bin(c).count("1") + 1, "ms": statistics.median(times),
+                     "model_bytes": K.kf_partition_traffic(ctx.h, c, W, H, T), "identical": same})
+    assert K.kf_device_error(ctx.h) == 0
+    ms = np.array([r["ms"] for r in rows])
+    mb = np.array([r["model_bytes"] for r in rows])
+    order = np.argsort(ms)
+    best = rows[int(order[0])]
+    chosen = next(r for r in rows if r["cuts"] == plan)
+    rank = 1 + int(np.sum(ms < chosen["ms"]))
+    out = {"workload": f"Harris 8-stage chain, {T} frames x {H} rows x {W} cols u8, seed {spec.seed}, FP32 maps",
+           "partitions": len(rows), "reps_per_partition": reps, "l2": "flushed before every timed launch",
+           "model_choice": {"cuts": plan, "ms": chosen["ms"], "model_bytes": plan_bytes, "measured_rank": rank},
+           "measured_best": {"cuts": best["cuts"], "ms": best["ms"], "model_bytes": best["model_bytes"]},
+           "regret": chosen["ms"] / best["ms"] - 1.0,
+           "spearman_model_bytes_vs_ms": spearman(mb, ms),
+           "all_identical_to_full_fusion": all(r["identical"] for r in rows),
+           "unfused": next(r for r in rows if r["cuts"] == 127),
+           "fastest_10": [rows[int(i)] for i in order[:10]],
+           "slowest_3": [rows[int(i)] for i in order[-3:]]}
+    if args.partitions_table:
+        with open(args.partitions_table, "w") as fh:
+            json.dump(rows, fh)
+    print(json.dumps(out), flush=True)
 
 
 BATCH48 = [(16, 192, 432, 600), (16, 480, 640, 300), (12, 800, 600, 1000), (4, 1080, 1920, 120)]  # count, H, W, T
@@ -889,6 +987,9 @@ def main():
     ap.add_argument("--pc-size", type=int, default=0, help="one square size instead of the three (--pchain)")
     ap.add_argument("--pc-once", action="store_true", help="run each partition once, untimed (profiler case)")
     ap.add_argument("--dagplan", action="store_true", help="recompute-vs-store DAG plans (learned costs)")
+    ap.add_argument("--partitions", action="store_true", help="all 128 partitions of the chain timed on "
+                    "600 x 192 x 432 (traffic model vs measured)")
+    ap.add_argument("--partitions-table", default="", help="--partitions: also write every row to this JSON file")
     ap.add_argument("--stbox", action="store_true", help="spatio-temporal boxes against Eq. 6 (uses --pc-frames, "
                     "--pc-size, --pc-once)")
     args = ap.parse_args()
@@ -896,7 +997,9 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.pchain:
+    if args.partitions:
+        run_partitions(args)
+    elif args.pchain:
         run_pchain(args)
     elif args.stbox:
         run_stbox(args)

@@ -26,6 +26,8 @@
  *     so that no byte count overflows 64 bits. Calls state tighter bounds where they
  *     have them (e.g. W * H below 2^31 for tracking).
  *   - One context per host thread; a context is not thread-safe.
+ *   - A call that works on a context's GPU makes that device current for its duration
+ *     and gives the caller's current device back before it returns.
  */
 #ifndef KFUSE_H
 #define KFUSE_H
@@ -132,9 +134,9 @@ const char *kf_status_str(kf_status s);
 int kf_last_cuda_error(const kf_ctx *ctx);
 kf_status kf_version(int *major, int *minor);
 
-/* Create a context on CUDA device `device` (selects it with cudaSetDevice and allocates
- * the context's 4-byte device error word), or a host-only planning context when
- * device < 0 (no CUDA call is ever made by it). */
+/* Create a context on CUDA device `device` (allocates the context's 4-byte device error
+ * word with that device current; the caller's current device is restored), or a
+ * host-only planning context when device < 0 (no CUDA call is ever made by it). */
 kf_status kf_create(int device, kf_ctx **out);
 kf_status kf_destroy(kf_ctx *ctx);
 
@@ -150,6 +152,17 @@ kf_status kf_device_error(kf_ctx *ctx, int *code);
 kf_status kf_set_precision(kf_ctx *ctx, int precision);
 /* Rows per warp job of the executor (default 200, >= 1). */
 kf_status kf_set_chunk_rows(kf_ctx *ctx, int rows);
+/* Bound of the device-side waits for staged input (the chain's TMA row blocks and the
+ * spatio-temporal box's frame copies): the number of mbarrier try_wait rounds a block
+ * gives one wait before it records KF_DEVERR_TIMEOUT in the context's error word,
+ * waits (bounded, 2^22 rounds each) for the copies it still has in flight, and ends
+ * its job, leaving that job's outputs incomplete. Default 2^22 (far beyond any copy's
+ * latency). A caller may lower it; 0 makes every such wait expire at once, which shows
+ * the timeout path end to end without a fault: kf_device_error then reports
+ * KF_DEVERR_TIMEOUT, and calls made after restoring the default give full results.
+ * Kernels launched afterwards take the value; a batch (kf_batch_create) keeps the value
+ * it was created with. */
+kf_status kf_set_wait_polls(kf_ctx *ctx, unsigned polls);
 
 /* Declare the next kernel of the chain (Sec. IV). Returns its 0-based index in *id.
  * KF_EINVAL if the chain already holds KF_MAX_STAGES stages or radii are negative. */
@@ -423,7 +436,11 @@ kf_status kf_costmodel_set(kf_ctx *ctx, const float *params, const float *norm);
  *   - All calls on a device share the one array and it keeps the last call's contents
  *     (the chain overwrites every map it reads, so nothing needs clearing). Calls whose
  *     kernels overlap on the GPU (other streams, other host threads) race on it:
- *     serialise them. */
+ *     serialise them.
+ *   - The looked-up address is kept for the life of the process. A caller that resets
+ *     a device (cudaDeviceReset) after its first call on it must not call this entry
+ *     point on that device again: the kept address belonged to the destroyed context.
+ *   - Like every entry point, the call leaves the caller's current device as it found it. */
 #define KF_STATIC_WORKSPACE_BYTES (64u << 20)
 kf_status kf_run_static(kf_ctx *ctx, uint32_t cuts, const kf_video *video, const kf_corners *out, void *stream);
 

@@ -21,6 +21,7 @@
 #include "kf_params.h"
 
 #include "kf_ctx.h"
+#include "kf_device.h"
 
 namespace {
 
@@ -207,6 +208,7 @@ kf_status fill_params(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &o
     for (int i = 0; i < in.channels; ++i)
         if (!encode_plane(&p.tmap[i], in.plane[i], in.dtype, in.pitch, in.frame_stride, W, H, T)) return KF_EINVAL;
     p.err = c->d_err;
+    p.wait_polls = c->wait_polls;
     p.cand = cand;
     p.cand_count = cand_count;
     p.cand_cap = (int)cand_cap;
@@ -373,7 +375,8 @@ kf_status kf_create(int device, kf_ctx **out)
     if (!c) return KF_ENOMEM;
     c->device = device < 0 ? -1 : device;
     if (device >= 0) {
-        cudaError_t e = cudaSetDevice(device);
+        kf::DeviceScope dev_scope(device);
+    cudaError_t e = dev_scope.status();
         if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
         if (e != cudaSuccess) {
@@ -388,33 +391,27 @@ kf_status kf_create(int device, kf_ctx **out)
 
 kf_status kf_destroy(kf_ctx *ctx)
 {
-    if (ctx) kf::costmodel_free(ctx);
-    if (ctx && ctx->s_in) {
-        cudaSetDevice(ctx->device);
-        cudaStreamDestroy(ctx->s_in);
-        cudaStreamDestroy(ctx->s_out);
-        for (int i = 0; i < kf_ctx::N_RING; ++i) cudaStreamDestroy(ctx->s_comp[i]);
-        for (int i = 0; i < kf_ctx::N_RING; ++i) {
-            cudaEventDestroy(ctx->ev_in[i]);
-            cudaEventDestroy(ctx->ev_comp[i]);
+    if (!ctx) return KF_OK;
+    kf::costmodel_free(ctx);
+    if (ctx->device >= 0) {  // device objects are released with their device current
+        kf::DeviceScope dev_scope(ctx->device);
+        if (ctx->s_in) {
+            cudaStreamDestroy(ctx->s_in);
+            cudaStreamDestroy(ctx->s_out);
+            for (int i = 0; i < kf_ctx::N_RING; ++i) cudaStreamDestroy(ctx->s_comp[i]);
+            for (int i = 0; i < kf_ctx::N_RING; ++i) {
+                cudaEventDestroy(ctx->ev_in[i]);
+                cudaEventDestroy(ctx->ev_comp[i]);
+            }
+            cudaEventDestroy(ctx->ev_edge);
         }
-        cudaEventDestroy(ctx->ev_edge);
-    }
-    if (ctx && ctx->pack_buf) {
-        cudaSetDevice(ctx->device);
-        cudaFree(ctx->pack_buf);
-    }
-    if (ctx && (!ctx->timed.empty() || !ctx->spare_events.empty())) {
-        cudaSetDevice(ctx->device);
+        if (ctx->pack_buf) cudaFree(ctx->pack_buf);
         for (const kf_ctx::Timed &t : ctx->timed) {
             cudaEventDestroy(t.a);
             cudaEventDestroy(t.b);
         }
         for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
-    }
-    if (ctx && ctx->d_err) {
-        cudaSetDevice(ctx->device);
-        cudaFree(ctx->d_err);
+        if (ctx->d_err) cudaFree(ctx->d_err);
     }
     delete ctx;
     return KF_OK;
@@ -424,7 +421,8 @@ kf_status kf_device_error(kf_ctx *ctx, int *code)
 {
     if (!ctx || !code) return KF_EINVAL;
     if (ctx->device < 0) return KF_ESTATE;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(code, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
@@ -443,6 +441,13 @@ kf_status kf_set_chunk_rows(kf_ctx *ctx, int rows)
 {
     if (!ctx || rows < 1) return KF_EINVAL;
     ctx->chunk_rows = rows;
+    return KF_OK;
+}
+
+kf_status kf_set_wait_polls(kf_ctx *ctx, unsigned polls)
+{
+    if (!ctx) return KF_EINVAL;
+    ctx->wait_polls = polls;
     return KF_OK;
 }
 
@@ -581,7 +586,8 @@ kf_status kf_run_group(kf_ctx *ctx, int first, int last, const kf_map *in, const
     s = check_map(out, B, ctx->precision, W, H);
     if (s != KF_OK) return s;
     if (B == 8 && (!counts || !aligned(counts, 4))) return KF_EINVAL;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     return launch_group(ctx, A, B, *in, *out, W, H, T, counts, static_cast<cudaStream_t>(stream));
 }
@@ -602,7 +608,8 @@ kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *v, const kf_corners
     const WsPlan w = plan_workspace(ctx, cuts, v->W, v->H, v->T);
     if (w.total > 0 && (!ws || !aligned(ws, 256))) return KF_EINVAL;
     if (ws_bytes < w.total) return KF_ENOMEM;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
 
@@ -803,7 +810,8 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf
 {
     kf_status st = check_track_args(ctx, v, o, tr, ws, ws_bytes);
     if (st != KF_OK || v->T == 0) return st;
-    const cudaError_t e = cudaSetDevice(ctx->device);
+    kf::DeviceScope dev_scope(ctx->device);
+    const cudaError_t e = dev_scope.status();
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     return track_range(ctx, v, o, tr, ws, 0, v->T, static_cast<cudaStream_t>(stream));
 }
@@ -829,7 +837,8 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
     if (!host_video->frames || !host_out->mask || !host_out->counts || !host_tracks->n_points || !host_tracks->idx ||
         !host_tracks->u || !host_tracks->v || !host_tracks->status)
         return KF_EINVAL;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     // packed masks: staged per chunk in a device ring of N_RING chunks (owned by the
     // context, grown on demand) and copied out from there; a chunk holds at most
@@ -1033,7 +1042,8 @@ kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners 
     const BatchLayout L = batch_layout(videos, n, track);
     if (!ws || !aligned(ws, 256)) return KF_EINVAL;
     if (ws_bytes < L.total) return KF_ENOMEM;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     char *base = static_cast<char *>(ws);
     auto *d_params = reinterpret_cast<kf::GroupParams *>(base + L.params);
@@ -1141,15 +1151,16 @@ kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners 
 kf_status kf_batch_run(kf_batch *b, void *stream)
 {
     if (!b || !b->exec) return KF_EINVAL;
-    if (cudaSetDevice(b->device) != cudaSuccess) return KF_ECUDA;
+    kf::DeviceScope dev_scope(b->device);
+    if (dev_scope.status() != cudaSuccess) return KF_ECUDA;
     return cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? KF_OK : KF_ECUDA;
 }
 
 kf_status kf_batch_destroy(kf_batch *b)
 {
     if (b) {
+        kf::DeviceScope dev_scope(b->device);
         if (b->exec) {
-            cudaSetDevice(b->device);
             cudaGraphExecDestroy(b->exec);
         }
         delete b;
@@ -1164,7 +1175,8 @@ kf_status kf_tune_chunk_rows(kf_ctx *ctx, const kf_video *v, const kf_corners *o
     if (ctx->device < 0) return KF_ESTATE;
     for (int i = 0; i < n; ++i)
         if (candidates[i] < 1) return KF_EINVAL;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;

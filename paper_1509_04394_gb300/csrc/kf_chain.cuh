@@ -370,9 +370,8 @@ __device__ __forceinline__ void nms_h(const float (&r)[C], float (&mh)[C])
 // mbarrier. Columns outside the frame and rows past its end arrive as zeros (handled by
 // the clamped reads below and by the vertical stages' replay). Every wait is bounded:
 // on expiry the kernel records KF_DEVERR_TIMEOUT in the device error word, waits once
-// more (bounded) for its copies in flight, and leaves.
+// more (bounded, WAIT_POLLS rounds each) for its copies in flight, and leaves.
 
-constexpr unsigned WAIT_LIMIT = 1u << 22;  // try_wait rounds before giving up
 constexpr int DEVERR_TIMEOUT = 1;
 constexpr int DEVERR_OVERFLOW = 2;  // a frame had more corner candidates than cand_cap
 
@@ -397,10 +396,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
         : "memory");
     return ok != 0;
 }
-// bounded wait; returns false if the limit expired
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+// bounded wait of at most `polls` try_wait rounds; returns false if they ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned polls = WAIT_POLLS)
 {
-    for (unsigned i = 0; i < WAIT_LIMIT; ++i)
+    for (unsigned i = 0; i < polls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -891,7 +890,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
 #pragma unroll 1
     for (int k = 0, t = t_begin; t < t_end; ++k, t += RB) {
         if (k < n_stages) {
-            const bool ok = __all_sync(FULL, mbar_wait(bars + slot(k), parity(k)));
+            const bool ok = __all_sync(FULL, mbar_wait(bars + slot(k), parity(k), p.wait_polls));
             if (!ok) {  // warp-uniform
                 failed = true;
                 k_fail = k;
@@ -923,7 +922,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
     if (failed) {
         // record, then give the copies still in flight a bounded chance to land
         if (lane == 0) atomicOr(p.err, DEVERR_TIMEOUT);
-        for (int k = k_fail; k < issued; ++k) mbar_wait(bars + slot(k), parity(k));
+        for (int k = k_fail; k < issued; ++k) mbar_wait(bars + slot(k), parity(k), WAIT_POLLS);
         return false;
     }
     emit_candidates();       // a block cut short by the end of the job

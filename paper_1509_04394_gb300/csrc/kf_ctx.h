@@ -25,6 +25,7 @@ struct kf_ctx {
     int device = -1;
     int precision = KF_PREC_F32;
     int chunk_rows = 200;
+    unsigned wait_polls = 1u << 22;  // kf::WAIT_POLLS unless kf_set_wait_polls lowered it
     int last_cuda = 0;
     int *d_err = nullptr;  // device error word of the bounded waits (4 bytes, owned)
     std::vector<kf_stage_desc> stages;

@@ -24,6 +24,7 @@
 
 #include "../../include/kfuse.h"
 #include "kf_ctx.h"
+#include "kf_device.h"
 
 namespace kf {
 int ctx_device(const kf_ctx *ctx);
@@ -532,7 +533,8 @@ kf_status kf_dag_run(kf_dag *d, uint32_t cuts, const kf_video *v, float *out, in
     size_t need = 0;
     if (kf_dag_workspace_bytes(d, v->W, v->H, v->T, &need) != KF_OK) return KF_EINVAL;
     if (!ws || ws_bytes < need) return KF_ENOMEM;
-    if (cudaSetDevice(d->device) != cudaSuccess) return KF_ECUDA;
+    kf::DeviceScope dev_scope(d->device);
+    if (dev_scope.status() != cudaSuccess) return KF_ECUDA;
     const Geo geo = geo_of(d, v->W, v->H, v->T);
     int a = 1;
     for (int b = 1; b <= d->n; ++b) {
@@ -671,7 +673,8 @@ kf_status kf_dag_run_x(kf_dag *d, uint32_t cuts, uint32_t inline_mask, const kf_
         if (!plans.back().feasible) return KF_ESMEM;
         a = b + 1;
     }
-    if (cudaSetDevice(d->device) != cudaSuccess) return KF_ECUDA;
+    kf::DeviceScope dev_scope(d->device);
+    if (dev_scope.status() != cudaSuccess) return KF_ECUDA;
     const Geo geo = geo_of(d, v->W, v->H, v->T);
     for (const GroupPlan &g : plans) {
         const kf_status st =

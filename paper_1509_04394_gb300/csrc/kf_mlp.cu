@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "kf_ctx.h"
+#include "kf_device.h"
 
 namespace kf {
 
@@ -230,7 +231,8 @@ kf_status kf_costmodel_grad(kf_ctx *ctx, const float *params, const float *x, co
 {
     if (!ctx || !params || !x || !y || !grad || n < 1) return KF_EINVAL;
     if (ctx->device < 0) return KF_ESTATE;
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return KF_ECUDA;
+    kf::DeviceScope dev_scope(ctx->device);
+    if (dev_scope.status() != cudaSuccess) return KF_ECUDA;
     DevBufs d;
     cudaError_t e = alloc_bufs(d, n);
     if (e == cudaSuccess) e = cudaMemcpy(d.p, params, sizeof(float) * NP, cudaMemcpyHostToDevice);
@@ -287,7 +289,8 @@ kf_status kf_costmodel_train(kf_ctx *ctx, const float *features, const float *ms
     for (int i = 0; i < HID * F; ++i) p[OFF_W1 + i] = (float)(gauss(st) * std::sqrt(2.0 / F));
     for (int i = 0; i < HID * HID; ++i) p[OFF_W2 + i] = (float)(gauss(st) * std::sqrt(2.0 / HID));
     for (int i = 0; i < HID; ++i) p[OFF_W3 + i] = (float)(gauss(st) * std::sqrt(1.0 / HID));
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return KF_ECUDA;
+    kf::DeviceScope dev_scope(ctx->device);
+    if (dev_scope.status() != cudaSuccess) return KF_ECUDA;
     DevBufs d;
     cudaError_t e = alloc_bufs(d, n);
     if (e == cudaSuccess) e = cudaMemcpy(d.p, p.data(), sizeof(float) * NP, cudaMemcpyHostToDevice);

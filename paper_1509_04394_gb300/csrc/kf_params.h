@@ -24,6 +24,7 @@ constexpr int MIN_BLOCKS_BOX = 12;  // ... for groups holding the 5-row box ring
 constexpr int NSTAGES = 8;
 constexpr int RB = 5;           // rows per TMA stage = rows per unrolled loop block
 constexpr int STRIP_ALIGN = 16; // strips start on multiples of 16 columns (16-byte TMA x for u8)
+constexpr unsigned WAIT_POLLS = 1u << 22;  // try_wait rounds of a bounded wait before it counts as expired
 
 // Stage table of the Harris chain, 1-based (stage 0 = the u8 frames). One-sided radii
 // along columns (rx) and rows (ry), Table I.
@@ -72,6 +73,9 @@ struct GroupParams {
     float thr;                // NMS threshold in the scaled units of R
     float in_scale;           // FP16 input maps: scaled value = stored * in_scale
     float out_scale;          // FP16 output maps: stored = scaled value * out_scale
+    unsigned wait_polls;      // try_wait rounds a job gives a staged block of input rows (WAIT_POLLS
+                              // unless a caller lowered it); the drain of copies in flight after an
+                              // expired wait always gets WAIT_POLLS
     // corner candidates for the tracking stage (B == 8, optional): per frame a list of
     // keys (R bits << 32 | ~raster index), cand_cap per frame, cand_count[frame] entries
     unsigned long long *cand;

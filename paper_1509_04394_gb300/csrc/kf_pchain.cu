@@ -28,6 +28,7 @@
 #include <stdint.h>
 
 #include "kf_ctx.h"
+#include "kf_device.h"
 
 namespace kf {
 int ctx_device(const kf_ctx *ctx);  // kf_api.cu
@@ -714,7 +715,8 @@ kf_status kf_pc_run(kf_ctx *ctx, uint32_t cuts, const kf_pc_video *video, const 
     if (kf_pc_workspace_bytes(ctx, cuts, video->W, video->H, video->T, &need) != KF_OK) return KF_EINVAL;
     if (need && (!workspace || !aligned(workspace, 256))) return KF_EINVAL;
     if (workspace_bytes < need) return KF_ENOMEM;
-    if (cudaSetDevice(dev) != cudaSuccess) return KF_ECUDA;
+    kf::DeviceScope dev_scope(dev);
+    if (dev_scope.status() != cudaSuccess) return KF_ECUDA;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t W = video->W, H = video->H, T = video->T, wp = ws_pitch(W);
     const size_t plane_a = ((size_t)(wp * H * T) * sizeof(float) + 255) / 256 * 256;
@@ -775,7 +777,8 @@ kf_status kf_pc_run_group(kf_ctx *ctx, int a, int b, const kf_pc_video *video, c
     }
     const int dev = kf::ctx_device(ctx);
     if (dev < 0) return KF_ESTATE;
-    if (cudaSetDevice(dev) != cudaSuccess) return KF_ECUDA;
+    kf::DeviceScope dev_scope(dev);
+    if (dev_scope.status() != cudaSuccess) return KF_ECUDA;
     const uint32_t *src = a == 0 ? reinterpret_cast<const uint32_t *>(video->rgba) : reinterpret_cast<const uint32_t *>(in);
     const int64_t sp = a == 0 ? video->pitch : in_pitch;
     void *dst = b == 4 ? static_cast<void *>(out_mask->mask) : static_cast<void *>(out);
@@ -797,7 +800,8 @@ kf_status kf_pc_kalman(kf_ctx *ctx, const int32_t *regions, int64_t T, int n_tra
         return KF_EINVAL;
     const int dev = kf::ctx_device(ctx);
     if (dev < 0) return KF_ESTATE;
-    if (cudaSetDevice(dev) != cudaSuccess) return KF_ECUDA;
+    kf::DeviceScope dev_scope(dev);
+    if (dev_scope.status() != cudaSuccess) return KF_ECUDA;
     pc_kalman_kernel<<<(n_tracks + KF_TRACKS - 1) / KF_TRACKS, KF_TRACKS, 0, static_cast<cudaStream_t>(stream)>>>(
         regions, (int)T, n_tracks, states, status);
     const cudaError_t e = cudaGetLastError();

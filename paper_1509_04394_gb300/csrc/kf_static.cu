@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "../../include/kfuse.h"
+#include "kf_device.h"
 
 namespace kf {
 int ctx_device(const kf_ctx *ctx);  // kf_api.cu
@@ -54,7 +55,8 @@ extern "C" kf_status kf_run_static(kf_ctx *ctx, uint32_t cuts, const kf_video *v
     kf_status s = kf_workspace_bytes(ctx, cuts, video->W, video->H, video->T, &need);
     if (s != KF_OK) return s;
     if (need > (size_t)KF_STATIC_WORKSPACE_BYTES) return KF_ENOMEM;  // larger than the fixed array
-    if (cudaSetDevice(device) != cudaSuccess) return KF_ECUDA;
+    kf::DeviceScope dev_scope(device);
+    if (dev_scope.status() != cudaSuccess) return KF_ECUDA;
     void *ws = nullptr;
     if (static_workspace(device, &ws) != cudaSuccess) return KF_ECUDA;
     // Every map the groups write in the workspace is written in full before it is read,

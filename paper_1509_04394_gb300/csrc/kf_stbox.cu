@@ -27,6 +27,7 @@
 #include <stdint.h>
 
 #include "kf_ctx.h"
+#include "kf_device.h"
 
 namespace kf {
 namespace {
@@ -44,6 +45,8 @@ struct StParams {
     int W, H, T;
     int t;                 // box depth in frames (the side is the kernel's X)
     int boxes_x, boxes_y;  // boxes per frame row / column
+    unsigned wait_polls;   // try_wait rounds of the wait for a frame's copy (the drain after an
+                           // expired wait always gets ST_WAIT_LIMIT)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -57,9 +60,9 @@ __device__ __forceinline__ void bar_expect(uint64_t *bar, unsigned bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool bar_wait(uint64_t *bar, unsigned parity)
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, unsigned parity, unsigned polls = ST_WAIT_LIMIT)
 {
-    for (unsigned i = 0; i < ST_WAIT_LIMIT; ++i) {
+    for (unsigned i = 0; i < polls; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -325,7 +328,7 @@ __global__ void __launch_bounds__(BoxCfg<X>::THREADS, 2) st_box_kernel(const __g
     // PAIRS + i]. No barrier guards it.
     for (int pl = 0; pl < n_planes; ++pl) {
         if (pl > N) pass_c<N, X>(p, b, G, t0 - N + pl - 1);
-        const bool ok = bar_wait(bar, (unsigned)(pl & 1));
+        const bool ok = bar_wait(bar, (unsigned)(pl & 1), p.wait_polls);
         if (ok) convert_frame<N, X>(p, b, stage, ring, Z, pl);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
@@ -471,7 +474,8 @@ kf_status kf_st_run(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64_
     if (smem > kf::ST_MAX_SMEM) return KF_EINVAL;
     const int64_t bxn = (W + x - 1) / x, byn = (H + x - 1) / x, btn = (T + t - 1) / t;
     if (bxn * byn * btn > 0x7fffffff) return KF_EINVAL;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
     if (e != cudaSuccess) return st_fail(ctx, e);
 
     StParams p{};
@@ -490,6 +494,7 @@ kf_status kf_st_run(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64_
     p.mask_fstride = mask_pitch * H;
     p.counts = counts;
     p.err = ctx->d_err;
+    p.wait_polls = ctx->wait_polls;
     p.W = (int)W;
     p.H = (int)H;
     p.T = (int)T;
@@ -535,7 +540,8 @@ kf_status kf_st_tune(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64
     if (ctx->device < 0) return KF_ESTATE;
     for (int i = 0; i < count; ++i)
         if (!kf::box_kernel(n, boxes[2 * i]) || boxes[2 * i + 1] < 1) return KF_EINVAL;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
     if (e != cudaSuccess) return st_fail(ctx, e);
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;

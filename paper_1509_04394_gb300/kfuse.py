@@ -79,6 +79,7 @@ def _lib():
             "kf_device_error": (i32, [P, P]),
             "kf_set_precision": (i32, [P, i32]),
             "kf_set_chunk_rows": (i32, [P, i32]),
+            "kf_set_wait_polls": (i32, [P, ctypes.c_uint32]),
             "kf_add_stage": (i32, [P, P, P]),
             "kf_add_harris_chain": (i32, [P]),
             "kf_num_stages": (i32, [P, P]),
@@ -142,7 +143,7 @@ def _lib():
 def exported_symbols() -> list[str]:
     """Names of the C entry points this binding wraps (all declared in kfuse.h)."""
     return ["kf_status_str", "kf_last_cuda_error", "kf_version", "kf_create", "kf_destroy", "kf_device_error",
-            "kf_set_precision", "kf_set_chunk_rows", "kf_add_stage", "kf_add_harris_chain",
+            "kf_set_precision", "kf_set_chunk_rows", "kf_set_wait_polls", "kf_add_stage", "kf_add_harris_chain",
             "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
             "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static",
             "kf_track_workspace_bytes", "kf_track", "kf_batch_workspace_bytes", "kf_batch_create",
@@ -208,6 +209,10 @@ def kf_set_precision(ctx, precision: int) -> None:
 
 def kf_set_chunk_rows(ctx, rows: int) -> None:
     _check("kf_set_chunk_rows", _lib().kf_set_chunk_rows(ctx, int(rows)), ctx)
+
+
+def kf_set_wait_polls(ctx, polls: int) -> None:
+    _check("kf_set_wait_polls", _lib().kf_set_wait_polls(ctx, int(polls)), ctx)
 
 
 def kf_add_stage(ctx, kind: int, rx: int = 0, ry: int = 0, rt: int = 0, in_bytes: float = 0.0,

@@ -53,3 +53,42 @@ def pitch16(W: int) -> int:
 
 def pitch4(W: int) -> int:
     return (W + 3) // 4 * 4
+
+
+def kalman_fp32_bound(states_o: np.ndarray, regions: np.ndarray, W: int, q: float = 0.5, r: float = 4.0,
+                      p0: float = 100.0) -> tuple[float, float]:
+    """Error budget of the FP32 constant-velocity Kalman filter against the FP64 one
+    (positions in px, velocities in px/frame), derived from the filter itself.
+
+    Each step adds rounding errors: the measured centroid z = sum / count (3 roundings of
+    |z| <= W), the state update (about 4 roundings of |p| <= W for the position and 3 of
+    the largest |v| for the velocity) and the gain computed from an FP32 covariance
+    (about 10 roundings of K, times the largest innovation |z - p_predicted|). The error
+    then evolves as e_t = A e_{t-1} + d_t with A = (I - K H) F, which is stable (its
+    spectral radius at the steady-state gain is 0.66 for q = 0.5, r = 4), so it stays
+    below sum_k |A^k| d. The steady-state sum is taken, times a margin of 4 for the
+    transient gains and second-order terms."""
+    u = 2.0 ** -24
+    F = np.array([[1.0, 1.0], [0.0, 1.0]])
+    Q = q * np.array([[1 / 3, 1 / 2], [1 / 2, 1.0]])
+    Hm = np.array([[1.0, 0.0]])
+    P = np.diag([r, p0])
+    for _ in range(500):  # Riccati iteration to the steady state
+        P = F @ P @ F.T + Q
+        K = P @ Hm.T / float((Hm @ P @ Hm.T)[0, 0] + r)
+        P = (np.eye(2) - K @ Hm) @ P
+    A = (np.eye(2) - K @ Hm) @ F
+    S, M = np.zeros((2, 2)), np.eye(2)
+    for _ in range(2000):
+        S += np.abs(M)
+        M = A @ M
+    cnt = regions[..., 0]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        z = np.where(cnt[..., None] > 0, regions[..., 1:] / np.maximum(cnt[..., None], 1), np.nan)
+    pred = states_o[:-1, :, :2] + states_o[:-1, :, 2:]
+    innov = np.nanmax(np.abs(z[1:] - pred)) if np.isfinite(z[1:] - pred).any() else 0.0
+    vmax = float(np.max(np.abs(states_o[..., 2:])))
+    k = np.abs(K.ravel())
+    d = k * (3 * u * W + 10 * u * innov) + np.array([4 * u * W, 3 * u * vmax])
+    b = 4.0 * (S @ d)
+    return float(b[0]), float(b[1])

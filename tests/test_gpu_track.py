@@ -17,7 +17,8 @@ from oracle import chain as oc  # noqa: E402
 from paper_1509_04394_gb300 import build as kbuild  # noqa: E402
 from paper_1509_04394_gb300 import kfuse as K  # noqa: E402
 from synth import video as sv  # noqa: E402
-from tests._parity import TOL_F32  # noqa: E402
+from tests._parity import TOL_F32, check_mask  # noqa: E402
+from tests._track_parity import check_frame  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -52,54 +53,6 @@ def run_track(dev, fr, W, Kp=256):
     return out
 
 
-def window_conditioning(maps_cur, g_prev, p, W, H):
-    """|det| / tr^2 of the oracle's LK matrix at raster index p (for the tolerance only)."""
-    py, px = divmod(int(p), W)
-    ys = np.clip(np.arange(py - 3, py + 4), 0, H - 1)
-    xs = np.clip(np.arange(px - 3, px + 4), 0, W - 1)
-    gx = maps_cur["ix"][np.ix_(ys, xs)] / 8
-    gy = maps_cur["iy"][np.ix_(ys, xs)] / 8
-    a00, a01, a11 = np.sum(gx * gx), np.sum(gx * gy), np.sum(gy * gy)
-    det, tr = a00 * a11 - a01 * a01, a00 + a11
-    return abs(det) / (tr * tr) if tr > 0 else 0.0
-
-
-def check_frame(fr, t, W, out, Kp):
-    H = fr.shape[1]
-    prev, cur = fr[t - 1][:, :W].copy(), fr[t][:, :W].copy()
-    idx_o, u_o, v_o, st_o = oc.track_pair(prev, cur, K=Kp)
-    maps, mask_o, _ = oc.chain_frame(cur)
-    n = int(out["n"][t])
-    assert n == len(idx_o)
-    got = out["idx"][t, :n]
-    r = maps["r"].ravel()
-    if n:
-        tau = TOL_F32 * np.max(np.abs(maps["r"]))
-        kth = r[idx_o[-1]]
-        diff = set(got.tolist()) ^ set(idx_o.tolist())
-        for p in diff:  # disagreements only at the selection boundary
-            assert abs(r[p] - kth) <= tau, (t, p, r[p], kth)
-        # order: strongest first (by the oracle's response, up to the FP32 tolerance)
-        assert np.all(np.diff(r[got]) <= tau)
-    g_prev = oc.chain_frame(prev)[0]["g"]
-    common = {p: i for i, p in enumerate(idx_o.tolist())}
-    checked = 0
-    for i, p in enumerate(got.tolist()):
-        if p not in common:
-            continue
-        j = common[p]
-        cond = window_conditioning(maps, g_prev, p, W, H)
-        if cond < 1e-9 or (1e-13 < cond < 1e-11):
-            continue  # at or near the singularity threshold: either answer is acceptable
-        assert out["st"][t, i] == st_o[j], (t, p)
-        if st_o[j] == 0:
-            tol = 2e-3 * max(1.0, 1e-4 / cond)  # FP32 window sums, amplified by conditioning
-            assert abs(out["u"][t, i] - u_o[j]) <= tol * max(1.0, abs(u_o[j])), (t, p, out["u"][t, i], u_o[j])
-            assert abs(out["v"][t, i] - v_o[j]) <= tol * max(1.0, abs(v_o[j])), (t, p, out["v"][t, i], v_o[j])
-            checked += 1
-    return checked
-
-
 @pytest.mark.parametrize("shape,Kp", [((4, 192, 432), 256), ((3, 77, 130), 64), ((3, 40, 50), 1024), ((3, 96, 150), 1),
                                       ((5, 120, 600), 256)])
 def test_tracking_matches_the_oracle(dev, shape, Kp):
@@ -109,6 +62,27 @@ def test_tracking_matches_the_oracle(dev, shape, Kp):
     assert out["n"][0] == 0
     checked = sum(check_frame(fr, t, W, out, Kp) for t in range(1, T))
     assert checked >= min(Kp, 5)
+
+
+def test_full_size_tracking_in_the_benchmark_configuration(dev):
+    """The benchmark's timed step itself: kf_track over the whole 1000 x 800 x 600 volume
+    (seed 3, 64 blobs, 32 patches; 256 points per frame) in the launch configuration the
+    benchmark times (the chain with corner lists, then selection and LK). The oracle checks
+    sampled frame pairs one by one: masks and counts under the exemption rule, the
+    selected points up to FP32 near-ties at the K-th response, velocities within the
+    conditioning-scaled tolerance."""
+    spec = sv.HSDV_800x600x1000
+    W = spec.W
+    fr, _ = sv.generate(spec, pitch=sv.pitch_for(W))
+    out = run_track(dev, fr, W, 256)
+    assert out["n"][0] == 0
+    checked = 0
+    for t in (1, 2, 499, 998, 999):
+        maps, m_ref, c_ref = oc.chain_frame(fr[t][:, :W].copy())
+        check_mask(out["mask"][t, :, :W], int(out["counts"][t]), m_ref, c_ref, maps["r"], TOL_F32)
+        assert out["n"][t] == min(256, int(out["counts"][t]))
+        checked += check_frame(fr, t, W, out, 256)
+    assert checked >= 5 * 200
 
 
 def test_constant_video_has_no_points_and_a_single_frame_has_no_tracks(dev):

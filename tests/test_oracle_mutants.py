@@ -282,6 +282,15 @@ PY_MUTANTS = {
         "product saturates below only": ("np.clip(a_in * b_in, -16.0, 16.0)", "np.clip(a_in * b_in, -16.0, None)"),
         "node 0 divides by 256": ("frame_u8.astype(np.float64) / 255.0", "frame_u8.astype(np.float64) / 256.0"),
         "second input read from the first": ("nodes[i2] if i2 >= 0 else None", "nodes[i1] if i2 >= 0 else None"),
+        "bound: node 0 rounded once": ("err = [2.0 * U32 * np.abs(nodes[0]) * grow]", "err = [U32 * np.abs(nodes[0]) * grow]"),
+        "bound: affine ignores its input error": ("bound = abs(a) * e + U32 * (2.0 * abs(a) * x + abs(b) + y)",
+                                                  "bound = U32 * (2.0 * abs(a) * x + abs(b) + y)"),
+        "bound: product drops a cross term": ("exact = x * e2 + x2 * e + e * e2", "exact = x * e2 + e * e2"),
+        "bound: stencil rounding of one pass": ("bound = _stencil_abs(e, r) + 2 * (2 * r + 1) * U32",
+                                                "bound = _stencil_abs(e, r) + (2 * r + 1) * U32"),
+        "bound: max3 keeps the centre only": ("bound = np.maximum(bound, _shift(e, dy, dx))",
+                                              "bound = np.maximum(bound, _shift(e, 0, 0))"),
+        "bound: abs drops the error": ("bound = e.copy()", "bound = 0.0 * e"),
     }),
     "mlp": (["test_mlp_oracle:mlp"], {
         "ReLU gate dropped in layer 2": ("dz2 = np.outer(dy, w3) * (z2 > 0)", "dz2 = np.outer(dy, w3)"),
