@@ -503,14 +503,14 @@ def run_partitions(args):
     from paper_1509_04394_gb300 import build as kbuild
     from paper_1509_04394_gb300 import kfuse as K
     kbuild.build()
-    spec = sv.PARTITIONS_192x432x600
+    spec = SPEC if args.partitions_full else sv.PARTITIONS_192x432x600
     T, H, W = spec.T, spec.H, spec.W
     P = sv.pitch_for(W)
     fr, _ = sv.generate(spec, pitch=P)
     dev = torch.device("cuda:0")
     frames = torch.from_numpy(fr).to(dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = K.Context(0)
+    ctx = K.Context(0, precision=K.KF_PREC_F16 if args.f16 else K.KF_PREC_F32)
     parts = K.kf_enumerate(ctx.h)
     plan, plan_bytes = K.kf_plan(ctx.h, W, H, T)
     ws_b = max(K.kf_workspace_bytes(ctx.h, c, W, H, T) for c in parts)
@@ -544,7 +544,8 @@ def run_partitions(args):
     best = rows[int(order[0])]
     chosen = next(r for r in rows if r["cuts"] == plan)
     rank = 1 + int(np.sum(ms < chosen["ms"]))
-    out = {"workload": f"Harris 8-stage chain, {T} frames x {H} rows x {W} cols u8, seed {spec.seed}, FP32 maps",
+    out = {"workload": f"Harris 8-stage chain, {T} frames x {H} rows x {W} cols u8, seed {spec.seed}, "
+                       f"{'16-bit' if args.f16 else 'FP32'} maps",
            "partitions": len(rows), "reps_per_partition": reps, "l2": "flushed before every timed launch",
            "model_choice": {"cuts": plan, "ms": chosen["ms"], "model_bytes": plan_bytes, "measured_rank": rank},
            "measured_best": {"cuts": best["cuts"], "ms": best["ms"], "model_bytes": best["model_bytes"]},
@@ -989,6 +990,7 @@ def main():
     ap.add_argument("--dagplan", action="store_true", help="recompute-vs-store DAG plans (learned costs)")
     ap.add_argument("--partitions", action="store_true", help="all 128 partitions of the chain timed on "
                     "600 x 192 x 432 (traffic model vs measured)")
+    ap.add_argument("--partitions-full", action="store_true", help="--partitions on the 1000 x 800 x 600 workload")
     ap.add_argument("--partitions-table", default="", help="--partitions: also write every row to this JSON file")
     ap.add_argument("--stbox", action="store_true", help="spatio-temporal boxes against Eq. 6 (uses --pc-frames, "
                     "--pc-size, --pc-once)")

@@ -311,6 +311,19 @@ kf_status kf_batch_destroy(kf_batch *batch);
  * ms when best_ms is not NULL). Synchronous. */
 kf_status kf_tune_chunk_rows(kf_ctx *ctx, const kf_video *video, const kf_corners *out, const int *candidates, int n,
                              int reps, void *stream, int *best_rows, float *best_ms);
+/* The partition of least MEASURED time: the exhaustive check that judges the traffic
+ * model's choice (Sec. VI, Fig. 5, against the measured No / Two / Full Fusion of
+ * Sec. VII-B). Runs each candidate cut mask (`cands`, n_cand of them; all 2^(n-1) when
+ * cands == NULL) on the video once untimed and then `reps` times, each run bracketed by
+ * a CUDA event pair on `stream`, and returns the cut mask of the least median time in
+ * *best_cuts (the first one on ties), that time in *best_ms and, when ms_all is not
+ * NULL, every candidate's median time (n entries, in candidate order). `ws` (device,
+ * 256-byte aligned) must hold kf_workspace_bytes of every candidate (KF_ENOMEM before
+ * any work otherwise). Synchronises `stream`; the outputs hold the last run's results.
+ * The context keeps its precision: with KF_PREC_F16 the cut maps are 16-bit. */
+kf_status kf_plan_measured(kf_ctx *ctx, const kf_video *video, const kf_corners *out, void *ws, size_t ws_bytes,
+                           const uint32_t *cands, int n_cand, int reps, void *stream, uint32_t *best_cuts, float *best_ms,
+                           float *ms_all);
 
 /* ------------------------------------------------------------------ kernel DAGs */
 /* Arbitrary DAGs of generic image kernels (Sec. III's chain generalised to one or two
@@ -409,8 +422,17 @@ kf_status kf_dag_run_x(kf_dag *dag, uint32_t cuts, uint32_t inline_mask, const k
  * returns. Returns the final mean squared error on the standardised log-runtimes. */
 kf_status kf_costmodel_train(kf_ctx *ctx, const float *features, const float *ms, int n, int steps, float lr,
                              unsigned seed, float *final_loss);
-/* Host-side prediction (ms) for n feature rows; KF_ESTATE before training or set. */
+/* Predicted runtime (ms) of n groups from their feature rows (host arrays, n x
+ * KF_NFEAT in, n out); KF_ESTATE before training or set. On a context with a GPU the
+ * network runs in the library's inference kernel (one thread per row, parameters in
+ * shared memory; device memory is allocated for the call's duration); a planning
+ * context without a GPU (device < 0) evaluates it on the host. The recompute planner
+ * (kf_dag_plan_recompute) evaluates its one-group-at-a-time queries on the host. */
 kf_status kf_costmodel_predict(kf_ctx *ctx, const float *features, int n, float *ms);
+/* The raw network (no standardisation) at `params` for n input rows x (n x KF_NFEAT),
+ * outputs y (n), computed by the inference kernel on the context's GPU (host arrays;
+ * KF_ESTATE on a context without a GPU). */
+kf_status kf_costmodel_forward(kf_ctx *ctx, const float *params, const float *x, int n, float *y);
 /* Loss and gradient of the raw network (no standardisation) at `params` for inputs x
  * (n x KF_NFEAT) and targets y, computed by the training kernels on the GPU. */
 kf_status kf_costmodel_grad(kf_ctx *ctx, const float *params, const float *x, const float *y, int n, float *grad,

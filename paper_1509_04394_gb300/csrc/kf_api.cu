@@ -9,6 +9,8 @@
 // footprint fits the limit (restriction c of Sec. VII).
 #include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <cudaTypedefs.h>
 
 #include <cmath>
@@ -1208,6 +1210,59 @@ kf_status kf_tune_chunk_rows(kf_ctx *ctx, const kf_video *v, const kf_corners *o
     ctx->chunk_rows = st == KF_OK ? best : keep;
     if (st != KF_OK) return st;
     *best_rows = best;
+    if (best_ms) *best_ms = best_t;
+    return KF_OK;
+}
+
+kf_status kf_plan_measured(kf_ctx *ctx, const kf_video *v, const kf_corners *o, void *ws, size_t ws_bytes,
+                           const uint32_t *cands, int n_cand, int reps, void *stream, uint32_t *best_cuts, float *best_ms,
+                           float *ms_all)
+{
+    if (!ctx || !v || !o || reps < 1 || !best_cuts || (cands && n_cand < 1)) return KF_EINVAL;
+    if (ctx->device < 0) return KF_ESTATE;
+    if (!builtin_chain(ctx)) return KF_EUNSUPPORTED;
+    const int n_all = 1 << (kf::NSTAGES - 1);
+    const int n = cands ? n_cand : n_all;
+    for (int i = 0; i < n; ++i) {
+        const uint32_t c = cands ? cands[i] : (uint32_t)i;
+        if (c >= (uint32_t)n_all) return KF_EINVAL;
+        if (plan_workspace(ctx, c, v->W, v->H, v->T).total > ws_bytes) return KF_ENOMEM;
+    }
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+    kf_status st = KF_OK;
+    for (cudaEvent_t &x : ev)
+        if (cudaEventCreate(&x) != cudaSuccess) st = KF_ECUDA;
+    uint32_t best = 0;
+    float best_t = INFINITY;
+    std::vector<float> t((size_t)reps);
+    for (int i = 0; i < n && st == KF_OK; ++i) {
+        const uint32_t c = cands ? cands[i] : (uint32_t)i;
+        st = kf_run(ctx, c, v, o, ws, ws_bytes, stream);  // warm-up
+        for (int r = 0; r < reps && st == KF_OK; ++r) {
+            cudaEventRecord(ev[2 * r], s);
+            st = kf_run(ctx, c, v, o, ws, ws_bytes, stream);
+            cudaEventRecord(ev[2 * r + 1], s);
+        }
+        if (st == KF_OK && cudaEventSynchronize(ev[2 * reps - 1]) != cudaSuccess) st = KF_ECUDA;
+        for (int r = 0; r < reps && st == KF_OK; ++r)
+            if (cudaEventElapsedTime(&t[r], ev[2 * r], ev[2 * r + 1]) != cudaSuccess) st = KF_ECUDA;
+        if (st != KF_OK) break;
+        std::sort(t.begin(), t.end());
+        const float med = t[(size_t)reps / 2];  // median (upper median for even counts)
+        if (ms_all) ms_all[i] = med;
+        if (med < best_t) {
+            best_t = med;
+            best = c;
+        }
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (st != KF_OK) return st;
+    *best_cuts = best;
     if (best_ms) *best_ms = best_t;
     return KF_OK;
 }

@@ -44,8 +44,63 @@ namespace kf {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float HARRIS_K = 0.04f;
 
-template <int N> struct Rows { float v[N][C]; };
+// The C = 4 columns of one lane in one row of one map, kept as two FP32 pairs, columns
+// (0, 1) and (2, 3). Operations that treat every column alike (vertical stencil passes,
+// products, the box's row sums, the Harris response) run as 2-wide FP32 instructions on
+// the pairs (add / sub / mul / fma .f32x2: IEEE round-to-nearest per element, so the
+// same bits as the scalar operations, at half the issued instructions); horizontal
+// stencils read and write single columns, which are halves of the pairs.
+struct V4 {
+    float2 p[2];
+    __device__ __forceinline__ float operator[](int c) const { return (c & 1) ? p[c >> 1].y : p[c >> 1].x; }
+    __device__ __forceinline__ float &operator[](int c) { return (c & 1) ? p[c >> 1].y : p[c >> 1].x; }
+};
+template <int N> struct Rows { V4 v[N]; };
 struct Empty {};
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ V4 add4(const V4 &a, const V4 &b)
+{
+    V4 r;
+    r.p[0] = __fadd2_rn(a.p[0], b.p[0]);
+    r.p[1] = __fadd2_rn(a.p[1], b.p[1]);
+    return r;
+}
+__device__ __forceinline__ V4 sub4(const V4 &a, const V4 &b)
+{
+    V4 r;
+    r.p[0] = sub2(a.p[0], b.p[0]);
+    r.p[1] = sub2(a.p[1], b.p[1]);
+    return r;
+}
+__device__ __forceinline__ V4 mul4(const V4 &a, const V4 &b)
+{
+    V4 r;
+    r.p[0] = __fmul2_rn(a.p[0], b.p[0]);
+    r.p[1] = __fmul2_rn(a.p[1], b.p[1]);
+    return r;
+}
+__device__ __forceinline__ V4 fma4(const V4 &a, const V4 &b, const V4 &c)
+{
+    V4 r;
+    r.p[0] = __ffma2_rn(a.p[0], b.p[0], c.p[0]);
+    r.p[1] = __ffma2_rn(a.p[1], b.p[1], c.p[1]);
+    return r;
+}
+__device__ __forceinline__ V4 splat4(float s)
+{
+    V4 r;
+    r.p[0] = r.p[1] = make_float2(s, s);
+    return r;
+}
 
 // ------------------------------------------------------------------ small helpers
 __device__ __forceinline__ float u8_to_float(uint32_t w, int c)
@@ -54,7 +109,7 @@ __device__ __forceinline__ float u8_to_float(uint32_t w, int c)
     return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (unsigned)c)) - 8388608.0f;
 }
 
-__device__ __forceinline__ float pick(const float (&v)[C], int c)
+__device__ __forceinline__ float pick(const V4 &v, int c)
 {
     float r = v[0];
 #pragma unroll
@@ -91,7 +146,7 @@ __device__ __forceinline__ void fix_edges(Rows<N> &r, int xs, int x0, int W, boo
 // Neighbour columns -R..-1 (from the lane to the left) and C..C+R-1 (from the right).
 template <int R> struct Halo { float l[R], r[R]; };
 template <int R>
-__device__ __forceinline__ Halo<R> halo(const float (&v)[C])
+__device__ __forceinline__ Halo<R> halo(const V4 &v)
 {
     Halo<R> h;
 #pragma unroll
@@ -102,7 +157,7 @@ __device__ __forceinline__ Halo<R> halo(const float (&v)[C])
     return h;
 }
 template <int R>
-__device__ __forceinline__ float at(const float (&v)[C], const Halo<R> &h, int c)
+__device__ __forceinline__ float at(const V4 &v, const Halo<R> &h, int c)
 {
     return c < 0 ? h.l[R + c] : (c >= C ? h.r[c - C] : v[c]);
 }
@@ -112,7 +167,7 @@ __device__ __forceinline__ float at(const float (&v)[C], const Halo<R> &h, int c
 // call the same code, so their results agree bit for bit.
 
 // Stage 2: [1 4 6 4 1] along the row (scaled: no division).
-__device__ __forceinline__ void gauss_h(const float (&x)[C], float (&o)[C])
+__device__ __forceinline__ void gauss_h(const V4 &x, V4 &o)
 {
     const Halo<2> h = halo<2>(x);
 #pragma unroll
@@ -126,25 +181,23 @@ __device__ __forceinline__ void gauss_h(const float (&x)[C], float (&o)[C])
 // Stage 3: [1 4 6 4 1] down the columns as four (1,1) passes; z[j] = previous value
 // at pass level j. Output row = input row - 2.
 struct GaussV {
-    float z[4][C];
-    __device__ __forceinline__ void fill(const float (&x)[C])
+    V4 z[4];
+    __device__ __forceinline__ void fill(const V4 &x)
     {
-#pragma unroll
-        for (int c = 0; c < C; ++c) { z[0][c] = x[c]; z[1][c] = 2.0f * x[c]; z[2][c] = 4.0f * x[c]; z[3][c] = 8.0f * x[c]; }
+        z[0] = x;
+        z[1] = add4(x, x);
+        z[2] = add4(z[1], z[1]);
+        z[3] = add4(z[2], z[2]);
     }
-    __device__ __forceinline__ void replay(float (&x)[C])
+    __device__ __forceinline__ void replay(V4 &x) { x = z[0]; }
+    __device__ __forceinline__ void push(const V4 &x, V4 &o)
     {
-#pragma unroll
-        for (int c = 0; c < C; ++c) x[c] = z[0][c];
-    }
-    __device__ __forceinline__ void push(const float (&x)[C], float (&o)[C])
-    {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const float a = x[c] + z[0][c], b = a + z[1][c], d = b + z[2][c];
-            o[c] = d + z[3][c];
-            z[0][c] = x[c]; z[1][c] = a; z[2][c] = b; z[3][c] = d;
-        }
+        const V4 a = add4(x, z[0]), b = add4(a, z[1]), d = add4(b, z[2]);
+        o = add4(d, z[3]);
+        z[0] = x;
+        z[1] = a;
+        z[2] = b;
+        z[3] = d;
     }
 };
 
@@ -193,40 +246,46 @@ struct GaussVPacked {
         }
     }
 };
-// the two 16-bit lanes of a word as FP32 (exact)
-__device__ __forceinline__ float lo16_to_float(uint32_t x) { return __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7610)) - 8388608.0f; }
-__device__ __forceinline__ float hi16_to_float(uint32_t x) { return __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7632)) - 8388608.0f; }
+// the two 16-bit lanes of a packed word as an FP32 pair (exact): each lane is placed
+// under the exponent of 2^23, and one 2-wide subtraction of 2^23 leaves its value
+__device__ __forceinline__ float2 u16x2_to_float2(uint32_t x)
+{
+    const float2 biased = make_float2(__uint_as_float(__byte_perm(x, 0x4B000000u, 0x7610)),
+                                      __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7632)));
+    return sub2(biased, make_float2(8388608.0f, 8388608.0f));
+}
 
 // Stage 4: Sobel. Per row: Dx = g(x+1) - g(x-1), Sx = g(x-1) + 2 g(x) + g(x+1);
 // then Ix = Dx(r-1) + 2 Dx(r) + Dx(r+1) = (1,1)^2 pass of Dx, Iy = Sx(r+1) - Sx(r-1)
 // directly from the Sx of two rows before (one subtraction; the values are integers
 // below 2^24, so every form gives the same bits). Output row = input row - 1.
 struct SobelV {
-    float d[2][C];  // Dx passes
-    float s[2][C];  // Sx of the previous row and of the one before it
-    __device__ __forceinline__ void fill(const float (&dx)[C], const float (&sx)[C])
+    V4 d[2];  // Dx passes
+    V4 s[2];  // Sx of the previous row and of the one before it
+    __device__ __forceinline__ void fill(const V4 &dx, const V4 &sx)
     {
-#pragma unroll
-        for (int c = 0; c < C; ++c) { d[0][c] = dx[c]; d[1][c] = 2.0f * dx[c]; s[0][c] = sx[c]; s[1][c] = sx[c]; }
+        d[0] = dx;
+        d[1] = add4(dx, dx);
+        s[0] = sx;
+        s[1] = sx;
     }
-    __device__ __forceinline__ void replay(float (&dx)[C], float (&sx)[C])
+    __device__ __forceinline__ void replay(V4 &dx, V4 &sx)
     {
-#pragma unroll
-        for (int c = 0; c < C; ++c) { dx[c] = d[0][c]; sx[c] = s[0][c]; }
+        dx = d[0];
+        sx = s[0];
     }
-    __device__ __forceinline__ void push(const float (&dx)[C], const float (&sx)[C], float (&ix)[C], float (&iy)[C])
+    __device__ __forceinline__ void push(const V4 &dx, const V4 &sx, V4 &ix, V4 &iy)
     {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const float a = dx[c] + d[0][c];
-            ix[c] = a + d[1][c];
-            d[0][c] = dx[c]; d[1][c] = a;
-            iy[c] = sx[c] - s[1][c];
-            s[1][c] = s[0][c]; s[0][c] = sx[c];
-        }
+        const V4 a = add4(dx, d[0]);
+        ix = add4(a, d[1]);
+        d[0] = dx;
+        d[1] = a;
+        iy = sub4(sx, s[1]);
+        s[1] = s[0];
+        s[0] = sx;
     }
 };
-__device__ __forceinline__ void sobel_h(const float (&g)[C], float (&dx)[C], float (&sx)[C])
+__device__ __forceinline__ void sobel_h(const V4 &g, V4 &dx, V4 &sx)
 {
     const Halo<1> h = halo<1>(g);
 #pragma unroll
@@ -240,67 +299,62 @@ __device__ __forceinline__ void sobel_h(const float (&g)[C], float (&dx)[C], flo
 // Stage 5: structure-tensor products.
 __device__ __forceinline__ void products(const Rows<2> &i, Rows<3> &p)
 {
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        p.v[0][c] = i.v[0][c] * i.v[0][c];
-        p.v[1][c] = i.v[0][c] * i.v[1][c];
-        p.v[2][c] = i.v[1][c] * i.v[1][c];
-    }
+    p.v[0] = mul4(i.v[0], i.v[0]);
+    p.v[1] = mul4(i.v[0], i.v[1]);
+    p.v[2] = mul4(i.v[1], i.v[1]);
 }
 
 // Stage 6: 5x5 box sum. Horizontal: the four 5-wide windows of a lane's columns share
-// the pair sums A = x-2 + x-1, B = x0 + x1, Cp = x2 + x3, D = x4 + x5 and E = B + Cp
-// (11 adds for 4 outputs). Vertical: each row's sum with the row before it is kept (a
-// 5-slot ring addressed by the compile-time loop phase: the row loop is unrolled by 5,
-// so no register is ever moved), and the window of rows t-4..t is
+// the pair sums A = x-2 + x-1, B = x0 + x1, Cp = x2 + x3, D = x4 + x5 and E = B + Cp;
+// A is the left lane's Cp and D the right lane's B (the same two columns added in the
+// same order), so they arrive by shuffle with the single columns x-1 and x4 (9 adds
+// for 4 outputs). Vertical: each row's sum with the row before it is kept (a 5-slot
+// ring addressed by the compile-time loop phase: the row loop is unrolled by 5, so no
+// register is ever moved), and the window of rows t-4..t is
 // ((r[t-4] + r[t-3]) + (r[t-2] + r[t-1])) + r[t]: 3 adds a value instead of 4, in an
 // order fixed by the rows' ages alone, the same in every partition and chunk height.
 // Output row = input row - 2.
-__device__ __forceinline__ void box_h(const float (&x)[C], float (&o)[C])
+__device__ __forceinline__ void box_h(const V4 &x, V4 &o)
 {
     static_assert(C == 4, "pair-sharing box assumes 4 columns per lane");
-    const Halo<2> h = halo<2>(x);
-    const float A = h.l[0] + h.l[1], B = x[0] + x[1], Cp = x[2] + x[3], D = h.r[0] + h.r[1];
+    const float B = x[0] + x[1], Cp = x[2] + x[3];
+    const float A = __shfl_up_sync(FULL, Cp, 1), D = __shfl_down_sync(FULL, B, 1);
+    const float xm1 = __shfl_up_sync(FULL, x[3], 1), x4 = __shfl_down_sync(FULL, x[0], 1);
     const float E = B + Cp;
     o[0] = (A + B) + x[2];
-    o[1] = h.l[1] + E;
-    o[2] = E + h.r[0];
+    o[1] = xm1 + E;
+    o[2] = E + x4;
     o[3] = x[1] + (Cp + D);
 }
 struct BoxV {
-    float pair[5][3][C];  // slot PH: the row pushed at phase PH plus the row before it
-    float last[3][C];     // the newest row
+    V4 pair[5][3];  // slot PH: the row pushed at phase PH plus the row before it
+    V4 last[3];     // the newest row
     // the first row of a frame: the rows above it clamp to it
     __device__ __forceinline__ void fill(const Rows<3> &h)
     {
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
+        for (int m = 0; m < 3; ++m) {
+            last[m] = h.v[m];
+            const V4 two = add4(h.v[m], h.v[m]);
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                last[m][c] = h.v[m][c];
-#pragma unroll
-                for (int s = 0; s < 5; ++s) pair[s][m][c] = h.v[m][c] + h.v[m][c];
-            }
+            for (int s = 0; s < 5; ++s) pair[s][m] = two;
+        }
     }
     // rows past the frame's end clamp to the last one
     template <int PH>
     __device__ __forceinline__ void newest(Rows<3> &h) const
     {
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
-#pragma unroll
-            for (int c = 0; c < C; ++c) h.v[m][c] = last[m][c];
+        for (int m = 0; m < 3; ++m) h.v[m] = last[m];
     }
     template <int PH>
     __device__ __forceinline__ void put(const Rows<3> &h)
     {
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                pair[PH][m][c] = last[m][c] + h.v[m][c];
-                last[m][c] = h.v[m][c];
-            }
+        for (int m = 0; m < 3; ++m) {
+            pair[PH][m] = add4(last[m], h.v[m]);
+            last[m] = h.v[m];
+        }
     }
     // after put<PH>: pair (PH + 4) % 5 = r[t-2] + r[t-1], pair (PH + 2) % 5 = r[t-4] + r[t-3]
     template <int PH>
@@ -308,56 +362,53 @@ struct BoxV {
     {
         constexpr int p1 = (PH + 4) % 5, p3 = (PH + 2) % 5;
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
-#pragma unroll
-            for (int c = 0; c < C; ++c) o.v[m][c] = (pair[p3][m][c] + pair[p1][m][c]) + last[m][c];
+        for (int m = 0; m < 3; ++m) o.v[m] = add4(add4(pair[p3][m], pair[p1][m]), last[m]);
     }
 };
 
-// Stage 7: Harris response.
-__device__ __forceinline__ void harris(const Rows<3> &s, float (&r)[C])
+// Stage 7: Harris response, R = (Sxx Syy - Sxy^2) - k (Sxx + Syy)^2.
+__device__ __forceinline__ void harris(const Rows<3> &s, V4 &r)
 {
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        const float sxx = s.v[0][c], sxy = s.v[1][c], syy = s.v[2][c];
-        const float det = fmaf(sxx, syy, -(sxy * sxy));
-        const float tr = sxx + syy;
-        r[c] = fmaf(-HARRIS_K * tr, tr, det);
-    }
+    const V4 det = sub4(mul4(s.v[0], s.v[2]), mul4(s.v[1], s.v[1]));
+    const V4 tr = add4(s.v[0], s.v[2]);
+    r = fma4(mul4(splat4(-HARRIS_K), tr), tr, det);
 }
 
 // Stage 8: threshold + 3x3 non-maximum suppression. Horizontal max of 3, then the
 // vertical max of the row and the two before it (one 3-input max); the centre row is one
 // row behind.
 struct NmsV {
-    float p[2][C];  // horizontal maxima of the previous row and of the one before it
-    float rc[C];    // R of the previous row (the centre of the output row)
-    __device__ __forceinline__ void fill(const float (&mh)[C], const float (&r)[C])
+    V4 p[2];  // horizontal maxima of the previous row and of the one before it
+    V4 rc;    // R of the previous row (the centre of the output row)
+    __device__ __forceinline__ void fill(const V4 &mh, const V4 &r)
     {
-#pragma unroll
-        for (int c = 0; c < C; ++c) { p[0][c] = mh[c]; p[1][c] = mh[c]; rc[c] = r[c]; }
+        p[0] = mh;
+        p[1] = mh;
+        rc = r;
     }
-    __device__ __forceinline__ void replay(float (&mh)[C], float (&r)[C])
+    __device__ __forceinline__ void replay(V4 &mh, V4 &r)
     {
-#pragma unroll
-        for (int c = 0; c < C; ++c) { mh[c] = p[0][c]; r[c] = rc[c]; }
+        mh = p[0];
+        r = rc;
     }
     // returns the 4 mask bits of the output row (input row - 1) in bits 0..C-1, and the
     // response of that row in `centre`
-    __device__ __forceinline__ unsigned push(const float (&mh)[C], const float (&r)[C], float thr, float (&centre)[C])
+    __device__ __forceinline__ unsigned push(const V4 &mh, const V4 &r, float thr, V4 &centre)
     {
         unsigned bits = 0;
+        centre = rc;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const float m9 = fmaxf(fmaxf(mh[c], p[0][c]), p[1][c]);
-            centre[c] = rc[c];
             bits |= ((centre[c] > thr) & (centre[c] >= m9)) ? (1u << c) : 0u;
-            p[1][c] = p[0][c]; p[0][c] = mh[c]; rc[c] = r[c];
         }
+        p[1] = p[0];
+        p[0] = mh;
+        rc = r;
         return bits;
     }
 };
-__device__ __forceinline__ void nms_h(const float (&r)[C], float (&mh)[C])
+__device__ __forceinline__ void nms_h(const V4 &r, V4 &mh)
 {
     const Halo<1> h = halo<1>(r);
 #pragma unroll
@@ -424,7 +475,7 @@ template <> struct Staged<uint8_t> {
         for (int c = 0; c < C; ++c) w |= (uint32_t)row[off[c]] << (8 * c);
         return w;
     }
-    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float, float (&v)[C])
+    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float, V4 &v)
     {
         const uint32_t w = word(row, lane, inside, off);
 #pragma unroll
@@ -432,12 +483,13 @@ template <> struct Staged<uint8_t> {
     }
 };
 template <> struct Staged<float> {
-    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float, float (&v)[C])
+    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float, V4 &v)
     {
         const float *r = reinterpret_cast<const float *>(row);
         if (inside) {
             const float4 q = reinterpret_cast<const float4 *>(r)[lane];
-            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            v.p[0] = make_float2(q.x, q.y);
+            v.p[1] = make_float2(q.z, q.w);
         } else {
 #pragma unroll
             for (int c = 0; c < C; ++c) v[c] = r[off[c]];
@@ -445,7 +497,7 @@ template <> struct Staged<float> {
     }
 };
 template <> struct Staged<__half> {
-    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float scale, float (&v)[C])
+    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float scale, V4 &v)
     {
         const __half *r = reinterpret_cast<const __half *>(row);
         if (inside) {
@@ -460,7 +512,7 @@ template <> struct Staged<__half> {
     }
 };
 template <> struct Staged<uint16_t> {
-    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float, float (&v)[C])
+    __device__ __forceinline__ static void read(const unsigned char *row, int lane, bool inside, const int (&off)[C], float, V4 &v)
     {
         const uint16_t *r = reinterpret_cast<const uint16_t *>(row);
         if (inside) {
@@ -476,7 +528,7 @@ template <> struct Staged<uint16_t> {
 // ------------------------------------------------------------------ map stores
 template <typename TM> struct Store;
 template <> struct Store<float> {
-    __device__ __forceinline__ static void row(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float)
+    __device__ __forceinline__ static void row(void *plane, int64_t off, const V4 &v, unsigned in_mask, float)
     {
         float *p = static_cast<float *>(plane) + off;
         if (in_mask == (1u << C) - 1) {
@@ -488,7 +540,7 @@ template <> struct Store<float> {
     }
 };
 template <> struct Store<__half> {
-    __device__ __forceinline__ static void row(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float scale)
+    __device__ __forceinline__ static void row(void *plane, int64_t off, const V4 &v, unsigned in_mask, float scale)
     {
         __half *p = static_cast<__half *>(plane) + off;
         if (in_mask == (1u << C) - 1) {
@@ -505,7 +557,7 @@ template <> struct Store<__half> {
     }
 };
 template <> struct Store<uint16_t> {
-    __device__ __forceinline__ static void row(void *plane, int64_t off, const float (&v)[C], unsigned in_mask, float)
+    __device__ __forceinline__ static void row(void *plane, int64_t off, const V4 &v, unsigned in_mask, float)
     {
         uint16_t *p = static_cast<uint16_t *>(plane) + off;
         if (in_mask == (1u << C) - 1) {
@@ -755,10 +807,8 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
                 if (i >= H) s3p.replay(h);
             }
             s3p.push(h, o);
-            g.v[0][0] = lo16_to_float(o[0]);
-            g.v[0][1] = hi16_to_float(o[0]);
-            g.v[0][2] = lo16_to_float(o[1]);
-            g.v[0][3] = hi16_to_float(o[1]);
+            g.v[0].p[0] = u16x2_to_float2(o[0]);
+            g.v[0].p[1] = u16x2_to_float2(o[1]);
         } else {
 #pragma unroll
         for (int m = 0; m < NIN; ++m) Staged<TIN>::read(srow + m * SP::CH_STRIDE, sl, lane_inside, off, in_scale, in.v[m]);
@@ -787,7 +837,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         if constexpr (HAS4) {
             if constexpr (hstencil_before(A, 4))
                 if (edgeL | edgeR) fix_edges<1>(g, xs, x0, W, edgeL, edgeR, lbase);
-            float dx[C], sx[C];
+            V4 dx, sx;
             sobel_h(g.v[0], dx, sx);
             if (border) {
                 const int i = t - D4;
@@ -832,11 +882,11 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         }
         // ---- stage 8 (threshold + NMS), input row t - D8
         [[maybe_unused]] unsigned bits = 0;
-        [[maybe_unused]] float centre[C];
+        [[maybe_unused]] V4 centre;
         if constexpr (HAS8) {
             if constexpr (hstencil_before(A, 8))
                 if (edgeL | edgeR) fix_edges<1>(r7, xs, x0, W, edgeL, edgeR, lbase);
-            float mh[C];
+            V4 mh;
             nms_h(r7.v[0], mh);
             if (border) {
                 const int i = t - D8;

@@ -28,6 +28,8 @@
 
 namespace kf {
 int ctx_device(const kf_ctx *ctx);
+// the learned model's prediction of one group on the host (kf_mlp.cu)
+kf_status predict_group_ms(kf_ctx *model, const float *features, float *ms);
 }
 
 namespace {
@@ -407,7 +409,7 @@ struct PlanCost {
             } else {
                 float f[KF_NFEAT], ms = 0.f;
                 features_of(d, g, mem, W, H, T, f);
-                if (kf_costmodel_predict(model, f, 1, &ms) == KF_OK) c = ms;
+                if (kf::predict_group_ms(model, f, &ms) == KF_OK) c = ms;
             }
         }
         memo.emplace(key, c);
@@ -604,7 +606,7 @@ kf_status kf_dag_plan_recompute(const kf_dag *d, int64_t W, int64_t H, int64_t T
     if (!d || !cuts || !inline_mask || W <= 0 || H <= 0 || T <= 0) return KF_EINVAL;
     if (model) {  // a model that is not trained (or set) predicts nothing
         float f[KF_NFEAT] = {}, ms = 0.f;
-        if (kf_costmodel_predict(model, f, 1, &ms) != KF_OK) return KF_ESTATE;
+        if (kf::predict_group_ms(model, f, &ms) != KF_OK) return KF_ESTATE;
     }
     const int n = d->n;
     PlanCost cost{d, W, H, T, (double)W * H * T / ((double)DAG_TX * DAG_TY),

@@ -157,6 +157,77 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, float 
 
 constexpr size_t GRAD_SMEM = sizeof(float) * (NP + SPB * F + 4 * SPB * HID + 2 * SPB);
 
+// Input and output scaling of the inference kernel (standardise = 1): features go in as
+// log1p(max(f, 0)) standardised by (fmean, fstd), and the raw output y comes out as
+// exp(y ystd + ymean) milliseconds.
+struct Norm {
+    float fmean[F], fstd[F], ymean, ystd;
+};
+
+constexpr int FWD_THREADS = 128;  // samples per block of the inference kernel
+
+// Inference: the forward pass for n samples, one thread per sample, the parameters
+// staged in shared memory (all threads of a warp read the same weight at the same time:
+// a broadcast, no bank conflicts). The first hidden layer stays in registers; the second
+// is consumed unit by unit into the output, so it is never stored. Same operation order
+// as the training kernel's forward pass.
+__global__ void __launch_bounds__(FWD_THREADS) mlp_forward_kernel(const float *__restrict__ p, const float *__restrict__ x,
+                                                                 int n, int standardise, Norm norm, float *__restrict__ y)
+{
+    __shared__ float w[NP];
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) w[i] = p[i];
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float xi[F], a1[HID];
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+        const float v = x[(int64_t)s * F + k];
+        xi[k] = standardise ? (log1pf(fmaxf(v, 0.0f)) - norm.fmean[k]) / norm.fstd[k] : v;
+    }
+#pragma unroll
+    for (int j = 0; j < HID; ++j) {
+        float z = w[OFF_B1 + j];
+#pragma unroll
+        for (int k = 0; k < F; ++k) z = fmaf(w[OFF_W1 + j * F + k], xi[k], z);
+        a1[j] = fmaxf(z, 0.0f);
+    }
+    float out = w[OFF_B3];
+#pragma unroll 4
+    for (int j = 0; j < HID; ++j) {
+        float z = w[OFF_B2 + j];
+#pragma unroll
+        for (int k = 0; k < HID; ++k) z = fmaf(w[OFF_W2 + j * HID + k], a1[k], z);
+        out = fmaf(w[OFF_W3 + j], fmaxf(z, 0.0f), out);
+    }
+    y[s] = standardise ? expf(fmaf(out, norm.ystd, norm.ymean)) : out;
+}
+
+// n rows of x (host) through the network with parameters p (host) on the current device:
+// raw outputs (standardise = 0) or predicted milliseconds (standardise = 1). Allocates
+// device memory for the call's duration only.
+cudaError_t forward_on_device(const float *p, const float *x, int n, int standardise, const Norm &norm, float *y)
+{
+    struct Bufs {
+        float *p = nullptr, *x = nullptr, *y = nullptr;
+        ~Bufs()
+        {
+            for (float *q : {p, x, y})
+                if (q) cudaFree(q);
+        }
+    } d;
+    cudaError_t e = cudaMalloc(&d.p, sizeof(float) * NP);
+    if (e == cudaSuccess) e = cudaMalloc(&d.x, sizeof(float) * (size_t)n * F);
+    if (e == cudaSuccess) e = cudaMalloc(&d.y, sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(d.p, p, sizeof(float) * NP, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d.x, x, sizeof(float) * (size_t)n * F, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    mlp_forward_kernel<<<(n + FWD_THREADS - 1) / FWD_THREADS, FWD_THREADS>>>(d.p, d.x, n, standardise, norm, d.y);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(y, d.y, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost);
+    return e;
+}
+
 struct DevBufs {
     float *p = nullptr, *x = nullptr, *y = nullptr, *part = nullptr, *pl = nullptr, *g = nullptr, *m = nullptr,
           *v = nullptr, *loss = nullptr;
@@ -220,6 +291,7 @@ CostModel *model_of(kf_ctx *ctx)
 }
 
 }  // namespace
+kf_status predict_on_host(const CostModel &c, const float *features, int n, float *ms);
 }  // namespace kf
 
 using namespace kf;
@@ -318,11 +390,55 @@ kf_status kf_costmodel_train(kf_ctx *ctx, const float *features, const float *ms
     return KF_OK;
 }
 
+kf_status kf_costmodel_forward(kf_ctx *ctx, const float *params, const float *x, int n, float *y)
+{
+    if (!ctx || !params || !x || !y || n < 0) return KF_EINVAL;
+    if (ctx->device < 0) return KF_ESTATE;
+    if (n == 0) return KF_OK;
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
+    if (e == cudaSuccess) e = forward_on_device(params, x, n, 0, Norm{}, y);
+    if (e != cudaSuccess) {
+        ctx->last_cuda = (int)e;
+        return KF_ECUDA;
+    }
+    return KF_OK;
+}
+
 kf_status kf_costmodel_predict(kf_ctx *ctx, const float *features, int n, float *ms)
 {
     if (!ctx || !features || !ms || n < 0) return KF_EINVAL;
     if (!ctx->cm || !ctx->cm->trained) return KF_ESTATE;
-    const CostModel &c = *ctx->cm;
+    if (n == 0) return KF_OK;
+    if (ctx->device >= 0) {  // a context with a GPU: the inference kernel
+        const CostModel &c = *ctx->cm;
+        Norm norm;
+        for (int k = 0; k < F; ++k) {
+            norm.fmean[k] = c.fmean[k];
+            norm.fstd[k] = c.fstd[k];
+        }
+        norm.ymean = c.ymean;
+        norm.ystd = c.ystd;
+        kf::DeviceScope dev_scope(ctx->device);
+        cudaError_t e = dev_scope.status();
+        if (e == cudaSuccess) e = forward_on_device(c.p.data(), features, n, 1, norm, ms);
+        if (e != cudaSuccess) {
+            ctx->last_cuda = (int)e;
+            return KF_ECUDA;
+        }
+        return KF_OK;
+    }
+    return kf::predict_on_host(*ctx->cm, features, n, ms);
+}
+
+}  // extern "C"
+
+namespace kf {
+// The network evaluated on the host: for planning contexts without a GPU, and for the
+// recompute planner's own queries, which it issues one group at a time from inside its
+// dynamic program (a kernel launch and two copies per query would dominate planning).
+kf_status predict_on_host(const CostModel &c, const float *features, int n, float *ms)
+{
     const float *w = c.p.data();
     for (int i = 0; i < n; ++i) {
         float x[F], h1[HID];
@@ -342,6 +458,15 @@ kf_status kf_costmodel_predict(kf_ctx *ctx, const float *features, int n, float 
     }
     return KF_OK;
 }
+
+kf_status predict_group_ms(kf_ctx *model, const float *features, float *ms)
+{
+    if (!model || !model->cm || !model->cm->trained) return KF_ESTATE;
+    return predict_on_host(*model->cm, features, 1, ms);
+}
+}  // namespace kf
+
+extern "C" {
 
 kf_status kf_costmodel_get(kf_ctx *ctx, float *params, float *norm)
 {

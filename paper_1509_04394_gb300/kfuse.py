@@ -101,6 +101,7 @@ def _lib():
             "kf_batch_run": (i32, [P, P]),
             "kf_batch_destroy": (i32, [P]),
             "kf_tune_chunk_rows": (i32, [P, P, P, P, i32, i32, P, P, P]),
+            "kf_plan_measured": (i32, [P, P, P, P, ctypes.c_size_t, P, i32, i32, P, P, P, P]),
             "kf_dag_create": (i32, [P, P, i32, P]),
             "kf_dag_destroy": (i32, [P]),
             "kf_dag_group_info": (i32, [P, i32, i32, i64, i64, i64, P, P, P]),
@@ -110,6 +111,7 @@ def _lib():
             "kf_dag_time_groups": (i32, [P, P, P, i64, P, ctypes.c_size_t, i32, P, P]),
             "kf_costmodel_train": (i32, [P, P, P, i32, i32, ctypes.c_float, ctypes.c_uint, P]),
             "kf_costmodel_predict": (i32, [P, P, i32, P]),
+            "kf_costmodel_forward": (i32, [P, P, P, i32, P]),
             "kf_costmodel_grad": (i32, [P, P, P, P, i32, P, P]),
             "kf_costmodel_get": (i32, [P, P, P]),
             "kf_costmodel_set": (i32, [P, P, P]),
@@ -147,9 +149,9 @@ def exported_symbols() -> list[str]:
             "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
             "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static",
             "kf_track_workspace_bytes", "kf_track", "kf_batch_workspace_bytes", "kf_batch_create",
-            "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows", "kf_dag_create", "kf_dag_destroy",
+            "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows", "kf_plan_measured", "kf_dag_create", "kf_dag_destroy",
             "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups",
-            "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_grad", "kf_costmodel_get",
+            "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_forward", "kf_costmodel_grad", "kf_costmodel_get",
             "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times", "kf_pc_traffic", "kf_pc_plan",
             "kf_pc_workspace_bytes", "kf_pc_run", "kf_pc_run_group", "kf_pc_kalman", "kf_pc_group_workspace_bytes",
             "kf_track_host", "kf_st_smem_bytes", "kf_st_traffic", "kf_st_box_eq6", "kf_st_run", "kf_st_plan_eq6", "kf_st_tune",
@@ -385,6 +387,25 @@ def kf_tune_chunk_rows(ctx, frames, W: int, mask, counts, candidates, reps: int 
     return best.value, ms.value
 
 
+def kf_plan_measured(ctx, frames, W: int, mask, counts, workspace, candidates=None, reps: int = 3, stream=None):
+    """Measured exhaustive partition choice: (best cut mask, its median ms, every candidate's
+    median ms in candidate order). candidates=None times all 2^(n-1) partitions."""
+    import numpy as np
+    T, H, P = frames.shape
+    vid = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
+    o = kf_corners(mask.data_ptr(), int(mask.shape[2]), counts.data_ptr())
+    n = len(candidates) if candidates is not None else 1 << 7
+    cand = (ctypes.c_uint32 * n)(*candidates) if candidates is not None else None
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    best, ms = ctypes.c_uint32(), ctypes.c_float()
+    all_ms = np.zeros(n, dtype=np.float32)
+    _check("kf_plan_measured", _lib().kf_plan_measured(ctx, ctypes.byref(vid), ctypes.byref(o), _ptr(workspace), ws_bytes,
+                                                       cand, n if candidates is not None else 0, int(reps),
+                                                       _stream(stream), ctypes.byref(best), ctypes.byref(ms),
+                                                       all_ms.ctypes.data), ctx)
+    return best.value, ms.value, all_ms
+
+
 KF_NFEAT = 12
 
 
@@ -518,6 +539,16 @@ def kf_costmodel_predict(ctx, features):
     f, fp = _fptr(features)
     out = np.empty(f.shape[0], dtype=np.float32)
     _check("kf_costmodel_predict", _lib().kf_costmodel_predict(ctx, fp, int(f.shape[0]), out.ctypes.data), ctx)
+    return out
+
+
+def kf_costmodel_forward(ctx, params, x):
+    """The raw network at `params` for the rows of x, on the context's GPU."""
+    import numpy as np
+    p, pp = _fptr(params)
+    xx, xp = _fptr(x)
+    out = np.empty(xx.shape[0], dtype=np.float32)
+    _check("kf_costmodel_forward", _lib().kf_costmodel_forward(ctx, pp, xp, int(xx.shape[0]), out.ctypes.data), ctx)
     return out
 
 

@@ -64,3 +64,51 @@ def test_the_learned_model_plans_better_than_the_traffic_model(ctx):
     ev = cm.evaluate(ctx, meas[40:])
     assert ev["mlp_mean_regret"] < ev["traffic_mean_regret"]
     assert ev["mlp_better_or_equal"] >= 8
+
+
+def forward_error_bound(p, x):
+    """Per-sample bound of |FP32 forward - FP64 forward|: each layer's dot products of
+    m terms (with the bias) round within gamma_m of the sum of their magnitudes
+    (Higham, Sec. 3.1), and the next layer carries the errors of its inputs through the
+    magnitudes of its weights (ReLU is 1-Lipschitz)."""
+    u = 2.0 ** -24
+    g = lambda m: m * u / (1 - m * u)  # noqa: E731
+    W1, b1, W2, b2, w3, b3 = mlp.unpack(p, x.shape[1])
+    h1 = np.maximum(x @ W1.T + b1, 0.0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0.0)
+    e1 = g(x.shape[1] + 1) * (np.abs(x) @ np.abs(W1).T + np.abs(b1))
+    e2 = e1 @ np.abs(W2).T + g(65) * ((h1 + e1) @ np.abs(W2).T + np.abs(b2))
+    return e2 @ np.abs(w3) + g(65) * ((h2 + e2) @ np.abs(w3) + abs(b3))
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 1000])
+def test_inference_kernel_matches_the_reference_forward(ctx, n):
+    """The inference kernel's raw outputs against the FP64 network of the oracle, within
+    the FP32 rounding bound of its dot products, and 1e-5 normwise."""
+    rng = np.random.default_rng(100 + n)
+    p = rng.normal(scale=0.3, size=K.KF_MLP_NPARAMS).astype(np.float32)
+    x = rng.normal(size=(n, K.KF_NFEAT)).astype(np.float32)
+    y = K.kf_costmodel_forward(ctx, p, x).astype(np.float64)
+    p64, x64 = p.astype(np.float64), x.astype(np.float64)
+    ref = mlp.forward(p64, x64)
+    bound = forward_error_bound(p64, x64)
+    assert np.all(np.abs(y - ref) <= bound)
+    assert np.max(np.abs(y - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+def test_predictions_are_the_standardised_network(ctx):
+    """kf_costmodel_predict on the GPU: log1p features standardised by the stored means
+    and deviations, the network, then exp(y * ystd + ymean) -- against the same steps in
+    FP64 on the oracle's network (relative error within 1e-4: the output's FP32 error
+    times ystd, plus the rounding of the standardisation and of exp)."""
+    rng = np.random.default_rng(5)
+    F = K.KF_NFEAT
+    p = rng.normal(scale=0.2, size=K.KF_MLP_NPARAMS).astype(np.float32)
+    fmean, fstd = rng.uniform(0, 2, F).astype(np.float32), rng.uniform(0.5, 2, F).astype(np.float32)
+    norm = np.concatenate([fmean, fstd, np.array([-1.5, 0.8], dtype=np.float32)])
+    K.kf_costmodel_set(ctx, p, norm)
+    feats = rng.uniform(0, 50, size=(500, F)).astype(np.float32)
+    ms = K.kf_costmodel_predict(ctx, feats).astype(np.float64)
+    xs = (np.log1p(feats.astype(np.float64)) - fmean) / fstd
+    ref = np.exp(mlp.forward(p.astype(np.float64), xs) * float(norm[-1]) + float(norm[-2]))
+    assert np.max(np.abs(ms / ref - 1.0)) <= 1e-4
