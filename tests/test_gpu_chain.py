@@ -228,3 +228,27 @@ def test_full_size_workload_on_sampled_frames(dev):
     for i, t in enumerate(sample):
         maps, m_ref, c_ref = oc.chain_frame(fr_s[i][:, :spec.W].copy())
         check_mask(mask[t, :, :spec.W].cpu().numpy(), int(counts[t]), m_ref, c_ref, maps["r"], TOL_F32)
+
+
+def test_measured_planner_times_every_partition(dev):
+    """kf_plan_measured: a median time for every candidate, the least one returned, the
+    outputs those of a correct run; a workspace too small for some candidate is refused
+    before any work."""
+    T, H, W = 6, 96, 150
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=17, n_blobs=6, n_patches=4), pitch=pitch16(W))
+    f = torch.from_numpy(fr).to(dev)
+    ctx = K.Context(0)
+    m_ref, c_ref = torch.zeros_like(f), torch.zeros(T, dtype=torch.int32, device=dev)
+    K.kf_run(ctx.h, 0, f, W, m_ref, c_ref, None)
+    ws = torch.empty(max(K.kf_workspace_bytes(ctx.h, c, W, H, T) for c in range(128)), dtype=torch.uint8, device=dev)
+    mask, counts = torch.zeros_like(f), torch.zeros(T, dtype=torch.int32, device=dev)
+    best, ms, all_ms = K.kf_plan_measured(ctx.h, f, W, mask, counts, ws, reps=3)
+    assert 0 <= best < 128 and ms > 0 and np.all(all_ms > 0)
+    assert all_ms[best] == ms and ms == all_ms.min()
+    assert torch.equal(mask, m_ref) and torch.equal(counts, c_ref)
+    best2, ms2, all2 = K.kf_plan_measured(ctx.h, f, W, mask, counts, ws, candidates=[127, 0, 8], reps=2)
+    assert best2 in (127, 0, 8) and len(all2) == 3 and ms2 == all2.min()
+    small = torch.empty(256, dtype=torch.uint8, device=dev)
+    with pytest.raises(K.KfuseError) as e:
+        K.kf_plan_measured(ctx.h, f, W, mask, counts, small, candidates=[0, 127], reps=1)
+    assert e.value.status == K.KF_ENOMEM
