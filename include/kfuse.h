@@ -70,9 +70,15 @@ typedef enum kf_stage_kind {
 
 typedef enum kf_precision {
     KF_PREC_F32 = 0, /* FP32 maps between groups, FP32 arithmetic                         */
-    KF_PREC_F16 = 1  /* 16-bit maps between groups: exact uint16 for the integer-valued
+    KF_PREC_F16 = 1, /* 16-bit maps between groups: exact uint16 for the integer-valued
                         maps of stages 1-3, FP16 (true units) for stages 4-7; FP32
                         arithmetic on chip                                               */
+    KF_PREC_F16_TILES = 2 /* 16-bit maps as KF_PREC_F16, and FP16 inter-stage tiles on chip
+                        in the groups that form the structure-tensor products and keep the
+                        response on chip (first stage <= 5, last stage 8): the box's row-pair
+                        sums are held in FP16 (products scaled by 2^-32), the window sums
+                        accumulated in FP32. Error within the FP16 tolerance (2e-3 of the
+                        frame's largest response); results differ from the FP32 groups'   */
 } kf_precision;
 
 typedef enum kf_dtype { KF_DT_U8 = 0, KF_DT_F32 = 1, KF_DT_F16 = 2, KF_DT_U16 = 3 } kf_dtype;
@@ -147,8 +153,9 @@ kf_status kf_destroy(kf_ctx *ctx);
 #define KF_DEVERR_TIMEOUT 1
 kf_status kf_device_error(kf_ctx *ctx, int *code);
 
-/* KF_PREC_F32 (default) or KF_PREC_F16. Changes the builtin byte counts and the dtype
- * of the maps kf_run keeps in the workspace. */
+/* KF_PREC_F32 (default), KF_PREC_F16 or KF_PREC_F16_TILES. Changes the builtin byte
+ * counts and the dtype of the maps kf_run keeps in the workspace (16-bit for both FP16
+ * forms), and with KF_PREC_F16_TILES the on-chip tiles of the groups it names. */
 kf_status kf_set_precision(kf_ctx *ctx, int precision);
 /* Rows per warp job of the executor (default 200, >= 1). */
 kf_status kf_set_chunk_rows(kf_ctx *ctx, int rows);
@@ -286,7 +293,8 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
  * launch, the counter resets and the batched selection and LK kernels are captured once
  * into a CUDA graph by kf_batch_create and replayed by kf_batch_run. FP32 contexts only
  * (full fusion has no maps between groups). The chunk height is the context's
- * (kf_set_chunk_rows / kf_tune_chunk_rows) at creation. */
+ * (kf_set_chunk_rows / kf_tune_chunk_rows) at creation, or chosen per video with
+ * kf_batch_create_ex. */
 typedef struct kf_batch kf_batch;
 /* Workspace of a batch of n videos; track_K = 0 without tracking, else the points per
  * frame (1..1024). */
@@ -298,6 +306,16 @@ kf_status kf_batch_workspace_bytes(const kf_ctx *ctx, const kf_video *videos, in
  * graph). */
 kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners *outs, const kf_tracks *tracks, int n,
                           void *workspace, size_t workspace_bytes, kf_batch **out);
+/* kf_batch_create with the tile shape chosen per video and the launch's size chosen:
+ * chunk_rows (NULL, or n entries >= 1) gives each video's rows per job (its tile height;
+ * the tile width is the warp strip, 112 output columns, or a half strip for the last
+ * one); warps_per_sm (0 = as many as fit) caps the persistent launch at that many
+ * resident warps per SM. The queue hands out jobs longest first (rows per job, then jobs
+ * per video), so the launch ends on its shortest jobs. kf_batch_create is this call with
+ * NULL and 0. */
+kf_status kf_batch_create_ex(kf_ctx *ctx, const kf_video *videos, const kf_corners *outs, const kf_tracks *tracks, int n,
+                             const int *chunk_rows, int warps_per_sm, void *workspace, size_t workspace_bytes,
+                             kf_batch **out);
 /* Enqueue one run of the batch on `stream` (asynchronous): every video's mask, counts and,
  * if requested, tracks are rewritten. */
 kf_status kf_batch_run(kf_batch *batch, void *stream);

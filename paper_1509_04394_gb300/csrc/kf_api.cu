@@ -41,7 +41,7 @@ bool builtin_chain(const kf_ctx *c)
 double builtin_map_bytes(int k, int precision)
 {
     if (k == 0 || k == 8) return 1.0;  // u8 frames, u8 mask
-    return kf::map_channels(k) * (precision == KF_PREC_F16 ? 2.0 : 4.0);
+    return kf::map_channels(k) * (precision != KF_PREC_F32 ? 2.0 : 4.0);
 }
 
 kf_stage_desc builtin_desc(int kind, int precision)
@@ -200,8 +200,10 @@ kf_status check_map(const kf_map *m, int stage_out, int precision, int64_t W, in
 
 // Parameter block of group [A..B] (1-based) over already validated maps.
 kf_status fill_params(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &out, int64_t W, int64_t H, int64_t T,
-                      int32_t *counts, unsigned long long *cand, int *cand_count, int64_t cand_cap, kf::GroupParams &p)
+                      int32_t *counts, unsigned long long *cand, int *cand_count, int64_t cand_cap, kf::GroupParams &p,
+                      int chunk_rows = 0)
 {
+    const int rows = chunk_rows > 0 ? chunk_rows : c->chunk_rows;
     p = kf::GroupParams{};
     for (int i = 0; i < 3; ++i) {
         p.in[i] = in.plane[i];
@@ -224,18 +226,21 @@ kf_status fill_params(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &o
     const kf::StripGeom sg = kf::strip_geometry(kf::sum_rx(A, B), (int)W);
     p.xs0 = sg.xs0;
     p.step = sg.step;
+    p.out_off = sg.out_off;
     p.n_strips = sg.n_strips;
     p.half_last = sg.half_last;
+    p.n_lead = sg.n_lead;
+    p.n_trail = sg.n_trail;
     if (p.half_last)
         for (int i = 0; i < in.channels; ++i)
             if (!encode_plane(&p.tmap_half[i], in.plane[i], in.dtype, in.pitch, in.frame_stride, W, H, T, kf::STRIP / 2))
                 return KF_EINVAL;
     p.T = (int)T;
-    p.chunk_rows = c->chunk_rows;
-    p.n_chunks = (int)((H + c->chunk_rows - 1) / c->chunk_rows);
+    p.chunk_rows = rows;
+    p.n_chunks = (int)((H + rows - 1) / rows);
     p.n_jobs = T * p.n_chunks * (p.n_strips - p.half_last) + (T + 1) / 2 * p.n_chunks * p.half_last;
     p.thr = (float)(NMS_THRESHOLD * kf::map_scale(7));
-    const bool f16 = c->precision == KF_PREC_F16;
+    const bool f16 = c->precision != KF_PREC_F32;
     // FP16 maps (stages 4-7) hold true units; uint16 and FP32 maps hold scaled units
     p.in_scale = (f16 && A - 1 >= 4) ? (float)kf::map_scale(A - 1) : 1.0f;
     p.out_scale = (f16 && B >= 4 && B < 8) ? (float)(1.0 / kf::map_scale(B)) : 1.0f;
@@ -296,14 +301,17 @@ kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &
     kf::GroupParams p;
     kf_status st = fill_params(c, A, B, in, out, W, H, T, counts, cand, cand_count, cand_cap, p);
     if (st != KF_OK) return st;
-    const bool f16 = c->precision == KF_PREC_F16;
+    // 0: FP32 maps; 1: 16-bit maps; 2: 16-bit maps and FP16 inter-stage tiles on chip
+    const int f16 = c->precision == KF_PREC_F32 ? 0 : c->precision == KF_PREC_F16_TILES ? 2 : 1;
     const int64_t blocks = p.n_jobs;  // one warp (one job) per block
     if (B == 8) {
         cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)T, s);
         if (e != cudaSuccess) return cuda_fail(c, e);
     }
-    kf::LaunchFn fn = cand ? ((A == 1 && B == kf::NSTAGES) ? kf::launch_chain_with_candidates : nullptr)
-                           : launcher(A, B, f16 ? 1 : 0);
+    kf::LaunchFn fn = cand ? ((A == 1 && B == kf::NSTAGES) ? (f16 == 2 ? kf::launch_chain_with_candidates_tiles
+                                                                      : kf::launch_chain_with_candidates)
+                                                          : nullptr)
+                           : launcher(A, B, f16);
     if (!fn) return KF_EINVAL;
     TimedLaunch tl(c, cand ? KF_KT_CHAIN_CORNERS : KF_KT_GROUP, s);
     const int e = fn(p, (unsigned)blocks, s);
@@ -322,7 +330,7 @@ struct WsPlan {
 WsPlan plan_workspace(const kf_ctx *c, uint32_t cuts, int64_t W, int64_t H, int64_t T)
 {
     WsPlan w;
-    const size_t elem = c->precision == KF_PREC_F16 ? 2 : 4;
+    const size_t elem = c->precision != KF_PREC_F32 ? 2 : 4;
     w.pitch_e = round_up(W, 8);
     w.plane_bytes = (size_t)round_up((int64_t)(w.pitch_e * H * T * (int64_t)elem), 256);
     int k = 0;
@@ -400,10 +408,12 @@ kf_status kf_destroy(kf_ctx *ctx)
         if (ctx->s_in) {
             cudaStreamDestroy(ctx->s_in);
             cudaStreamDestroy(ctx->s_out);
-            for (int i = 0; i < kf_ctx::N_RING; ++i) cudaStreamDestroy(ctx->s_comp[i]);
             for (int i = 0; i < kf_ctx::N_RING; ++i) {
+                cudaStreamDestroy(ctx->s_comp[i]);
+                if (ctx->s_trk[i]) cudaStreamDestroy(ctx->s_trk[i]);
                 cudaEventDestroy(ctx->ev_in[i]);
                 cudaEventDestroy(ctx->ev_comp[i]);
+                if (ctx->ev_chain[i]) cudaEventDestroy(ctx->ev_chain[i]);
             }
             cudaEventDestroy(ctx->ev_edge);
         }
@@ -434,7 +444,7 @@ kf_status kf_device_error(kf_ctx *ctx, int *code)
 
 kf_status kf_set_precision(kf_ctx *ctx, int precision)
 {
-    if (!ctx || (precision != KF_PREC_F32 && precision != KF_PREC_F16)) return KF_EINVAL;
+    if (!ctx || (precision != KF_PREC_F32 && precision != KF_PREC_F16 && precision != KF_PREC_F16_TILES)) return KF_EINVAL;
     ctx->precision = precision;
     return KF_OK;
 }
@@ -561,7 +571,7 @@ kf_status kf_enumerate(const kf_ctx *ctx, uint32_t *buf, int64_t cap, int64_t *n
 kf_status kf_map_scale(const kf_ctx *ctx, int stage, double *factor)
 {
     if (!ctx || !factor || stage < 0 || stage >= kf::NSTAGES) return KF_EINVAL;
-    if (stage == kf::NSTAGES - 1 || (ctx->precision == KF_PREC_F16 && stage >= 3)) *factor = 1.0;
+    if (stage == kf::NSTAGES - 1 || (ctx->precision != KF_PREC_F32 && stage >= 3)) *factor = 1.0;
     else *factor = 1.0 / kf::map_scale(stage + 1);
     return KF_OK;
 }
@@ -684,7 +694,7 @@ kf_status check_track_args(kf_ctx *ctx, const kf_video *v, const kf_corners *o, 
 // (LK of frame t0 reads frame t0 - 1): the chain with corner lists over the frame range,
 // then selection and LK from frame t0 on.
 kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf_tracks *tr, void *ws, int64_t t0,
-                      int64_t t1, cudaStream_t s)
+                      int64_t t1, cudaStream_t s, cudaStream_t s_trk = nullptr, cudaEvent_t ev_chain = nullptr)
 {
     const int64_t n = t1 - t0;
     if (n <= 0) return KF_OK;
@@ -709,6 +719,13 @@ kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const
     kf_status st = launch_group(ctx, 1, kf::NSTAGES, fin, fout, v->W, v->H, n, o->counts + t0, s, cand + t0 * cap,
                                 cand_count + t0, cap);
     if (st != KF_OK) return st;
+    // the tracking set on its own stream when one is given (after the chain's event)
+    if (s_trk && ev_chain) {
+        e = cudaEventRecord(ev_chain, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_trk, ev_chain, 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+        s = s_trk;
+    }
     // the tracking set, after the kernel-to-kernel dependency
     kf::TrackVideo tv{};
     tv.frames = v->frames;
@@ -796,10 +813,14 @@ kf_status copy_streams(kf_ctx *c)
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_out, cudaStreamNonBlocking, hi_prio);
+    // each chunk's selection and LK on a high-priority stream of their own: they then run
+    // as soon as the chunk's chain blocks retire, not behind the next chunks' chains
     for (int i = 0; e == cudaSuccess && i < kf_ctx::N_RING; ++i) {
         e = cudaStreamCreateWithFlags(&c->s_comp[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_trk[i], cudaStreamNonBlocking, hi_prio);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_chain[i], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_edge, cudaEventDisableTiming);
     return e == cudaSuccess ? KF_OK : cuda_fail(c, e);
@@ -871,11 +892,15 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
     for (int i = 0; e == cudaSuccess && i < kf_ctx::N_RING; ++i) e = cudaStreamWaitEvent(ctx->s_comp[i], ctx->ev_edge, 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     const int64_t fstride = video->pitch * H, mstride = out->mask_pitch * H;
-    // the first chunk is a quarter of the others, so the hot path starts sooner
+    // the first chunk is a quarter of the others, so the hot path starts sooner, and so is
+    // the last one, so little of the hot path and of the copy out is left once the last
+    // frames have arrived: after the first chunk, full chunks while more than a chunk and
+    // a quarter remain, then the rest less a quarter chunk, then that quarter
     const int64_t first = chunk / 4 > 0 ? chunk / 4 : 1;
     int64_t t1 = 0;
     for (int64_t t0 = 0, k = 0; t0 < T && e == cudaSuccess; t0 = t1, ++k) {
-        const int64_t len = k == 0 ? first : chunk;
+        const int64_t rest = T - t0;
+        const int64_t len = k == 0 ? first : rest > chunk + first ? chunk : rest > first ? rest - first : rest;
         t1 = t0 + len < T ? t0 + len : T;
         const int64_t n = t1 - t0;
         const int r = (int)(k % kf_ctx::N_RING);
@@ -890,9 +915,9 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
         if (e == cudaSuccess) e = cudaEventRecord(ein, ctx->s_in);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ein, 0);
         if (e != cudaSuccess) break;
-        st = track_range(ctx, video, out, tracks, workspace, t0, t1, cs);
+        st = track_range(ctx, video, out, tracks, workspace, t0, t1, cs, ctx->s_trk[r], ctx->ev_chain[r]);
         if (st != KF_OK) return st;
-        e = cudaEventRecord(ecomp, cs);
+        e = cudaEventRecord(ecomp, ctx->s_trk[r]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ecomp, 0);
         auto d2h = [&](void *dst, const void *src, size_t bytes) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s_out);
@@ -1024,7 +1049,16 @@ kf_status kf_batch_workspace_bytes(const kf_ctx *ctx, const kf_video *videos, in
 kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners *outs, const kf_tracks *tracks, int n,
                           void *ws, size_t ws_bytes, kf_batch **out)
 {
-    if (!ctx || !videos || !outs || n < 1 || !out) return KF_EINVAL;
+    return kf_batch_create_ex(ctx, videos, outs, tracks, n, nullptr, 0, ws, ws_bytes, out);
+}
+
+kf_status kf_batch_create_ex(kf_ctx *ctx, const kf_video *videos, const kf_corners *outs, const kf_tracks *tracks, int n,
+                             const int *chunk_rows, int warps_per_sm, void *ws, size_t ws_bytes, kf_batch **out)
+{
+    if (!ctx || !videos || !outs || n < 1 || !out || warps_per_sm < 0) return KF_EINVAL;
+    if (chunk_rows)
+        for (int i = 0; i < n; ++i)
+            if (chunk_rows[i] < 1) return KF_EINVAL;
     *out = nullptr;
     if (ctx->device < 0) return KF_ESTATE;
     if (!builtin_chain(ctx) || ctx->precision != KF_PREC_F32) return KF_EUNSUPPORTED;
@@ -1075,9 +1109,8 @@ kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners 
         const int64_t cap = track ? kf::cand_capacity(v.W, v.H) : 0;
         kf_status st = fill_params(ctx, 1, kf::NSTAGES, fin, fout, v.W, v.H, v.T, outs[i].counts,
                                    track ? d_cand + cand_off : nullptr, track ? d_cand_count + frame_begin : nullptr, cap,
-                                   hp[(size_t)i]);
+                                   hp[(size_t)i], chunk_rows ? chunk_rows[i] : 0);
         if (st != KF_OK) return st;
-        items[(size_t)i + 1] = items[(size_t)i] + hp[(size_t)i].n_jobs;
         if (track) {
             kf::TrackVideo &tv = ht[(size_t)i];
             tv.frames = v.frames;
@@ -1098,7 +1131,22 @@ kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners 
         frame_begin += v.T;
         cand_off += v.T * cap;
     }
-    e = cudaMemcpy(d_params, hp.data(), sizeof(kf::GroupParams) * (size_t)n, cudaMemcpyHostToDevice);
+    // The queue hands out the jobs of the videos in order of decreasing job length (rows
+    // per job, then jobs per video), so the last jobs of the launch are the shortest and
+    // the tail of the persistent launch is short (longest-job-first order).
+    std::vector<int> order((size_t)n);
+    for (int i = 0; i < n; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const kf::GroupParams &pa = hp[(size_t)a], &pb = hp[(size_t)b];
+        if (pa.chunk_rows != pb.chunk_rows) return pa.chunk_rows > pb.chunk_rows;
+        return pa.n_jobs > pb.n_jobs;
+    });
+    std::vector<kf::GroupParams> hq((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        hq[(size_t)k] = hp[(size_t)order[(size_t)k]];
+        items[(size_t)k + 1] = items[(size_t)k] + hq[(size_t)k].n_jobs;
+    }
+    e = cudaMemcpy(d_params, hq.data(), sizeof(kf::GroupParams) * (size_t)n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_items, items.data(), sizeof(int64_t) * items.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && track)
         e = cudaMemcpy(d_tracks, ht.data(), sizeof(kf::TrackVideo) * (size_t)n, cudaMemcpyHostToDevice);
@@ -1108,8 +1156,9 @@ kf_status kf_batch_create(kf_ctx *ctx, const kf_video *videos, const kf_corners 
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
-    const int per_sm = kf::batch_chain_blocks_per_sm(track);
+    int per_sm = kf::batch_chain_blocks_per_sm(track);
     if (per_sm < 1) return cuda_fail(ctx, cudaErrorInvalidConfiguration);
+    if (warps_per_sm > 0 && warps_per_sm < per_sm) per_sm = warps_per_sm;  // one warp per block
     if (track) {
         const int r = kf::prepare_select();
         if (r) return cuda_fail(ctx, (cudaError_t)r);

@@ -366,6 +366,57 @@ struct BoxV {
     }
 };
 
+// The box's vertical state in the FP16 form: the same ring of row-pair sums held as FP16
+// pairs (half the registers), the newest row in FP32. The pair sums are rounded to FP16
+// once when formed, the two of a window are added in FP16, and the window's sum is
+// accumulated in FP32 with the newest row. Inputs are the products scaled by 2^-32 (an
+// exact power of two; see run_job), so every pair sum fits FP16's range.
+struct BoxV16 {
+    __half2 pair[5][3][2];  // slot PH: the row pushed at phase PH plus the row before it
+    V4 last[3];             // the newest row
+    __device__ __forceinline__ void fill(const Rows<3> &h)
+    {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            last[m] = h.v[m];
+            const V4 two = add4(h.v[m], h.v[m]);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const __half2 t = __float22half2_rn(two.p[k]);
+#pragma unroll
+                for (int s = 0; s < 5; ++s) pair[s][m][k] = t;
+            }
+        }
+    }
+    template <int PH>
+    __device__ __forceinline__ void newest(Rows<3> &h) const
+    {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) h.v[m] = last[m];
+    }
+    template <int PH>
+    __device__ __forceinline__ void put(const Rows<3> &h)
+    {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const V4 ps = add4(last[m], h.v[m]);
+            pair[PH][m][0] = __float22half2_rn(ps.p[0]);
+            pair[PH][m][1] = __float22half2_rn(ps.p[1]);
+            last[m] = h.v[m];
+        }
+    }
+    template <int PH>
+    __device__ __forceinline__ void sum(Rows<3> &o) const
+    {
+        constexpr int p1 = (PH + 4) % 5, p3 = (PH + 2) % 5;
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                o.v[m].p[k] = __fadd2_rn(__half22float2(__hadd2(pair[p3][m][k], pair[p1][m][k])), last[m].p[k]);
+    }
+};
+
 // Stage 7: Harris response, R = (Sxx Syy - Sxy^2) - k (Sxx + Syy)^2.
 __device__ __forceinline__ void harris(const Rows<3> &s, V4 &r)
 {
@@ -605,21 +656,32 @@ template <int A, int B, bool F16, bool CAND = false> struct SmemPlan {
 };
 
 // ------------------------------------------------------------------ the group kernel
-// Job order: the full strips (strip fastest, then chunk, then frame), then the half-strip
-// jobs of the frame pairs (chunk fastest). The half-strip jobs run a second instance of
-// the row loop; kept together at the end, each SM runs one instance at a time, which
-// keeps the instruction cache to one loop body (interleaving them with the full strips,
-// to find their columns still in L2, measured 40% slower).
-struct JobPos { int strip, chunk, frame0; bool paired; };
+// Job order: the full strips away from the frame's edges (strip fastest, then chunk,
+// then frame), then the full strips at an edge (likewise), then the half-strip jobs of
+// the frame pairs (chunk fastest). Each kind runs its own instance of the row loop (the
+// interior one without any edge handling); kept together, each SM runs one instance at
+// a time, which keeps the instruction cache to one loop body (interleaving the half
+// strips with the full strips, to find their columns still in L2, measured 40% slower).
+struct JobPos { int strip, chunk, frame0; bool paired, edge; };
 __device__ __forceinline__ JobPos decode_job(const GroupParams &p, int64_t job)
 {
     JobPos j;
     const int F = p.n_strips - p.half_last;  // full strips per frame
+    const int E = p.n_lead + p.n_trail, I = F - E;
+    const int64_t inner_jobs = (int64_t)p.T * p.n_chunks * I;
     const int64_t full_jobs = (int64_t)p.T * p.n_chunks * F;
     j.paired = job >= full_jobs;
-    if (!j.paired) {
-        j.strip = (int)(job % F);
-        const int64_t rest = job / F;
+    j.edge = job >= inner_jobs;
+    if (!j.edge) {
+        j.strip = p.n_lead + (int)(job % I);
+        const int64_t rest = job / I;
+        j.chunk = (int)(rest % p.n_chunks);
+        j.frame0 = (int)(rest / p.n_chunks);
+    } else if (!j.paired) {
+        const int64_t q = job - inner_jobs;
+        const int e = (int)(q % E);
+        j.strip = e < p.n_lead ? e : F - p.n_trail + (e - p.n_lead);
+        const int64_t rest = q / E;
         j.chunk = (int)(rest % p.n_chunks);
         j.frame0 = (int)(rest / p.n_chunks);
     } else {
@@ -631,7 +693,7 @@ __device__ __forceinline__ JobPos decode_job(const GroupParams &p, int64_t job)
     return j;
 }
 
-template <int A, int B, bool F16, bool CAND, bool PAIRED>
+template <int A, int B, bool F16, bool CAND, bool PAIRED, bool TILES, bool EDGE>
 __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, unsigned char *smem, unsigned &kbase,
                                         bool global_desc)
 {
@@ -647,6 +709,12 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
     constexpr int NOUT = map_channels(B);
     constexpr int D3 = sum_ry(A, 2), D4 = sum_ry(A, 3), D6 = sum_ry(A, 5), D8 = sum_ry(A, 7);
     constexpr bool HAS3 = A <= 3 && 3 <= B, HAS4 = A <= 4 && 4 <= B, HAS6 = SP::HAS6, HAS8 = A <= 8 && 8 <= B;
+    // FP16 inter-stage tiles (KF_PREC_F16_TILES) in a group that forms the products on
+    // chip and keeps the response on chip (A <= 5, B == 8): the box's ring of row-pair
+    // sums in FP16 (BoxV16), on products scaled by 2^-32, so the response and the
+    // threshold are scaled by 2^-64 (exact).
+    static_assert(!TILES || (F16 && A <= 5 && B == 8), "FP16 tiles: groups forming the products and the response");
+    constexpr bool ONCHIP16 = TILES;
 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SP::BAR_OFF);
     unsigned char *stage_buf = smem + SP::IN_OFF;
@@ -665,14 +733,18 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
     // per-job copies of the fields the row loop uses: with `p` in global memory the
     // compiler could not keep them in registers across the loop's stores
     const int64_t out_pitch = p.out_pitch;
-    const float thr = p.thr, in_scale = p.in_scale, out_scale = p.out_scale;
+    const float thr = ONCHIP16 ? p.thr * 0x1p-64f : p.thr, in_scale = p.in_scale, out_scale = p.out_scale;
     void *const out_plane[3] = {p.out[0], p.out[1], p.out[2]};
 
     const int xs = p.xs0 + strip * p.step;  // multiple of 16 columns: TMA-aligned
     const int x0 = xs + C * sl;
-    const int xo0 = max(xs + RXT, 0), xo1 = min(xs + RXT + p.step, W);
-    const bool edgeL = xs < 0, edgeR = xs + (paired ? STRIP / 2 : STRIP) > W;
-    const bool lane_inside = (x0 >= 0) && (x0 + C <= W);
+    const int xo0 = max(xs + p.out_off, 0), xo1 = min(xs + p.out_off + p.step, W);
+    // EDGE == false: the strip's input box lies inside the frame, so every lane reads its
+    // own columns, no on-chip map needs an edge fix-up, and (outputs starting on a lane
+    // boundary) each lane outputs all of its columns or none
+    static_assert(EDGE || !PAIRED, "half strips are the last strip: an edge");
+    const bool edgeL = EDGE && xs < 0, edgeR = EDGE && xs + (paired ? STRIP / 2 : STRIP) > W;
+    const bool lane_inside = !EDGE || ((x0 >= 0) && (x0 + C <= W));
     int off[C];  // staged-tile offset of each column's clamped source
 #pragma unroll
     for (int c = 0; c < C; ++c) off[c] = min(max(x0 + c, 0), W - 1) - xs;
@@ -729,7 +801,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
     std::conditional_t<HAS3 && !PACKED, GaussV, Empty> s3{};
     std::conditional_t<PACKED, GaussVPacked, Empty> s3p{};
     std::conditional_t<HAS4, SobelV, Empty> s4{};
-    std::conditional_t<HAS6, BoxV, Empty> s6{};
+    std::conditional_t<HAS6, std::conditional_t<ONCHIP16, BoxV16, BoxV>, Empty> s6{};
     std::conditional_t<HAS8, NmsV, Empty> s8{};
     unsigned count = 0;
     [[maybe_unused]] unsigned long long *cand_buf = reinterpret_cast<unsigned long long *>(smem + SP::CAND_OFF);
@@ -836,7 +908,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         [[maybe_unused]] Rows<2> ixy;
         if constexpr (HAS4) {
             if constexpr (hstencil_before(A, 4))
-                if (edgeL | edgeR) fix_edges<1>(g, xs, x0, W, edgeL, edgeR, lbase);
+                if (EDGE && (edgeL | edgeR)) fix_edges<1>(g, xs, x0, W, edgeL, edgeR, lbase);
             V4 dx, sx;
             sobel_h(g.v[0], dx, sx);
             if (border) {
@@ -852,7 +924,11 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         [[maybe_unused]] Rows<3> pr;
         if constexpr (A <= 5 && 5 <= B) {
             if constexpr (hstencil_before(A, 6) && HAS6)
-                if (edgeL | edgeR) fix_edges<2>(ixy, xs, x0, W, edgeL, edgeR, lbase);
+                if (EDGE && (edgeL | edgeR)) fix_edges<2>(ixy, xs, x0, W, edgeL, edgeR, lbase);
+            if constexpr (ONCHIP16) {
+#pragma unroll
+                for (int m = 0; m < 2; ++m) ixy.v[m] = mul4(ixy.v[m], splat4(0x1p-16f));
+            }
             products(ixy, pr);
         } else if constexpr (A == 6) {
             pr = in;
@@ -885,7 +961,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         [[maybe_unused]] V4 centre;
         if constexpr (HAS8) {
             if constexpr (hstencil_before(A, 8))
-                if (edgeL | edgeR) fix_edges<1>(r7, xs, x0, W, edgeL, edgeR, lbase);
+                if (EDGE && (edgeL | edgeR)) fix_edges<1>(r7, xs, x0, W, edgeL, edgeR, lbase);
             V4 mh;
             nms_h(r7.v[0], mh);
             if (border) {
@@ -908,8 +984,11 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
             if constexpr (B == 8) {
                 const unsigned kept = bits & out_mask;
                 uint8_t *mp = static_cast<uint8_t *>(out_plane[0]) + ooff;
-                if (out_mask == (1u << C) - 1) {
-                    *reinterpret_cast<uint32_t *>(mp) = (kept & 1u) | (kept & 2u) << 7 | (kept & 4u) << 14 | (kept & 8u) << 21;
+                if (!EDGE || out_mask == (1u << C) - 1) {
+                    // bit k of `kept` to byte k: kept * (1 + 2^7 + 2^14 + 2^21) puts bit k of the
+                    // copy shifted by 7j at 8j when k == j, and elsewhere at k + 7j, never a
+                    // multiple of 8 for k != j (|k - j| < 7)
+                    *reinterpret_cast<uint32_t *>(mp) = (kept * 0x00204081u) & 0x01010101u;
                 } else {
 #pragma unroll
                     for (int c = 0; c < C; ++c) if (out_mask >> c & 1) mp[c] = (uint8_t)(kept >> c & 1);
@@ -925,7 +1004,10 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
                 else if constexpr (B == 6) res = &sm;
                 else res = &r7;
 #pragma unroll
-                for (int m = 0; m < NOUT; ++m) Store<MapT<B, F16>>::row(out_plane[m], ooff, res->v[m], out_mask, out_scale);
+                // an interior lane that outputs anything outputs all of its columns
+                const unsigned st_mask = EDGE ? out_mask : (1u << C) - 1;
+#pragma unroll
+                for (int m = 0; m < NOUT; ++m) Store<MapT<B, F16>>::row(out_plane[m], ooff, res->v[m], st_mask, out_scale);
             }
         }
     };
@@ -1002,24 +1084,25 @@ __device__ __forceinline__ void init_ring(unsigned char *smem)
 }
 
 // a job of either kind: full strip, or a pair of half strips (warp-uniform choice)
-template <int A, int B, bool F16, bool CAND>
+template <int A, int B, bool F16, bool CAND, bool TILES = false>
 __device__ __forceinline__ bool run_any_job(const GroupParams &p, int64_t job, unsigned char *smem, unsigned &kbase,
                                             bool global_desc)
 {
     const JobPos jp = decode_job(p, job);
-    if (!jp.paired) return run_job<A, B, F16, CAND, false>(p, jp, smem, kbase, global_desc);
-    return run_job<A, B, F16, CAND, true>(p, jp, smem, kbase, global_desc);
+    if (!jp.edge) return run_job<A, B, F16, CAND, false, TILES, false>(p, jp, smem, kbase, global_desc);
+    if (!jp.paired) return run_job<A, B, F16, CAND, false, TILES, true>(p, jp, smem, kbase, global_desc);
+    return run_job<A, B, F16, CAND, true, TILES, true>(p, jp, smem, kbase, global_desc);
 }
 
 // One job per block (one warp): the launch's blocks enumerate the jobs.
-template <int A, int B, bool F16, bool CAND = false>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, (A <= 6 && 6 <= B) ? MIN_BLOCKS_BOX : MIN_BLOCKS) group_kernel(const __grid_constant__ GroupParams p)
+template <int A, int B, bool F16, bool CAND = false, bool TILES = false>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, TILES ? MIN_BLOCKS_BOX16 : (A <= 6 && 6 <= B) ? MIN_BLOCKS_BOX : MIN_BLOCKS) group_kernel(const __grid_constant__ GroupParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     if ((int64_t)blockIdx.x >= p.n_jobs) return;
     init_ring<SmemPlan<A, B, F16, CAND>::NST>(smem);
     unsigned kbase = 0;
-    run_any_job<A, B, F16, CAND>(p, blockIdx.x, smem, kbase, false);
+    run_any_job<A, B, F16, CAND, TILES>(p, blockIdx.x, smem, kbase, false);
 }
 
 // Persistent batch over many videos (the fully fused chain): each resident warp pops

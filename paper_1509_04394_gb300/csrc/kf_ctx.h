@@ -37,8 +37,8 @@ struct kf_ctx {
     std::vector<cudaEvent_t> spare_events;
     // kf_track_host: the copy-in, compute and copy-out streams and their event rings (owned)
     static constexpr int N_RING = 3;
-    cudaStream_t s_in = nullptr, s_out = nullptr, s_comp[N_RING] = {};
-    cudaEvent_t ev_in[N_RING] = {}, ev_comp[N_RING] = {}, ev_edge = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_comp[N_RING] = {}, s_trk[N_RING] = {};
+    cudaEvent_t ev_in[N_RING] = {}, ev_comp[N_RING] = {}, ev_chain[N_RING] = {}, ev_edge = nullptr;
     // kf_track_host with packed masks: device staging of the packed chunks (owned)
     uint8_t *pack_buf = nullptr;
     size_t pack_bytes = 0;

@@ -6,10 +6,11 @@
 
 namespace kf {
 namespace {
-template <int A, int B, bool F16>
+template <int A, int B, bool F16, bool TILES = false>
 int launch(const GroupParams &p, unsigned grid, void *stream)
 {
-    group_kernel<A, B, F16><<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<A, B, F16>::BYTES, static_cast<cudaStream_t>(stream)>>>(p);
+    group_kernel<A, B, F16, false, TILES>
+        <<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<A, B, F16>::BYTES, static_cast<cudaStream_t>(stream)>>>(p);
     return (int)cudaGetLastError();
 }
 }  // namespace
@@ -45,6 +46,14 @@ int launch_chain_with_candidates(const GroupParams &p, unsigned grid, void *stre
     return (int)cudaGetLastError();
 }
 
+// the same with FP16 inter-stage tiles (the box's ring in FP16, see run_job)
+int launch_chain_with_candidates_tiles(const GroupParams &p, unsigned grid, void *stream)
+{
+    group_kernel<1, 8, true, true, true><<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<1, 8, true, true>::BYTES,
+                                           static_cast<cudaStream_t>(stream)>>>(p);
+    return (int)cudaGetLastError();
+}
+
 LaunchFn launcher_a1(int B, int f16)
 {
     switch (B) {
@@ -55,7 +64,7 @@ LaunchFn launcher_a1(int B, int f16)
     case 5: return f16 ? launch<1, 5, true> : launch<1, 5, false>;
     case 6: return f16 ? launch<1, 6, true> : launch<1, 6, false>;
     case 7: return f16 ? launch<1, 7, true> : launch<1, 7, false>;
-    case 8: return f16 ? launch<1, 8, true> : launch<1, 8, false>;
+    case 8: return f16 == 2 ? launch<1, 8, true, true> : f16 ? launch<1, 8, true> : launch<1, 8, false>;
     default: return nullptr;
     }
 }

@@ -6,10 +6,11 @@
 
 namespace kf {
 namespace {
-template <int A, int B, bool F16>
+template <int A, int B, bool F16, bool TILES = false>
 int launch(const GroupParams &p, unsigned grid, void *stream)
 {
-    group_kernel<A, B, F16><<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<A, B, F16>::BYTES, static_cast<cudaStream_t>(stream)>>>(p);
+    group_kernel<A, B, F16, false, TILES>
+        <<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<A, B, F16>::BYTES, static_cast<cudaStream_t>(stream)>>>(p);
     return (int)cudaGetLastError();
 }
 }  // namespace
@@ -23,7 +24,7 @@ LaunchFn launcher_a2(int B, int f16)
     case 5: return f16 ? launch<2, 5, true> : launch<2, 5, false>;
     case 6: return f16 ? launch<2, 6, true> : launch<2, 6, false>;
     case 7: return f16 ? launch<2, 7, true> : launch<2, 7, false>;
-    case 8: return f16 ? launch<2, 8, true> : launch<2, 8, false>;
+    case 8: return f16 == 2 ? launch<2, 8, true, true> : f16 ? launch<2, 8, true> : launch<2, 8, false>;
     default: return nullptr;
     }
 }

@@ -6,10 +6,11 @@
 
 namespace kf {
 namespace {
-template <int A, int B, bool F16>
+template <int A, int B, bool F16, bool TILES = false>
 int launch(const GroupParams &p, unsigned grid, void *stream)
 {
-    group_kernel<A, B, F16><<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<A, B, F16>::BYTES, static_cast<cudaStream_t>(stream)>>>(p);
+    group_kernel<A, B, F16, false, TILES>
+        <<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<A, B, F16>::BYTES, static_cast<cudaStream_t>(stream)>>>(p);
     return (int)cudaGetLastError();
 }
 }  // namespace

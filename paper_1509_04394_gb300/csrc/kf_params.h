@@ -21,6 +21,7 @@ constexpr int STRIP = 32 * C;  // columns per warp strip
 constexpr int WARPS_PER_BLOCK = 1;  // warps never cooperate: one warp per block
 constexpr int MIN_BLOCKS = 16;      // resident blocks per SM the register budget targets
 constexpr int MIN_BLOCKS_BOX = 12;  // ... for groups holding the 5-row box ring in registers
+constexpr int MIN_BLOCKS_BOX16 = 16; // ... for groups with FP16 inter-stage tiles (the box ring in FP16)
 constexpr int NSTAGES = 8;
 constexpr int RB = 5;           // rows per TMA stage = rows per unrolled loop block
 constexpr int STRIP_ALIGN = 16; // strips start on multiples of 16 columns (16-byte TMA x for u8)
@@ -66,7 +67,9 @@ struct GroupParams {
     int32_t *counts;          // per-frame corner counts (B == 8), pre-zeroed
     int W, H;                 // frame size
     int xs0, step, n_strips;  // strip s covers input columns [xs0 + s*step, +STRIP)
+    int out_off;              // strip s outputs columns [xs + out_off, + step): out_off a multiple of C
     int half_last;            // 1: the last strip is half wide, and one warp runs it for two frames
+    int n_lead, n_trail;      // full strips at the frame's left edge (a prefix) and right edge (a suffix)
     int T;                    // frames
     int chunk_rows, n_chunks;
     int64_t n_jobs;           // T * n_chunks * (n_strips - half_last) + ceil(T/2) * n_chunks * half_last
@@ -100,20 +103,29 @@ struct TrackVideo {
 
 // Strip geometry of a group with accumulated horizontal radius rxt: input strips start
 // on a multiple of STRIP_ALIGN columns (a legal TMA x for every map type), outputs tile
-// the frame exactly.
+// the frame exactly. A strip's outputs start out_off = rxt rounded up to whole lanes
+// after its first column, so a lane away from the frame's edges outputs all of its
+// columns or none.
 // The last strip is a half strip (STRIP/2 columns) when that width still reaches the
 // frame's last column; a warp then runs the half strips of two frames side by side
 // (lanes 0-15 and 16-31), so the mostly idle last strip costs half a warp per frame.
-struct StripGeom { int xs0, step, n_strips, half_last; };
+struct StripGeom { int xs0, step, out_off, n_strips, half_last, n_lead, n_trail; };
 inline StripGeom strip_geometry(int rxt, int W)
 {
     StripGeom g;
     g.xs0 = -((rxt + STRIP_ALIGN - 1) / STRIP_ALIGN) * STRIP_ALIGN;
-    g.step = ((STRIP - 2 * rxt) / STRIP_ALIGN) * STRIP_ALIGN;
-    const int o0 = g.xs0 + rxt;  // first output column of strip 0 (<= 0)
+    g.out_off = (rxt + C - 1) / C * C;
+    g.step = ((STRIP - g.out_off - rxt) / STRIP_ALIGN) * STRIP_ALIGN;
+    const int o0 = g.xs0 + g.out_off;  // first output column of strip 0 (<= 0)
     g.n_strips = (W - o0 + g.step - 1) / g.step;
     const int xs_last = g.xs0 + (g.n_strips - 1) * g.step;
     g.half_last = (g.n_strips > 1 && xs_last + STRIP / 2 - rxt >= W) ? 1 : 0;
+    // full strips whose input box crosses a frame edge: a prefix (xs < 0) and a suffix
+    // (xs + STRIP > W); a strip crossing both counts once, in the prefix
+    const int F = g.n_strips - g.half_last;
+    g.n_lead = (F > 0 && g.xs0 < 0) ? 1 : 0;
+    g.n_trail = 0;
+    while (g.n_lead + g.n_trail < F && g.xs0 + (F - 1 - g.n_trail) * g.step + STRIP > W) ++g.n_trail;
     return g;
 }
 
@@ -121,6 +133,7 @@ inline StripGeom strip_geometry(int rxt, int W)
 typedef int (*LaunchFn)(const GroupParams &p, unsigned grid, void *stream);
 // bytes per element of the map written by 1-based stage k (0 = frames) at a precision
 inline int map_elem_bytes(int k, bool f16) { return (k == 0 || k == 8) ? 1 : (f16 ? 2 : 4); }
+// f16: 0 = FP32 maps, 1 = 16-bit maps, 2 = 16-bit maps and FP16 inter-stage tiles on chip
 LaunchFn launcher_a1(int B, int f16);
 LaunchFn launcher_a2(int B, int f16);
 LaunchFn launcher_a3(int B, int f16);
@@ -130,6 +143,7 @@ LaunchFn launcher_a6(int B, int f16);
 LaunchFn launcher_a7(int B, int f16);
 LaunchFn launcher_a8(int B, int f16);
 int launch_chain_with_candidates(const GroupParams &p, unsigned grid, void *stream);
+int launch_chain_with_candidates_tiles(const GroupParams &p, unsigned grid, void *stream);
 // tracking kernels over one video (vids == nullptr: `one`) or a table of n videos with
 // total_frames frames in all
 int prepare_select();  // per-device launch attributes of the selection kernel (before graph capture)

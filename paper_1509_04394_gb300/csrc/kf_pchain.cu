@@ -90,8 +90,9 @@ template <int A, int B> struct Group {
     static constexpr int OUTH = TS - 2 * HALO;
     static constexpr bool TEMPORAL = H1;
     // resident blocks per SM the register budget targets (measured: the fused filter with
-    // spatial stages keeps its states and the next frame's rows in registers, so fewer)
-    static constexpr int MIN_BLOCKS = (H1 && HALO) ? 3 : 4;
+    // spatial stages keeps its states and the next frame's rows in registers; at 3 blocks
+    // of 8 warps it spilled 88-152 bytes and ran 9 % slower than at 2 without spills)
+    static constexpr int MIN_BLOCKS = (H1 && HALO) ? 2 : 4;
 };
 
 // One block of TW = 8 warps per tile of TX = 128 columns (4 per lane) x TS = 32 rows of

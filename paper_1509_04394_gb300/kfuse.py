@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkfuse.so")
 
 KF_OK, KF_EINVAL, KF_ENOMEM, KF_ECUDA, KF_ESMEM, KF_EUNSUPPORTED, KF_ESTATE, KF_ETIMEOUT = range(8)
-KF_PREC_F32, KF_PREC_F16 = 0, 1
+KF_PREC_F32, KF_PREC_F16, KF_PREC_F16_TILES = 0, 1, 2
 KF_DT_U8, KF_DT_F32, KF_DT_F16, KF_DT_U16 = 0, 1, 2, 3
 NSTAGES = 8
 STAGE_NAMES = ("convert", "gauss_h", "gauss_v", "sobel", "products", "box5", "harris", "nms")
@@ -98,6 +98,7 @@ def _lib():
             "kf_track_host": (i32, [P, P, P, P, P, P, P, P, ctypes.c_size_t, i64, i32, P]),
             "kf_batch_workspace_bytes": (i32, [P, P, i32, i32, P]),
             "kf_batch_create": (i32, [P, P, P, P, i32, P, ctypes.c_size_t, P]),
+            "kf_batch_create_ex": (i32, [P, P, P, P, i32, P, i32, P, ctypes.c_size_t, P]),
             "kf_batch_run": (i32, [P, P]),
             "kf_batch_destroy": (i32, [P]),
             "kf_tune_chunk_rows": (i32, [P, P, P, P, i32, i32, P, P, P]),
@@ -148,7 +149,7 @@ def exported_symbols() -> list[str]:
             "kf_set_precision", "kf_set_chunk_rows", "kf_set_wait_polls", "kf_add_stage", "kf_add_harris_chain",
             "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
             "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static",
-            "kf_track_workspace_bytes", "kf_track", "kf_batch_workspace_bytes", "kf_batch_create",
+            "kf_track_workspace_bytes", "kf_track", "kf_batch_workspace_bytes", "kf_batch_create", "kf_batch_create_ex",
             "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows", "kf_plan_measured", "kf_dag_create", "kf_dag_destroy",
             "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups",
             "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_forward", "kf_costmodel_grad", "kf_costmodel_get",
@@ -351,8 +352,11 @@ def kf_batch_workspace_bytes(ctx, frames_list, W_list, K: int = 0) -> int:
     return b.value
 
 
-def kf_batch_create(ctx, frames_list, W_list, masks, counts_list, workspace, tracks=None):
-    """tracks: None or a list of (K, n_points, idx, u, v, status) tensors per video."""
+def kf_batch_create(ctx, frames_list, W_list, masks, counts_list, workspace, tracks=None, chunk_rows=None,
+                    warps_per_sm: int = 0):
+    """tracks: None or a list of (K, n_points, idx, u, v, status) tensors per video;
+    chunk_rows: None (the context's) or one tile height per video; warps_per_sm: 0 = as
+    many resident warps as fit (kf_batch_create_ex)."""
     n = len(frames_list)
     v = _videos(frames_list, W_list)
     o = (kf_corners * n)(*[kf_corners(m.data_ptr(), int(m.shape[2]), c.data_ptr()) for m, c in zip(masks, counts_list)])
@@ -362,8 +366,9 @@ def kf_batch_create(ctx, frames_list, W_list, masks, counts_list, workspace, tra
                                for (K, a, b, c, d, e) in tracks])
     h = ctypes.c_void_p()
     ws_bytes = workspace.numel() * workspace.element_size()
-    _check("kf_batch_create", _lib().kf_batch_create(ctx, v, o, tr, n, workspace.data_ptr(), ws_bytes, ctypes.byref(h)),
-           ctx)
+    rows = None if chunk_rows is None else (ctypes.c_int * n)(*[int(r) for r in chunk_rows])
+    _check("kf_batch_create_ex", _lib().kf_batch_create_ex(ctx, v, o, tr, n, rows, int(warps_per_sm), workspace.data_ptr(),
+                                                           ws_bytes, ctypes.byref(h)), ctx)
     return h
 
 

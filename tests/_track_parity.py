@@ -11,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 
 from oracle import chain as oc
-from tests._parity import TOL_F32
+from tests._parity import TOL_F32, exempt_pixels
 
 
 def window_conditioning(maps_cur, g_prev, p, W, H):
@@ -26,7 +26,11 @@ def window_conditioning(maps_cur, g_prev, p, W, H):
     return abs(det) / (tr * tr) if tr > 0 else 0.0
 
 
-def check_frame(fr, t, W, out, Kp):
+def check_frame(fr, t, W, out, Kp, tol=TOL_F32, exempt_corners=False):
+    """One frame pair. With exempt_corners, a point may also differ where the corner
+    decision itself is exempt under the mask rule (its response within tol * max|R| of
+    the threshold or of a neighbour's): a lower precision may flip such a decision at any
+    strength, not only at the K-th response."""
     H = fr.shape[1]
     prev, cur = fr[t - 1][:, :W].copy(), fr[t][:, :W].copy()
     idx_o, u_o, v_o, st_o = oc.track_pair(prev, cur, K=Kp)
@@ -36,11 +40,12 @@ def check_frame(fr, t, W, out, Kp):
     got = out["idx"][t, :n]
     r = maps["r"].ravel()
     if n:
-        tau = TOL_F32 * np.max(np.abs(maps["r"]))
+        tau = tol * np.max(np.abs(maps["r"]))
         kth = r[idx_o[-1]]
         diff = set(got.tolist()) ^ set(idx_o.tolist())
-        for p in diff:  # disagreements only at the selection boundary
-            assert abs(r[p] - kth) <= tau, (t, p, r[p], kth)
+        ex = exempt_pixels(maps["r"], tol).ravel() if exempt_corners else None
+        for p in diff:  # disagreements only at the selection boundary (or exempt decisions)
+            assert abs(r[p] - kth) <= tau or (ex is not None and ex[p]), (t, p, r[p], kth)
         # order: strongest first (by the oracle's response, up to the FP32 tolerance)
         assert np.all(np.diff(r[got]) <= tau)
     g_prev = oc.chain_frame(prev)[0]["g"]
@@ -55,8 +60,8 @@ def check_frame(fr, t, W, out, Kp):
             continue  # at or near the singularity threshold: either answer is acceptable
         assert out["st"][t, i] == st_o[j], (t, p)
         if st_o[j] == 0:
-            tol = 2e-3 * max(1.0, 1e-4 / cond)  # FP32 window sums, amplified by conditioning
-            assert abs(out["u"][t, i] - u_o[j]) <= tol * max(1.0, abs(u_o[j])), (t, p, out["u"][t, i], u_o[j])
-            assert abs(out["v"][t, i] - v_o[j]) <= tol * max(1.0, abs(v_o[j])), (t, p, out["v"][t, i], v_o[j])
+            vtol = 2e-3 * max(1.0, 1e-4 / cond)  # FP32 window sums, amplified by conditioning
+            assert abs(out["u"][t, i] - u_o[j]) <= vtol * max(1.0, abs(u_o[j])), (t, p, out["u"][t, i], u_o[j])
+            assert abs(out["v"][t, i] - v_o[j]) <= vtol * max(1.0, abs(v_o[j])), (t, p, out["v"][t, i], v_o[j])
             checked += 1
     return checked

@@ -166,3 +166,47 @@ def test_batch_of_the_48_video_shapes_matches_the_oracle(dev):
         assert tr_np["n"][0] == 0
         checked += _check_against_oracle(fr, W, m.cpu().numpy(), c.cpu().numpy(), tr_np, (1, 32, T // 2, T - 1))
     assert checked >= 4 * 4 * 100
+
+
+def test_batch_with_per_video_tiles_and_fewer_warps_gives_the_same_bits(dev):
+    """kf_batch_create_ex: each video with its own tile height, the launch capped at 3
+    resident warps per SM, the queue in longest-job-first order: every result equals the
+    video's own kf_track (tile heights never change the bits)."""
+    ctx = K.Context(0)
+    vids = _videos(dev)
+    KP = 16
+    masks = [torch.zeros_like(f) for f, _ in vids]
+    counts = [torch.zeros((f.shape[0],), dtype=torch.int32, device=dev) for f, _ in vids]
+    tracks = [(KP, torch.zeros((f.shape[0],), dtype=torch.int32, device=dev),
+               torch.full((f.shape[0], KP), -1, dtype=torch.int32, device=dev), torch.zeros((f.shape[0], KP), device=dev),
+               torch.zeros((f.shape[0], KP), device=dev), torch.zeros((f.shape[0], KP), dtype=torch.int32, device=dev))
+              for f, _ in vids]
+    ws = torch.empty(K.kf_batch_workspace_bytes(ctx.h, [f for f, _ in vids], [w for _, w in vids], KP),
+                     dtype=torch.uint8, device=dev)
+    rows = [37, 100, 5, 200, 1, 3]
+    b = K.kf_batch_create(ctx.h, [f for f, _ in vids], [w for _, w in vids], masks, counts, ws, tracks,
+                          chunk_rows=rows, warps_per_sm=3)
+    try:
+        K.kf_batch_run(b)
+        torch.cuda.synchronize()
+        assert K.kf_device_error(ctx.h) == 0
+    finally:
+        K.kf_batch_destroy(b)
+    for i, (f, W) in enumerate(vids):
+        T = f.shape[0]
+        m_r, c_r = torch.zeros_like(f), torch.zeros(T, dtype=torch.int32, device=dev)
+        n_r = torch.zeros(T, dtype=torch.int32, device=dev)
+        i_r = torch.full((T, KP), -1, dtype=torch.int32, device=dev)
+        u_r, v_r = torch.zeros((T, KP), device=dev), torch.zeros((T, KP), device=dev)
+        s_r = torch.zeros((T, KP), dtype=torch.int32, device=dev)
+        wst = torch.empty(K.kf_track_workspace_bytes(ctx.h, W, f.shape[1], T), dtype=torch.uint8, device=dev)
+        K.kf_track(ctx.h, f, W, m_r, c_r, KP, n_r, i_r, u_r, v_r, s_r, wst)
+        assert torch.equal(masks[i][:, :, :W], m_r[:, :, :W]) and torch.equal(counts[i], c_r), i
+        _, n_b, i_b, u_b, v_b, s_b = tracks[i]
+        assert torch.equal(n_b, n_r), i
+        for t in range(1, T):
+            n = int(n_r[t])
+            assert torch.equal(i_b[t, :n], i_r[t, :n]) and torch.equal(u_b[t, :n], u_r[t, :n]), (i, t)
+    with pytest.raises(K.KfuseError):  # a tile height below 1
+        K.kf_batch_create(ctx.h, [f for f, _ in vids], [w for _, w in vids], masks, counts, ws, tracks,
+                          chunk_rows=[0] * len(vids))

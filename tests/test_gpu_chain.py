@@ -252,3 +252,24 @@ def test_measured_planner_times_every_partition(dev):
     with pytest.raises(K.KfuseError) as e:
         K.kf_plan_measured(ctx.h, f, W, mask, counts, small, candidates=[0, 127], reps=1)
     assert e.value.status == K.KF_ENOMEM
+
+
+@pytest.mark.parametrize("cuts", [0, 0b0000100, 0b0001000, 0b0010000, 127])
+def test_fp16_tiles_match_the_oracle(dev, cuts):
+    """KF_PREC_F16_TILES: 16-bit maps between groups, and FP16 row-pair sums of the box on
+    chip in the groups that form the products and the response (here full fusion and
+    the groups [4..8], [5..8]); masks and counts within the FP16 exemption rule."""
+    T, H, W = 3, 150, 237
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=29, n_blobs=10, n_patches=6), pitch=pitch16(W))
+    fd = torch.from_numpy(fr).to(dev)
+    ctx = K.Context(0, precision=K.KF_PREC_F16_TILES)
+    ws_b = K.kf_workspace_bytes(ctx.h, cuts, W, H, T)
+    ws = torch.empty(max(ws_b, 1), dtype=torch.uint8, device=dev)
+    mask = torch.zeros((T, H, pitch16(W)), dtype=torch.uint8, device=dev)
+    counts = torch.zeros(T, dtype=torch.int32, device=dev)
+    K.kf_run(ctx.h, cuts, fd, W, mask, counts, ws if ws_b else None)
+    assert K.kf_device_error(ctx.h) == 0
+    for t in range(T):
+        maps, m_ref, c_ref = oc.chain_frame(fr[t][:, :W].copy(), want_maps=True)
+        check_mask(mask[t, :, :W].cpu().numpy(), int(counts[t]), m_ref, c_ref, maps["r"], TOL_F16)
+    assert int(counts.sum()) > 0

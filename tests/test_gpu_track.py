@@ -17,7 +17,7 @@ from oracle import chain as oc  # noqa: E402
 from paper_1509_04394_gb300 import build as kbuild  # noqa: E402
 from paper_1509_04394_gb300 import kfuse as K  # noqa: E402
 from synth import video as sv  # noqa: E402
-from tests._parity import TOL_F32, check_mask  # noqa: E402
+from tests._parity import TOL_F16, TOL_F32, check_mask  # noqa: E402
 from tests._track_parity import check_frame  # noqa: E402
 
 
@@ -29,9 +29,9 @@ def dev():
     return torch.device("cuda:0")
 
 
-def run_track(dev, fr, W, Kp=256):
+def run_track(dev, fr, W, Kp=256, precision=None):
     T, H, P = fr.shape
-    ctx = K.Context(0)
+    ctx = K.Context(0) if precision is None else K.Context(0, precision=precision)
     frames = torch.from_numpy(fr).to(dev)
     mask = torch.zeros_like(frames)
     counts = torch.zeros(T, dtype=torch.int32, device=dev)
@@ -83,6 +83,31 @@ def test_full_size_tracking_in_the_benchmark_configuration(dev):
         assert out["n"][t] == min(256, int(out["counts"][t]))
         checked += check_frame(fr, t, W, out, 256)
     assert checked >= 5 * 200
+
+
+@pytest.mark.parametrize("shape,sample", [((5, 120, 600), (1, 2, 3, 4)), ((1000, 800, 600), (1, 2, 499, 998, 999))])
+def test_fp16_form_of_the_tracking_step(dev, shape, sample):
+    """The FP16-tile form (KF_PREC_F16_TILES): the fused chain keeps the box's row-pair
+    sums in FP16 on chip; masks and counts within the FP16 exemption rule (2e-3 of the
+    frame's largest response), selected points up to near-ties or exempt corner decisions
+    within the same tolerance, velocities by the FP32 rule (LK reads the frames, not the
+    response). The full size is the
+    benchmark's volume, checked on sampled frame pairs."""
+    T, H, W = shape
+    if T == 1000:
+        spec = sv.HSDV_800x600x1000
+        fr, _ = sv.generate(spec, pitch=sv.pitch_for(W))
+    else:
+        fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=43, n_blobs=12, n_patches=8), pitch=sv.pitch_for(W))
+    out = run_track(dev, fr, W, 256, precision=K.KF_PREC_F16_TILES)
+    assert out["n"][0] == 0
+    checked = 0
+    for t in sample:
+        maps, m_ref, c_ref = oc.chain_frame(fr[t][:, :W].copy())
+        check_mask(out["mask"][t, :, :W], int(out["counts"][t]), m_ref, c_ref, maps["r"], TOL_F16)
+        assert out["n"][t] == min(256, int(out["counts"][t]))
+        checked += check_frame(fr, t, W, out, 256, tol=TOL_F16, exempt_corners=True)
+    assert checked >= len(sample) * 150
 
 
 def test_constant_video_has_no_points_and_a_single_frame_has_no_tracks(dev):

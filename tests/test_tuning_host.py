@@ -81,3 +81,63 @@ def test_unreadable_file_starts_empty(tmp_path):
     assert json.loads(path.read_text()) == {"k": {"rows": 1}}
     path.write_text("[1, 2]")  # valid JSON, not an object
     assert tuning.TuneCache(str(path)).entries == {}
+
+
+def test_batch_rows_measures_each_shape_once(ctx, tmp_path):
+    """A batch's tile heights: one measurement per distinct frame shape (on a prefix of its
+    first video), shared by every video of that shape and reused from the cache later."""
+    path = str(tmp_path / "tune.json")
+    calls = []
+
+    def tune(c, frames, W, mask, counts, cands, reps, stream):
+        calls.append((int(W), frames.shape[1], frames.shape[0]))
+        return {60: 160, 90: 267}[int(W)], 1.0
+    vids = [(np.zeros((100, 48, 64), np.uint8), 60), (np.zeros((7, 40, 96), np.uint8), 90),
+            (np.zeros((30, 48, 64), np.uint8), 60)]
+    rows = tuning.batch_rows(ctx, vids, tuning.TuneCache(path), "GB300", K.KF_PREC_F32, sample_frames=64, tune=tune)
+    assert rows == [160, 267, 160]
+    assert calls == [(60, 48, 64), (90, 40, 7)]
+    rows2 = tuning.batch_rows(ctx, vids, tuning.TuneCache(path), "GB300", K.KF_PREC_F32, tune=_no_tune)
+    assert rows2 == rows and len(calls) == 2
+
+
+def test_batch_warps_keeps_the_fastest_and_caches_it(tmp_path):
+    """The persistent launch's warps per SM: every candidate timed once, the fastest kept
+    (ties to the smaller setting), stored under the batch's shape mix and tile heights."""
+    path = str(tmp_path / "tune.json")
+    vids = [(np.zeros((10, 48, 64), np.uint8), 60), (np.zeros((10, 48, 64), np.uint8), 60),
+            (np.zeros((4, 40, 96), np.uint8), 90)]
+    seen = []
+
+    def time_batch(w):
+        seen.append(w)
+        return {0: 5.0, 10: 4.0, 8: 4.0}[w]
+    best, cached = tuning.batch_warps(None, vids, None, None, None, None, [200, 200, 100], tuning.TuneCache(path), "GB300",
+                                      candidates=(0, 10, 8), time_batch=time_batch)
+    assert (best, cached) == (8, False) and seen == [0, 10, 8]
+    best, cached = tuning.batch_warps(None, vids, None, None, None, None, [200, 200, 100], tuning.TuneCache(path), "GB300",
+                                      candidates=(0, 10, 8), time_batch=lambda w: pytest.fail("measured again"))
+    assert (best, cached) == (8, True)
+    # another tile-height choice is another entry
+    best, cached = tuning.batch_warps(None, vids, None, None, None, None, [100, 100, 100], tuning.TuneCache(path),
+                                      "GB300", candidates=(0, 10, 8), time_batch=lambda w: {0: 1.0, 10: 2.0, 8: 3.0}[w])
+    assert (best, cached) == (0, False)
+
+
+def test_batch_launch_picks_the_fastest_assignment_and_caches_it(tmp_path):
+    """Tile heights and warps per SM measured on the batch itself: every pair of a
+    candidate assignment and a warps setting timed once, the fastest kept and stored."""
+    path = str(tmp_path / "tune.json")
+    vids = [(np.zeros((10, 48, 64), np.uint8), 60), (np.zeros((4, 40, 96), np.uint8), 90)]
+    choices = [[100, 160], [200, 200], [267, 267]]
+    seen = []
+
+    def time_batch(rows, w):
+        seen.append((tuple(rows), w))
+        return {(200, 200): 3.0, (100, 160): 4.0, (267, 267): 3.5}[tuple(rows)] + (0.5 if w else 0.0)
+    rows, w, cached = tuning.batch_launch(None, vids, None, None, None, None, choices, tuning.TuneCache(path), "GB300",
+                                          warp_candidates=(0, 10), time_batch=time_batch)
+    assert (rows, w, cached) == ([200, 200], 0, False) and len(seen) == 6
+    rows, w, cached = tuning.batch_launch(None, vids, None, None, None, None, choices, tuning.TuneCache(path), "GB300",
+                                          warp_candidates=(0, 10), time_batch=lambda r, w: pytest.fail("again"))
+    assert (rows, w, cached) == ([200, 200], 0, True)
