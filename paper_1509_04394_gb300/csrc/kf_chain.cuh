@@ -979,15 +979,24 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
             r_ring[PH * 32 + lane] = make_float4(centre[0], centre[1], centre[2], centre[3]);
             if (o >= y0) cand_bits |= (bits & out_mask) << (4 * PH);  // warp-uniform test
         }
-        if (o >= y0 && out_mask) {  // o < y1 holds: t < y1 + RYT
+        if constexpr (B == 8 && !EDGE) {
+            // interior strip: out_mask is 0 (halo lanes) or every column, so the row's mask
+            // word is one predicated store per lane, with no divergent block around it
+            const bool row_out = o >= y0;  // warp-uniform; o < y1 holds: t < y1 + RYT
+            const unsigned kept = row_out ? bits & out_mask : 0u;
+            count += __popc(kept);
+            uint32_t *mp = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(out_plane[0]) + out_frame +
+                                                        (int64_t)o * out_pitch + x0);
+            // bit k of `kept` to byte k: kept * (1 + 2^7 + 2^14 + 2^21) puts bit k of the copy
+            // shifted by 7j at 8j when k == j, and elsewhere at k + 7j, never a multiple of 8
+            // for k != j (|k - j| < 7)
+            if (row_out && out_mask) *mp = (kept * 0x00204081u) & 0x01010101u;
+        } else if (o >= y0 && out_mask) {  // o < y1 holds: t < y1 + RYT
             const int64_t ooff = out_frame + (int64_t)o * out_pitch + x0;
             if constexpr (B == 8) {
                 const unsigned kept = bits & out_mask;
                 uint8_t *mp = static_cast<uint8_t *>(out_plane[0]) + ooff;
-                if (!EDGE || out_mask == (1u << C) - 1) {
-                    // bit k of `kept` to byte k: kept * (1 + 2^7 + 2^14 + 2^21) puts bit k of the
-                    // copy shifted by 7j at 8j when k == j, and elsewhere at k + 7j, never a
-                    // multiple of 8 for k != j (|k - j| < 7)
+                if (out_mask == (1u << C) - 1) {
                     *reinterpret_cast<uint32_t *>(mp) = (kept * 0x00204081u) & 0x01010101u;
                 } else {
 #pragma unroll
@@ -1003,7 +1012,6 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
                 else if constexpr (B == 5) res = &pr;
                 else if constexpr (B == 6) res = &sm;
                 else res = &r7;
-#pragma unroll
                 // an interior lane that outputs anything outputs all of its columns
                 const unsigned st_mask = EDGE ? out_mask : (1u << C) - 1;
 #pragma unroll
@@ -1019,6 +1027,7 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
     using P2 = std::integral_constant<int, 2>;
     using P3 = std::integral_constant<int, 3>;
     using P4 = std::integral_constant<int, 4>;
+
 #pragma unroll 1
     for (int k = 0, t = t_begin; t < t_end; ++k, t += RB) {
         if (k < n_stages) {
