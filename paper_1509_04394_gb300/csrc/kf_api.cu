@@ -942,13 +942,18 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
         } else {
             d2h(host_out->mask + t0 * mstride, out->mask + t0 * mstride, (size_t)(n * mstride));
         }
-        d2h(host_out->counts + t0, out->counts + t0, sizeof(int32_t) * (size_t)n);
-        d2h(host_tracks->n_points + t0, tracks->n_points + t0, sizeof(int32_t) * (size_t)n);
-        d2h(host_tracks->idx + t0 * K, tracks->idx + t0 * K, sizeof(int32_t) * (size_t)(n * K));
-        d2h(host_tracks->u + t0 * K, tracks->u + t0 * K, sizeof(float) * (size_t)(n * K));
-        d2h(host_tracks->v + t0 * K, tracks->v + t0 * K, sizeof(float) * (size_t)(n * K));
-        d2h(host_tracks->status + t0 * K, tracks->status + t0 * K, sizeof(int32_t) * (size_t)(n * K));
     }
+    // the counts and tracks (a few bytes a frame) once, after the last chunk: one copy
+    // each instead of one per chunk (every copy costs the copy engine a fixed setup)
+    auto d2h_all = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s_out);
+    };
+    d2h_all(host_out->counts, out->counts, sizeof(int32_t) * (size_t)T);
+    d2h_all(host_tracks->n_points, tracks->n_points, sizeof(int32_t) * (size_t)T);
+    d2h_all(host_tracks->idx, tracks->idx, sizeof(int32_t) * (size_t)(T * K));
+    d2h_all(host_tracks->u, tracks->u, sizeof(float) * (size_t)(T * K));
+    d2h_all(host_tracks->v, tracks->v, sizeof(float) * (size_t)(T * K));
+    d2h_all(host_tracks->status, tracks->status, sizeof(int32_t) * (size_t)(T * K));
     // the caller's stream ends after the last copy out
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_edge, ctx->s_out);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_edge, 0);

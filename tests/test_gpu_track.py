@@ -110,6 +110,25 @@ def test_fp16_form_of_the_tracking_step(dev, shape, sample):
     assert checked >= len(sample) * 150
 
 
+@pytest.mark.parametrize("H,W", [(1, 1), (2, 3), (5, 7), (12, 12), (9, 30), (30, 9), (13, 13)])
+def test_tracking_on_frames_smaller_than_the_lk_window(dev, H, W):
+    """Frames no larger than LK's 13 x 13 input patch: every point takes the clamped path
+    (half-warp 9 x 9 grids with every frame access clamped); masks, counts, points and
+    velocities against the oracle."""
+    rng = np.random.default_rng(H * 100 + W)
+    T, Kp = 4, 16
+    fr = np.zeros((T, H, sv.pitch_for(W)), dtype=np.uint8)
+    base = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    for t in range(T):  # a slowly drifting texture, so consecutive frames are related
+        fr[t, :, :W] = np.roll(base, t % 2, axis=1) // 2 + rng.integers(0, 64, (H, W), dtype=np.uint8)
+    out = run_track(dev, fr, W, Kp)
+    assert out["n"][0] == 0
+    for t in range(1, T):
+        maps, m_ref, c_ref = oc.chain_frame(fr[t][:, :W].copy())
+        check_mask(out["mask"][t, :, :W], int(out["counts"][t]), m_ref, c_ref, maps["r"], TOL_F32)
+        check_frame(fr, t, W, out, Kp)
+
+
 def test_constant_video_has_no_points_and_a_single_frame_has_no_tracks(dev):
     fr = np.full((3, 40, 64), 90, dtype=np.uint8)
     out = run_track(dev, fr, 64)
