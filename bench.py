@@ -42,6 +42,7 @@ OPS_BY_STAGE = {"S1 convert": 1, "S2 Gaussian-H (2 adds, 2 FMAs)": 4, "S3 Gaussi
                 "S4 Sobel (Dx 1, Sx 2, Ix 2, Iy 1)": 6, "S5 products": 3, "S6 box 5x5 (3 x (4 + 4) adds)": 24,
                 "S7 Harris (det 2, trace 1, response 2)": 5, "S8 threshold + 3x3 max (2 + 2 max3, 2 compares)": 6}
 OPS_PER_PX = sum(OPS_BY_STAGE.values())
+TUNE_ROWS = [100, 160, 200, 267, 320, 400, 800]  # chunk heights the autotuner tries on the workload
 
 
 def kernel_counters():
@@ -291,6 +292,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     def chain():  # the dominant kernel alone: the fused chain as the planner partitions it
         K.kf_run(ctx.h, cuts, frames, W, mask, counts, None, stream)
 
+    # the executor's tile height for this workload from its autotuner (CUDA-event timing of
+    # the fused chain inside the library, on a context of its own), applied to the step
+    tctx = K.Context(local_rank)
+    best_rows, best_ms = K.kf_tune_chunk_rows(tctx.h, frames, W, torch.zeros_like(frames), torch.zeros_like(counts),
+                                              TUNE_ROWS, reps=3, stream=stream)
+    K.kf_set_chunk_rows(ctx.h, best_rows)
+
     # clocks: sample across a ~1.5 s soak and the timed region
     try:
         gid = str(torch.cuda.get_device_properties(dev).uuid)
@@ -403,10 +411,6 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     batch_same = bool(torch.equal(bmask, mask) and torch.equal(bcounts, counts) and torch.equal(btr[1], n_pts))
     K.kf_batch_destroy(batch)
     del bws
-    # autotuned chunk height of the executor (CUDA-event timing inside the library)
-    tctx = K.Context(local_rank)
-    best_rows, best_ms = K.kf_tune_chunk_rows(tctx.h, frames, W, torch.zeros_like(frames), torch.zeros_like(counts),
-                                              [100, 200, 400, 800], reps=3, stream=stream)
 
     # unfused sequence (one kernel per stage, volume-wide maps through HBM)
     unf_cuts = (1 << 7) - 1
@@ -435,7 +439,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames": T, "rows": H, "cols": W, "step": "fused 8-stage chain + "
                    f"top-{KP} corner selection + LK tracking per frame pair", "partition_cuts": cuts,
-                   "groups": n_groups, "chunk_rows": 200, "cols_per_lane": 4,
+                   "groups": n_groups, "chunk_rows": best_rows, "chunk_rows_from": "autotuner", "cols_per_lane": 4,
                    "l2": "inputs larger than L2 (480 MB frames, 480 MB mask), no flush",
                    "parallelism": (f"frame shards x{world} of one {world * owned}-frame video, merged on the host"
                                    if world > 1 else "single GPU")},
@@ -463,7 +467,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "batched_form": {"value": world * px / (ms_batch / 1000) / 1e6, "ms_per_step": ms_batch,
                          "what": "the same step as one video of a persistent-kernel batch replayed from a CUDA graph",
                          "identical_results": batch_same},
-        "autotuned_chunk_rows": {"best": best_rows, "chain_ms": best_ms, "candidates": [100, 200, 400, 800]},
+        "autotuned_chunk_rows": {"best": best_rows, "chain_ms": best_ms, "candidates": TUNE_ROWS},
         "unfused": {"value": world * px / (ms_unf / 1000) / 1e6, "ms_per_step": ms_unf, "kernels": 8,
                     "hbm_frac": unf_bytes / (ms_unf / 1000) / 1e9 / hbm_peak,
                     "bit_identical_to_fused": bool(same and chain_same),

@@ -1011,7 +1011,7 @@ BatchLayout batch_layout(const kf_video *videos, int n, bool track)
     size_t o = 0;
     auto take = [&](size_t bytes) { const size_t at = o; o = (size_t)round_up((int64_t)(o + bytes), 256); return at; };
     L.params = take(sizeof(kf::GroupParams) * (size_t)n);
-    L.items = take(sizeof(int64_t) * (size_t)(n + 1));
+    L.items = take(sizeof(int64_t) * (size_t)(3 * n + 1));  // queue segments, kind-major
     L.queue = take(sizeof(unsigned long long));
     if (track) {
         int64_t frames = 0, cand = 0;
@@ -1095,7 +1095,7 @@ kf_status kf_batch_create_ex(kf_ctx *ctx, const kf_video *videos, const kf_corne
     auto *d_cand = reinterpret_cast<unsigned long long *>(base + L.cand);
 
     std::vector<kf::GroupParams> hp((size_t)n);
-    std::vector<int64_t> items((size_t)n + 1, 0);
+    std::vector<int64_t> items((size_t)(3 * n) + 1, 0);
     std::vector<kf::TrackVideo> ht(track ? (size_t)n : 0);
     int64_t frame_begin = 0, cand_off = 0;
     for (int i = 0; i < n; ++i) {
@@ -1147,10 +1147,19 @@ kf_status kf_batch_create_ex(kf_ctx *ctx, const kf_video *videos, const kf_corne
         return pa.n_jobs > pb.n_jobs;
     });
     std::vector<kf::GroupParams> hq((size_t)n);
-    for (int k = 0; k < n; ++k) {
-        hq[(size_t)k] = hp[(size_t)order[(size_t)k]];
-        items[(size_t)k + 1] = items[(size_t)k] + hq[(size_t)k].n_jobs;
-    }
+    for (int k = 0; k < n; ++k) hq[(size_t)k] = hp[(size_t)order[(size_t)k]];
+    // queue segments, kind-major (the batch kernel's order): interior-strip jobs of every
+    // video, then edge-strip jobs, then half-strip jobs, each in the longest-first order
+    for (int kind = 0, s = 0; kind < 3; ++kind)
+        for (int k = 0; k < n; ++k, ++s) {
+            const kf::GroupParams &q = hq[(size_t)k];
+            const int F = q.n_strips - q.half_last;
+            const int64_t per = (int64_t)q.T * q.n_chunks;
+            const int64_t cnt = kind == 0 ? per * (F - q.n_lead - q.n_trail)
+                              : kind == 1 ? per * (q.n_lead + q.n_trail)
+                                          : q.n_jobs - per * F;
+            items[(size_t)s + 1] = items[(size_t)s] + cnt;
+        }
     e = cudaMemcpy(d_params, hq.data(), sizeof(kf::GroupParams) * (size_t)n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_items, items.data(), sizeof(int64_t) * items.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && track)

@@ -1115,28 +1115,40 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, TILES ? MIN_BLOCKS_BOX16
 }
 
 // Persistent batch over many videos (the fully fused chain): each resident warp pops
-// jobs from one global counter until the queue is empty. Job j of the batch belongs to
-// the video v with item_begin[v] <= j < item_begin[v + 1] (binary search) and is that
-// video's job j - item_begin[v], run with its own descriptor.
+// jobs from one global counter until the queue is empty; a job's queue segment (binary
+// search over item_begin) names its video and the kind of its strip, and the job runs
+// with that video's descriptor.
 template <bool CAND>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, MIN_BLOCKS_BOX) batch_kernel(const GroupParams *videos, const int64_t *item_begin,
                                                                                       int n_videos, unsigned long long *queue)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     init_ring<SmemPlan<1, 8, false, CAND>::NST>(smem);
-    const int64_t n_items = item_begin[n_videos];
+    // The queue is kind-major: every video's interior-strip jobs, then every video's
+    // edge-strip jobs, then every video's half-strip jobs (segment s = kind * n + video,
+    // item_begin[s] its first item), so the launch runs one instance of the row loop at a
+    // time, as a single video's launch does.
+    const int n_seg = 3 * n_videos;
+    const int64_t n_items = item_begin[n_seg];
     unsigned kbase = 0;
     for (;;) {
         unsigned long long item = 0;
         if ((threadIdx.x & 31) == 0) item = atomicAdd(queue, 1ull);
         item = __shfl_sync(FULL, item, 0);
         if ((int64_t)item >= n_items) break;
-        int lo = 0, hi = n_videos - 1;  // last v with item_begin[v] <= item
+        int lo = 0, hi = n_seg - 1;  // last s with item_begin[s] <= item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (item_begin[mid] <= (int64_t)item) lo = mid; else hi = mid - 1;
         }
-        if (!run_any_job<1, 8, false, CAND>(videos[lo], (int64_t)item - item_begin[lo], smem, kbase, true)) break;
+        const int kind = lo / n_videos, v = lo - kind * n_videos;
+        const GroupParams &p = videos[v];
+        int64_t job = (int64_t)item - item_begin[lo];  // the video's job number (decode_job's order)
+        if (kind > 0) {
+            const int F = p.n_strips - p.half_last;
+            job += (int64_t)p.T * p.n_chunks * (kind == 1 ? F - p.n_lead - p.n_trail : F);
+        }
+        if (!run_any_job<1, 8, false, CAND>(p, job, smem, kbase, true)) break;
     }
 }
 
