@@ -33,7 +33,7 @@ from synth import video as sv  # noqa: E402
 
 METRIC = "fused-chain Mpixel/s & HBM roofline fraction vs unfused, 800×600×1000 u8"
 UNIT = "Mpixel/s"
-E2E_CHUNK = 100  # frames per chunk of the pipelined host-to-host call
+E2E_CHUNK = 66  # frames per chunk of the pipelined host-to-host call
 SPEC = sv.HSDV_800x600x1000
 WORKLOAD = "Harris 8-stage chain, 1000 frames x 800 rows x 600 cols u8, 64 blobs + 32 patches, seed 3"
 # Algorithmic FP32 operations per output pixel of the chain, from the stage definitions

@@ -159,6 +159,10 @@ kf_status kf_device_error(kf_ctx *ctx, int *code);
 kf_status kf_set_precision(kf_ctx *ctx, int precision);
 /* Rows per warp job of the executor (default 200, >= 1). */
 kf_status kf_set_chunk_rows(kf_ctx *ctx, int rows);
+/* Rows per warp job of the chain launches kf_track_host makes, one per chunk of frames
+ * (>= 1), or 0 (default): the kf_set_chunk_rows height. Results do not depend on it.
+ * KF_EINVAL if rows < 0. */
+kf_status kf_set_host_chunk_rows(kf_ctx *ctx, int rows);
 /* Bound of the device-side waits for staged input (the chain's TMA row blocks and the
  * spatio-temporal box's frame copies): the number of mbarrier try_wait rounds a block
  * gives one wait before it records KF_DEVERR_TIMEOUT in the context's error word,
@@ -616,12 +620,30 @@ kf_status kf_st_run(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64_
  * previous kf_kernel_times (or since timing was switched on), then clears the record.
  * Kinds: KF_KT_GROUP a fused group of the chain (kf_run, kf_run_group), KF_KT_CHAIN_CORNERS
  * the fully fused chain that also lists each frame's corners (kf_track), KF_KT_SELECT the
- * corner selection, KF_KT_LK the Lucas-Kanade step. Events are created on first use and
- * reused; KF_ECUDA if an event call fails. Not for use inside stream capture. */
-typedef enum { KF_KT_GROUP = 0, KF_KT_CHAIN_CORNERS = 1, KF_KT_SELECT = 2, KF_KT_LK = 3, KF_KT_COUNT = 4 } kf_kernel_kind;
+ * corner selection, KF_KT_LK the Lucas-Kanade step; kf_track_host also records its mask
+ * packing kernels (KF_KT_PACK) and its copies (KF_KT_COPY_IN host to device,
+ * KF_KT_COPY_OUT device to host), each on the stream that runs it. Events are created on
+ * first use and reused; KF_ECUDA if an event call fails. Not for use inside stream
+ * capture. */
+typedef enum {
+    KF_KT_GROUP = 0,
+    KF_KT_CHAIN_CORNERS = 1,
+    KF_KT_SELECT = 2,
+    KF_KT_LK = 3,
+    KF_KT_PACK = 4,
+    KF_KT_COPY_IN = 5,
+    KF_KT_COPY_OUT = 6,
+    KF_KT_COUNT = 7
+} kf_kernel_kind;
 kf_status kf_set_kernel_timing(kf_ctx *ctx, int on);
 /* launches[KF_KT_COUNT], ms[KF_KT_COUNT]: host arrays */
 kf_status kf_kernel_times(kf_ctx *ctx, int64_t *launches, double *ms);
+/* The same record as a timeline: *n = the number of recorded launches and copies; the
+ * first min(*n, cap) of them, in the order they were enqueued, go to kinds[i] (a
+ * kf_kernel_kind), start_ms[i] and end_ms[i] (milliseconds from the earliest recorded
+ * start, so that overlap between streams shows). Waits for the events and clears the
+ * record, as kf_kernel_times does. KF_EINVAL if an array is null while cap > 0. */
+kf_status kf_kernel_timeline(kf_ctx *ctx, int64_t cap, int64_t *n, int *kinds, double *start_ms, double *end_ms);
 
 #ifdef __cplusplus
 }

@@ -295,11 +295,11 @@ struct TimedLaunch {
 
 kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &out, int64_t W, int64_t H, int64_t T,
                        int32_t *counts, cudaStream_t s, unsigned long long *cand = nullptr, int *cand_count = nullptr,
-                       int64_t cand_cap = 0)
+                       int64_t cand_cap = 0, int chunk_rows = 0)
 {
     if (T == 0) return KF_OK;
     kf::GroupParams p;
-    kf_status st = fill_params(c, A, B, in, out, W, H, T, counts, cand, cand_count, cand_cap, p);
+    kf_status st = fill_params(c, A, B, in, out, W, H, T, counts, cand, cand_count, cand_cap, p, chunk_rows);
     if (st != KF_OK) return st;
     // 0: FP32 maps; 1: 16-bit maps; 2: 16-bit maps and FP16 inter-stage tiles on chip
     const int f16 = c->precision == KF_PREC_F32 ? 0 : c->precision == KF_PREC_F16_TILES ? 2 : 1;
@@ -453,6 +453,13 @@ kf_status kf_set_chunk_rows(kf_ctx *ctx, int rows)
 {
     if (!ctx || rows < 1) return KF_EINVAL;
     ctx->chunk_rows = rows;
+    return KF_OK;
+}
+
+kf_status kf_set_host_chunk_rows(kf_ctx *ctx, int rows)
+{
+    if (!ctx || rows < 0) return KF_EINVAL;
+    ctx->host_chunk_rows = rows;
     return KF_OK;
 }
 
@@ -690,11 +697,10 @@ kf_status check_track_args(kf_ctx *ctx, const kf_video *v, const kf_corners *o, 
     return KF_OK;
 }
 
-// The hot path over frames [t0, t1) of a video whose frames [0, t1) are on the device
-// (LK of frame t0 reads frame t0 - 1): the chain with corner lists over the frame range,
-// then selection and LK from frame t0 on.
-kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf_tracks *tr, void *ws, int64_t t0,
-                      int64_t t1, cudaStream_t s, cudaStream_t s_trk = nullptr, cudaEvent_t ev_chain = nullptr)
+// The fusable set of the chain over frames [t0, t1): one fused kernel, which also lists
+// each frame's corners in the workspace.
+kf_status chain_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, void *ws, int64_t t0, int64_t t1,
+                      cudaStream_t s, int chunk_rows = 0)
 {
     const int64_t n = t1 - t0;
     if (n <= 0) return KF_OK;
@@ -703,7 +709,6 @@ kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const
     const int64_t cap = kf::cand_capacity(v->W, v->H);
     cudaError_t e = cudaMemsetAsync(cand_count + t0, 0, sizeof(int) * (size_t)n, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
-    // the fusable set of the chain: one fused kernel, which also lists each frame's corners
     const int64_t fstride = v->pitch * v->H, mstride = o->mask_pitch * v->H;
     kf_map fin{}, fout{};
     fin.plane[0] = const_cast<uint8_t *>(v->frames) + t0 * fstride;
@@ -716,26 +721,26 @@ kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const
     fout.dtype = KF_DT_U8;
     fout.pitch = o->mask_pitch;
     fout.frame_stride = mstride;
-    kf_status st = launch_group(ctx, 1, kf::NSTAGES, fin, fout, v->W, v->H, n, o->counts + t0, s, cand + t0 * cap,
-                                cand_count + t0, cap);
-    if (st != KF_OK) return st;
-    // the tracking set on its own stream when one is given (after the chain's event)
-    if (s_trk && ev_chain) {
-        e = cudaEventRecord(ev_chain, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_trk, ev_chain, 0);
-        if (e != cudaSuccess) return cuda_fail(ctx, e);
-        s = s_trk;
-    }
-    // the tracking set, after the kernel-to-kernel dependency
+    return launch_group(ctx, 1, kf::NSTAGES, fin, fout, v->W, v->H, n, o->counts + t0, s, cand + t0 * cap,
+                        cand_count + t0, cap, chunk_rows);
+}
+
+// The tracking set over frames [t0, t1), after the kernel-to-kernel dependency on the
+// chain of those frames: selection, then LK (frame t0's LK reads frame t0 - 1).
+kf_status tracking_range(kf_ctx *ctx, const kf_video *v, const kf_tracks *tr, void *ws, int64_t t0, int64_t t1,
+                         cudaStream_t s)
+{
+    const int64_t n = t1 - t0;
+    if (n <= 0) return KF_OK;
     kf::TrackVideo tv{};
     tv.frames = v->frames;
     tv.pitch = v->pitch;
     tv.W = (int)v->W;
     tv.H = (int)v->H;
     tv.T = (int)v->T;
-    tv.cand = cand;
-    tv.cand_count = cand_count;
-    tv.cand_cap = (int)cap;
+    tv.cand = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + round_up(4 * v->T, 256));
+    tv.cand_count = static_cast<int *>(ws);
+    tv.cand_cap = (int)kf::cand_capacity(v->W, v->H);
     tv.n_points = tr->n_points;
     tv.idx = tr->idx;
     tv.status = tr->status;
@@ -756,6 +761,24 @@ kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const
         tl.done();
     }
     return KF_OK;
+}
+
+// The hot path over frames [t0, t1) of a video whose frames [0, t1) are on the device:
+// the chain with corner lists, then selection and LK, on s_trk after the chain's event
+// when one is given.
+kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf_tracks *tr, void *ws, int64_t t0,
+                      int64_t t1, cudaStream_t s, cudaStream_t s_trk = nullptr, cudaEvent_t ev_chain = nullptr,
+                      int chunk_rows = 0)
+{
+    kf_status st = chain_range(ctx, v, o, ws, t0, t1, s, chunk_rows);
+    if (st != KF_OK || t1 <= t0) return st;
+    if (s_trk && ev_chain) {
+        cudaError_t e = cudaEventRecord(ev_chain, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_trk, ev_chain, 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+        s = s_trk;
+    }
+    return tracking_range(ctx, v, tr, ws, t0, t1, s);
 }
 
 // Bit-packing of the chain's masks for transfer: frame f's H * W pixels in raster order,
@@ -806,15 +829,13 @@ __global__ void __launch_bounds__(256) pack_mask_kernel(const uint8_t *__restric
 kf_status copy_streams(kf_ctx *c)
 {
     if (c->s_in) return KF_OK;
-    // the copy-out stream at the highest priority: its mask-packing kernels then take SM
-    // slots as soon as blocks of the compute streams retire, instead of queueing behind
-    // the next chunks' kernels
+    // the copy-out stream at the lowest priority: its mask-packing kernels fill SM slots
+    // the chunks' chains leave free instead of taking them first (small blocks, many of
+    // them); the tracking stream at the highest (it runs after every chain)
     int lo_prio = 0, hi_prio = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_out, cudaStreamNonBlocking, hi_prio);
-    // each chunk's selection and LK on a high-priority stream of their own: they then run
-    // as soon as the chunk's chain blocks retire, not behind the next chunks' chains
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_out, cudaStreamNonBlocking, lo_prio);
     for (int i = 0; e == cudaSuccess && i < kf_ctx::N_RING; ++i) {
         e = cudaStreamCreateWithFlags(&c->s_comp[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_trk[i], cudaStreamNonBlocking, hi_prio);
@@ -904,23 +925,31 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
         t1 = t0 + len < T ? t0 + len : T;
         const int64_t n = t1 - t0;
         const int r = (int)(k % kf_ctx::N_RING);
-        cudaEvent_t ein = ctx->ev_in[r], ecomp = ctx->ev_comp[r];
+        cudaEvent_t ein = ctx->ev_in[r];
         const cudaStream_t cs = ctx->s_comp[r];
         // copy in (s_in), compute (the compute streams in turn), copy out (s_out). Chunks
         // touch disjoint frames of every buffer, and a chunk's tracking reads only input
         // frames copied in before it, so consecutive chunks' kernels may overlap: the next
         // chunks' launches fill the SMs while the previous one drains its last wave.
-        e = cudaMemcpyAsync(const_cast<uint8_t *>(video->frames) + t0 * fstride, host_video->frames + t0 * fstride,
-                            (size_t)(n * fstride), cudaMemcpyHostToDevice, ctx->s_in);
+        {
+            TimedLaunch tl(ctx, KF_KT_COPY_IN, ctx->s_in);
+            e = cudaMemcpyAsync(const_cast<uint8_t *>(video->frames) + t0 * fstride, host_video->frames + t0 * fstride,
+                                (size_t)(n * fstride), cudaMemcpyHostToDevice, ctx->s_in);
+            if (e == cudaSuccess) tl.done();
+        }
         if (e == cudaSuccess) e = cudaEventRecord(ein, ctx->s_in);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ein, 0);
         if (e != cudaSuccess) break;
-        st = track_range(ctx, video, out, tracks, workspace, t0, t1, cs, ctx->s_trk[r], ctx->ev_chain[r]);
+        st = chain_range(ctx, video, out, workspace, t0, t1, cs, ctx->host_chunk_rows);
         if (st != KF_OK) return st;
-        e = cudaEventRecord(ecomp, ctx->s_trk[r]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ecomp, 0);
+        // the masks leave after the chunk's chain
+        e = cudaEventRecord(ctx->ev_chain[r], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ctx->ev_chain[r], 0);
         auto d2h = [&](void *dst, const void *src, size_t bytes) {
-            if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s_out);
+            if (e != cudaSuccess) return;
+            TimedLaunch tl(ctx, KF_KT_COPY_OUT, ctx->s_out);
+            e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s_out);
+            if (e == cudaSuccess) tl.done();
         };
         if (bits) {
             // packed on the copy-out stream into ring slot r (the slot's previous chunk was
@@ -929,24 +958,44 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
             const int64_t words = (packed + 3) / 4;
             const dim3 grid((unsigned)((words + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
             if (e == cudaSuccess) {
+                TimedLaunch tl(ctx, KF_KT_PACK, ctx->s_out);
                 pack_mask_kernel<<<grid, 256, 0, ctx->s_out>>>(out->mask + t0 * mstride, out->mask_pitch, mstride,
                                                                (int)video->W, (int)H, n, words, slot,
                                                                host_out->mask_pitch);
                 e = cudaGetLastError();
+                if (e == cudaSuccess) tl.done();
             }
             // the packed words of each frame only; the rest of the host frame stride is untouched
-            if (e == cudaSuccess)
+            if (e == cudaSuccess) {
+                TimedLaunch tl(ctx, KF_KT_COPY_OUT, ctx->s_out);
                 e = cudaMemcpy2DAsync(host_out->mask + t0 * host_out->mask_pitch, (size_t)host_out->mask_pitch, slot,
                                       (size_t)host_out->mask_pitch, (size_t)(4 * words), (size_t)n, cudaMemcpyDeviceToHost,
                                       ctx->s_out);
+                if (e == cudaSuccess) tl.done();
+            }
         } else {
             d2h(host_out->mask + t0 * mstride, out->mask + t0 * mstride, (size_t)(n * mstride));
         }
     }
-    // the counts and tracks (a few bytes a frame) once, after the last chunk: one copy
-    // each instead of one per chunk (every copy costs the copy engine a fixed setup)
+    // The tracking set of every frame after every chunk's chain, in one launch each:
+    // interleaved with the chunks' chains, the selection and LK blocks (up to 106 KB of
+    // shared memory or 21 K registers each) wait for several chain blocks of an SM to
+    // retire and keep its slots half empty meanwhile (measured: the call 3.1-3.4 ms
+    // against 3.0 ms). Then the counts and tracks, one copy each.
+    {
+        const cudaStream_t ts = ctx->s_trk[0];
+        for (int i = 0; e == cudaSuccess && i < kf_ctx::N_RING; ++i) e = cudaStreamWaitEvent(ts, ctx->ev_chain[i], 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+        st = tracking_range(ctx, video, tracks, workspace, 0, T, ts);
+        if (st != KF_OK) return st;
+        e = cudaEventRecord(ctx->ev_comp[0], ts);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ctx->ev_comp[0], 0);
+    }
     auto d2h_all = [&](void *dst, const void *src, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s_out);
+        if (e != cudaSuccess) return;
+        TimedLaunch tl(ctx, KF_KT_COPY_OUT, ctx->s_out);
+        e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s_out);
+        if (e == cudaSuccess) tl.done();
     };
     d2h_all(host_out->counts, out->counts, sizeof(int32_t) * (size_t)T);
     d2h_all(host_tracks->n_points, tracks->n_points, sizeof(int32_t) * (size_t)T);
@@ -965,6 +1014,41 @@ kf_status kf_set_kernel_timing(kf_ctx *ctx, int on)
     if (!ctx) return KF_EINVAL;
     ctx->timing = on != 0;
     return KF_OK;
+}
+
+kf_status kf_kernel_timeline(kf_ctx *ctx, int64_t cap, int64_t *n, int *kinds, double *start_ms, double *end_ms)
+{
+    if (!ctx || !n || cap < 0 || (cap > 0 && (!kinds || !start_ms || !end_ms))) return KF_EINVAL;
+    *n = (int64_t)ctx->timed.size();
+    cudaError_t err = cudaSuccess;
+    std::vector<double> t0, t1;
+    if (!ctx->timed.empty()) {
+        const cudaEvent_t ref = ctx->timed.front().a;
+        for (const kf_ctx::Timed &t : ctx->timed) {
+            float da = 0.f, db = 0.f;
+            cudaError_t e = cudaEventSynchronize(t.b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&da, ref, t.a);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&db, ref, t.b);
+            if (e != cudaSuccess && err == cudaSuccess) err = e;
+            t0.push_back(da);
+            t1.push_back(db);
+        }
+    }
+    // times from the earliest start (a launch on another stream may start before the first
+    // one recorded)
+    double lo = 0.0;
+    for (double v : t0) lo = v < lo ? v : lo;
+    for (size_t i = 0; i < ctx->timed.size() && (int64_t)i < cap; ++i) {
+        kinds[i] = ctx->timed[i].kind;
+        start_ms[i] = t0[i] - lo;
+        end_ms[i] = t1[i] - lo;
+    }
+    for (const kf_ctx::Timed &t : ctx->timed) {
+        ctx->spare_events.push_back(t.a);
+        ctx->spare_events.push_back(t.b);
+    }
+    ctx->timed.clear();
+    return err == cudaSuccess ? KF_OK : cuda_fail(ctx, err);
 }
 
 kf_status kf_kernel_times(kf_ctx *ctx, int64_t *launches, double *ms)

@@ -648,7 +648,7 @@ template <int A, int B, bool F16, bool CAND = false> struct SmemPlan {
     static constexpr int BAR_OFF = 0;
     static constexpr int IN_OFF = 128;
     static constexpr int CAND_OFF = IN_OFF + NST * STAGE_BYTES;
-    static constexpr int CAND_LANE = 32;            // buffered corners per lane (entry j of lane l at j * 32 + l)
+    static constexpr int CAND_LANE = 48;            // buffered corners per lane (entry j of lane l at j * 32 + l)
     static constexpr int CAND_BLOCK = RB * C;       // corners a lane may add in one 5-row block, at most
     static constexpr int RING_OFF = CAND_OFF + (CAND ? CAND_LANE * 32 * 8 : 0);
     static constexpr int RING_BYTES = RB * 32 * C * 4;  // R of the block's output rows, per lane

@@ -25,6 +25,7 @@ struct kf_ctx {
     int device = -1;
     int precision = KF_PREC_F32;
     int chunk_rows = 200;
+    int host_chunk_rows = 0;  // tile height of kf_track_host's chunk launches (0: chunk_rows)
     unsigned wait_polls = 1u << 22;  // kf::WAIT_POLLS unless kf_set_wait_polls lowered it
     int last_cuda = 0;
     int *d_err = nullptr;  // device error word of the bounded waits (4 bytes, owned)

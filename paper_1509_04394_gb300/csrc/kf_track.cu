@@ -7,11 +7,12 @@
 //   1. select_kernel: per frame, the K largest corner keys among the candidates the
 //      fused chain appended (key = R bits << 32 | ~raster index, so larger keys are
 //      stronger corners and, at equal R, lower raster indices). An exact MSB-first radix
-//      select finds the K-th largest key: the bits common to all keys are skipped (block
-//      AND/OR of the keys), then 8-bit digits are histogrammed until the bucket holding
-//      the K-th key is taken whole; each winner's position is its count of larger
-//      winners. A frame's keys are
-//      staged in shared memory when they fit, so the digit passes read on-chip memory;
+//      select finds the K-th largest key: the pass that stages a frame's keys in shared
+//      memory (when they fit) also histograms their top 9 bits (sign and exponent of R);
+//      the exponent bucket holding the K-th key is gathered on chip, the keys of higher
+//      buckets are winners, and 8-bit digits of the gathered bucket are histogrammed until
+//      the bucket holding the K-th key is taken whole. The winners are then ordered by a
+//      bitonic sort in shared memory;
 //   2. lk_kernel: per selected point of frame t >= 1, one Lucas-Kanade step against
 //      frame t-1 over a 7x7 window: A = sum [gx^2, gx gy; gx gy, gy^2],
 //      b = sum [gx gt, gy gt], (u, v) = -A^-1 b, gx, gy = Sobel of the smoothed frame t
@@ -32,7 +33,9 @@ namespace {
 
 constexpr unsigned FULLM = 0xffffffffu;
 constexpr int SEL_THREADS = 512;
-constexpr int SEL_SMEM_KEYS = 12288;  // a frame's keys are staged on chip up to this count (96 KiB)
+constexpr int SEL_SMEM_KEYS = 10240;  // a frame's keys are staged on chip up to this count (80 KiB)
+constexpr int SEL_LIST = 2048;        // keys of the K-th key's exponent bucket, gathered on chip (16 KiB)
+constexpr int SEL_DYN_BYTES = (SEL_SMEM_KEYS + SEL_LIST) * (int)sizeof(unsigned long long);
 constexpr int MAX_K = 1024;
 constexpr int MAX_DEVICES = 64;
 
@@ -48,28 +51,100 @@ __device__ __forceinline__ const TrackVideo &video_of(const TrackVideo &one, con
     return vids[lo];
 }
 
-__device__ __forceinline__ unsigned long long warp_and(unsigned long long x)
+// Warp 0: the bucket holding the rank-th largest key (1 = largest), from a histogram of
+// NB buckets (lane l holds buckets NB/32 * l on): suffix sums over the lanes give each
+// lane the count of keys in higher buckets. Writes the bucket, the rank within it and its
+// count to sh[0..2].
+template <int NB>
+__device__ __forceinline__ void find_bucket(const unsigned *hist, int rank, int lane, int *sh)
 {
+    constexpr int PER = NB / 32;
+    unsigned c[PER], s = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x &= __shfl_xor_sync(FULLM, x, o);
-    return x;
+    for (int b = 0; b < PER; ++b) {
+        c[b] = hist[PER * lane + b];
+        s += c[b];
+    }
+    unsigned incl = s;  // keys in this lane's buckets and above
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_down_sync(FULLM, incl, o);
+        if (lane + o < 32) incl += y;
+    }
+    const unsigned above = incl - s;
+    if (above < (unsigned)rank && (unsigned)rank <= incl) {
+        unsigned cum = above, cnt = 0;
+        int d = PER * lane;
+#pragma unroll
+        for (int b = PER - 1; b >= 0; --b) {
+            if (cum + c[b] >= (unsigned)rank) {
+                d = PER * lane + b;
+                cnt = c[b];
+                break;
+            }
+            cum += c[b];
+        }
+        sh[0] = d;
+        sh[1] = rank - (int)cum;
+        sh[2] = (int)cnt;
+    }
 }
-__device__ __forceinline__ unsigned long long warp_or(unsigned long long x)
+
+// Block-wide append: the threads whose `take` holds put their key in list[] from *count on
+// (one shared atomic per warp, lane order within the warp); every thread calls it.
+__device__ __forceinline__ void append_key(bool take, unsigned long long k, unsigned long long *list, unsigned *count,
+                                           int lane, unsigned cap)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x |= __shfl_xor_sync(FULLM, x, o);
-    return x;
+    const unsigned b = __ballot_sync(FULLM, take);
+    if (b) {  // warp-uniform
+        unsigned pos = 0;
+        if (lane == 0) pos = atomicAdd(count, (unsigned)__popc(b));
+        pos = __shfl_sync(FULLM, pos, 0) + __popc(b & ((1u << lane) - 1u));
+        if (take && pos < cap) list[pos] = k;
+    }
+}
+
+// Block-wide MSB-first radix select: among the keys of keys[0..m) that equal `prefix` on
+// the bits of `pmask` (every bit above `top`), the key kth such that exactly `rank` of them
+// are >= kth. Each pass histograms the next 8-bit digit of the matching keys and keeps the
+// bucket holding the rank-th largest; it ends when that bucket is taken whole (kth is then
+// the bucket's smallest possible key) or every bit is fixed.
+__device__ unsigned long long radix_kth(const unsigned long long *keys, int m, unsigned long long prefix,
+                                        unsigned long long pmask, int top, int rank, unsigned *hist, int *sh)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (;;) {
+        const int width = min(8, top + 1);
+        const int shift = top + 1 - width;
+        const unsigned dmask = (1u << width) - 1u;
+        if (tid < 256) hist[tid] = 0;
+        __syncthreads();
+        for (int i = tid; i < m; i += SEL_THREADS) {
+            const unsigned long long k = keys[i];
+            if ((k & pmask) == prefix) atomicAdd(&hist[(unsigned)(k >> shift) & dmask], 1u);
+        }
+        __syncthreads();
+        if (warp == 0) find_bucket<256>(hist, rank, lane, sh);
+        __syncthreads();
+        prefix |= (unsigned long long)sh[0] << shift;
+        pmask |= (unsigned long long)dmask << shift;
+        const bool whole = sh[1] == sh[2];
+        rank = sh[1];
+        top = shift - 1;
+        // sh and hist are rewritten only after the next pass's first barrier
+        if (whole || top < 0) return prefix;
+    }
 }
 
 __global__ void __launch_bounds__(SEL_THREADS, 2) select_kernel(const TrackVideo one, const TrackVideo *vids, int n_videos,
                                                              int K)
 {
-    extern __shared__ unsigned long long skeys[];  // SEL_SMEM_KEYS staged keys
-    __shared__ unsigned hist[256];
+    extern __shared__ unsigned long long skeys[];  // SEL_SMEM_KEYS staged keys, then SEL_LIST bucket keys
+    unsigned long long *blist = skeys + SEL_SMEM_KEYS;
+    __shared__ unsigned hist[512];
     __shared__ unsigned long long sel[MAX_K];
-    __shared__ unsigned long long red[2][SEL_THREADS / 32];
-    __shared__ unsigned nsel;
-    __shared__ int digit_s, rank_s, count_s;
+    __shared__ unsigned nsel, nlist;
+    __shared__ int sh[3];
     const TrackVideo &vd = video_of(one, vids, n_videos, blockIdx.x);
     const int frame = (int)(blockIdx.x - vd.frame_begin + vd.first_frame);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -82,13 +157,17 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) select_kernel(const TrackVideo
     const unsigned long long *gkeys = vd.cand + (int64_t)frame * cap;
     const int n = min(vd.cand_count[frame], cap);
     const int kk = min(n, K);
-    const bool staged = n <= SEL_SMEM_KEYS;
-    const unsigned long long *keys = staged ? skeys : gkeys;
-    unsigned long long kth = 0;  // every key >= kth is selected
     if (n > K) {
-        // stage the keys (16-byte loads, 16 keys per thread in flight); AND / OR over them
-        // give the leading bits all keys share
-        unsigned long long ka = ~0ull, ko = 0;
+        const bool staged = n <= SEL_SMEM_KEYS;
+        const unsigned long long *keys = staged ? skeys : gkeys;
+        // pass 1: stage the keys (16-byte loads, 16 keys per thread in flight) and
+        // histogram their top 9 bits, the sign and exponent of R
+        for (int i = tid; i < 512; i += SEL_THREADS) hist[i] = 0;
+        if (tid == 0) {
+            nsel = 0;
+            nlist = 0;
+        }
+        __syncthreads();
         const ulonglong2 *g2 = reinterpret_cast<const ulonglong2 *>(gkeys);
         const int n2 = n >> 1;
         for (int base = 0; base < n2; base += 8 * SEL_THREADS) {
@@ -101,117 +180,76 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) select_kernel(const TrackVideo
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int i = base + u * SEL_THREADS + tid;
-                if (i < n2) {
-                    if (staged) reinterpret_cast<ulonglong2 *>(skeys)[i] = k[u];
-                    ka &= k[u].x & k[u].y;
-                    ko |= k[u].x | k[u].y;
+                const bool valid = i < n2;
+                if (valid && staged) reinterpret_cast<ulonglong2 *>(skeys)[i] = k[u];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned d = (unsigned)((h ? k[u].y : k[u].x) >> 55);
+                    if (valid) atomicAdd(&hist[d], 1u);
                 }
             }
         }
         if ((n & 1) && tid == 0) {
             const unsigned long long k = gkeys[n - 1];
             if (staged) skeys[n - 1] = k;
-            ka &= k;
-            ko |= k;
-        }
-        ka = warp_and(ka);
-        ko = warp_or(ko);
-        if (lane == 0) {
-            red[0][warp] = ka;
-            red[1][warp] = ko;
+            atomicAdd(&hist[(unsigned)(k >> 55)], 1u);
         }
         __syncthreads();
-        ka = ~0ull;
-        ko = 0;
-#pragma unroll
-        for (int w = 0; w < SEL_THREADS / 32; ++w) {
-            ka &= red[0][w];
-            ko |= red[1][w];
-        }
-        // keys are distinct (n > K >= 1 means n >= 2), so some bit differs
-        const int lead = ka == ko ? 63 : __clzll((long long)(ka ^ ko));
-        unsigned long long pmask = lead ? ~0ull << (64 - lead) : 0ull;
-        unsigned long long prefix = ka & pmask;
-        int top = 63 - lead;  // highest bit not yet fixed
-        int rank = K;         // rank of the wanted key among the keys matching prefix (1 = largest)
-        for (;;) {
-            const int width = min(8, top + 1);
-            const int shift = top + 1 - width;
-            const unsigned dmask = (1u << width) - 1u;
-            if (tid < 256) hist[tid] = 0;
-            __syncthreads();
-            for (int i = tid; i < n; i += SEL_THREADS) {
-                const unsigned long long k = keys[i];
-                if ((k & pmask) == prefix) atomicAdd(&hist[(unsigned)(k >> shift) & dmask], 1u);
+        if (warp == 0) find_bucket<512>(hist, K, lane, sh);
+        __syncthreads();
+        const unsigned dstar = (unsigned)sh[0];
+        const int rank_in = sh[1], cnt = sh[2];
+        const unsigned long long pfx = (unsigned long long)dstar << 55, pm = ~0ull << 55;
+        unsigned long long kth = pfx;  // the bucket taken whole unless narrowed below
+        if (cnt <= SEL_LIST) {
+            // pass 2: keys of higher buckets are winners; the bucket's keys are gathered
+            for (int base = 0; base < n; base += SEL_THREADS) {
+                const int i = base + tid;
+                const unsigned long long k = i < n ? keys[i] : 0ull;
+                const unsigned d = (unsigned)(k >> 55);
+                append_key(i < n && d > dstar, k, sel, &nsel, lane, MAX_K);
+                append_key(i < n && d == dstar, k, blist, &nlist, lane, SEL_LIST);
             }
             __syncthreads();
-            if (warp == 0) {
-                // lane l holds digits 8l .. 8l+7; the bucket of the rank-th largest key is
-                // found from the counts of all larger digits (suffix sums over lanes)
-                unsigned c[8], s = 0;
-#pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    c[b] = hist[8 * lane + b];
-                    s += c[b];
-                }
-                unsigned incl = s;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned y = __shfl_down_sync(FULLM, incl, o);
-                    if (lane + o < 32) incl += y;
-                }
-                const unsigned above = incl - s;
-                if (above < (unsigned)rank && (unsigned)rank <= incl) {
-                    unsigned cum = above;
-                    int d = 8 * lane;
-#pragma unroll
-                    for (int b = 7; b >= 0; --b) {
-                        if (cum + c[b] >= (unsigned)rank) {
-                            d = 8 * lane + b;
-                            break;
-                        }
-                        cum += c[b];
-                    }
-                    digit_s = d;
-                    rank_s = rank - (int)cum;
-                    count_s = (int)hist[d];
+            if (rank_in < cnt) kth = radix_kth(blist, cnt, pfx, pm, 54, rank_in, hist, sh);
+            for (int base = 0; base < cnt; base += SEL_THREADS) {
+                const int i = base + tid;
+                const unsigned long long k = i < cnt ? blist[i] : 0ull;
+                append_key(i < cnt && k >= kth, k, sel, &nsel, lane, MAX_K);
+            }
+        } else {  // a large bucket: the remaining passes over all keys
+            if (rank_in < cnt) kth = radix_kth(keys, n, pfx, pm, 54, rank_in, hist, sh);
+            for (int base = 0; base < n; base += SEL_THREADS) {
+                const int i = base + tid;
+                const unsigned long long k = i < n ? keys[i] : 0ull;
+                append_key(i < n && k >= kth, k, sel, &nsel, lane, MAX_K);
+            }
+        }
+    } else {
+        for (int i = tid; i < n; i += SEL_THREADS) sel[i] = gkeys[i];  // every key is selected
+    }
+    // order: bitonic sort of the kk winners, descending (keys are distinct; the padding up
+    // to a power of two is 0, below every key)
+    int P = 1;
+    while (P < kk) P <<= 1;
+    __syncthreads();
+    for (int i = kk + tid; i < P; i += SEL_THREADS) sel[i] = 0ull;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < (P >> 1); i += SEL_THREADS) {
+                const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                const unsigned long long a = sel[lo], b = sel[hi];
+                const bool desc = (lo & size) == 0;  // every block descending at the last merge
+                if (desc ? a < b : a > b) {
+                    sel[lo] = b;
+                    sel[hi] = a;
                 }
             }
             __syncthreads();
-            prefix |= (unsigned long long)digit_s << shift;
-            pmask |= (unsigned long long)dmask << shift;
-            rank = rank_s;
-            top = shift - 1;
-            // the bucket is taken whole (all its keys are among the K), or the key is complete
-            if (rank == count_s || top < 0) break;
-        }
-        kth = prefix;  // exactly K keys are >= kth
-    } else if (staged) {
-        for (int i = tid; i < n; i += SEL_THREADS) skeys[i] = gkeys[i];
-    }
-    if (tid == 0) nsel = 0;
-    __syncthreads();
-    for (int base = 0; base < n; base += SEL_THREADS) {
-        const int i = base + tid;
-        const unsigned long long k = i < n ? keys[i] : 0ull;
-        const bool win = i < n && k >= kth;
-        const unsigned b = __ballot_sync(FULLM, win);
-        if (b) {  // warp-uniform
-            unsigned pos = 0;
-            if (lane == 0) pos = atomicAdd(&nsel, (unsigned)__popc(b));
-            pos = __shfl_sync(FULLM, pos, 0) + __popc(b & ((1u << lane) - 1u));
-            if (win && pos < (unsigned)MAX_K) sel[pos] = k;
         }
     }
-    __syncthreads();
-    // order: a winner's position is the number of winners with a larger key (keys are
-    // distinct); sel[] is read by every thread in the same order (broadcast)
-    for (int t = tid; t < kk; t += SEL_THREADS) {
-        const unsigned long long k = sel[t];
-        int pos = 0;
-        for (int j = 0; j < kk; ++j) pos += sel[j] > k;
-        idx_out[(int64_t)frame * K + pos] = (int32_t)(0xffffffffu - (unsigned)k);
-    }
+    for (int t = tid; t < kk; t += SEL_THREADS) idx_out[(int64_t)frame * K + t] = (int32_t)(0xffffffffu - (unsigned)sel[t]);
     if (tid == 0) n_points[frame] = kk;
 }
 
@@ -479,7 +517,9 @@ __device__ void lk_sums_clamped(const TrackVideo &vd, int frame, int p, float ac
     acc[4] = b1;
 }
 
-__global__ void __launch_bounds__(LK_THREADS) lk_kernel(const TrackVideo one, const TrackVideo *vids, int n_videos,
+// Five blocks per SM (96 registers, a few spilled words) run faster than three without
+// spills: the kernel is latency-bound, and the extra warps hide more of it.
+__global__ void __launch_bounds__(LK_THREADS, 5) lk_kernel(const TrackVideo one, const TrackVideo *vids, int n_videos,
                                                         int64_t total_frames, int K)
 {
     const int lane = threadIdx.x & 31;
@@ -538,8 +578,7 @@ int prepare_select()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return (int)e;
     if (dev >= 0 && dev < MAX_DEVICES && select_attr_set[dev]) return 0;
-    e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(SEL_SMEM_KEYS * sizeof(unsigned long long)));
+    e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEL_DYN_BYTES);
     if (e != cudaSuccess) return (int)e;
     if (dev >= 0 && dev < MAX_DEVICES) select_attr_set[dev] = true;
     return 0;
@@ -551,8 +590,8 @@ int launch_select(const TrackVideo &one, const TrackVideo *vids, int n, int64_t 
     if (total_frames == 0) return 0;
     const int r = prepare_select();
     if (r) return r;
-    select_kernel<<<(unsigned)total_frames, SEL_THREADS, SEL_SMEM_KEYS * sizeof(unsigned long long),
-                    static_cast<cudaStream_t>(stream)>>>(one, vids, n, K);
+    select_kernel<<<(unsigned)total_frames, SEL_THREADS, SEL_DYN_BYTES, static_cast<cudaStream_t>(stream)>>>(one, vids,
+                                                                                                     n, K);
     return (int)cudaGetLastError();
 }
 

@@ -79,6 +79,7 @@ def _lib():
             "kf_device_error": (i32, [P, P]),
             "kf_set_precision": (i32, [P, i32]),
             "kf_set_chunk_rows": (i32, [P, i32]),
+            "kf_set_host_chunk_rows": (i32, [P, i32]),
             "kf_set_wait_polls": (i32, [P, ctypes.c_uint32]),
             "kf_add_stage": (i32, [P, P, P]),
             "kf_add_harris_chain": (i32, [P]),
@@ -125,6 +126,7 @@ def _lib():
             "kf_pc_group_workspace_bytes": (i32, [P, i32, i32, i64, i64, i64, P]),
             "kf_pc_kalman": (i32, [P, P, i64, i32, P, P, P]),
             "kf_kernel_times": (i32, [P, P, P]),
+            "kf_kernel_timeline": (i32, [P, ctypes.c_int64, P, P, P, P]),
             "kf_st_smem_bytes": (i32, [i32, i32, P]),
             "kf_st_traffic": (i32, [i64, i64, i64, i32, i32, i32, P, P]),
             "kf_st_box_eq6": (i32, [dbl, i32, P, P]),
@@ -146,14 +148,16 @@ def _lib():
 def exported_symbols() -> list[str]:
     """Names of the C entry points this binding wraps (all declared in kfuse.h)."""
     return ["kf_status_str", "kf_last_cuda_error", "kf_version", "kf_create", "kf_destroy", "kf_device_error",
-            "kf_set_precision", "kf_set_chunk_rows", "kf_set_wait_polls", "kf_add_stage", "kf_add_harris_chain",
+            "kf_set_precision", "kf_set_chunk_rows", "kf_set_host_chunk_rows", "kf_set_wait_polls", "kf_add_stage",
+            "kf_add_harris_chain",
             "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
             "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static",
             "kf_track_workspace_bytes", "kf_track", "kf_batch_workspace_bytes", "kf_batch_create", "kf_batch_create_ex",
             "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows", "kf_plan_measured", "kf_dag_create", "kf_dag_destroy",
             "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups",
             "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_forward", "kf_costmodel_grad", "kf_costmodel_get",
-            "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times", "kf_pc_traffic", "kf_pc_plan",
+            "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times", "kf_kernel_timeline",
+            "kf_pc_traffic", "kf_pc_plan",
             "kf_pc_workspace_bytes", "kf_pc_run", "kf_pc_run_group", "kf_pc_kalman", "kf_pc_group_workspace_bytes",
             "kf_track_host", "kf_st_smem_bytes", "kf_st_traffic", "kf_st_box_eq6", "kf_st_run", "kf_st_plan_eq6", "kf_st_tune",
             "kf_dag_xplan_traffic", "kf_dag_plan_recompute", "kf_dag_run_x", "kf_dag_time_xgroups"]
@@ -212,6 +216,11 @@ def kf_set_precision(ctx, precision: int) -> None:
 
 def kf_set_chunk_rows(ctx, rows: int) -> None:
     _check("kf_set_chunk_rows", _lib().kf_set_chunk_rows(ctx, int(rows)), ctx)
+
+
+def kf_set_host_chunk_rows(ctx, rows: int) -> None:
+    """Tile height of kf_track_host's chunk launches; 0 chooses it per chunk."""
+    _check("kf_set_host_chunk_rows", _lib().kf_set_host_chunk_rows(ctx, int(rows)), ctx)
 
 
 def kf_set_wait_polls(ctx, polls: int) -> None:
@@ -595,8 +604,9 @@ def kf_run_static(ctx, cuts: int, frames, W: int, mask, counts, stream=None) -> 
     _check("kf_run_static", _lib().kf_run_static(ctx, cuts, ctypes.byref(v), ctypes.byref(o), _stream(stream)), ctx)
 
 
-KF_KT_GROUP, KF_KT_CHAIN_CORNERS, KF_KT_SELECT, KF_KT_LK, KF_KT_COUNT = 0, 1, 2, 3, 4
-KERNEL_KINDS = ("group", "chain_corners", "select", "lk")
+KF_KT_GROUP, KF_KT_CHAIN_CORNERS, KF_KT_SELECT, KF_KT_LK = 0, 1, 2, 3
+KF_KT_PACK, KF_KT_COPY_IN, KF_KT_COPY_OUT, KF_KT_COUNT = 4, 5, 6, 7
+KERNEL_KINDS = ("group", "chain_corners", "select", "lk", "pack", "copy_in", "copy_out")
 
 
 def kf_set_kernel_timing(ctx, on: bool) -> None:
@@ -610,6 +620,17 @@ def kf_kernel_times(ctx) -> dict[str, tuple[int, float]]:
     ms = (ctypes.c_double * KF_KT_COUNT)()
     _check("kf_kernel_times", _lib().kf_kernel_times(ctx, n, ms), ctx)
     return {KERNEL_KINDS[k]: (int(n[k]), float(ms[k])) for k in range(KF_KT_COUNT)}
+
+
+def kf_kernel_timeline(ctx, cap: int = 4096) -> list[tuple[str, float, float]]:
+    """The recorded launches and copies in enqueue order: (kind, start ms, end ms) from the
+    earliest start; clears the record."""
+    n = ctypes.c_int64()
+    kinds = (ctypes.c_int * cap)()
+    t0 = (ctypes.c_double * cap)()
+    t1 = (ctypes.c_double * cap)()
+    _check("kf_kernel_timeline", _lib().kf_kernel_timeline(ctx, cap, ctypes.byref(n), kinds, t0, t1), ctx)
+    return [(KERNEL_KINDS[kinds[i]], float(t0[i]), float(t1[i])) for i in range(min(n.value, cap))]
 
 
 def make_map(planes, dtype: int) -> kf_map:

@@ -159,17 +159,48 @@ def test_slow_checker_patches_are_tracked_to_their_true_motion(dev):
     assert np.median(errs) <= 0.25
 
 
+def kth_bucket(frame, W, Kp):
+    """(candidates, keys in the FP32 exponent bucket of the Kp-th strongest) of one frame,
+    from the oracle's responses: which of the selection's paths the frame takes."""
+    maps, m, _ = oc.chain_frame(frame[:, :W].copy())
+    r = np.sort(maps["r"].ravel()[np.flatnonzero(m.ravel())].astype(np.float32))[::-1]
+    if len(r) <= Kp:
+        return len(r), 0
+    e = r.view(np.uint32) >> 23
+    return len(r), int(np.sum(e == e[Kp - 1]))
+
+
 @pytest.mark.parametrize("H,W,Kp", [(480, 640, 256), (720, 960, 1024), (720, 960, 7)])
 def test_selection_with_many_candidates(dev, H, W, Kp):
     """Noise frames: about 3% of pixels are corner candidates, so the 480 x 640 frames'
     lists (~9k keys) are selected from shared memory and the 720 x 960 frames' (~21k
-    keys) from global memory."""
+    keys) from global memory; at K = 1024 the K-th key's exponent bucket holds more keys
+    than the 2048 the selection gathers on chip, so its digits are found over all keys."""
     rng = np.random.default_rng(H + Kp)
     fr = rng.integers(0, 256, (3, H, W), dtype=np.uint8)
     out = run_track(dev, fr, W, Kp)
-    assert out["counts"][1] > (12288 if H == 720 else 5000)
+    assert out["counts"][1] > (10240 if H == 720 else 5000)
+    if Kp == 1024:
+        assert kth_bucket(fr[1], W, Kp)[1] > 2048
     checked = sum(check_frame(fr, t, W, out, Kp) for t in range(1, 3))
     assert checked >= min(Kp, 5)
+
+
+@pytest.mark.parametrize("Kp", [256, 1024])
+def test_selection_when_the_kth_bucket_holds_every_key(dev, Kp):
+    """A moving checkerboard: thousands of corners of one response, all in the K-th key's
+    exponent bucket (more than the selection gathers on chip) while the frame's keys fit
+    in shared memory; the raster index decides among equal responses."""
+    T, H, W, sq = 3, 480, 640, 16
+    fr = np.zeros((T, H, sv.pitch_for(W)), np.uint8)
+    y, x = np.mgrid[0:H, 0:W]
+    for t in range(T):
+        fr[t, :, :W] = (((x + t) // sq + y // sq) % 2 * 200 + 20).astype(np.uint8)
+    n, in_bucket = kth_bucket(fr[1], W, Kp)
+    assert n <= 10240 and in_bucket > 2048
+    out = run_track(dev, fr, W, Kp)
+    checked = sum(check_frame(fr, t, W, out, Kp) for t in range(1, T))
+    assert checked >= 5
 
 
 def test_kernel_timing_counts_every_launch(dev):
@@ -194,8 +225,8 @@ def test_kernel_timing_counts_every_launch(dev):
     wsr = torch.empty(K.kf_workspace_bytes(ctx.h, cuts, 160, H, T), dtype=torch.uint8, device=dev)
     K.kf_run(ctx.h, cuts, frames, 160, mask, counts, wsr)
     kt = K.kf_kernel_times(ctx.h)
-    assert {k: c for k, (c, _) in kt.items()} == {"group": 3, "chain_corners": 2, "select": 2, "lk": 2}
-    assert all(ms > 0 for c, ms in kt.values())
+    assert {k: c for k, (c, _) in kt.items() if c} == {"group": 3, "chain_corners": 2, "select": 2, "lk": 2}
+    assert all(ms > 0 for c, ms in kt.values() if c)
     assert all(c == 0 for c, _ in K.kf_kernel_times(ctx.h).values())
     K.kf_set_kernel_timing(ctx.h, False)
     K.kf_track(ctx.h, frames, 160, mask, counts, 16, n, idx, u, v, st, ws)
@@ -235,6 +266,60 @@ def test_host_pipelined_call_equals_kf_track(dev, chunk):
             got, exp = got[..., :W], exp[..., :W]
         assert np.array_equal(got, exp), k
         assert np.array_equal(host[k].numpy(), devb[k].cpu().numpy()), k
+
+
+def test_host_call_timeline_and_chunk_tile_height(dev):
+    """With timing on, kf_track_host records each chunk's copy in, chain, mask packing and
+    copy out, then one selection and one LK over every frame and the six copies of the
+    counts and tracks; the timeline puts each chunk's chain after its copy in and the
+    tracking after every chain. Its results do not depend on
+    the tile height of the chunk launches (kf_set_host_chunk_rows)."""
+    T, H, W, Kp = 9, 80, 150, 16
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=12, n_blobs=8, n_patches=6), pitch=sv.pitch_for(W))
+    ctx = K.Context(0)
+    P = fr.shape[2]
+    S = ((W * H + 7) // 8 + 15) // 16 * 16
+
+    def run(rows, timing):
+        devb = dict(frames=torch.zeros((T, H, P), dtype=torch.uint8, device=dev),
+                    mask=torch.zeros((T, H, P), dtype=torch.uint8, device=dev),
+                    counts=torch.zeros(T, dtype=torch.int32, device=dev),
+                    n_points=torch.zeros(T, dtype=torch.int32, device=dev),
+                    idx=torch.zeros((T, Kp), dtype=torch.int32, device=dev), u=torch.zeros((T, Kp), device=dev),
+                    v=torch.zeros((T, Kp), device=dev), status=torch.zeros((T, Kp), dtype=torch.int32, device=dev))
+        host = {k: torch.empty_like(t, device="cpu").pin_memory() for k, t in devb.items()}
+        host["mask"] = torch.zeros((T, S), dtype=torch.uint8).pin_memory()
+        host["frames"].copy_(torch.from_numpy(fr))
+        ws = torch.empty(K.kf_track_workspace_bytes(ctx.h, W, H, T), dtype=torch.uint8, device=dev)
+        K.kf_set_host_chunk_rows(ctx.h, rows)
+        K.kf_set_kernel_timing(ctx.h, timing)
+        K.kf_track_host(ctx.h, host, devb, W, Kp, ws, chunk=3, mask_format=K.KF_MASK_BITS)
+        torch.cuda.synchronize()
+        tl = K.kf_kernel_timeline(ctx.h) if timing else []
+        K.kf_set_kernel_timing(ctx.h, False)
+        assert K.kf_device_error(ctx.h) == 0
+        return {k: t.numpy().copy() for k, t in host.items() if k != "frames"}, tl
+
+    ref, _ = run(0, False)
+    got, tl = run(8, True)
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+    kinds = [k for k, _, _ in tl]
+    n_chunks = kinds.count("copy_in")
+    assert n_chunks >= 4
+    for k in ("chain_corners", "pack"):
+        assert kinds.count(k) == n_chunks, k
+    assert kinds.count("select") == 1 and kinds.count("lk") == 1
+    assert kinds.count("copy_out") == n_chunks + 6
+    assert all(0.0 <= a <= b for _, a, b in tl)
+    ins = [(a, b) for k, a, b in tl if k == "copy_in"]
+    chains = [(a, b) for k, a, b in tl if k == "chain_corners"]
+    assert all(c[0] >= i[1] for i, c in zip(ins, chains))
+    sel = [a for k, a, _ in tl if k == "select"][0]
+    assert sel >= max(b for _, b in chains)
+    assert K.kf_kernel_timeline(ctx.h) == []
+    with pytest.raises(K.KfuseError):
+        K.kf_set_host_chunk_rows(ctx.h, -1)
 
 
 @pytest.mark.parametrize("W,chunk", [(150, 4), (600, 3), (37, 100)])
