@@ -33,7 +33,7 @@ from synth import video as sv  # noqa: E402
 
 METRIC = "fused-chain Mpixel/s & HBM roofline fraction vs unfused, 800×600×1000 u8"
 UNIT = "Mpixel/s"
-E2E_CHUNK = 66  # frames per chunk of the pipelined host-to-host call
+E2E_CHUNK = 50  # frames per chunk of the pipelined host-to-host call
 SPEC = sv.HSDV_800x600x1000
 WORKLOAD = "Harris 8-stage chain, 1000 frames x 800 rows x 600 cols u8, 64 blobs + 32 patches, seed 3"
 # Algorithmic FP32 operations per output pixel of the chain, from the stage definitions
@@ -166,6 +166,8 @@ def run_profile(args):
     mask = torch.zeros_like(frames)
     counts = torch.zeros(T, dtype=torch.int32, device=dev)
     ctx = K.Context(0, precision=K.KF_PREC_F16 if args.f16 else K.KF_PREC_F32)
+    if args.rows > 0:
+        K.kf_set_chunk_rows(ctx.h, args.rows)
     cuts = args.cuts if args.cuts >= 0 else K.kf_plan(ctx.h, W, H, T)[0]
     if args.track:  # the whole hot path: fused chain with corner lists, selection, LK
         KP = 256
@@ -294,9 +296,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # the executor's tile height for this workload from its autotuner (CUDA-event timing of
     # the fused chain inside the library, on a context of its own), applied to the step
-    tctx = K.Context(local_rank)
-    best_rows, best_ms = K.kf_tune_chunk_rows(tctx.h, frames, W, torch.zeros_like(frames), torch.zeros_like(counts),
-                                              TUNE_ROWS, reps=3, stream=stream)
+    # (--rows fixes it instead: profiler runs, whose serialised launches would mislead it)
+    if args.rows > 0:
+        best_rows, best_ms, rows_from = args.rows, None, "fixed (--rows)"
+    else:
+        tctx = K.Context(local_rank)
+        best_rows, best_ms = K.kf_tune_chunk_rows(tctx.h, frames, W, torch.zeros_like(frames),
+                                                  torch.zeros_like(counts), TUNE_ROWS, reps=3, stream=stream)
+        rows_from = "autotuner"
     K.kf_set_chunk_rows(ctx.h, best_rows)
 
     # clocks: sample across a ~1.5 s soak and the timed region
@@ -390,6 +397,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     alg_bytes = 2 * px + 8 * n_corners + 8 * T
     achieved = alg_bytes / (dom / 1000) / 1e9
     rec = kernel_counters() if T == 1000 else None
+    if rec and rec.get("captured_tile_rows", best_rows) != best_rows:
+        rec = None  # counters of another tile height (other halo rows, other job count)
     traffic = rec["dram_bytes_per_launch_1000_frames"] if rec else None
     # issue view: executed warp instructions (ncu) over 152 SMs x 4 schedulers x clock
     issue_peak = n_sm * 4 * sm_mhz * 1e6 / 1e9  # G warp-instructions / s
@@ -439,7 +448,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames": T, "rows": H, "cols": W, "step": "fused 8-stage chain + "
                    f"top-{KP} corner selection + LK tracking per frame pair", "partition_cuts": cuts,
-                   "groups": n_groups, "chunk_rows": best_rows, "chunk_rows_from": "autotuner", "cols_per_lane": 4,
+                   "groups": n_groups, "chunk_rows": best_rows, "chunk_rows_from": rows_from, "cols_per_lane": 4,
                    "l2": "inputs larger than L2 (480 MB frames, 480 MB mask), no flush",
                    "parallelism": (f"frame shards x{world} of one {world * owned}-frame video, merged on the host"
                                    if world > 1 else "single GPU")},
@@ -1017,6 +1026,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--rows", type=int, default=0, help="fixed tile height for the step (default: autotuned)")
     ap.add_argument("--profile", type=int, default=0, help="profiler case: fused chain only, on T frames")
     ap.add_argument("--cuts", type=int, default=-1, help="partition for --profile (default: planned)")
     ap.add_argument("--f16", action="store_true", help="FP16 maps for --profile")

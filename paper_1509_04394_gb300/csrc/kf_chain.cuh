@@ -1092,13 +1092,20 @@ __device__ __forceinline__ void init_ring(unsigned char *smem)
     __syncwarp();
 }
 
-// a job of either kind: full strip, or a pair of half strips (warp-uniform choice)
+// a job of either kind: full strip, or a pair of half strips (warp-uniform choice).
+// Interior strips have a row loop of their own, without edge handling, which a long launch
+// runs for most of its time alone (its queue is kind-major). A launch of about one wave
+// runs every kind at once instead, and warps of different row loops on one SM then miss
+// the instruction cache (the stall on instruction fetch rose from 1.3 to 6.2 per issue);
+// with p.one_full_body interior strips take the edge strips' loop, which is correct for
+// them too: two loop bodies instead of three.
 template <int A, int B, bool F16, bool CAND, bool TILES = false>
 __device__ __forceinline__ bool run_any_job(const GroupParams &p, int64_t job, unsigned char *smem, unsigned &kbase,
                                             bool global_desc)
 {
     const JobPos jp = decode_job(p, job);
-    if (!jp.edge) return run_job<A, B, F16, CAND, false, TILES, false>(p, jp, smem, kbase, global_desc);
+    if (!jp.edge && !p.one_full_body)
+        return run_job<A, B, F16, CAND, false, TILES, false>(p, jp, smem, kbase, global_desc);
     if (!jp.paired) return run_job<A, B, F16, CAND, false, TILES, true>(p, jp, smem, kbase, global_desc);
     return run_job<A, B, F16, CAND, true, TILES, true>(p, jp, smem, kbase, global_desc);
 }

@@ -70,6 +70,7 @@ struct GroupParams {
     int out_off;              // strip s outputs columns [xs + out_off, + step): out_off a multiple of C
     int half_last;            // 1: the last strip is half wide, and one warp runs it for two frames
     int n_lead, n_trail;      // full strips at the frame's left edge (a prefix) and right edge (a suffix)
+    int one_full_body;        // 1: interior strips run the edge strips' row loop too (see run_any_job)
     int T;                    // frames
     int chunk_rows, n_chunks;
     int64_t n_jobs;           // T * n_chunks * (n_strips - half_last) + ceil(T/2) * n_chunks * half_last
