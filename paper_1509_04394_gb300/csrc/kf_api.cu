@@ -1236,16 +1236,16 @@ kf_status kf_batch_create_ex(kf_ctx *ctx, const kf_video *videos, const kf_corne
     });
     std::vector<kf::GroupParams> hq((size_t)n);
     for (int k = 0; k < n; ++k) hq[(size_t)k] = hp[(size_t)order[(size_t)k]];
-    // queue segments, kind-major (the batch kernel's order): interior-strip jobs of every
-    // video, then edge-strip jobs, then half-strip jobs, each in the longest-first order
+    // queue segments, kind-major (the batch kernel's order): half-strip jobs of every
+    // video, then edge-strip jobs, then interior-strip jobs, each in the longest-first order
     for (int kind = 0, s = 0; kind < 3; ++kind)
         for (int k = 0; k < n; ++k, ++s) {
             const kf::GroupParams &q = hq[(size_t)k];
             const int F = q.n_strips - q.half_last;
             const int64_t per = (int64_t)q.T * q.n_chunks;
-            const int64_t cnt = kind == 0 ? per * (F - q.n_lead - q.n_trail)
+            const int64_t cnt = kind == 0 ? q.n_jobs - per * F
                               : kind == 1 ? per * (q.n_lead + q.n_trail)
-                                          : q.n_jobs - per * F;
+                                          : per * (F - q.n_lead - q.n_trail);
             items[(size_t)s + 1] = items[(size_t)s] + cnt;
         }
     e = cudaMemcpy(d_params, hq.data(), sizeof(kf::GroupParams) * (size_t)n, cudaMemcpyHostToDevice);
