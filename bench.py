@@ -351,6 +351,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     def e2e_bytes_step():
         K.kf_track_host(ctx.h, host_b, devb, W, KP, ws_track, chunk=E2E_CHUNK, stream=stream,
                         mask_format=K.KF_MASK_BYTES)
+    # the tile height of the call's chunk launches: the step's or 160 rows, whichever the
+    # call itself measures faster (a chunk launch is about one wave long, not fifteen)
+    e2e_rows = {}
+    for r in sorted({best_rows, 160}):
+        K.kf_set_host_chunk_rows(ctx.h, r)
+        e2e_rows[r] = timed(e2e_step, 3, 1)
+    host_rows = min(e2e_rows, key=e2e_rows.get)
+    K.kf_set_host_chunk_rows(ctx.h, host_rows)
     ms_e2e = timed(e2e_step, max(3, args.steps // 2), 1)
     m_bits = np.packbits(mask[:, :, :W].reshape(T, -1).cpu().numpy(), axis=1, bitorder="little")
     e2e_same = bool(np.array_equal(host["mask"].numpy()[:, :m_bits.shape[1]], m_bits)
@@ -485,6 +493,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                         "hbm_frac": 50 * px / (ms_unf16 / 1000) / 1e9 / hbm_peak},
         "e2e": {"value": world * px / (ms_e2e / 1000) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e, "chunk_frames": E2E_CHUNK,
+                "chunk_tile_rows": host_rows, "chunk_tile_rows_ms": {str(k): v for k, v in e2e_rows.items()},
                 "call": "kf_track_host, KF_MASK_BITS (copy in, hot path on three streams, mask packed 8 px/byte "
                         "on the device, packed mask and tracks copied out)",
                 "results_equal_device_step": e2e_same, "ms_per_step_repeated_at_end": ms_e2e_end},
