@@ -251,7 +251,8 @@ typedef struct kf_tracks {
 } kf_tracks;
 
 /* Workspace of kf_track: per frame a corner-candidate list of max(1024, ceil(W*H/4))
- * 8-byte entries and a counter. A frame with more corners than that sets
+ * 8-byte entries and a counter, and the chain launch's job counters (so two calls in
+ * flight at once need two workspaces). A frame with more corners than that sets
  * KF_DEVERR_OVERFLOW in the device error word (its selection then covers only the
  * listed corners). */
 #define KF_DEVERR_OVERFLOW 2

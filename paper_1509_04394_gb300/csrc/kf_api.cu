@@ -295,13 +295,27 @@ struct TimedLaunch {
 
 kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &out, int64_t W, int64_t H, int64_t T,
                        int32_t *counts, cudaStream_t s, unsigned long long *cand = nullptr, int *cand_count = nullptr,
-                       int64_t cand_cap = 0, int chunk_rows = 0, bool one_full_body = false)
+                       int64_t cand_cap = 0, int chunk_rows = 0, bool one_full_body = false,
+                       unsigned long long *job_ctr = nullptr)
 {
     if (T == 0) return KF_OK;
     kf::GroupParams p;
     kf_status st = fill_params(c, A, B, in, out, W, H, T, counts, cand, cand_count, cand_cap, p, chunk_rows);
     if (st != KF_OK) return st;
     p.one_full_body = one_full_body ? 1 : 0;
+    if (job_ctr) {
+        // jobs taken by SM: the share of SMs that start on interior strips follows the
+        // interior strips' share of the work, a half-strip or edge job weighing 1.2
+        // interior ones (their edge handling)
+        const int F = p.n_strips - p.half_last;
+        const double n_other = (double)(p.n_jobs - (int64_t)T * p.n_chunks * F) +
+                               (double)((int64_t)T * p.n_chunks * (p.n_lead + p.n_trail));
+        const double n_in = (double)p.n_jobs - n_other;
+        p.sm_split = n_in + n_other > 0 ? (int)(1024.0 * n_in / (n_in + 1.2 * n_other) + 0.5) : 1024;
+        p.job_ctr = job_ctr;
+        cudaError_t e = cudaMemsetAsync(job_ctr, 0, 3 * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
     // 0: FP32 maps; 1: 16-bit maps; 2: 16-bit maps and FP16 inter-stage tiles on chip
     const int f16 = c->precision == KF_PREC_F32 ? 0 : c->precision == KF_PREC_F16_TILES ? 2 : 1;
     const int64_t blocks = p.n_jobs;  // one warp (one job) per block
@@ -669,7 +683,8 @@ kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *v, const kf_corners
 kf_status kf_track_workspace_bytes(const kf_ctx *ctx, int64_t W, int64_t H, int64_t T, size_t *bytes)
 {
     if (!ctx || !bytes || !kf::volume_ok(W, H, T) || W * H > 0x7fffffffLL) return KF_EINVAL;
-    *bytes = (size_t)round_up(4 * T, 256) + (size_t)(8 * kf::cand_capacity(W, H) * T);
+    // candidate counts, candidate lists, then the chain launch's three job counters
+    *bytes = (size_t)round_up(4 * T, 256) + (size_t)(8 * kf::cand_capacity(W, H) * T) + 256;
     return KF_OK;
 }
 
@@ -701,13 +716,16 @@ kf_status check_track_args(kf_ctx *ctx, const kf_video *v, const kf_corners *o, 
 // The fusable set of the chain over frames [t0, t1): one fused kernel, which also lists
 // each frame's corners in the workspace.
 kf_status chain_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, void *ws, int64_t t0, int64_t t1,
-                      cudaStream_t s, int chunk_rows = 0, bool one_full_body = false)
+                      cudaStream_t s, int chunk_rows = 0, bool one_full_body = false, bool by_sm = false)
 {
     const int64_t n = t1 - t0;
     if (n <= 0) return KF_OK;
     int *cand_count = static_cast<int *>(ws);
     auto *cand = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + round_up(4 * v->T, 256));
     const int64_t cap = kf::cand_capacity(v->W, v->H);
+    // the job counters after the lists (one launch at a time uses them: by_sm is only
+    // given for a call's single chain launch)
+    unsigned long long *job_ctr = by_sm ? cand + cap * v->T : nullptr;
     cudaError_t e = cudaMemsetAsync(cand_count + t0, 0, sizeof(int) * (size_t)n, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     const int64_t fstride = v->pitch * v->H, mstride = o->mask_pitch * v->H;
@@ -723,7 +741,7 @@ kf_status chain_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, void 
     fout.pitch = o->mask_pitch;
     fout.frame_stride = mstride;
     return launch_group(ctx, 1, kf::NSTAGES, fin, fout, v->W, v->H, n, o->counts + t0, s, cand + t0 * cap,
-                        cand_count + t0, cap, chunk_rows, one_full_body);
+                        cand_count + t0, cap, chunk_rows, one_full_body, job_ctr);
 }
 
 // The tracking set over frames [t0, t1), after the kernel-to-kernel dependency on the
@@ -771,7 +789,7 @@ kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const
                       int64_t t1, cudaStream_t s, cudaStream_t s_trk = nullptr, cudaEvent_t ev_chain = nullptr,
                       int chunk_rows = 0)
 {
-    kf_status st = chain_range(ctx, v, o, ws, t0, t1, s, chunk_rows);
+    kf_status st = chain_range(ctx, v, o, ws, t0, t1, s, chunk_rows, false, true);
     if (st != KF_OK || t1 <= t0) return st;
     if (s_trk && ev_chain) {
         cudaError_t e = cudaEventRecord(ev_chain, s);

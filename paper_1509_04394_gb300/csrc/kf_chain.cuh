@@ -117,29 +117,27 @@ __device__ __forceinline__ float pick(const V4 &v, int c)
     return r;
 }
 
-// Columns of this lane outside [0, W) take the value of the edge column (per-stage
-// clamp of an on-chip map). Warp-uniform: called only by warps that cross an edge.
-// lbase: first lane of the lane's strip (16 for the second half strip of a pair).
+// The lanes at a frame's edges, in a strip that crosses one: l for the lane holding
+// column 0 (always at its register 0: strips start on a multiple of 16 columns), r for the
+// lane holding column W-1 (at register rreg). Each stage clamps its own input map at the
+// frame's edges; of the lanes outside the frame only these two lanes' stencils would read,
+// so the stencils of a map computed on chip take the clamp in the halo of these lanes (the
+// edge column's value in place of the neighbour's), and the lanes outside hold values no
+// output depends on. The same additions in the same order as a clamped map gives, so the
+// results equal those of groups that read the map clamped from memory, bit for bit.
+struct EdgeLanes { bool l, r; int rreg; };
+constexpr EdgeLanes NO_EDGE{false, false, 0};
+
+// The right-edge lane's columns past W-1 take column W-1's value (when W is not a multiple
+// of 4; otherwise column W-1 is a lane's last). Every lane runs it; it changes only that one.
 template <int N>
-__device__ __forceinline__ void fix_edges(Rows<N> &r, int xs, int x0, int W, bool L, bool R, int lbase)
+__device__ __forceinline__ void clamp_right_lane(Rows<N> &r, const EdgeLanes &e)
 {
-    if (L) {
-        const int src = lbase + (-xs) / C;  // column 0 sits at register 0 of lane src (xs % C == 0)
 #pragma unroll
-        for (int m = 0; m < N; ++m) {
-            const float e = __shfl_sync(FULL, r.v[m][0], src);
+    for (int m = 0; m < N; ++m) {
+        const float x = pick(r.v[m], e.rreg);
 #pragma unroll
-            for (int c = 0; c < C; ++c) r.v[m][c] = (x0 + c < 0) ? e : r.v[m][c];
-        }
-    }
-    if (R) {
-        const int src = lbase + (W - 1 - xs) / C, reg = (W - 1 - xs) % C;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            const float e = __shfl_sync(FULL, pick(r.v[m], reg), src);
-#pragma unroll
-            for (int c = 0; c < C; ++c) r.v[m][c] = (x0 + c >= W) ? e : r.v[m][c];
-        }
+        for (int c = 0; c < C; ++c) r.v[m][c] = (e.r && c > e.rreg) ? x : r.v[m][c];
     }
 }
 
@@ -285,9 +283,11 @@ struct SobelV {
         s[0] = sx;
     }
 };
-__device__ __forceinline__ void sobel_h(const V4 &g, V4 &dx, V4 &sx)
+__device__ __forceinline__ void sobel_h(const V4 &g, V4 &dx, V4 &sx, const EdgeLanes &e = NO_EDGE)
 {
-    const Halo<1> h = halo<1>(g);
+    Halo<1> h = halo<1>(g);
+    h.l[0] = e.l ? g[0] : h.l[0];
+    h.r[0] = e.r ? g[C - 1] : h.r[0];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const float l = at<1>(g, h, c - 1), r = at<1>(g, h, c + 1);
@@ -314,12 +314,17 @@ __device__ __forceinline__ void products(const Rows<2> &i, Rows<3> &p)
 // ((r[t-4] + r[t-3]) + (r[t-2] + r[t-1])) + r[t]: 3 adds a value instead of 4, in an
 // order fixed by the rows' ages alone, the same in every partition and chunk height.
 // Output row = input row - 2.
-__device__ __forceinline__ void box_h(const V4 &x, V4 &o)
+__device__ __forceinline__ void box_h(const V4 &x, V4 &o, const EdgeLanes &e = NO_EDGE)
 {
     static_assert(C == 4, "pair-sharing box assumes 4 columns per lane");
     const float B = x[0] + x[1], Cp = x[2] + x[3];
-    const float A = __shfl_up_sync(FULL, Cp, 1), D = __shfl_down_sync(FULL, B, 1);
-    const float xm1 = __shfl_up_sync(FULL, x[3], 1), x4 = __shfl_down_sync(FULL, x[0], 1);
+    float A = __shfl_up_sync(FULL, Cp, 1), D = __shfl_down_sync(FULL, B, 1);
+    float xm1 = __shfl_up_sync(FULL, x[3], 1), x4 = __shfl_down_sync(FULL, x[0], 1);
+    // at the frame's edges: the clamped neighbours' pair sums and columns
+    A = e.l ? x[0] + x[0] : A;
+    xm1 = e.l ? x[0] : xm1;
+    D = e.r ? x[3] + x[3] : D;
+    x4 = e.r ? x[3] : x4;
     const float E = B + Cp;
     o[0] = (A + B) + x[2];
     o[1] = xm1 + E;
@@ -459,9 +464,11 @@ struct NmsV {
         return bits;
     }
 };
-__device__ __forceinline__ void nms_h(const V4 &r, V4 &mh)
+__device__ __forceinline__ void nms_h(const V4 &r, V4 &mh, const EdgeLanes &e = NO_EDGE)
 {
-    const Halo<1> h = halo<1>(r);
+    Halo<1> h = halo<1>(r);
+    h.l[0] = e.l ? r[0] : h.l[0];
+    h.r[0] = e.r ? r[C - 1] : h.r[0];
 #pragma unroll
     for (int c = 0; c < C; ++c) mh[c] = fmaxf(fmaxf(at<1>(r, h, c - 1), r[c]), at<1>(r, h, c + 1));
 }
@@ -730,7 +737,6 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
     // those lanes then recompute frame0's half strip and store nothing)
     const int half = paired ? lane >> 4 : 0;
     const int sl = paired ? lane & 15 : lane;  // lane within its strip
-    const int lbase = lane - sl;
     const bool active = frame0 + half < p.T;
     const int frame = active ? frame0 + half : frame0;
     const int W = p.W, H = p.H;
@@ -748,6 +754,9 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
     // boundary) each lane outputs all of its columns or none
     static_assert(EDGE || !PAIRED, "half strips are the last strip: an edge");
     const bool edgeL = EDGE && xs < 0, edgeR = EDGE && xs + (paired ? STRIP / 2 : STRIP) > W;
+    // the lanes holding columns 0 and W-1, and whether the latter has columns past W-1
+    [[maybe_unused]] const EdgeLanes edge{edgeL && x0 == 0, edgeR && x0 <= W - 1 && W - 1 < x0 + C, W - 1 - x0};
+    [[maybe_unused]] const bool rpart = edgeR && (W % C) != 0;
     const bool lane_inside = !EDGE || ((x0 >= 0) && (x0 + C <= W));
     int off[C];  // staged-tile offset of each column's clamped source
 #pragma unroll
@@ -911,10 +920,13 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         // ---- stage 4 (Sobel), input row t - D4
         [[maybe_unused]] Rows<2> ixy;
         if constexpr (HAS4) {
-            if constexpr (hstencil_before(A, 4))
-                if (EDGE && (edgeL | edgeR)) fix_edges<1>(g, xs, x0, W, edgeL, edgeR, lbase);
+            [[maybe_unused]] EdgeLanes e4 = NO_EDGE;
+            if constexpr (EDGE && hstencil_before(A, 4)) {
+                if (rpart) clamp_right_lane<1>(g, edge);
+                e4 = edge;
+            }
             V4 dx, sx;
-            sobel_h(g.v[0], dx, sx);
+            sobel_h(g.v[0], dx, sx, e4);
             if (border) {
                 const int i = t - D4;
                 if (i == 0) s4.fill(dx, sx);
@@ -927,8 +939,8 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         // ---- stage 5 (products)
         [[maybe_unused]] Rows<3> pr;
         if constexpr (A <= 5 && 5 <= B) {
-            if constexpr (hstencil_before(A, 6) && HAS6)
-                if (EDGE && (edgeL | edgeR)) fix_edges<2>(ixy, xs, x0, W, edgeL, edgeR, lbase);
+            if constexpr (EDGE && hstencil_before(A, 6) && HAS6)
+                if (rpart) clamp_right_lane<2>(ixy, edge);
             if constexpr (ONCHIP16) {
 #pragma unroll
                 for (int m = 0; m < 2; ++m) ixy.v[m] = mul4(ixy.v[m], splat4(0x1p-16f));
@@ -941,8 +953,10 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         [[maybe_unused]] Rows<3> sm;
         if constexpr (HAS6) {
             Rows<3> hs;
+            [[maybe_unused]] EdgeLanes e6 = NO_EDGE;
+            if constexpr (EDGE && hstencil_before(A, 6)) e6 = edge;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) box_h(pr.v[m], hs.v[m]);
+            for (int m = 0; m < 3; ++m) box_h(pr.v[m], hs.v[m], e6);
             if (border) {
                 const int i = t - D6;
                 if (i == 0) s6.fill(hs);
@@ -964,10 +978,13 @@ __device__ __forceinline__ bool run_job(const GroupParams &p, const JobPos &jp, 
         [[maybe_unused]] unsigned bits = 0;
         [[maybe_unused]] V4 centre;
         if constexpr (HAS8) {
-            if constexpr (hstencil_before(A, 8))
-                if (EDGE && (edgeL | edgeR)) fix_edges<1>(r7, xs, x0, W, edgeL, edgeR, lbase);
+            [[maybe_unused]] EdgeLanes e8 = NO_EDGE;
+            if constexpr (EDGE && hstencil_before(A, 8)) {
+                if (rpart) clamp_right_lane<1>(r7, edge);
+                e8 = edge;
+            }
             V4 mh;
-            nms_h(r7.v[0], mh);
+            nms_h(r7.v[0], mh, e8);
             if (border) {
                 const int i = t - D8;
                 if (i == 0) s8.fill(mh, r7.v[0]);
@@ -1114,15 +1131,50 @@ __device__ __forceinline__ bool run_any_job(const GroupParams &p, int64_t job, u
     return run_job<A, B, F16, CAND, true, TILES, true>(p, jp, smem, kbase, global_desc);
 }
 
-// One job per block (one warp): the launch's blocks enumerate the jobs.
+// The job of this block when jobs are taken by SM (p.job_ctr): the SMs below p.sm_split
+// (of 1024, over %nsmid) take interior jobs first, the others half-strip jobs, then edge
+// jobs, so each SM runs one instance of the row loop for most of the launch instead of
+// all three kinds meeting on every SM as the queue passes from one kind to the next (a
+// launch of interior jobs alone runs 1.10 against 1.31 ms). A kind whose counter has run
+// out is passed over for the next; the blocks are as many as the jobs, so every block
+// finds one (a block passes over a kind only once all its jobs are taken, and a block
+// that passed over all three would mean every job was taken by the others). -1 if not.
+__device__ __forceinline__ int64_t pick_job(const GroupParams &p)
+{
+    long long job = -1;
+    if ((threadIdx.x & 31) == 0) {
+        unsigned sm, nsm;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+        asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+        const bool inner_first = (unsigned long long)sm * 1024ull < (unsigned long long)p.sm_split * nsm;
+        const int F = p.n_strips - p.half_last;
+        const int64_t n_pair = p.n_jobs - (int64_t)p.T * p.n_chunks * F;
+        const int64_t n_edge = (int64_t)p.T * p.n_chunks * (p.n_lead + p.n_trail);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (job >= 0) break;
+            const int k = inner_first ? 2 - i : i;  // 0 half strips, 1 edge, 2 interior
+            const int64_t base = k == 0 ? 0 : k == 1 ? n_pair : n_pair + n_edge;
+            const int64_t cnt = k == 0 ? n_pair : k == 1 ? n_edge : p.n_jobs - n_pair - n_edge;
+            if (cnt <= 0) continue;
+            const unsigned long long t = atomicAdd(p.job_ctr + k, 1ull);
+            if ((int64_t)t < cnt) job = (long long)(base + (int64_t)t);
+        }
+    }
+    return __shfl_sync(FULL, job, 0);
+}
+
+// One job per block (one warp): the launch's blocks enumerate the jobs, or take them by SM.
 template <int A, int B, bool F16, bool CAND = false, bool TILES = false>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, TILES ? MIN_BLOCKS_BOX16 : (A <= 6 && 6 <= B) ? MIN_BLOCKS_BOX : MIN_BLOCKS) group_kernel(const __grid_constant__ GroupParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     if ((int64_t)blockIdx.x >= p.n_jobs) return;
+    const int64_t job = p.job_ctr ? pick_job(p) : (int64_t)blockIdx.x;
+    if (job < 0) return;
     init_ring<SmemPlan<A, B, F16, CAND>::NST>(smem);
     unsigned kbase = 0;
-    run_any_job<A, B, F16, CAND, TILES>(p, blockIdx.x, smem, kbase, false);
+    run_any_job<A, B, F16, CAND, TILES>(p, job, smem, kbase, false);
 }
 
 // Persistent batch over many videos (the fully fused chain): each resident warp pops

@@ -71,6 +71,11 @@ struct GroupParams {
     int half_last;            // 1: the last strip is half wide, and one warp runs it for two frames
     int n_lead, n_trail;      // full strips at the frame's left edge (a prefix) and right edge (a suffix)
     int one_full_body;        // 1: interior strips run the edge strips' row loop too (see run_any_job)
+    unsigned long long *job_ctr;  // null: block b runs job b; else three counters of jobs taken
+                                  // (half-strip, edge, interior; zeroed before the launch) from
+                                  // which each block takes its job by the kind its SM prefers
+    int sm_split;             // with job_ctr: SMs whose index (scaled to 1024) is below this take
+                              // interior jobs first, the others half-strip and edge jobs first
     int T;                    // frames
     int chunk_rows, n_chunks;
     int64_t n_jobs;           // T * n_chunks * (n_strips - half_last) + ceil(T/2) * n_chunks * half_last
