@@ -291,19 +291,28 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     def step():  # the whole hot path: fused chain, corner selection, LK tracking
         K.kf_track(ctx.h, frames, W, mask, counts, KP, n_pts, idx, uu, vv, st, ws_track, stream)
 
-    def chain():  # the dominant kernel alone: the fused chain as the planner partitions it
-        K.kf_run(ctx.h, cuts, frames, W, mask, counts, None, stream)
+    # the dominant kernel alone: the fused chain as the planner partitions it, on a
+    # context of its own at the height kf_tune_chunk_rows finds for it
+    cctx = K.Context(local_rank)
+
+    def chain():
+        K.kf_run(cctx.h, cuts, frames, W, mask, counts, None, stream)
 
     # the executor's tile height for this workload from its autotuner (CUDA-event timing of
     # the fused chain inside the library, on a context of its own), applied to the step
-    # (--rows fixes it instead: profiler runs, whose serialised launches would mislead it)
+    # (--rows fixes it instead: profiler runs, whose serialised launches would mislead it).
+    # The autotuner times the step itself (kf_tune_track_rows): the chain's launch with
+    # corner lists takes its jobs by SM kind, and its best height is not the plain chain's
     if args.rows > 0:
         best_rows, best_ms, rows_from = args.rows, None, "fixed (--rows)"
+        K.kf_set_chunk_rows(cctx.h, args.rows)
+        chain_rows = args.rows
     else:
-        tctx = K.Context(local_rank)
-        best_rows, best_ms = K.kf_tune_chunk_rows(tctx.h, frames, W, torch.zeros_like(frames),
-                                                  torch.zeros_like(counts), TUNE_ROWS, reps=3, stream=stream)
-        rows_from = "autotuner"
+        chain_rows, _ = K.kf_tune_chunk_rows(cctx.h, frames, W, torch.zeros_like(frames), torch.zeros_like(counts),
+                                             TUNE_ROWS, reps=3, stream=stream)
+        best_rows, best_ms = K.kf_tune_track_rows(ctx.h, frames, W, mask, counts, KP, n_pts, idx, uu, vv, st,
+                                                  ws_track, TUNE_ROWS, reps=3, stream=stream)
+        rows_from = "autotuner (kf_tune_track_rows, on the step)"
     K.kf_set_chunk_rows(ctx.h, best_rows)
 
     # clocks: sample across a ~1.5 s soak and the timed region
@@ -367,6 +376,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     e2e_same_b = bool(torch.equal(host_b["mask"], mask.cpu()) and torch.equal(host_b["idx"], idx.cpu()))
     # the FP16-tile form: the same step and chain with the box's row-pair sums in FP16 on chip
     ctx16t = K.Context(local_rank, precision=K.KF_PREC_F16_TILES)
+    K.kf_set_chunk_rows(ctx16t.h, best_rows)  # the FP32 step's height
     ctx16 = K.Context(local_rank, precision=K.KF_PREC_F16)
     mask16, counts16 = torch.zeros_like(frames), torch.zeros_like(counts)
     tr16 = (torch.zeros_like(n_pts), torch.zeros_like(idx), torch.zeros_like(uu), torch.zeros_like(vv), torch.zeros_like(st))
@@ -464,6 +474,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "tracked_points_per_s": world * tracked / (ms / 1000),
         "chain_only": {"value": world * px / (ms_chain / 1000) / 1e6, "ms_per_step": ms_chain,
                        "kernel": "group_kernel<1,8> (full fusion, no corner lists), timed alone by kf_run",
+                       "chunk_rows": chain_rows,
                        "identical_to_step": chain_same,
                        "hbm_frac": (2 * px + 4 * T) / (ms_chain / 1000) / 1e9 / hbm_peak},
         "roofline": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Gop/s",
@@ -484,7 +495,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "batched_form": {"value": world * px / (ms_batch / 1000) / 1e6, "ms_per_step": ms_batch,
                          "what": "the same step as one video of a persistent-kernel batch replayed from a CUDA graph",
                          "identical_results": batch_same},
-        "autotuned_chunk_rows": {"best": best_rows, "chain_ms": best_ms, "candidates": TUNE_ROWS},
+        "autotuned_chunk_rows": {"best": best_rows, "step_ms": best_ms, "candidates": TUNE_ROWS},
         "unfused": {"value": world * px / (ms_unf / 1000) / 1e6, "ms_per_step": ms_unf, "kernels": 8,
                     "hbm_frac": unf_bytes / (ms_unf / 1000) / 1e9 / hbm_peak,
                     "bit_identical_to_fused": bool(same and chain_same),

@@ -334,6 +334,13 @@ kf_status kf_batch_destroy(kf_batch *batch);
  * ms when best_ms is not NULL). Synchronous. */
 kf_status kf_tune_chunk_rows(kf_ctx *ctx, const kf_video *video, const kf_corners *out, const int *candidates, int n,
                              int reps, void *stream, int *best_rows, float *best_ms);
+/* The same autotuner on the whole hot path: times kf_track (the chain with corner lists,
+ * selection, LK; same arguments) per candidate height, keeps the fastest in the context.
+ * The chain's launch with corner lists takes its jobs by SM kind, so its best height can
+ * differ from the plain chain's. Synchronous. */
+kf_status kf_tune_track_rows(kf_ctx *ctx, const kf_video *video, const kf_corners *out, const kf_tracks *tracks,
+                             void *workspace, size_t workspace_bytes, const int *candidates, int n, int reps,
+                             void *stream, int *best_rows, float *best_ms);
 /* The partition of least MEASURED time: the exhaustive check that judges the traffic
  * model's choice (Sec. VI, Fig. 5, against the measured No / Two / Full Fusion of
  * Sec. VII-B). Runs each candidate cut mask (`cands`, n_cand of them; all 2^(n-1) when

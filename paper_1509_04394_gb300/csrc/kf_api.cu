@@ -305,13 +305,14 @@ kf_status launch_group(kf_ctx *c, int A, int B, const kf_map &in, const kf_map &
     p.one_full_body = one_full_body ? 1 : 0;
     if (job_ctr) {
         // jobs taken by SM: the share of SMs that start on interior strips follows the
-        // interior strips' share of the work, a half-strip or edge job weighing 1.2
-        // interior ones (their edge handling)
+        // interior strips' share of the work, a half-strip or edge job weighing 1.8
+        // interior ones (measured best among 1.0-2.2 on the 1000 x 800 x 600 video: the
+        // step 1.48 ms at 1.8 against 1.51 at 1.0 and 1.49 at 2.2, 267-row tiles)
         const int F = p.n_strips - p.half_last;
         const double n_other = (double)(p.n_jobs - (int64_t)T * p.n_chunks * F) +
                                (double)((int64_t)T * p.n_chunks * (p.n_lead + p.n_trail));
         const double n_in = (double)p.n_jobs - n_other;
-        p.sm_split = n_in + n_other > 0 ? (int)(1024.0 * n_in / (n_in + 1.2 * n_other) + 0.5) : 1024;
+        p.sm_split = n_in + n_other > 0 ? (int)(1024.0 * n_in / (n_in + 1.8 * n_other) + 0.5) : 1024;
         p.job_ctr = job_ctr;
         cudaError_t e = cudaMemsetAsync(job_ctr, 0, 3 * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return cuda_fail(c, e);
@@ -1366,6 +1367,51 @@ kf_status kf_tune_chunk_rows(kf_ctx *ctx, const kf_video *v, const kf_corners *o
         if (st != KF_OK) break;
         cudaEventRecord(e0, s);
         for (int r = 0; r < reps && st == KF_OK; ++r) st = kf_run(ctx, 0, v, o, nullptr, 0, stream);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = KF_ECUDA;
+        float ms = 0;
+        if (st == KF_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / reps < best_t) {
+            best_t = ms / reps;
+            best = candidates[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->chunk_rows = st == KF_OK ? best : keep;
+    if (st != KF_OK) return st;
+    *best_rows = best;
+    if (best_ms) *best_ms = best_t;
+    return KF_OK;
+}
+
+kf_status kf_tune_track_rows(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const kf_tracks *tr, void *ws,
+                             size_t ws_bytes, const int *candidates, int n, int reps, void *stream, int *best_rows,
+                             float *best_ms)
+{
+    if (!ctx || !v || !o || !tr || !candidates || n < 1 || reps < 1 || !best_rows) return KF_EINVAL;
+    if (ctx->device < 0) return KF_ESTATE;
+    for (int i = 0; i < n; ++i)
+        if (candidates[i] < 1) return KF_EINVAL;
+    kf::DeviceScope dev_scope(ctx->device);
+    cudaError_t e = dev_scope.status();
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return KF_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return KF_ECUDA;
+    }
+    const int keep = ctx->chunk_rows;
+    int best = keep;
+    float best_t = INFINITY;
+    kf_status st = KF_OK;
+    for (int i = 0; i < n && st == KF_OK; ++i) {
+        ctx->chunk_rows = candidates[i];
+        st = kf_track(ctx, v, o, tr, ws, ws_bytes, stream);  // warm-up
+        if (st != KF_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == KF_OK; ++r) st = kf_track(ctx, v, o, tr, ws, ws_bytes, stream);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) st = KF_ECUDA;
         float ms = 0;

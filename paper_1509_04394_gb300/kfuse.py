@@ -103,6 +103,7 @@ def _lib():
             "kf_batch_run": (i32, [P, P]),
             "kf_batch_destroy": (i32, [P]),
             "kf_tune_chunk_rows": (i32, [P, P, P, P, i32, i32, P, P, P]),
+            "kf_tune_track_rows": (i32, [P, P, P, P, P, ctypes.c_size_t, P, i32, i32, P, P, P]),
             "kf_plan_measured": (i32, [P, P, P, P, ctypes.c_size_t, P, i32, i32, P, P, P, P]),
             "kf_dag_create": (i32, [P, P, i32, P]),
             "kf_dag_destroy": (i32, [P]),
@@ -153,7 +154,8 @@ def exported_symbols() -> list[str]:
             "kf_num_stages", "kf_group_traffic", "kf_group_onchip", "kf_partition_traffic", "kf_plan",
             "kf_enumerate", "kf_map_scale", "kf_workspace_bytes", "kf_run", "kf_run_group", "kf_run_static",
             "kf_track_workspace_bytes", "kf_track", "kf_batch_workspace_bytes", "kf_batch_create", "kf_batch_create_ex",
-            "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows", "kf_plan_measured", "kf_dag_create", "kf_dag_destroy",
+            "kf_batch_run", "kf_batch_destroy", "kf_tune_chunk_rows", "kf_tune_track_rows", "kf_plan_measured",
+            "kf_dag_create", "kf_dag_destroy",
             "kf_dag_group_info", "kf_dag_plan", "kf_dag_workspace_bytes", "kf_dag_run", "kf_dag_time_groups",
             "kf_costmodel_train", "kf_costmodel_predict", "kf_costmodel_forward", "kf_costmodel_grad", "kf_costmodel_get",
             "kf_costmodel_set", "kf_set_kernel_timing", "kf_kernel_times", "kf_kernel_timeline",
@@ -398,6 +400,22 @@ def kf_tune_chunk_rows(ctx, frames, W: int, mask, counts, candidates, reps: int 
     _check("kf_tune_chunk_rows", _lib().kf_tune_chunk_rows(ctx, ctypes.byref(vid), ctypes.byref(o), cand, len(candidates),
                                                            int(reps), _stream(stream), ctypes.byref(best),
                                                            ctypes.byref(ms)), ctx)
+    return best.value, ms.value
+
+
+def kf_tune_track_rows(ctx, frames, W: int, mask, counts, K: int, n_points, idx, u, v, status, workspace, candidates,
+                       reps: int = 3, stream=None):
+    """The tile-height autotuner on kf_track (same tensors); returns (best rows, its ms)."""
+    T, H, P = frames.shape
+    vid = kf_video(frames.data_ptr(), int(W), int(H), int(T), int(P))
+    o = kf_corners(mask.data_ptr(), int(mask.shape[2]), counts.data_ptr())
+    tr = kf_tracks(int(K), n_points.data_ptr(), idx.data_ptr(), u.data_ptr(), v.data_ptr(), status.data_ptr())
+    cand = (ctypes.c_int * len(candidates))(*candidates)
+    best, ms = ctypes.c_int(), ctypes.c_float()
+    _check("kf_tune_track_rows", _lib().kf_tune_track_rows(
+        ctx, ctypes.byref(vid), ctypes.byref(o), ctypes.byref(tr), workspace.data_ptr(),
+        workspace.numel() * workspace.element_size(), cand, len(candidates), int(reps), _stream(stream),
+        ctypes.byref(best), ctypes.byref(ms)), ctx)
     return best.value, ms.value
 
 

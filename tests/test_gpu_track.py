@@ -203,6 +203,42 @@ def test_selection_when_the_kth_bucket_holds_every_key(dev, Kp):
     assert checked >= 5
 
 
+def test_step_is_the_same_at_every_tile_height_and_the_tuner_keeps_the_fastest(dev):
+    """kf_track's chain launch takes its jobs by SM kind from counters in the workspace:
+    whatever the tile height (so the job count and the mix of kinds per wave), the step
+    gives the same masks, counts and tracks; kf_tune_track_rows returns one of its
+    candidates and leaves the context on it."""
+    T, H, W, Kp = 6, 150, 300, 32
+    fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=17, n_blobs=10, n_patches=6), pitch=sv.pitch_for(W))
+    ctx = K.Context(0)
+    frames = torch.from_numpy(fr).to(dev)
+    mask = torch.zeros_like(frames)
+    counts = torch.zeros(T, dtype=torch.int32, device=dev)
+    n = torch.zeros(T, dtype=torch.int32, device=dev)
+    idx = torch.zeros((T, Kp), dtype=torch.int32, device=dev)
+    u, v = torch.zeros((T, Kp), device=dev), torch.zeros((T, Kp), device=dev)
+    st = torch.zeros((T, Kp), dtype=torch.int32, device=dev)
+    ws = torch.empty(K.kf_track_workspace_bytes(ctx.h, W, H, T), dtype=torch.uint8, device=dev)
+    ref = None
+    for rows in (16, 48, 200, 7):
+        K.kf_set_chunk_rows(ctx.h, rows)
+        mask.fill_(3)
+        idx.fill_(-2)
+        K.kf_track(ctx.h, frames, W, mask, counts, Kp, n, idx, u, v, st, ws)
+        got = [t.cpu().clone() for t in (mask, counts, n, idx, u, v, st)]
+        assert K.kf_device_error(ctx.h) == 0
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(got, ref):
+                assert torch.equal(a, b), rows
+    best, ms = K.kf_tune_track_rows(ctx.h, frames, W, mask, counts, Kp, n, idx, u, v, st, ws, [24, 64, 160], reps=2)
+    assert best in (24, 64, 160) and ms > 0
+    K.kf_track(ctx.h, frames, W, mask, counts, Kp, n, idx, u, v, st, ws)
+    for a, b in zip([t.cpu() for t in (mask, counts, n, idx, u, v, st)], ref):
+        assert torch.equal(a, b)
+
+
 def test_kernel_timing_counts_every_launch(dev):
     """With timing on, kf_track records one event pair per kernel it launches (the chain
     with corner lists, selection, LK) and kf_run one per fused group; the record clears."""
