@@ -684,7 +684,9 @@ kf_status kf_run(kf_ctx *ctx, uint32_t cuts, const kf_video *v, const kf_corners
 kf_status kf_track_workspace_bytes(const kf_ctx *ctx, int64_t W, int64_t H, int64_t T, size_t *bytes)
 {
     if (!ctx || !bytes || !kf::volume_ok(W, H, T) || W * H > 0x7fffffffLL) return KF_EINVAL;
-    // candidate counts, candidate lists, then the chain launch's three job counters
+    // candidate counts, candidate lists, then three job counters for each chain launch
+    // that may be in flight at once (one per compute stream of kf_track_host)
+    static_assert(3 * 8 * kf_ctx::N_RING <= 256, "job counters");
     *bytes = (size_t)round_up(4 * T, 256) + (size_t)(8 * kf::cand_capacity(W, H) * T) + 256;
     return KF_OK;
 }
@@ -717,16 +719,16 @@ kf_status check_track_args(kf_ctx *ctx, const kf_video *v, const kf_corners *o, 
 // The fusable set of the chain over frames [t0, t1): one fused kernel, which also lists
 // each frame's corners in the workspace.
 kf_status chain_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, void *ws, int64_t t0, int64_t t1,
-                      cudaStream_t s, int chunk_rows = 0, bool one_full_body = false, bool by_sm = false)
+                      cudaStream_t s, int chunk_rows = 0, bool one_full_body = false, int ctr_slot = -1)
 {
     const int64_t n = t1 - t0;
     if (n <= 0) return KF_OK;
     int *cand_count = static_cast<int *>(ws);
     auto *cand = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + round_up(4 * v->T, 256));
     const int64_t cap = kf::cand_capacity(v->W, v->H);
-    // the job counters after the lists (one launch at a time uses them: by_sm is only
-    // given for a call's single chain launch)
-    unsigned long long *job_ctr = by_sm ? cand + cap * v->T : nullptr;
+    // jobs taken by SM kind with the counters of slot ctr_slot after the lists (launches
+    // in flight at once use different slots; -1: jobs by block index)
+    unsigned long long *job_ctr = ctr_slot >= 0 ? cand + cap * v->T + 3 * ctr_slot : nullptr;
     cudaError_t e = cudaMemsetAsync(cand_count + t0, 0, sizeof(int) * (size_t)n, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     const int64_t fstride = v->pitch * v->H, mstride = o->mask_pitch * v->H;
@@ -790,7 +792,7 @@ kf_status track_range(kf_ctx *ctx, const kf_video *v, const kf_corners *o, const
                       int64_t t1, cudaStream_t s, cudaStream_t s_trk = nullptr, cudaEvent_t ev_chain = nullptr,
                       int chunk_rows = 0)
 {
-    kf_status st = chain_range(ctx, v, o, ws, t0, t1, s, chunk_rows, false, true);
+    kf_status st = chain_range(ctx, v, o, ws, t0, t1, s, chunk_rows, false, 0);
     if (st != KF_OK || t1 <= t0) return st;
     if (s_trk && ev_chain) {
         cudaError_t e = cudaEventRecord(ev_chain, s);
@@ -963,7 +965,7 @@ kf_status kf_track_host(kf_ctx *ctx, const kf_video *host_video, const kf_corner
         // chunk launches are about a wave long and run with other chunks' launches: one
         // full-strip loop body for all of them (measured: the call 2.82-2.92 ms against
         // 2.94-3.09 with interior strips on their own loop)
-        st = chain_range(ctx, video, out, workspace, t0, t1, cs, ctx->host_chunk_rows, true);
+        st = chain_range(ctx, video, out, workspace, t0, t1, cs, ctx->host_chunk_rows, true, r);
         if (st != KF_OK) return st;
         // the masks leave after the chunk's chain
         e = cudaEventRecord(ctx->ev_chain[r], cs);
