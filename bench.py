@@ -1052,7 +1052,7 @@ def main():
     ap.add_argument("--f16", action="store_true", help="FP16 maps for --profile")
     ap.add_argument("--track", action="store_true", help="--profile the whole path with tracking")
     ap.add_argument("--batch48", action="store_true", help="the 48-video batching workload")
-    ap.add_argument("--tune-cache", default=os.path.join(ROOT, "gpurun_out", "tune_cache.json"),
+    ap.add_argument("--tune-cache", default=os.path.join(ROOT, ".kfuse_tune_cache.json"),
                     help="JSON file of autotuning results (--batch48)")
     ap.add_argument("--costmodel", action="store_true", help="the learned-cost-model workload")
     ap.add_argument("--cm-frames", type=int, default=24, help="frames the groups are timed on (--costmodel; 24 "
