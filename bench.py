@@ -415,8 +415,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     alg_bytes = 2 * px + 8 * n_corners + 8 * T
     achieved = alg_bytes / (dom / 1000) / 1e9
     rec = kernel_counters() if T == 1000 else None
-    if rec and rec.get("captured_tile_rows", best_rows) != best_rows:
-        rec = None  # counters of another tile height (other halo rows, other job count)
+    # the counters taken at the step's tile height (each height has its own halo rows and
+    # job count), if that height was captured
+    rec = (dict(rec["by_rows"][str(best_rows)], kernel=rec["kernel"])
+           if rec and str(best_rows) in rec.get("by_rows", {}) else None)
     traffic = rec["dram_bytes_per_launch_1000_frames"] if rec else None
     # issue view: executed warp instructions (ncu) over 152 SMs x 4 schedulers x clock
     issue_peak = n_sm * 4 * sm_mhz * 1e6 / 1e9  # G warp-instructions / s
