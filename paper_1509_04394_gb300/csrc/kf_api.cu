@@ -1121,7 +1121,7 @@ BatchLayout batch_layout(const kf_video *videos, int n, bool track)
     auto take = [&](size_t bytes) { const size_t at = o; o = (size_t)round_up((int64_t)(o + bytes), 256); return at; };
     L.params = take(sizeof(kf::GroupParams) * (size_t)n);
     L.items = take(sizeof(int64_t) * (size_t)(3 * n + 1));  // queue segments, kind-major
-    L.queue = take(sizeof(unsigned long long));
+    L.queue = take(3 * sizeof(unsigned long long));  // one counter per kind of job
     if (track) {
         int64_t frames = 0, cand = 0;
         for (int i = 0; i < n; ++i) {
@@ -1291,11 +1291,15 @@ kf_status kf_batch_create_ex(kf_ctx *ctx, const kf_video *videos, const kf_corne
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_queue, 0, 3 * sizeof(unsigned long long), cs);
     if (e == cudaSuccess && track) e = cudaMemsetAsync(d_cand_count, 0, sizeof(int) * (size_t)frame_begin, cs);
     for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaMemsetAsync(outs[i].counts, 0, sizeof(int32_t) * (size_t)videos[i].T, cs);
     if (e == cudaSuccess) {
-        const int r = kf::launch_batch_chain(d_params, d_items, n, d_queue, track, (unsigned)(sms * per_sm), cs);
+        // the share of SMs that start on interior strips, as in a single video's launch
+        const double n_in = (double)(items[(size_t)(3 * n)] - items[(size_t)(2 * n)]);
+        const double n_other = (double)items[(size_t)(2 * n)];
+        const int sm_split = n_in + n_other > 0 ? (int)(1024.0 * n_in / (n_in + 1.8 * n_other) + 0.5) : 1024;
+        const int r = kf::launch_batch_chain(d_params, d_items, n, d_queue, track, (unsigned)(sms * per_sm), sm_split, cs);
         if (r) e = (cudaError_t)r;
     }
     if (e == cudaSuccess && track) {

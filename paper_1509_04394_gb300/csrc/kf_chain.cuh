@@ -1184,7 +1184,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, TILES ? MIN_BLOCKS_BOX16
 // with that video's descriptor.
 template <bool CAND>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, MIN_BLOCKS_BOX) batch_kernel(const GroupParams *videos, const int64_t *item_begin,
-                                                                                      int n_videos, unsigned long long *queue)
+                                                                                      int n_videos, unsigned long long *queue,
+                                                                                      int sm_split)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     init_ring<SmemPlan<1, 8, false, CAND>::NST>(smem);
@@ -1192,14 +1193,33 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, MIN_BLOCKS_BOX) batch_ke
     // edge-strip jobs, then every video's interior-strip jobs (segment s = kind * n +
     // video, item_begin[s] its first item), so the launch runs one instance of the row
     // loop at a time, as a single video's launch does, and ends on the shortest jobs.
+    // Each kind has its own counter (queue[kind]), and a warp takes its next job from the
+    // kind its SM prefers while that kind lasts, as a single video's launch does
+    // (pick_job): SMs below sm_split (of 1024) prefer interior strips.
     const int n_seg = 3 * n_videos;
-    const int64_t n_items = item_begin[n_seg];
     unsigned kbase = 0;
+    bool inner_first = false;
+    if ((threadIdx.x & 31) == 0) {
+        unsigned sm, nsm;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+        asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+        inner_first = (unsigned long long)sm * 1024ull < (unsigned long long)sm_split * nsm;
+    }
     for (;;) {
-        unsigned long long item = 0;
-        if ((threadIdx.x & 31) == 0) item = atomicAdd(queue, 1ull);
+        long long item = -1;
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (item >= 0) break;
+                const int k = inner_first ? 2 - i : i;  // 0 half strips, 1 edge, 2 interior
+                const int64_t b0 = item_begin[k * n_videos], b1 = item_begin[(k + 1) * n_videos];
+                if (b1 <= b0) continue;
+                const unsigned long long t = atomicAdd(queue + k, 1ull);
+                if ((int64_t)t < b1 - b0) item = (long long)(b0 + (int64_t)t);
+            }
+        }
         item = __shfl_sync(FULL, item, 0);
-        if ((int64_t)item >= n_items) break;
+        if (item < 0) break;
         int lo = 0, hi = n_seg - 1;  // last s with item_begin[s] <= item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;

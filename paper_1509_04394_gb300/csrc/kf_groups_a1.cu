@@ -17,14 +17,14 @@ int launch(const GroupParams &p, unsigned grid, void *stream)
 
 // the persistent batch of fully fused chains over many videos
 int launch_batch_chain(const GroupParams *videos, const int64_t *item_begin, int n_videos, unsigned long long *queue,
-                       bool cand, unsigned grid, void *stream)
+                       bool cand, unsigned grid, int sm_split, void *stream)
 {
     if (cand)
         batch_kernel<true><<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<1, 8, false, true>::BYTES, static_cast<cudaStream_t>(stream)>>>(
-            videos, item_begin, n_videos, queue);
+            videos, item_begin, n_videos, queue, sm_split);
     else
         batch_kernel<false><<<grid, 32 * WARPS_PER_BLOCK, SmemPlan<1, 8, false, false>::BYTES, static_cast<cudaStream_t>(stream)>>>(
-            videos, item_begin, n_videos, queue);
+            videos, item_begin, n_videos, queue, sm_split);
     return (int)cudaGetLastError();
 }
 

@@ -156,7 +156,7 @@ int prepare_select();  // per-device launch attributes of the selection kernel (
 int launch_select(const TrackVideo &one, const TrackVideo *vids, int n, int64_t total_frames, int K, void *stream);
 int launch_lk(const TrackVideo &one, const TrackVideo *vids, int n, int64_t total_frames, int K, void *stream);
 int launch_batch_chain(const GroupParams *videos, const int64_t *item_begin, int n_videos, unsigned long long *queue,
-                       bool cand, unsigned grid, void *stream);
+                       bool cand, unsigned grid, int sm_split, void *stream);
 int batch_chain_blocks_per_sm(bool cand);
 #endif
 
