@@ -264,10 +264,12 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *video, const kf_corners *out, co
                    void *workspace, size_t workspace_bytes, void *stream);
 /* kf_track from host memory to host memory, pipelined (the paper has no counterpart; a
  * serving path for video that arrives in host memory). The frames go in and the results
- * come back in chunks of `chunk` frames (the first one a quarter of that) on the
- * context's own streams (one copy-in, three compute used in turn, one copy-out at the
- * highest priority): the copy in of chunk k, the hot path over the chunks before it and
- * the copies out of earlier ones overlap. Chunks below ~100 frames of 800x600 leave the
+ * come back in chunks of `chunk` frames (the first and the last a quarter of that) on
+ * the context's own streams (one copy-in, three compute used in turn, one copy-out at the
+ * lowest priority, one for the tracking at the highest): the copy in of chunk k, the
+ * chains of the chunks before it and the copies out of earlier ones overlap; selection
+ * and LK run over the frames up to the first chunk end at or past T/2 once those
+ * chains are done, and over the rest after the last chain. Chunks below ~100 frames of 800x600 leave the
  * SMs partly idle (a chunk's fused chain has 22 warps of work per frame). host_video / host_out / host_tracks: host buffers of the same shapes and
  * pitches as the device ones (page-locked, e.g. cudaHostAlloc, for the copies to be
  * asynchronous; pageable memory still gives correct results, without overlap). video /

@@ -306,10 +306,11 @@ def test_host_pipelined_call_equals_kf_track(dev, chunk):
 
 def test_host_call_timeline_and_chunk_tile_height(dev):
     """With timing on, kf_track_host records each chunk's copy in, chain, mask packing and
-    copy out, then one selection and one LK over every frame and the six copies of the
-    counts and tracks; the timeline puts each chunk's chain after its copy in and the
-    tracking after every chain. Its results do not depend on
-    the tile height of the chunk launches (kf_set_host_chunk_rows)."""
+    copy out, two selections and two LK steps (the frames up to the first chunk end at or
+    past T/2, then the rest) and the six copies of the counts and tracks; the timeline
+    puts each chunk's chain after its copy in, the first tracking after the chains of its
+    frames and the second after every chain. Its results do not depend on the tile height
+    of the chunk launches (kf_set_host_chunk_rows)."""
     T, H, W, Kp = 9, 80, 150, 16
     fr, _ = sv.generate(sv.VideoSpec(T=T, H=H, W=W, seed=12, n_blobs=8, n_patches=6), pitch=sv.pitch_for(W))
     ctx = K.Context(0)
@@ -342,17 +343,20 @@ def test_host_call_timeline_and_chunk_tile_height(dev):
         assert np.array_equal(got[k], ref[k]), k
     kinds = [k for k, _, _ in tl]
     n_chunks = kinds.count("copy_in")
-    assert n_chunks >= 4
     for k in ("chain_corners", "pack"):
         assert kinds.count(k) == n_chunks, k
-    assert kinds.count("select") == 1 and kinds.count("lk") == 1
+    # 9 frames in chunks of 3: [0, 1), [1, 4), [4, 7), [7, 8), [8, 9); the first tracking
+    # covers [0, 4), after the first two chains
+    assert n_chunks == 5
+    assert kinds.count("select") == 2 and kinds.count("lk") == 2
     assert kinds.count("copy_out") == n_chunks + 6
     assert all(0.0 <= a <= b for _, a, b in tl)
     ins = [(a, b) for k, a, b in tl if k == "copy_in"]
     chains = [(a, b) for k, a, b in tl if k == "chain_corners"]
     assert all(c[0] >= i[1] for i, c in zip(ins, chains))
-    sel = [a for k, a, _ in tl if k == "select"][0]
-    assert sel >= max(b for _, b in chains)
+    sel = [a for k, a, _ in tl if k == "select"]
+    assert sel[0] >= max(b for _, b in chains[:2])
+    assert sel[1] >= max(b for _, b in chains)
     assert K.kf_kernel_timeline(ctx.h) == []
     with pytest.raises(K.KfuseError):
         K.kf_set_host_chunk_rows(ctx.h, -1)
