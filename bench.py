@@ -34,6 +34,7 @@ from synth import video as sv  # noqa: E402
 METRIC = "fused-chain Mpixel/s & HBM roofline fraction vs unfused, 800×600×1000 u8"
 UNIT = "Mpixel/s"
 E2E_CHUNK = 50  # frames per chunk of the pipelined host-to-host call
+GATE_CYCLES = 100_000_000  # SM clock cycles of the blocking kernel ahead of a timed region
 SPEC = sv.HSDV_800x600x1000
 WORKLOAD = "Harris 8-stage chain, 1000 frames x 800 rows x 600 cols u8, 64 blobs + 32 patches, seed 3"
 # Algorithmic FP32 operations per output pixel of the chain, from the stage definitions
@@ -91,6 +92,12 @@ class ClockSampler:
             self.proc = None
             return
         threading.Thread(target=self._read, daemon=True).start()
+        # nvidia-smi's start-up (driver library initialisation) took over a second on some
+        # hosts, and the first timed leg after it came out 20-30 ms longer in total while
+        # its kernels kept their times: wait for the first sample before going on
+        t_end = time.time() + 10.0
+        while not self.rows and self.proc.poll() is None and time.time() < t_end:
+            time.sleep(0.02)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -103,6 +110,7 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+            time.sleep(0.5)  # its shutdown too, before the next timed leg
 
     def summary(self, t0: float, t1: float) -> dict:
         rows = [r for (ts, r) in self.rows if t0 <= ts <= t1 and len(r) >= 9]
@@ -274,13 +282,19 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(fn, k, w, between=None):
+    def timed(fn, k, w, between=None, gate=True):
         for _ in range(w):
             fn()
         barrier()
         if between:
             between()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if gate:
+            # a blocking kernel (a device sleep of about 50 ms) ahead of the first event: the
+            # K steps' launches queue up behind it, so a stall of the host while it enqueues
+            # them (a shared host's other work) cannot leave the GPU idle inside the timed
+            # region. The end-to-end leg runs ungated: host-side work is part of what it times.
+            torch.cuda._sleep(GATE_CYCLES)
         ev0.record(stream)
         for _ in range(k):
             fn()
@@ -360,19 +374,23 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     def e2e_bytes_step():
         K.kf_track_host(ctx.h, host_b, devb, W, KP, ws_track, chunk=E2E_CHUNK, stream=stream,
                         mask_format=K.KF_MASK_BYTES)
-    # the tile height of the call's chunk launches: the step's or 160 rows, whichever the
-    # call itself measures faster (a chunk launch is about one wave long, not fifteen)
+    # the tile height of the call's chunk launches: the step's, 160 or 200 rows, whichever
+    # the call itself measures fastest (a chunk launch is about one wave long, not fifteen);
+    # each candidate timed in two interleaved rounds and kept at its faster one, so that one
+    # round slowed by other work on the host's link does not decide
     e2e_rows = {}
-    for r in sorted({best_rows, 160}):
-        K.kf_set_host_chunk_rows(ctx.h, r)
-        e2e_rows[r] = timed(e2e_step, 3, 1)
+    for _ in range(2):
+        for r in sorted({best_rows, 160, 200}):
+            K.kf_set_host_chunk_rows(ctx.h, r)
+            ms = timed(e2e_step, 3, 1, gate=False)
+            e2e_rows[r] = min(e2e_rows.get(r, ms), ms)
     host_rows = min(e2e_rows, key=e2e_rows.get)
     K.kf_set_host_chunk_rows(ctx.h, host_rows)
-    ms_e2e = timed(e2e_step, max(3, args.steps // 2), 1)
+    ms_e2e = timed(e2e_step, max(3, args.steps // 2), 1, gate=False)
     m_bits = np.packbits(mask[:, :, :W].reshape(T, -1).cpu().numpy(), axis=1, bitorder="little")
     e2e_same = bool(np.array_equal(host["mask"].numpy()[:, :m_bits.shape[1]], m_bits)
                     and torch.equal(host["idx"], idx.cpu()) and torch.equal(host["u"], uu.cpu()))
-    ms_e2e_b = timed(e2e_bytes_step, max(3, args.steps // 2), 1)
+    ms_e2e_b = timed(e2e_bytes_step, max(3, args.steps // 2), 1, gate=False)
     e2e_same_b = bool(torch.equal(host_b["mask"], mask.cpu()) and torch.equal(host_b["idx"], idx.cpu()))
     # the FP16-tile form: the same step and chain with the box's row-pair sums in FP16 on chip
     ctx16t = K.Context(local_rank, precision=K.KF_PREC_F16_TILES)
@@ -455,7 +473,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                      max(3, args.steps // 4), 1)
     del ws, ws16
 
-    ms_e2e_end = timed(e2e_step, max(3, args.steps // 2), 1)  # the same call once more, after every other form
+    ms_e2e_end = timed(e2e_step, max(3, args.steps // 2), 1, gate=False)  # the same call once more, after every other form
     h2d = frames_pin.numel()
     d2h_tracks = sum(t.numel() * t.element_size() for k, t in host.items() if k not in ("frames", "mask"))
     d2h = T * ((W * H + 7) // 8) + d2h_tracks
@@ -470,6 +488,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    f"top-{KP} corner selection + LK tracking per frame pair", "partition_cuts": cuts,
                    "groups": n_groups, "chunk_rows": best_rows, "chunk_rows_from": rows_from, "cols_per_lane": 4,
                    "l2": "inputs larger than L2 (480 MB frames, 480 MB mask), no flush",
+                   "host_gate": "device-timed legs queued behind a ~50 ms blocking kernel before the first event",
                    "parallelism": (f"frame shards x{world} of one {world * owned}-frame video, merged on the host"
                                    if world > 1 else "single GPU")},
         "frames_per_s": world * owned / (ms / 1000),

@@ -632,8 +632,9 @@ kf_status kf_st_run(kf_ctx *ctx, const kf_pc_video *video, uint8_t *mask, int64_
  * the fully fused chain that also lists each frame's corners (kf_track), KF_KT_SELECT the
  * corner selection, KF_KT_LK the Lucas-Kanade step; kf_track_host also records its mask
  * packing kernels (KF_KT_PACK) and its copies (KF_KT_COPY_IN host to device,
- * KF_KT_COPY_OUT device to host), each on the stream that runs it. Events are created on
- * first use and reused; KF_ECUDA if an event call fails. Not for use inside stream
+ * KF_KT_COPY_OUT device to host), each on the stream that runs it. kf_set_kernel_timing
+ * with on != 0 creates the events for 512 launches (more are created on demand beyond
+ * that) and all are reused; KF_ECUDA if an event call fails. Not for use inside stream
  * capture. */
 typedef enum {
     KF_KT_GROUP = 0,

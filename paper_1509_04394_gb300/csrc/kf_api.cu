@@ -1057,6 +1057,18 @@ kf_status kf_set_kernel_timing(kf_ctx *ctx, int on)
 {
     if (!ctx) return KF_EINVAL;
     ctx->timing = on != 0;
+    if (ctx->timing && ctx->device >= 0) {
+        // the record's events are made here, not between the launches they time: creating
+        // one may map memory for the device while kernels run
+        kf::DeviceScope dev_scope(ctx->device);
+        cudaError_t e = dev_scope.status();
+        while (e == cudaSuccess && ctx->spare_events.size() < kf_ctx::TIMING_EVENTS) {
+            cudaEvent_t ev = nullptr;
+            e = cudaEventCreate(&ev);
+            if (e == cudaSuccess) ctx->spare_events.push_back(ev);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+    }
     return KF_OK;
 }
 

@@ -36,6 +36,8 @@ struct kf_ctx {
     bool timing = false;
     std::vector<Timed> timed;
     std::vector<cudaEvent_t> spare_events;
+    // events made when timing is switched on: pairs for 512 launches, more on demand
+    static constexpr size_t TIMING_EVENTS = 1024;
     // kf_track_host: the copy-in, compute and copy-out streams and their event rings (owned)
     static constexpr int N_RING = 3;
     cudaStream_t s_in = nullptr, s_out = nullptr, s_comp[N_RING] = {}, s_trk[N_RING] = {};
