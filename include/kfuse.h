@@ -269,9 +269,10 @@ kf_status kf_track(kf_ctx *ctx, const kf_video *video, const kf_corners *out, co
  * lowest priority, one for the tracking at the highest): the copy in of chunk k, the
  * chains of the chunks before it and the copies out of earlier ones overlap; selection
  * and LK run over the frames up to the first chunk end at or past T/2 once those
- * chains are done, and over the rest after the last chain. Chunks below ~100 frames of 800x600 leave the
- * SMs partly idle (a chunk's fused chain has 22 warps of work per frame). host_video / host_out / host_tracks: host buffers of the same shapes and
- * pitches as the device ones (page-locked, e.g. cudaHostAlloc, for the copies to be
+ * chains are done, and over the rest after the last chain. A chunk's chain is a short
+ * launch (50 frames of 800x600 about one wave) whose last wave the next chunks' launches
+ * fill; kf_set_host_chunk_rows sets its tile height. host_video / host_out /
+ * host_tracks: host buffers of the same shapes and pitches as the device ones (page-locked, e.g. cudaHostAlloc, for the copies to be
  * asynchronous; pageable memory still gives correct results, without overlap). video /
  * out / tracks / workspace: device buffers as for kf_track (video holds all T frames; LK
  * of a chunk's first frame reads the previous chunk's last). mask_format: KF_MASK_BYTES,

@@ -325,8 +325,9 @@ KF_MASK_BYTES, KF_MASK_BITS = 0, 1
 
 def kf_track_host(ctx, host, dev, W: int, K: int, workspace, chunk: int = 100, stream=None,
                   mask_format: int = KF_MASK_BYTES) -> None:
-    """kf_track from host tensors to host tensors, pipelined in chunks of `chunk` frames.
-    host, dev: dicts of tensors (host: pinned CPU, dev: CUDA) with keys frames [T, H, P]
+    """kf_track from host tensors to host tensors, pipelined in chunks of `chunk` frames
+    (copies in, chains on three streams, masks copied out after each chunk's chain,
+    tracking of the first half of the frames while later copies arrive). host, dev: dicts of tensors (host: pinned CPU, dev: CUDA) with keys frames [T, H, P]
     u8, mask [T, H, MP] u8 (KF_MASK_BITS: host mask [T, S] u8, S >= ceil(W H / 8) a
     multiple of 16), counts [T] i32, n_points [T] i32, idx / status [T, K] i32, u / v
     [T, K] f32."""
